@@ -1,0 +1,119 @@
+"""Exact Coulomb potentials (kernel 1/(4 pi r)) of the synthetic densities.
+
+Test infrastructure.  These are not steps of the FSA method: they are the
+exact answers the method approximates, derived from the densities'
+definitions (the paper refers to its sources for them in Sec. 5 and does not
+print them).
+
+* Isotropic Gaussian a exp(-|x-c|^2/(2 w^2)): total charge a (2 pi w^2)^{3/2},
+  potential a (2 pi w^2)^{3/2} erf(r/(sqrt2 w)) / (4 pi r), value a w^2 at r = 0.
+* Anisotropic Gaussian a exp(-sum_j (x_j-c_j)^2/(2 s_j^2)): from
+  1/(4 pi r) = (1/(2 pi^{3/2})) int_0^inf exp(-r^2 t^2) dt and the 1-D
+  Gaussian convolution identity,
+      Phi(x) = a/(2 pi^{3/2}) int_0^inf prod_j sqrt(pi/(t^2+a_j))
+               exp(-a_j t^2 x_j^2/(t^2+a_j)) dt,   a_j = 1/(2 s_j^2),
+  evaluated by the exp-sinh (double-exponential) trapezoid rule
+  t = exp((pi/2) sinh s), step 1/32 on s in [-4.5, 4.5] (Takahashi & Mori,
+  1974), which converges to ~1e-16 here (checked against adaptive quadrature).
+* Example 1 Case II: rho = -Laplacian(Phi0) + shifted copy, so
+  Phi = Phi0(x) + Phi0(x - x0) exactly (the Coulomb kernel is the Green's
+  function of -Laplacian in 3-D).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.special as sp
+
+from workloads import grid_axes
+
+
+def iso_gaussian_potential(amp, center, w, L, n):
+    x = grid_axes(L, n)
+    r = np.sqrt((x[0] - center[0])[:, None, None] ** 2 + (x[1] - center[1])[None, :, None] ** 2
+                + (x[2] - center[2])[None, None, :] ** 2)
+    q = amp * (2.0 * math.pi * w * w) ** 1.5
+    out = np.empty_like(r)
+    nz = r > 0
+    out[nz] = q * sp.erf(r[nz] / (math.sqrt(2.0) * w)) / (4.0 * math.pi * r[nz])
+    out[~nz] = amp * w * w
+    return out
+
+
+def _exp_sinh(step=1.0 / 32.0, span=4.5):
+    """Nodes and weights of the exp-sinh rule on [0, inf)."""
+    s = np.arange(-span, span + 0.5 * step, step)
+    t = np.exp(0.5 * math.pi * np.sinh(s))
+    w = step * t * 0.5 * math.pi * np.cosh(s)
+    return t, w
+
+
+def _axis_factor(xj, aj, t2):
+    """sqrt(pi/(t^2+a)) exp(-a t^2 x^2/(t^2+a)) for x (array) against nodes t^2."""
+    return (np.sqrt(math.pi / (t2 + aj))[None, :]
+            * np.exp(-aj * t2[None, :] * (xj * xj)[:, None] / (t2 + aj)[None, :]))
+
+
+def aniso_gaussian_potential_points(amp, center, sigma, pts):
+    """Potential at physical points pts (k x 3) by the 1-D integral above."""
+    t, w = _exp_sinh()
+    t2 = t * t
+    pts = np.atleast_2d(np.asarray(pts, dtype=np.float64))
+    val = np.ones((len(pts), len(t)))
+    for j in range(3):
+        val *= _axis_factor(pts[:, j] - center[j], 1.0 / (2.0 * sigma[j] ** 2), t2)
+    return amp * (val @ w) / (2.0 * math.pi ** 1.5)
+
+
+def aniso_gaussian_potential_grid(amp, center, sigma, L, n):
+    """The same on a whole grid: the integrand factorises per axis."""
+    t, w = _exp_sinh()
+    t2 = t * t
+    x = grid_axes(L, n)
+    F = [_axis_factor(x[j] - center[j], 1.0 / (2.0 * sigma[j] ** 2), t2) for j in range(3)]
+    out = np.einsum("iq,jq,kq,q->ijk", F[0], F[1], F[2], w, optimize=True)
+    return amp * out / (2.0 * math.pi ** 1.5)
+
+
+def density_potential(d):
+    """Exact potential of a workloads.Density on its grid (sum over its terms)."""
+    out = np.zeros(d.n)
+    for g in d.terms:
+        s = g.sigma
+        if s[0] == s[1] == s[2]:
+            out += iso_gaussian_potential(g.amp, g.center, s[0], d.L, d.n)
+        else:
+            out += aniso_gaussian_potential_grid(g.amp, g.center, s, d.L, d.n)
+    return out
+
+
+def density_potential_points(d, pts):
+    """Exact potential of a workloads.Density at grid indices pts (k x 3 ints)."""
+    pts = np.atleast_2d(pts)
+    h = [2.0 * d.L[j] / d.n[j] for j in range(3)]
+    xyz = np.stack([h[j] * (pts[:, j] - d.n[j] // 2) for j in range(3)], axis=1)
+    out = np.zeros(len(pts))
+    for g in d.terms:
+        s = g.sigma
+        if s[0] == s[1] == s[2]:
+            r = np.sqrt(np.sum((xyz - np.array(g.center)) ** 2, axis=1))
+            q = g.amp * (2.0 * math.pi * s[0] ** 2) ** 1.5
+            rr = np.where(r > 0, r, 1.0)
+            out += np.where(r > 0, q * sp.erf(rr / (math.sqrt(2.0) * s[0])) / (4.0 * math.pi * rr),
+                            g.amp * s[0] ** 2)
+        else:
+            out += aniso_gaussian_potential_points(g.amp, g.center, s, xyz)
+    return out
+
+
+def case2_potential(c):
+    """Exact potential of workloads.Case2: Phi0(x) + Phi0(x - x0)."""
+    x = grid_axes(c.L, c.n)
+    out = np.zeros(c.n)
+    for ctr in ((0.0, 0.0, 0.0), c.x0):
+        X = (x[0] - ctr[0])[:, None, None]
+        Y = (x[1] - ctr[1])[None, :, None]
+        Z = (x[2] - ctr[2])[None, None, :]
+        out += np.exp(-(X ** 2 + Y ** 2 + Z ** 2 / c.gamma3 ** 2) / c.sigma2)
+    return out

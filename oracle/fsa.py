@@ -1,0 +1,193 @@
+"""The FSA convolution stated literally, in numpy FP64 (test infrastructure).
+
+Every function follows one passage of the paper (Liu & Zhang, "Fast
+convolution solver based on far-field smooth approximation",
+arXiv 2504.19410).  Library primitives used as steps: numpy's FFT and
+scipy's erf / erfc / quad.  There is no pruning, blocking or symmetry trick:
+the convolution tensor T is built on the full doubled grid and the
+convolution is a full-size complex FFT product, as Sec. 2.3 states it.
+
+Index convention.  A tensor on the doubled grid has shape (2 n_0, 2 n_1,
+2 n_2); entry k_j holds the offset o_j = k_j for k_j < n_j and
+o_j = k_j - 2 n_j otherwise, i.e. offsets -n_j .. n_j - 1 in FFT order (the
+index set I_{2N} of Sec. 2.2).  Densities and potentials are n_0 x n_1 x n_2
+arrays on the mesh of Sec. 2 (x = h l, l = -n/2 .. n/2 - 1).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.integrate as si
+import scipy.special as sp
+
+# ---------------------------------------------------------------- kernel ----
+
+
+def coulomb3d_U(r):
+    """3-D Coulomb kernel U(r) = 1/(4 pi r) (Table 1)."""
+    return 1.0 / (4.0 * math.pi * r)
+
+
+def coulomb3d_Ueps(r, eps):
+    """Far-field smooth approximation U^eps(r) = U(r) erf(r/eps) (Sec. 4,
+    Eq. KerAppr; Table 1, 3-D Coulomb row).  At r = 0 the value is the limit
+    erf(r/eps)/(4 pi r) -> 1/(2 pi^{3/2} eps); the paper does not state it."""
+    r = np.asarray(r, dtype=np.float64)
+    out = np.empty_like(r)
+    nz = r > 0
+    out[nz] = sp.erf(r[nz] / eps) / (4.0 * math.pi * r[nz])
+    out[~nz] = 1.0 / (2.0 * math.pi ** 1.5 * eps)
+    return out
+
+
+def coulomb3d_What(k, eps):
+    """Whole-space Fourier transform of U - U^eps (Table 1, 3-D Coulomb row):
+    (1 - exp(-k^2 eps^2 / 4)) / k^2, written with expm1.  At k = 0 the value is
+    the limit eps^2/4; the paper gives only the k != 0 form."""
+    k = np.asarray(k, dtype=np.float64)
+    out = np.empty_like(k)
+    nz = k > 0
+    out[nz] = -np.expm1(-(k[nz] * eps) ** 2 / 4.0) / k[nz] ** 2
+    out[~nz] = eps * eps / 4.0
+    return out
+
+
+def What_by_quadrature(k, eps):
+    """Eq. (Fourier-Symmetric), d = 3, evaluated by adaptive quadrature:
+    4 pi int_0^inf (U - U^eps)(r) sin(kr)/(kr) r^2 dr, with
+    (U - U^eps)(r) = erfc(r/eps)/(4 pi r).  Used to pin coulomb3d_What."""
+    if k == 0:
+        f = lambda r: sp.erfc(r / eps) * r
+    else:
+        f = lambda r: sp.erfc(r / eps) * math.sin(k * r) / k
+    val, _ = si.quad(f, 0.0, 12.0 * eps, limit=400, epsabs=0.0, epsrel=1e-13)
+    return val
+
+
+def appendix_b_bound(R0, eps):
+    """App. B: int_{R0}^inf |U - U^eps| r^2 dr = R0^2 f(c), c = R0/eps,
+    f(c) = (1/(4 pi c^2)) int_c^inf s erfc(s) ds (3-D Coulomb)."""
+    c = R0 / eps
+    tail, _ = si.quad(lambda s: s * sp.erfc(s), c, np.inf, epsabs=0.0, epsrel=1e-12, limit=200)
+    return R0 * R0 * tail / (4.0 * math.pi * c * c)
+
+
+# ---------------------------------------------------------------- tensor ----
+
+
+def _offsets(n):
+    k = np.arange(2 * n)
+    return np.where(k < n, k, k - 2 * n).astype(np.float64)
+
+
+def mesh_steps(L, n):
+    """h_j = 2 L_j / n_j (Sec. 2; Sec. 2.4 for the anisotropic box)."""
+    return [2.0 * L[j] / n[j] for j in range(3)]
+
+
+def tensor_T1(L, n, eps):
+    """T^(1) on the doubled grid: T^(1)_o = h_0 h_1 h_2 U^eps(|(o_0 h_0, o_1 h_1,
+    o_2 h_2)|) (Sec. 2.1, Eq. Tensor1; Sec. 2.4, Eq. TensorAnis first term)."""
+    h = mesh_steps(L, n)
+    x = [_offsets(n[j]) * h[j] for j in range(3)]
+    r = np.sqrt(x[0][:, None, None] ** 2 + x[1][None, :, None] ** 2 + x[2][None, None, :] ** 2)
+    return h[0] * h[1] * h[2] * coulomb3d_Ueps(r, eps)
+
+
+def fourier_W(L, n, eps):
+    """W on the Fourier mesh Lambda: mu_{p,j} = pi p_j / (2 L_j),
+    p_j = -n_j .. n_j - 1 (Sec. 2.2, Eqs. DisFourierSeries, Wk; Sec. 2.4,
+    Eq. WkAnis), with the bounded-domain transform replaced by the whole-space
+    one (Eq. FouTran), i.e. W(mu) = What(|mu|).  Stored in FFT order."""
+    mu = [math.pi * _offsets(n[j]) / (2.0 * L[j]) for j in range(3)]
+    k = np.sqrt(mu[0][:, None, None] ** 2 + mu[1][None, :, None] ** 2 + mu[2][None, None, :] ** 2)
+    return coulomb3d_What(k, eps)
+
+
+def tensor_T2(L, n, eps, return_imag=False):
+    """T^(2)_o = (2N)^{-d} sum_p W(mu_p) exp(2 pi i p.o / 2N) (Sec. 2.2,
+    Eq. Tensor2; Eq. TensorAnis second term): numpy's ifftn carries exactly
+    this sign and normalisation.  The imaginary part vanishes in exact
+    arithmetic (W is real and even); its max is returned on request."""
+    T2 = np.fft.ifftn(fourier_W(L, n, eps))
+    if return_imag:
+        return T2.real.copy(), float(np.abs(T2.imag).max())
+    return T2.real.copy()
+
+
+def tensor_T(L, n, eps):
+    """T = T^(1) + T^(2) (Sec. 2.3, Eq. DiscConv)."""
+    return tensor_T1(L, n, eps) + tensor_T2(L, n, eps)
+
+
+def spectrum(T):
+    """DFT over the doubled grid of T, divided by prod_j 2 n_j (the inverse
+    transform's normalisation), real part.  T is real and even per axis
+    (Sec. 2.3), so this is real up to round-off."""
+    S = np.fft.fftn(T)
+    return S.real / T.size
+
+
+def spectrum_octant(T, n):
+    """The spectrum on p_j in [0, n_j]: all of it, since it is even per axis."""
+    return spectrum(T)[: n[0] + 1, : n[1] + 1, : n[2] + 1].copy()
+
+
+# ----------------------------------------------------------- convolution ----
+
+
+def apply_fft(T, rho):
+    """Phi_m = sum_i T_{m-i} rho_i (Eq. DiscConv) by the route of Sec. 2.3:
+    zero-pad rho to the doubled grid, FFT, multiply by the FFT of T, inverse
+    FFT, keep the first n_j entries per axis."""
+    n = rho.shape
+    pad = np.zeros(T.shape)
+    pad[: n[0], : n[1], : n[2]] = rho
+    out = np.fft.ifftn(np.fft.fftn(T) * np.fft.fftn(pad))
+    return out.real[: n[0], : n[1], : n[2]].copy()
+
+
+def apply_spectrum(S, rho):
+    """Same as apply_fft with the spectrum of T (from ``spectrum``) cached:
+    the 'Execution' phase of Example 2."""
+    n = rho.shape
+    pad = np.zeros(S.shape)
+    pad[: n[0], : n[1], : n[2]] = rho
+    out = np.fft.ifftn(S * S.size * np.fft.fftn(pad))
+    return out.real[: n[0], : n[1], : n[2]].copy()
+
+
+def T_at(T, o):
+    """T at signed offsets o = (o0, o1, o2) (arrays), |o_j| < n_j."""
+    return T[o[0] % T.shape[0], o[1] % T.shape[1], o[2] % T.shape[2]]
+
+
+def apply_direct(T, rho):
+    """Eq. DiscConv by brute force, O(V^2): for every output point m, the
+    sum over all source points i of T_{m-i} rho_i.  Small grids only."""
+    n = rho.shape
+    i0, i1, i2 = np.meshgrid(*[np.arange(n[j]) for j in range(3)], indexing="ij")
+    i0, i1, i2, r = i0.ravel(), i1.ravel(), i2.ravel(), rho.ravel()
+    out = np.empty(rho.size)
+    for m, (m0, m1, m2) in enumerate(np.ndindex(*n)):
+        out[m] = np.dot(T_at(T, (m0 - i0, m1 - i1, m2 - i2)), r)
+    return out.reshape(n)
+
+
+def apply_direct_at(T, rho, points):
+    """Eq. DiscConv by brute force at selected output indices only."""
+    n = rho.shape
+    i0, i1, i2 = np.meshgrid(*[np.arange(n[j]) for j in range(3)], indexing="ij")
+    i0, i1, i2, r = i0.ravel(), i1.ravel(), i2.ravel(), rho.ravel()
+    return np.array([np.dot(T_at(T, (m0 - i0, m1 - i1, m2 - i2)), r) for (m0, m1, m2) in points])
+
+
+def rel_error(a, b):
+    """The error norm of Sec. 5: max|a - b| / max|b| over the grid."""
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(b)))
+
+
+def solve(L, n, eps, rho):
+    """Tensor generation followed by the FFT route: the whole method."""
+    return apply_fft(tensor_T(L, n, eps), rho)

@@ -1,0 +1,128 @@
+"""Plant plausible mistakes in the oracle and check that its pins catch them.
+
+Each mutation replaces one oracle function (CPU only, via monkeypatch) with a
+version carrying a typical error: a dropped term, a wrong limit, a wrong
+scale, a transposed operand, a wrong crop.  The compact pin suite below (the
+paper's Table 2 values, the anisotropic Case I round-off level and brute
+force) must fail for every one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.special as sp
+
+import workloads as W
+from oracle import closed_forms as cf
+from oracle import fsa
+
+
+def pins_pass():
+    # Table 2 iso Case I, h = 1 and 1/2 (printed 2.0681E-02, 2.5036E-06)
+    for h, want in ((1.0, 2.0681e-2), (0.5, 2.5036e-6)):
+        d = W.paper_case1(L=8.0, sigma2=0.8, h_over_gamma=h)
+        e = fsa.rel_error(fsa.solve(d.L, d.n, 1.0, d.rho()), cf.density_potential(d))
+        if abs(e - want) > 5e-4 * want:
+            return False
+    # Table 2 aniso Case I, gamma = 1/4: round-off
+    d = W.paper_case1(L=8.0, sigma2=1.2, gamma3=0.25, h_over_gamma=0.25)
+    if fsa.rel_error(fsa.solve(d.L, d.n, 0.5, d.rho()), cf.density_potential(d)) > 6e-15:
+        return False
+    # brute force
+    n, L = (4, 6, 8), (3.0, 4.0, 2.5)
+    T = fsa.tensor_T(L, n, 0.6)
+    rho = np.random.default_rng(7).standard_normal(n)
+    if fsa.rel_error(fsa.apply_fft(T, rho), fsa.apply_direct(T, rho)) > 1e-13:
+        return False
+    return True
+
+
+def test_unmutated_pins_pass():
+    assert pins_pass()
+
+
+def _ueps_zero_limit(r, eps):
+    r = np.asarray(r, dtype=np.float64)
+    return np.where(r > 0, sp.erf(r / eps) / (4 * math.pi * np.where(r > 0, r, 1)), 0.0)
+
+
+def _what_no_limit(k, eps):
+    k = np.asarray(k, dtype=np.float64)
+    return np.where(k > 0, -np.expm1(-(k * eps) ** 2 / 4) / np.where(k > 0, k, 1) ** 2, 0.0)
+
+
+def _what_sign(k, eps):
+    return -fsa_orig["coulomb3d_What"](k, eps)
+
+
+def _what_no_quarter(k, eps):
+    return fsa_orig["coulomb3d_What"](k, 2.0 * eps)
+
+
+def _ueps_erfc(r, eps):
+    r = np.asarray(r, dtype=np.float64)
+    return np.where(r > 0, sp.erfc(r / eps) / (4 * math.pi * np.where(r > 0, r, 1)), 0.0)
+
+
+fsa_orig = {k: getattr(fsa, k) for k in ("coulomb3d_What", "coulomb3d_Ueps", "tensor_T",
+                                         "tensor_T1", "tensor_T2", "fourier_W", "apply_fft")}
+
+
+def _mu_wrong_scale(L, n, eps):
+    return fsa_orig["fourier_W"](tuple(2 * l for l in L), n, eps)
+
+
+def _W_axes_transposed(L, n, eps):
+    return fsa_orig["fourier_W"](tuple(L[::-1]), n, eps)
+
+
+def _T1_no_h(L, n, eps):
+    h = fsa.mesh_steps(L, n)
+    return fsa_orig["tensor_T1"](L, n, eps) / (h[0] * h[1] * h[2])
+
+
+def _T_no_T2(L, n, eps):
+    return fsa_orig["tensor_T1"](L, n, eps)
+
+
+def _T_no_T1(L, n, eps):
+    return fsa_orig["tensor_T2"](L, n, eps)
+
+
+def _apply_wrong_crop(T, rho):
+    n = rho.shape
+    pad = np.zeros(T.shape)
+    pad[: n[0], : n[1], : n[2]] = rho
+    out = np.fft.ifftn(np.fft.fftn(T) * np.fft.fftn(pad)).real
+    return out[1: n[0] + 1, : n[1], : n[2]].copy()
+
+
+def _apply_pad_at_end(T, rho):
+    n = rho.shape
+    pad = np.zeros(T.shape)
+    pad[-n[0]:, : n[1], : n[2]] = rho
+    out = np.fft.ifftn(np.fft.fftn(T) * np.fft.fftn(pad)).real
+    return out[: n[0], : n[1], : n[2]].copy()
+
+
+MUTATIONS = {
+    "Ueps limit at r=0 dropped": ("coulomb3d_Ueps", _ueps_zero_limit),
+    "Ueps uses erfc": ("coulomb3d_Ueps", _ueps_erfc),
+    "What limit at k=0 dropped": ("coulomb3d_What", _what_no_limit),
+    "What sign flipped": ("coulomb3d_What", _what_sign),
+    "What eps^2/4 -> eps^2": ("coulomb3d_What", _what_no_quarter),
+    "Fourier mesh pi p/L": ("fourier_W", _mu_wrong_scale),
+    "Fourier mesh axes transposed": ("fourier_W", _W_axes_transposed),
+    "T1 without h^3": ("tensor_T1", _T1_no_h),
+    "T2 dropped": ("tensor_T", _T_no_T2),
+    "T1 dropped": ("tensor_T", _T_no_T1),
+    "crop shifted": ("apply_fft", _apply_wrong_crop),
+    "pad on the wrong side": ("apply_fft", _apply_pad_at_end),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(name, monkeypatch):
+    attr, fn = MUTATIONS[name]
+    monkeypatch.setattr(fsa, attr, fn)
+    assert not pins_pass(), f"pins missed the planted mistake: {name}"

@@ -1,0 +1,235 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+Each test checks the oracle (oracle/) against something other than itself:
+printed values of the paper (tests/golden/, each with its citation), closed
+forms, quadrature of the defining integral, brute force, and invariants.
+CPU only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import closed_forms as cf
+from oracle import fsa
+from tests.conftest import read_golden
+
+
+# ---- Table 1 / Eq. (Fourier-Symmetric): the singular part's transform ----------
+
+def test_What_table1_values():
+    for k, eps, val in read_golden("table1_coulomb3d_What.txt"):
+        got = fsa.coulomb3d_What(np.array([float(k)]), float(eps))[0]
+        assert got == pytest.approx(float(val), rel=1e-15, abs=0)
+
+
+@pytest.mark.parametrize("eps", [0.4, 1.0])
+@pytest.mark.parametrize("k", [0.0, 0.05, 0.3, 1.0, 3.0, 10.0, 40.0])
+def test_What_equals_radial_fourier_integral(k, eps):
+    """Table 1's closed form equals Eq. (Fourier-Symmetric) d=3 evaluated by quadrature."""
+    a = fsa.coulomb3d_What(np.array([k]), eps)[0]
+    b = fsa.What_by_quadrature(k, eps)
+    assert abs(a - b) <= 2e-15 * abs(b) + 1e-18
+
+
+def test_What_small_k_no_cancellation():
+    # expm1 form keeps full relative accuracy as k -> 0 (limit eps^2/4).
+    eps = 1.0
+    for k in [1e-9, 1e-6, 1e-4]:
+        x = (k * eps) ** 2 / 4
+        series = eps ** 2 / 4 * (1 - x / 2 + x * x / 6)
+        assert fsa.coulomb3d_What(np.array([k]), eps)[0] == pytest.approx(series, rel=1e-14)
+
+
+def test_Ueps_limit_and_far_field():
+    eps = 0.7
+    r = np.array([0.0, 1e-7, 6 * eps, 9 * eps])
+    u = fsa.coulomb3d_Ueps(r, eps)
+    assert u[0] == pytest.approx(1 / (2 * math.pi ** 1.5 * eps), rel=1e-15)
+    assert u[1] == pytest.approx(u[0], rel=1e-12)
+    # erf(r/eps) ~ 1 to 16 digits for r >= 6 eps (Sec. 1)
+    assert u[2] == pytest.approx(1 / (4 * math.pi * r[2]), rel=1e-15)
+    assert u[3] == pytest.approx(1 / (4 * math.pi * r[3]), rel=1e-16)
+
+
+# ---- App. B: eps thresholds ---------------------------------------------------
+
+def test_appendix_b_thresholds():
+    for R0, c, tol in read_golden("appendix_b_thresholds.txt"):
+        R0, c, tol = float(R0), float(c), float(tol)
+        assert fsa.appendix_b_bound(R0, R0 / c) <= tol
+        # and the printed threshold is sharp to its printed digits
+        assert fsa.appendix_b_bound(R0, R0 / (c - 0.05)) > tol
+
+
+# ---- Table 2: the whole scheme against the paper's printed errors -------------
+
+@pytest.mark.parametrize("h,n,printed", [tuple(r) for r in read_golden("table2_coulomb3d_iso_double.txt")][:3])
+def test_table2_iso_case1(h, n, printed):
+    """Table 2, 3-D double, isotropic Case I.  At h = 1 and 1/2 the error is
+    the scheme's discretisation error, so matching the printed value to 3-4
+    digits pins T^(1), T^(2), the mesh, the Fourier mesh and the crop.  At
+    h = 1/4 the printed value is round-off."""
+    d = W.paper_case1(L=8.0, sigma2=0.8, gamma3=1.0, h_over_gamma=float(h))
+    assert d.n[0] == int(n)
+    err = fsa.rel_error(fsa.solve(d.L, d.n, 1.0, d.rho()), cf.density_potential(d))
+    printed = float(printed)
+    if printed > 1e-10:
+        assert err == pytest.approx(printed, rel=5e-4)
+    else:
+        assert err < 4 * printed
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.5, 0.25, 0.125])
+def test_table2_aniso_case1(gamma):
+    """Table 2, 3-D double, anisotropic Case I (L=8, sigma^2=1.2, eps=0.5,
+    h = gamma/4): round-off level (printed <= 5.4e-15)."""
+    rows = {float(g): float(e) for c, g, e in read_golden("table2_coulomb3d_aniso_double.txt") if c == "I"}
+    d = W.paper_case1(L=8.0, sigma2=1.2, gamma3=gamma, h_over_gamma=0.25)
+    err = fsa.rel_error(fsa.solve(d.L, d.n, 0.5, d.rho()), cf.density_potential(d))
+    assert err < max(6e-15, 2 * rows[gamma])
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("gamma", [1.0, 0.125])
+def test_table2_aniso_case2(gamma):
+    """Table 2, Case II (L=12, sigma^2=0.8, eps=0.4, x0=(1,1,0), h=gamma/8, n=192)."""
+    rows = {float(g): float(e) for c, g, e in read_golden("table2_coulomb3d_aniso_double.txt") if c == "II"}
+    c = W.paper_case2(gamma3=gamma, h_over_gamma=0.125)
+    err = fsa.rel_error(fsa.solve(c.L, c.n, c.eps, c.rho()), cf.case2_potential(c))
+    assert err < max(5e-15, 4 * rows[gamma])
+
+
+def test_spectral_convergence_then_floor():
+    """Thm 1: the error falls faster than any power of h until round-off."""
+    errs = []
+    for h in (1.0, 0.5, 0.25):
+        d = W.paper_case1(L=8.0, sigma2=0.8, h_over_gamma=h)
+        errs.append(fsa.rel_error(fsa.solve(d.L, d.n, 1.0, d.rho()), cf.density_potential(d)))
+    assert errs[1] < errs[0] * 1e-3 and errs[2] < 1e-14
+
+
+# ---- the convolution routes ----------------------------------------------------
+
+@pytest.mark.parametrize("n", [(4, 6, 8), (8, 8, 8), (6, 12, 4)])
+def test_fft_route_equals_brute_force(n):
+    """Sec. 2.3's FFT route reproduces Eq. (DiscConv) summed directly."""
+    rng = np.random.default_rng(7)
+    L = (3.0, 4.0, 2.5)
+    T = fsa.tensor_T(L, n, 0.6)
+    rho = rng.standard_normal(n)
+    a = fsa.apply_fft(T, rho)
+    b = fsa.apply_direct(T, rho)
+    assert fsa.rel_error(a, b) < 1e-13
+    pts = [(0, 0, 0), (n[0] - 1, n[1] - 1, n[2] - 1), (1, 2, 3)]
+    assert np.allclose(fsa.apply_direct_at(T, rho, pts), [b[p] for p in pts], rtol=1e-13, atol=0)
+
+
+def test_brute_force_on_a_hand_example():
+    """A 2-point case worked by hand: rho nonzero at two cells, so each output
+    is T at the offsets to those two cells."""
+    n, L, eps = (4, 4, 4), (2.0, 2.0, 2.0), 0.8
+    T = fsa.tensor_T(L, n, eps)
+    rho = np.zeros(n)
+    rho[0, 0, 0] = 2.0
+    rho[3, 1, 2] = -1.0
+    out = fsa.apply_fft(T, rho)
+    for m in [(0, 0, 0), (3, 1, 2), (2, 3, 1)]:
+        want = 2.0 * T[m[0], m[1], m[2]] - 1.0 * T[(m[0] - 3) % 8, (m[1] - 1) % 8, (m[2] - 2) % 8]
+        assert out[m] == pytest.approx(want, rel=1e-13, abs=1e-15)
+
+
+def test_tensor_real_even_and_T2_imaginary_vanishes():
+    n, L = (6, 8, 4), (3.0, 4.0, 1.0)
+    T2, imag = fsa.tensor_T2(L, n, 0.5, return_imag=True)
+    assert imag < 1e-15 * np.abs(T2).max()
+    T = fsa.tensor_T(L, n, 0.5)
+    for ax in range(3):
+        m = T.shape[ax]
+        idx = (-np.arange(m)) % m   # offset o -> -o (o = -n maps to itself)
+        assert np.allclose(np.take(T, idx, axis=ax), T, rtol=1e-14, atol=0)
+    S = np.fft.fftn(T)
+    assert np.abs(S.imag).max() < 1e-12 * np.abs(S.real).max()
+
+
+def test_linearity_and_translation():
+    n, L, eps = (8, 8, 8), (4.0, 4.0, 4.0), 1.0
+    T = fsa.tensor_T(L, n, eps)
+    rng = np.random.default_rng(3)
+    a, b = rng.standard_normal(n), rng.standard_normal(n)
+    lhs = fsa.apply_fft(T, 2.0 * a - 0.5 * b)
+    rhs = 2.0 * fsa.apply_fft(T, a) - 0.5 * fsa.apply_fft(T, b)
+    assert fsa.rel_error(lhs, rhs) < 1e-13
+    # translation by whole cells: support inside the box on both sides
+    r = np.zeros(n)
+    r[1:4, 2:5, 1:3] = rng.standard_normal((3, 3, 2))
+    s = np.roll(r, (2, 1, 3), axis=(0, 1, 2))
+    pa, pb = fsa.apply_fft(T, r), fsa.apply_fft(T, s)
+    assert np.allclose(np.roll(pa, (2, 1, 3), axis=(0, 1, 2))[2:, 1:, 3:], pb[2:, 1:, 3:], rtol=0, atol=1e-14)
+
+
+def test_eps_independence_within_discretisation_error():
+    d = W.paper_case1(L=8.0, sigma2=0.8, h_over_gamma=0.25)
+    rho = d.rho()
+    a = fsa.solve(d.L, d.n, 1.0, rho)
+    b = fsa.solve(d.L, d.n, 1.4, rho)
+    assert fsa.rel_error(a, b) < 1e-13
+
+
+def test_spectrum_octant_is_whole_spectrum():
+    n, L = (4, 6, 8), (2.0, 3.0, 4.0)
+    T = fsa.tensor_T(L, n, 0.5)
+    S = fsa.spectrum(T)
+    O = fsa.spectrum_octant(T, n)
+    for k in np.ndindex(*S.shape):
+        p = tuple(min(k[j], S.shape[j] - k[j]) for j in range(3))
+        assert S[k] == pytest.approx(O[p], rel=1e-12, abs=1e-15 * np.abs(S).max())
+
+
+# ---- closed forms (the exact answers) ------------------------------------------
+
+def test_closed_form_iso_solves_poisson():
+    """-Laplacian of the erf potential reproduces the Gaussian density
+    (4th-order finite differences, away from r = 0)."""
+    w, hh = 0.9, 1e-2
+    pts = np.array([[0.3, -0.2, 0.5], [1.1, 0.4, -0.7], [-0.5, 2.0, 0.1]])
+    def phi(p):
+        r = np.linalg.norm(p, axis=-1)
+        return (2 * math.pi * w * w) ** 1.5 * np.vectorize(math.erf)(r / (math.sqrt(2) * w)) / (4 * math.pi * r)
+    lap = 0
+    for j in range(3):
+        e = np.zeros(3); e[j] = hh
+        lap = lap + (-phi(pts + 2 * e) + 16 * phi(pts + e) - 30 * phi(pts) + 16 * phi(pts - e) - phi(pts - 2 * e)) / (12 * hh * hh)
+    rho = np.exp(-np.sum(pts ** 2, axis=1) / (2 * w * w))
+    assert np.allclose(-lap, rho, rtol=1e-6, atol=1e-8)
+
+
+def test_closed_form_aniso_reduces_to_iso_and_solves_poisson():
+    pts = np.array([[0.0, 0.0, 0.0], [0.3, -1.2, 0.8], [3.0, 2.0, -4.0]])
+    iso = cf.aniso_gaussian_potential_points(1.3, (0.1, 0.2, -0.3), (0.8, 0.8, 0.8), pts)
+    r = np.linalg.norm(pts - np.array([0.1, 0.2, -0.3]), axis=1)
+    q = 1.3 * (2 * math.pi * 0.64) ** 1.5
+    ref = q * np.array([math.erf(x / (math.sqrt(2) * 0.8)) for x in r]) / (4 * math.pi * r)
+    assert np.allclose(iso, ref, rtol=1e-14, atol=0)
+    # anisotropic: finite-difference Laplacian
+    sig, hh = (0.4, 0.7, 1.5), 1e-2
+    p0 = np.array([[0.2, 0.1, -0.3], [0.5, -0.6, 1.0]])
+    f = lambda p: cf.aniso_gaussian_potential_points(1.0, (0, 0, 0), sig, p)
+    lap = 0
+    for j in range(3):
+        e = np.zeros(3); e[j] = hh
+        lap = lap + (-f(p0 + 2 * e) + 16 * f(p0 + e) - 30 * f(p0) + 16 * f(p0 - e) - f(p0 - 2 * e)) / (12 * hh * hh)
+    rho = np.exp(-np.sum(p0 ** 2 / (2 * np.array(sig) ** 2), axis=1))
+    assert np.allclose(-lap, rho, rtol=1e-6, atol=1e-8)
+
+
+def test_case2_density_is_minus_laplacian():
+    c = W.paper_case2(L=4.0, gamma3=0.5, h_over_gamma=0.25)
+    rho = c.rho()
+    phi = cf.case2_potential(c)
+    h = [2 * c.L[j] / c.n[j] for j in range(3)]
+    lap = sum((np.roll(phi, -1, j) - 2 * phi + np.roll(phi, 1, j))[2:-2, 2:-2, 2:-2] / h[j] ** 2 for j in range(3))
+    inner = rho[2:-2, 2:-2, 2:-2]
+    # second-order stencil: O(h^2) agreement
+    assert np.max(np.abs(-lap - inner)) < 0.05 * np.max(np.abs(inner))
