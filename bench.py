@@ -1,0 +1,360 @@
+"""Benchmark of the FSA apply path (libfsaconv) on GB300.
+
+One step = one solve Phi = T * rho of the headline workload: the 3-D Coulomb
+FSA convolution of an 8-Gaussian density on [-16,16]^3 with 256^3 points
+(all five passes of the apply path; the spectrum is cached on the device,
+as in the paper's Execution phase).  Inputs are resident in HBM when the
+timed region starts; each step reads one of 4 rotating rho buffers and
+writes one of 4 phi buffers, and one step moves ~0.6 GB (FP32) through
+memory, far above the 129 MB L2, so no step finds its inputs in L2.
+
+Prints one JSON line (see --help).  Under torchrun every rank runs its own
+replica on its own GPU (solves are independent: replicas only, weak
+scaling), the ranks are barrier-synchronised around the timed region, the
+time is the max over ranks and the value is all ranks' solves / that time.
+
+--impl reference times the CPU oracle (oracle/, numpy FP64) on the host
+cores instead: each step is one oracle solve of the same density family on
+a smaller grid, scaled to 256^3 by the ratio of FFT work (M log M).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/s and HBM-roofline % at 256^3 FP64/FP32; p50/p99 latency under serving"
+UNIT = "solves/s"
+PASSES = ["r2c_ax0", "row_fwd", "col_mid", "row_inv", "c2r_ax0"]
+
+
+def pass_bytes(n, s):
+    """Algorithmic HBM bytes of each pass for one solve (reads + writes of the
+    pass's compulsory input and output; s = bytes per real).  V = n0 n1 n2,
+    X = (n0+1) n1 n2 complex, Y = (n0+1) n1 (2 n2) complex, S = octant."""
+    n0, n1, n2 = n
+    V = n0 * n1 * n2
+    X = (n0 + 1) * n1 * n2 * 2
+    Y = (n0 + 1) * n1 * 2 * n2 * 2
+    S = (n0 + 1) * (n1 + 1) * (n2 + 1)
+    return {"r2c_ax0": (V + X) * s, "row_fwd": (X + Y) * s, "col_mid": (2 * Y + S) * s,
+            "row_inv": (Y + X) * s, "c2r_ax0": (X + V) * s}
+
+
+def reference_model_bytes(n, s):
+    """Reference 5-pass byte model: E = 2V + 24 n0 n1 (n2+1) + octant reals per solve."""
+    n0, n1, n2 = n
+    return (2 * n0 * n1 * n2 + 24 * n0 * n1 * (n2 + 1) + (n0 + 1) * (n1 + 1) * (n2 + 1)) * s
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def read_traffic(kernel, workload, dtype):
+    """DRAM bytes per launch from the committed ncu summary, if it lists this
+    kernel for this workload and dtype (lines: kernel workload dtype bytes)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        for line in f:
+            t = line.split("#", 1)[0].split()
+            if len(t) >= 4 and t[0] == kernel and t[1] == workload and t[2] == dtype:
+                return float(t[3])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                t = [x.strip() for x in line.split(",")]
+                if len(t) >= 9:
+                    rows.append(t)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ ours ----
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_19410_gb300 as fsa
+    from paper_2504_19410_gb300 import capi
+    import workloads as W
+
+    d = W.gaussian_sum(seed=2504)  # 8 Gaussians, [-16,16]^3, 256^3, eps = 1
+    n = d.n
+    rho64 = d.rho()
+    hbm_peak, peak_kind = peaks()
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def bench_tier(dt):
+        tdt = torch.float32 if dt == "f32" else torch.float64
+        s = 4 if dt == "f32" else 8
+        t0 = time.perf_counter()
+        plan = fsa.Plan(d.L, n, dt, eps=d.eps)
+        torch.cuda.synchronize()
+        precomp_ms = (time.perf_counter() - t0) * 1e3
+        rhos = [torch.from_numpy(rho64).to(tdt).cuda() for _ in range(4)]
+        phis = [torch.empty_like(rhos[0]) for _ in range(4)]
+        for i in range(args.warmup):
+            plan.apply(rhos[i % 4], phis[i % 4])
+        prof = capi.fsa_profiler_create(args.steps)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        clk.start()
+        time.sleep(0.25)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for i in range(args.steps):
+            capi.fsa_apply_profiled(plan.handle, rhos[i % 4], phis[i % 4], stream, prof)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        elapsed = ev0.elapsed_time(ev1)
+        clocks = clk.stop()
+        barrier()
+        if dist is not None:
+            t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            elapsed = float(t.item())
+        pass_ms, step_ms, steps = capi.fsa_profiler_read(prof)
+        capi.fsa_profiler_destroy(prof)
+        pb = pass_bytes(n, s)
+        dom = max(range(5), key=lambda i: pass_ms[i])
+        kname = PASSES[dom]
+        achieved = pb[kname] / (pass_ms[dom] * 1e-3) / 1e9
+        model_s = reference_model_bytes(n, s) / (hbm_peak * 1e9)
+        res = {
+            "value": ws * args.steps / (elapsed * 1e-3),
+            "ms_per_step": elapsed / args.steps,
+            "precomp_ms": precomp_ms,
+            "pass_ms": dict(zip(PASSES, [round(x, 5) for x in pass_ms])),
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": f"of {peak_kind}",
+                         "alg_bytes_per_launch": pb[kname],
+                         "traffic": read_traffic(kname, "c2_256", dt)},
+            "step_roofline_frac_27V_model": model_s * 1e3 / (elapsed / args.steps),
+            "clocks": clocks,
+            "gpu_launches": 5 * args.steps,
+        }
+        # e2e through the C-ABI host-buffer entry point (H2D and D2H inside the timed region)
+        res["e2e"] = None
+        if not args.no_e2e:
+            hin = torch.from_numpy(rho64).to(tdt).pin_memory()
+            hout = torch.empty_like(hin).pin_memory()
+            for _ in range(2):
+                plan.apply_host(hin, hout)
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            k = max(3, args.steps // 2)
+            e0.record(stream)
+            for _ in range(k):
+                plan.apply_host(hin, hout)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            et = e0.elapsed_time(e1)
+            if dist is not None:
+                t = torch.tensor([et], device="cuda", dtype=torch.float64)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                et = float(t.item())
+            nb = int(np.prod(n)) * s
+            res["e2e"] = {"value": ws * k / (et * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nb,
+                          "d2h_bytes_per_step": nb, "ms_per_step": et / k}
+        plan.close()
+        del rhos, phis
+        torch.cuda.empty_cache()
+        return res
+
+    tiers = {}
+    for dt in ("f32", "f64"):
+        tiers[dt] = bench_tier(dt)
+    main = tiers["f32"]
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_n)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c2_256: 3-D Coulomb FSA apply, 8-Gaussian density (seed 2504) on "
+                                   "[-16,16]^3, 256^3 grid, eps=1, spectrum cached on device",
+                       "grid": list(n), "l2": "per-step working set ~0.6 GB (FP32) > 129 MB L2; "
+                                             "4 rotating rho/phi buffers",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": main["roofline"],
+            "cpu_baseline": cpu,
+            "e2e": main["e2e"],
+            "gpu_launches": main["gpu_launches"],
+            "clocks": main["clocks"],
+            "pass_ms": main["pass_ms"],
+            "precomp_ms": main["precomp_ms"],
+            "step_roofline_frac_27V_model": main["step_roofline_frac_27V_model"],
+            "f64": {k: tiers["f64"][k] for k in ("value", "ms_per_step", "roofline", "pass_ms", "precomp_ms",
+                                                   "step_roofline_frac_27V_model", "e2e", "clocks")},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# -------------------------------------------------------------- oracle ----
+
+def fft_work(n):
+    M = 8 * n[0] * n[1] * n[2]
+    return M * math.log2(M)
+
+
+def oracle_sample(n_sample):
+    """One oracle solve (FFT route, spectrum precomputed) of the 8-Gaussian
+    density family on an n_sample^3 grid of the same box; returns seconds."""
+    import workloads as W
+    from oracle import fsa as oracle
+    d = W.gaussian_sum(seed=2504, n=n_sample)
+    rho = d.rho()
+    S = oracle.spectrum(oracle.tensor_T(d.L, d.n, d.eps))
+    t0 = time.perf_counter()
+    oracle.apply_spectrum(S, rho)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(n_sample):
+    secs = oracle_sample(n_sample)
+    scale = fft_work((256, 256, 256)) / fft_work((n_sample,) * 3)
+    return {"value": 1.0 / (secs * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one oracle solve (numpy FP64 FFT route, cached spectrum) of the same 8-Gaussian "
+                      f"density on a {n_sample}^3 grid of [-16,16]^3, {secs:.2f} s, scaled to 256^3 by the "
+                      f"FFT-work ratio {scale:.2f} (M log2 M); numpy's FFT is single-threaded"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return
+    n_ref = args.ref_n
+    for _ in range(args.warmup):
+        oracle_sample(n_ref)
+    secs = [oracle_sample(n_ref) for _ in range(args.steps)]
+    scale = fft_work((256, 256, 256)) / fft_work((n_ref,) * 3)
+    total = sum(secs) * scale
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "c2_256: 3-D Coulomb FSA apply, 8-Gaussian density (seed 2504) on "
+                               "[-16,16]^3, 256^3 grid, eps=1, spectrum cached",
+                   "grid": [256, 256, 256], "parallelism": "host cores (oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step one oracle solve on a {n_ref}^3 grid of the same density "
+                                   f"family, scaled to 256^3 by the FFT-work ratio {scale:.2f}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-n", type=int, default=128, help="cpu_baseline oracle sample grid (per axis)")
+    ap.add_argument("--ref-n", type=int, default=96, help="--impl reference: oracle grid per step")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * libfsaconv -- GB300 (sm_103a) apply path of the far-field smooth
+ * approximation (FSA) convolution solver of Liu & Zhang, "Fast convolution
+ * solver based on far-field smooth approximation" (arXiv 2504.19410).
+ *
+ * The library computes the discrete aperiodic convolution of Sec. 2.3,
+ * Eq. (DiscConv):
+ *
+ *     Phi_m = sum_{i in I_N} T_{m-i} rho_i ,   T = T^(1) + T^(2),
+ *
+ * on an n_0 x n_1 x n_2 grid x_{j,l} = h_j l, l = -n_j/2 .. n_j/2 - 1,
+ * h_j = 2 L_j / n_j (Sec. 2, the uniform mesh; Sec. 2.4 for a box with
+ * different L_j).  T^(1)_o = h_0 h_1 h_2 U^eps(|o.h|) (Sec. 2.1, Eq. Tensor1)
+ * and T^(2) is the inverse DFT over the doubled grid of W(mu_p), the
+ * whole-space Fourier transform of U - U^eps at mu_{p,j} = pi p_j / (2 L_j)
+ * (Sec. 2.2, Eqs. Tensor2, FouTran; Table 1).  The kernel is the 3-D Coulomb
+ * kernel U = 1/(4 pi r) with U^eps = U erf(r/eps) (Sec. 4, Eq. KerAppr).
+ *
+ * Arrays.  Densities rho and potentials phi are dense C-order arrays of
+ * n_0 * n_1 * n_2 elements of the plan's dtype (axis 2 fastest), array index
+ * i_j = l_j + n_j/2.  Every pointer named rho / phi below is a DEVICE pointer
+ * unless the function name says _host.  The caller owns rho and phi.
+ *
+ * Sizes.  Each n_j must be even, 4 <= n_j <= 512, and of the form 2^a or
+ * 3 * 2^a (the doubled length 2 n_j then factors into the radices 2, 3, 4
+ * and 8 the FFT kernels implement).
+ *
+ * Errors.  Every call returns an fsa_status; no C++ exception crosses the
+ * ABI.  On error a message is kept per thread (fsa_last_error).  Calls that
+ * enqueue device work are asynchronous with respect to the host and return
+ * FSA_ERR_CUDA if a launch fails; device faults surface on a later
+ * synchronisation, as with any CUDA library.
+ *
+ * Streams.  fsa_stream_t is a cudaStream_t (NULL = the legacy default stream).
+ */
+#ifndef FSACONV_H
+#define FSACONV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* fsa_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  FSA_OK = 0,
+  FSA_ERR_INVALID_ARG = 1,    /* a size, pointer or option is out of range      */
+  FSA_ERR_UNSUPPORTED = 2,    /* kernel x dimension not implemented             */
+  FSA_ERR_EPS = 3,            /* eps fails the App. B far-field bound          */
+  FSA_ERR_OOM = 4,            /* device allocation failed or over budget        */
+  FSA_ERR_CUDA = 5,           /* a CUDA runtime call failed                     */
+  FSA_ERR_NOT_GENERATED = 6,  /* fsa_apply before fsa_tensor_generate           */
+  FSA_ERR_BUSY = 7,           /* serving queue full                             */
+  FSA_ERR_TIMEOUT = 8,        /* a host-side wait ran out                       */
+  FSA_ERR_DEVICE_TIMEOUT = 9, /* a bounded device-side wait gave up             */
+  FSA_ERR_NOT_FOUND = 10      /* unknown serving ticket                         */
+} fsa_status;
+
+typedef enum {
+  FSA_KERNEL_COULOMB3D = 0 /* U = 1/(4 pi r), U^eps = U erf(r/eps) (Table 1) */
+} fsa_kernel;
+
+typedef enum {
+  FSA_F32 = 0, /* rho, phi, stored spectrum and FFT arithmetic in FP32 */
+  FSA_F64 = 1  /* the same in FP64                                      */
+} fsa_dtype;
+
+typedef struct {
+  double eps;     /* FSA parameter; 0 selects min(1, R0/6), R0 = min_j 2 L_j     */
+  double eps_tol; /* App. B bound R0^2 f(R0/eps) must not exceed this;         */
+                  /* 0 selects 1e-8, a negative value disables the check       */
+  int device;     /* CUDA device ordinal; -1 = the calling thread's current one */
+  int reserved;
+} fsa_plan_opts;
+
+typedef struct fsa_plan fsa_plan;
+
+typedef struct {
+  int n[3];                 /* grid points per axis                                   */
+  double L[3];              /* box half-widths                                        */
+  double h[3];              /* mesh steps 2 L_j / n_j                                 */
+  double eps;               /* the FSA parameter in use                               */
+  double R0;                /* min_j 2 L_j (Sec. 1)                                   */
+  double eps_bound;         /* App. B: R0^2 f(R0/eps)                                 */
+  fsa_dtype dtype;
+  int device;
+  int generated;            /* 1 once fsa_tensor_generate has been enqueued           */
+  size_t workspace_bytes;   /* device scratch the plan owns                           */
+  size_t spectrum_bytes;    /* device bytes of the stored spectrum octant             */
+  const void* spectrum;     /* device pointer: (n0+1) x (n1+1) x (n2+1) dtype, C order */
+} fsa_plan_info;
+
+/* Create a plan (the "Precomp" object of Sec. 5, Example 2) for the grid
+ * n[0..d-1] on the box prod_j [-L_j, L_j].  d must be 3.  The plan owns,
+ * on the chosen device, the spectrum octant and the apply workspace
+ * (fsa_plan_info.workspace_bytes); both are freed by fsa_plan_destroy.
+ * eps follows Remark 2.1 / App. B: the plan computes R0^2 f(R0/eps) with
+ * f(c) = (1/(4 pi c^2)) int_c^inf s erfc(s) ds and rejects eps with
+ * FSA_ERR_EPS when it exceeds opts->eps_tol.  opts may be NULL.
+ * Errors: FSA_ERR_INVALID_ARG (out == NULL, d != 3, unsupported n_j,
+ * L_j <= 0, eps < 0), FSA_ERR_UNSUPPORTED (kernel), FSA_ERR_EPS,
+ * FSA_ERR_OOM, FSA_ERR_CUDA.  On error *out is set to NULL. */
+fsa_status fsa_plan_create(fsa_plan** out, fsa_kernel kernel, int d, const double* L,
+                           const int* n, fsa_dtype dtype, const fsa_plan_opts* opts);
+
+/* Generate the kernel tensor's spectrum on the device, in FP64, and store it
+ * in the plan's dtype (Sec. 2.1-2.3: T^(1) by the trapezoid rule, T^(2) from
+ * W; the spectrum of T is DFT(T^(1)) + W because T^(2) = iDFT(W)).  Stored:
+ * S[p] = (DFT_{2n}(T^(1))[p] + W(|mu_p|)) / (8 n0 n1 n2) for p_j in [0, n_j];
+ * T is real and even per axis (Sec. 2.3), so this octant is the whole
+ * spectrum.  The DFT of the even tensor is a separable DCT-I, computed with
+ * the library's FFT kernels.  Asynchronous on stream; idempotent. */
+fsa_status fsa_tensor_generate(fsa_plan* plan, fsa_stream_t stream);
+
+/* Phi = T * rho (Eq. DiscConv) by zero-padding to 2n per axis, FFT, multiply
+ * by the stored spectrum and inverse FFT, keeping the first n_j outputs per
+ * axis (Sec. 2.3).  rho, phi: device arrays of n0*n1*n2 plan-dtype elements;
+ * phi == rho is allowed.  Uses the plan's workspace, so calls on one plan
+ * must not overlap on the GPU.  Asynchronous on stream.
+ * Errors: FSA_ERR_INVALID_ARG (NULL pointer), FSA_ERR_NOT_GENERATED,
+ * FSA_ERR_CUDA. */
+fsa_status fsa_apply(const fsa_plan* plan, const void* rho, void* phi, fsa_stream_t stream);
+
+/* fsa_apply with HOST buffers: copies rho_host to the device, applies, copies
+ * the result to phi_host, all enqueued on stream (pinned host memory gives
+ * asynchronous copies).  The caller must synchronise the stream before
+ * reading phi_host.  Staging goes through the plan's workspace. */
+fsa_status fsa_apply_host(const fsa_plan* plan, const void* rho_host, void* phi_host,
+                          fsa_stream_t stream);
+
+/* Apply count plans to count densities in one launch sequence.  Plans may
+ * differ in n, L, eps and dtype but must share a device; request k's result
+ * equals fsa_apply(plans[k], rho[k], phi[k]) bit for bit.  Requests with the
+ * same grid and dtype are grouped; each group's passes run as grid-strided
+ * persistent kernels over the tiles of all its requests, the groups on
+ * concurrent streams, and the whole sequence is captured once per batch
+ * signature into a CUDA graph and replayed.  Uses each plan's workspace, so
+ * a plan may appear at most once per call (FSA_ERR_INVALID_ARG otherwise). */
+fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void* const* rho,
+                             void* const* phi, int count, fsa_stream_t stream);
+
+fsa_status fsa_plan_info_get(const fsa_plan* plan, fsa_plan_info* info);
+fsa_status fsa_plan_destroy(fsa_plan* plan); /* NULL is a no-op */
+
+/* Copy the stored spectrum octant ((n0+1)(n1+1)(n2+1) plan-dtype values,
+ * C order, p_j in [0, n_j]) to dst, a device or host buffer of at least
+ * fsa_plan_info.spectrum_bytes bytes (cudaMemcpyDefault).  Asynchronous on
+ * stream for device or pinned destinations.  FSA_ERR_INVALID_ARG if
+ * nbytes is too small. */
+fsa_status fsa_plan_spectrum_copy(const fsa_plan* plan, void* dst, size_t nbytes, fsa_stream_t stream);
+
+/* App. B far-field bound for the 3-D Coulomb kernel: R0^2 f(R0/eps) with
+ * f(c) = (1/(4 pi c^2)) int_c^inf s erfc(s) ds (host-only; NaN for
+ * non-positive arguments).  fsa_plan_create checks it against eps_tol. */
+double fsa_appendix_b_bound(double R0, double eps);
+
+const char* fsa_status_string(fsa_status s);
+const char* fsa_last_error(void); /* calling thread's last error message ("" if none) */
+
+/* ------------------------------------------------------------ profiling -- */
+/* Per-pass timing with CUDA events on the launching stream.  A profiler holds
+ * up to max_steps x 6 events (created with cudaEventCreate: no device memory).
+ * fsa_apply_profiled is fsa_apply plus an event before the first pass and
+ * after each of the five passes; fsa_profiler_read synchronises on the last
+ * event and returns, averaged over the recorded steps, the duration of each
+ * pass (pass_ms[5]: r2c_ax0, row_fwd, col_mid, row_inv, c2r_ax0) and of the
+ * whole step (step_ms), then resets.  FSA_ERR_BUSY if more than max_steps
+ * steps are recorded before a read. */
+typedef struct fsa_profiler fsa_profiler;
+fsa_status fsa_profiler_create(fsa_profiler** out, int max_steps);
+fsa_status fsa_apply_profiled(const fsa_plan* plan, const void* rho, void* phi, fsa_stream_t stream,
+                              fsa_profiler* prof);
+fsa_status fsa_profiler_read(fsa_profiler* prof, double* pass_ms, double* step_ms, int* steps);
+fsa_status fsa_profiler_destroy(fsa_profiler* prof);
+
+/* Tuning table for the pass kernels (tile widths), filled by the autotuner
+ * on first use of each (pass, length, dtype) unless disabled.  mode: 0 = off
+ * (defaults), 1 = tune on first use. */
+fsa_status fsa_autotune_set(int mode);
+
+/* ---------------------------------------------------------------- serving -- */
+
+typedef struct fsa_server fsa_server;
+
+typedef struct {
+  int max_inflight;        /* requests on the GPU at once (0 = 64)                    */
+  int streams;             /* device streams the requests are spread over (0 = 8)    */
+  double hbm_fraction;     /* admit while workspace fits this share of free HBM (0 = 0.9) */
+  size_t hbm_budget_bytes; /* hard cap on server-held device bytes (0 = none)        */
+  int plan_cache_max;      /* plans kept resident (0 = 64), least recently used out  */
+  int queue_max;           /* pending requests before FSA_ERR_BUSY (0 = 1 << 20)     */
+  int device;              /* -1 = current                                           */
+} fsa_serve_opts;
+
+typedef struct {
+  fsa_kernel kernel;
+  int d;          /* 3 */
+  double L[3];
+  int n[3];
+  fsa_dtype dtype;
+  double eps;     /* 0 = default rule */
+  const void* rho; /* device, caller-owned until the ticket is DONE or FAILED */
+  void* phi;       /* device, caller-owned */
+} fsa_request;
+
+typedef enum {
+  FSA_REQ_QUEUED = 0,
+  FSA_REQ_RUNNING = 1,
+  FSA_REQ_DONE = 2,
+  FSA_REQ_FAILED = 3
+} fsa_req_state;
+
+typedef struct {
+  double submit_s; /* host clock (s, monotonic) at submit   */
+  double admit_s;  /* when its work was enqueued            */
+  double done_s;   /* when its completion event was seen    */
+  int plan_hit;    /* 1 if its plan was already resident    */
+  fsa_status status;
+} fsa_req_times;
+
+typedef struct {
+  uint64_t submitted, completed, failed, plan_hits, plan_misses;
+  size_t device_bytes_held; /* plans + workspaces */
+  int inflight;
+  int queued;
+} fsa_serve_stats;
+
+/* A serving loop: one host thread admits queued requests while their
+ * workspace fits the free-HBM budget and fewer than max_inflight are on the
+ * GPU, launches each on one of the server's streams (requests that arrive
+ * while others run are admitted as soon as a slot and memory free up, and
+ * their kernels overlap on the device), keeps plans resident in an LRU
+ * cache, and marks a ticket DONE when its completion event has fired.
+ * Results do not depend on the mix: every request runs the same kernels on
+ * its own workspace, with no cross-request reduction. */
+fsa_status fsa_serve_create(fsa_server** out, const fsa_serve_opts* opts);
+fsa_status fsa_serve_submit(fsa_server* s, const fsa_request* req, uint64_t* ticket);
+/* Non-blocking unless timeout_s > 0: waits up to timeout_s for DONE/FAILED
+ * and returns FSA_ERR_TIMEOUT if it does not come.  times may be NULL.
+ * A DONE or FAILED ticket is forgotten after it has been reported. */
+fsa_status fsa_serve_poll(fsa_server* s, uint64_t ticket, double timeout_s,
+                          fsa_req_state* state, fsa_req_times* times);
+fsa_status fsa_serve_stats_get(fsa_server* s, fsa_serve_stats* st);
+/* Waits for in-flight work, then frees everything the server holds. */
+fsa_status fsa_serve_destroy(fsa_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSACONV_H */

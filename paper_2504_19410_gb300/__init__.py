@@ -1,0 +1,101 @@
+"""libfsaconv: the GB300 apply path of the FSA convolution solver (arXiv 2504.19410).
+
+``capi`` exposes the C-ABI calls under their own names; ``Plan`` and
+``Server`` wrap them for torch tensors.  Torch provides device memory and
+streams only: every step of a solve runs in libfsaconv's CUDA kernels, and
+there is no CPU path.  Build the library with ``__graft_entry__.build()``
+(or ``python -m paper_2504_19410_gb300.build``).
+"""
+from __future__ import annotations
+
+from . import capi
+from .capi import FSA_F32, FSA_F64, FSA_KERNEL_COULOMB3D, FsaError
+
+_DT = {"f32": FSA_F32, "f64": FSA_F64, FSA_F32: FSA_F32, FSA_F64: FSA_F64}
+
+
+def _torch_dtype(dt):
+    import torch
+    return torch.float32 if dt == FSA_F32 else torch.float64
+
+
+def _cur_stream(stream):
+    if stream is not None:
+        return stream
+    import torch
+    return torch.cuda.current_stream()
+
+
+class Plan:
+    """A device-resident FSA plan: grid n (3 ints), box half-widths L, dtype
+    'f32' or 'f64'.  eps = 0 picks min(1, R0/6).  The spectrum is generated
+    on construction unless generate=False."""
+
+    def __init__(self, L, n, dtype="f32", eps=0.0, eps_tol=0.0, device=-1, generate=True, stream=None):
+        self.dtype = _DT[dtype]
+        self.n = tuple(int(x) for x in n)
+        self.L = tuple(float(x) for x in L)
+        self.handle = capi.fsa_plan_create(FSA_KERNEL_COULOMB3D, 3, self.L, self.n, self.dtype, eps, eps_tol, device)
+        if generate:
+            self.generate(stream)
+
+    @property
+    def info(self):
+        return capi.fsa_plan_info_get(self.handle)
+
+    @property
+    def eps(self):
+        return self.info.eps
+
+    def generate(self, stream=None):
+        capi.fsa_tensor_generate(self.handle, _cur_stream(stream))
+
+    def _check(self, t, what):
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{what} must be a CUDA tensor")
+        if t.dtype != _torch_dtype(self.dtype) or tuple(t.shape) != self.n or not t.is_contiguous():
+            raise ValueError(f"{what} must be a contiguous {_torch_dtype(self.dtype)} tensor of shape {self.n}")
+
+    def apply(self, rho, phi=None, stream=None):
+        """phi = T * rho on the device; returns phi."""
+        import torch
+        self._check(rho, "rho")
+        if phi is None:
+            phi = torch.empty_like(rho)
+        self._check(phi, "phi")
+        capi.fsa_apply(self.handle, rho, phi, _cur_stream(stream))
+        return phi
+
+    def apply_host(self, rho_host, phi_host, stream=None):
+        """Host-buffer variant (copies inside); caller synchronises the stream."""
+        capi.fsa_apply_host(self.handle, rho_host, phi_host, _cur_stream(stream))
+        return phi_host
+
+    def spectrum(self, stream=None):
+        """A copy of the stored spectrum octant, shape (n0+1, n1+1, n2+1)."""
+        import torch
+        shp = tuple(x + 1 for x in self.n)
+        out = torch.empty(shp, dtype=_torch_dtype(self.dtype), device="cuda")
+        capi.fsa_plan_spectrum_copy(self.handle, out, out.numel() * out.element_size(), _cur_stream(stream))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            capi.fsa_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def apply_batched(plans, rhos, phis, stream=None):
+    """fsa_apply_batched over Plan objects and torch tensors."""
+    capi.fsa_apply_batched([p.handle for p in plans], rhos, phis, _cur_stream(stream))
+    return phis
+
+
+__all__ = ["Plan", "apply_batched", "capi", "FsaError", "FSA_F32", "FSA_F64"]

@@ -1,0 +1,189 @@
+// fsa_apply_batched: many solves of uneven size in one launch sequence.
+//
+// Solves with the same grid and dtype form a group.  Each pass of a group is
+// ONE persistent launch that walks the tiles of all the group's solves (the
+// kernels take a by-value job table); the groups run on forked streams so
+// their passes overlap on the device.  The whole sequence is captured once per
+// batch signature (plans, buffers) into a CUDA graph and replayed, so a
+// repeated batch costs one graph launch on the caller's stream.
+#include <algorithm>
+#include <tuple>
+#include <list>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "fsa_internal.h"
+
+namespace fsa {
+namespace {
+
+struct GroupKey {
+  int n0, n1, n2, dt;
+  bool operator<(const GroupKey& o) const {
+    return std::tie(n0, n1, n2, dt) < std::tie(o.n0, o.n1, o.n2, o.dt);
+  }
+};
+
+struct Sig {
+  std::vector<const void*> v;
+  bool operator<(const Sig& o) const { return v < o.v; }
+  bool operator==(const Sig& o) const { return v == o.v; }
+};
+
+struct DeviceCtx {
+  cudaStream_t capture = nullptr;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev;
+  std::map<Sig, cudaGraphExec_t> graphs;
+  std::list<Sig> lru;  // front = most recent
+};
+
+std::mutex g_mu;
+std::map<int, DeviceCtx> g_ctx;
+constexpr size_t kMaxGraphs = 32;
+
+cudaError_t ensure_ctx(DeviceCtx& c, size_t groups) {
+  cudaError_t e = cudaSuccess;
+  if (!c.capture) e = cudaStreamCreateWithFlags(&c.capture, cudaStreamNonBlocking);
+  while (e == cudaSuccess && c.side.size() < groups) {
+    cudaStream_t s;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) c.side.push_back(s);
+  }
+  while (e == cudaSuccess && c.ev.size() < 2 * groups + 2) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) c.ev.push_back(ev);
+  }
+  return e;
+}
+
+cudaError_t launch_group(const std::vector<int>& idx, const fsa_plan* const* plans, const void* const* rho,
+                         void* const* phi, cudaStream_t s) {
+  const fsa_plan* p0 = plans[idx[0]];
+  std::vector<const void*> r, S;
+  std::vector<void*> f, X, Y;
+  for (int k : idx) {
+    const fsa_plan* p = plans[k];
+    r.push_back(rho[k]);
+    f.push_back(phi[k]);
+    X.push_back(p->ws);
+    Y.push_back((char*)p->ws + p->x_bytes);
+    S.push_back(p->spectrum);
+  }
+  const int m = (int)idx.size();
+  return p0->dtype == FSA_F32
+             ? group_passes<float2>(p0->n, m, r.data(), f.data(), X.data(), Y.data(), S.data(), s)
+             : group_passes<double2>(p0->n, m, r.data(), f.data(), X.data(), Y.data(), S.data(), s);
+}
+
+}  // namespace
+}  // namespace fsa
+
+using namespace fsa;
+
+extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void* const* rho, void* const* phi,
+                                        int count, fsa_stream_t stream) {
+  if (count < 0 || (count > 0 && (!plans || !rho || !phi)))
+    return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched: bad arguments");
+  if (count == 0) return FSA_OK;
+  const int dev = plans[0] ? plans[0]->device : -1;
+  std::map<GroupKey, std::vector<int>> groups;
+  std::vector<const fsa_plan*> seen;
+  for (int k = 0; k < count; ++k) {
+    const fsa_plan* p = plans[k];
+    if (!p || !rho[k] || !phi[k]) return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched: NULL entry");
+    if (p->device != dev) return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched: plans on different devices");
+    if (!p->generated) return set_error(FSA_ERR_NOT_GENERATED, "fsa_apply_batched: plan not generated");
+    if (((uintptr_t)rho[k] | (uintptr_t)phi[k]) & 15u)
+      return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched: rho and phi must be 16-byte aligned");
+    seen.push_back(p);
+    groups[GroupKey{p->n[0], p->n[1], p->n[2], (int)p->dtype}].push_back(k);
+  }
+  std::sort(seen.begin(), seen.end());
+  if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+    return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched: a plan appears twice (its workspace is shared)");
+
+  Sig sig;
+  for (int k = 0; k < count; ++k) {
+    sig.v.push_back(plans[k]);
+    sig.v.push_back(rho[k]);
+    sig.v.push_back(phi[k]);
+  }
+
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != dev) cudaSetDevice(dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  DeviceCtx& c = g_ctx[dev];
+  cudaError_t e = ensure_ctx(c, groups.size());
+  cudaGraphExec_t exec = nullptr;
+  auto it = c.graphs.find(sig);
+  if (e == cudaSuccess && it != c.graphs.end()) {
+    exec = it->second;
+    c.lru.remove(sig);
+    c.lru.push_front(sig);
+  } else if (e == cudaSuccess) {
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(c.capture, cudaStreamCaptureModeThreadLocal);
+    size_t g = 0;
+    cudaError_t le = e;
+    for (auto& kv : groups) {
+      if (le != cudaSuccess) break;
+      if (g == 0) {
+        le = launch_group(kv.second, plans, rho, phi, c.capture);
+      } else {
+        cudaStream_t s = c.side[g - 1];
+        le = cudaEventRecord(c.ev[2 * g], c.capture);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(s, c.ev[2 * g], 0);
+        if (le == cudaSuccess) le = launch_group(kv.second, plans, rho, phi, s);
+        if (le == cudaSuccess) le = cudaEventRecord(c.ev[2 * g + 1], s);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(c.capture, c.ev[2 * g + 1], 0);
+      }
+      ++g;
+    }
+    if (e == cudaSuccess) e = cudaStreamEndCapture(c.capture, &graph);
+    if (e == cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e == cudaSuccess) {
+      c.graphs[sig] = exec;
+      c.lru.push_front(sig);
+      while (c.lru.size() > kMaxGraphs) {
+        cudaGraphExecDestroy(c.graphs[c.lru.back()]);
+        c.graphs.erase(c.lru.back());
+        c.lru.pop_back();
+      }
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, (cudaStream_t)stream);
+  if (prev != dev) cudaSetDevice(prev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_error(e, "fsa_apply_batched");
+  }
+  return FSA_OK;
+}
+
+// Graphs hold plan pointers and workspace addresses: drop any that mention a
+// plan about to be destroyed.
+namespace fsa {
+void batched_forget_plan(const fsa_plan* p) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& dc : g_ctx) {
+    DeviceCtx& c = dc.second;
+    for (auto it = c.lru.begin(); it != c.lru.end();) {
+      bool uses = false;
+      for (size_t i = 0; i < it->v.size(); i += 3) uses |= (it->v[i] == p);
+      if (uses) {
+        cudaGraphExecDestroy(c.graphs[*it]);
+        c.graphs.erase(*it);
+        it = c.lru.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+}
+}  // namespace fsa

@@ -1,0 +1,240 @@
+// Device FFT building blocks for the FSA apply path (sm_103a).
+//
+// A transform of length M = 2n (the doubled grid of Sec. 2.2, Eqs.
+// DisFourierSeries / rhoTildeK) runs as a Stockham auto-sort FFT: stage s of
+// radix R_s reads R_s elements spaced M/R_s apart, multiplies them by the
+// stage twiddles, applies a radix-R_s DFT in registers and writes them back
+// spaced by the product of the earlier radices; after the last stage the
+// data is in natural order.  Stages exchange data through shared memory in
+// place: every thread loads and transforms its butterflies, the CTA
+// synchronises, then every thread stores.
+//
+// Twiddles come from a table of exp(-2 pi i k / 3072) (3072 = 3 * 1024 is a
+// multiple of every supported length), built on the host in extended
+// precision and rounded once; each translation unit holds its own copy in a
+// file-scope __device__ array that the host fills once per device.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fsa_consts.h"
+
+namespace fsa {
+
+// ------------------------------------------------------------ complex ----
+__device__ __forceinline__ float2 mk(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ double2 mk(double x, double y) { return make_double2(x, y); }
+
+template <typename V> struct RealOf;
+template <> struct RealOf<float2> { using T = float; };
+template <> struct RealOf<double2> { using T = double; };
+
+template <typename V> __device__ __forceinline__ V czero() { return mk(typename RealOf<V>::T(0), typename RealOf<V>::T(0)); }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
+  return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename V> __device__ __forceinline__ V cscale(V a, typename RealOf<V>::T s) { return mk(a.x * s, a.y * s); }
+// -i * a for the forward direction, +i * a for the inverse one
+template <bool FWD, typename V> __device__ __forceinline__ V rot_mi(V a) {
+  return FWD ? mk(a.y, -a.x) : mk(-a.y, a.x);
+}
+
+// ------------------------------------------------------------ codelets ----
+template <bool FWD, typename V> __device__ __forceinline__ void dft2(V* v) {
+  V a = v[0];
+  v[0] = cadd(a, v[1]);
+  v[1] = csub(a, v[1]);
+}
+
+template <bool FWD, typename V> __device__ __forceinline__ void dft3(V* v) {
+  using R = typename RealOf<V>::T;
+  const R s = R(0.86602540378443864676372317075294);  // sin(2 pi / 3)
+  V t1 = cadd(v[1], v[2]);
+  V t2 = mk(v[0].x - R(0.5) * t1.x, v[0].y - R(0.5) * t1.y);
+  V d = rot_mi<FWD>(cscale(csub(v[1], v[2]), s));
+  v[0] = cadd(v[0], t1);
+  v[1] = cadd(t2, d);
+  v[2] = csub(t2, d);
+}
+
+template <bool FWD, typename V> __device__ __forceinline__ void dft4(V* v) {
+  V a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+  V c = cadd(v[1], v[3]), d = rot_mi<FWD>(csub(v[1], v[3]));
+  v[0] = cadd(a, c);
+  v[2] = csub(a, c);
+  v[1] = cadd(b, d);
+  v[3] = csub(b, d);
+}
+
+template <bool FWD, typename V> __device__ __forceinline__ void dft8(V* v) {
+  using R = typename RealOf<V>::T;
+  const R h = R(0.70710678118654752440084436210485);  // 1/sqrt(2)
+  V a[4], b[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    a[k] = cadd(v[k], v[k + 4]);
+    b[k] = csub(v[k], v[k + 4]);
+  }
+  // b_k *= w8^k, w8 = exp(-+ 2 pi i / 8)
+  if (FWD) {
+    b[1] = mk(h * (b[1].x + b[1].y), h * (b[1].y - b[1].x));
+    b[3] = mk(h * (b[3].y - b[3].x), -h * (b[3].x + b[3].y));
+  } else {
+    b[1] = mk(h * (b[1].x - b[1].y), h * (b[1].x + b[1].y));
+    b[3] = mk(-h * (b[3].x + b[3].y), h * (b[3].x - b[3].y));
+  }
+  b[2] = rot_mi<FWD>(b[2]);
+  dft4<FWD>(a);
+  dft4<FWD>(b);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    v[2 * q] = a[q];
+    v[2 * q + 1] = b[q];
+  }
+}
+
+template <int R, bool FWD, typename V> __device__ __forceinline__ void dft(V* v) {
+  if constexpr (R == 2) dft2<FWD>(v);
+  else if constexpr (R == 3) dft3<FWD>(v);
+  else if constexpr (R == 4) dft4<FWD>(v);
+  else if constexpr (R == 8) dft8<FWD>(v);
+  else static_assert(R == 2, "unsupported radix");
+}
+
+// ------------------------------------------------------------ plans ------
+template <int M_, int... Rs> struct Plan {
+  static constexpr int M = M_;
+  static constexpr int NST = sizeof...(Rs);
+  static constexpr int R[NST] = {Rs...};
+  static constexpr int rmax() {
+    int m = 1;
+    for (int i = 0; i < NST; ++i) m = R[i] > m ? R[i] : m;
+    return m;
+  }
+  static constexpr int ns(int s) {
+    int p = 1;
+    for (int i = 0; i < s; ++i) p *= R[i];
+    return p;
+  }
+};
+
+// Radix plan per supported length 2n, n in {4,6,8,12,...,384,512}.
+template <int M> struct PlanFor;
+template <> struct PlanFor<8> { using type = Plan<8, 8>; };
+template <> struct PlanFor<12> { using type = Plan<12, 4, 3>; };
+template <> struct PlanFor<16> { using type = Plan<16, 4, 4>; };
+template <> struct PlanFor<24> { using type = Plan<24, 8, 3>; };
+template <> struct PlanFor<32> { using type = Plan<32, 8, 4>; };
+template <> struct PlanFor<48> { using type = Plan<48, 4, 4, 3>; };
+template <> struct PlanFor<64> { using type = Plan<64, 8, 8>; };
+template <> struct PlanFor<96> { using type = Plan<96, 8, 4, 3>; };
+template <> struct PlanFor<128> { using type = Plan<128, 8, 4, 4>; };
+template <> struct PlanFor<192> { using type = Plan<192, 8, 8, 3>; };
+template <> struct PlanFor<256> { using type = Plan<256, 8, 8, 4>; };
+template <> struct PlanFor<384> { using type = Plan<384, 8, 4, 4, 3>; };
+template <> struct PlanFor<512> { using type = Plan<512, 8, 8, 8>; };
+template <> struct PlanFor<768> { using type = Plan<768, 8, 8, 4, 3>; };
+template <> struct PlanFor<1024> { using type = Plan<1024, 8, 8, 4, 4>; };
+
+#define FSA_FOR_EACH_M(X) \
+  X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
+
+}  // namespace fsa
+
+// ------------------------------------------------------------ twiddles ---
+// One copy per translation unit that includes this header.
+static __device__ float2 g_tw32[fsa::kTwN];
+static __device__ double2 g_tw64[fsa::kTwN];
+
+namespace fsa {
+
+template <typename V> __device__ __forceinline__ const V* tw_table();
+template <> __device__ __forceinline__ const float2* tw_table<float2>() { return g_tw32; }
+template <> __device__ __forceinline__ const double2* tw_table<double2>() { return g_tw64; }
+
+// exp(-2 pi i e / L) for 0 <= e < L, L | 3072
+template <typename V, int L> __device__ __forceinline__ V twiddle(int e) {
+  static_assert(kTwN % L == 0, "length must divide the twiddle table");
+  return __ldg(tw_table<V>() + e * (kTwN / L));
+}
+
+// One Stockham stage S of plan P over a line, with T threads per line and
+// thread index t.  `ld(p)` returns element p of the stage input, `st(p, v)`
+// stores element p of the stage output.  All threads of the CTA must call it
+// (it contains two barriers: between loads and stores, and after stores).
+template <class P, int S, bool FWD, int T, typename V, class Ld, class St>
+__device__ __forceinline__ void stage(int t, const Ld& ld, const St& st) {
+  constexpr int R = P::R[S];
+  constexpr int NS = P::ns(S);
+  constexpr int M = P::M;
+  constexpr int NB = M / R;
+  constexpr int PER = (NB + T - 1) / T;
+  V v[PER][R];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int b = t + q * T;
+    if (PER * T == NB || b < NB) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = ld(b + r * NB);
+      if constexpr (NS > 1) {
+        const int k = b % NS;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const V w = twiddle<V, NS * R>(r * k);
+          v[q][r] = FWD ? cmul(v[q][r], w) : cmulc(v[q][r], w);
+        }
+      }
+      dft<R, FWD>(v[q]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int b = t + q * T;
+    if (PER * T == NB || b < NB) {
+      const int j = (b / NS) * NS * R + (b % NS);
+#pragma unroll
+      for (int r = 0; r < R; ++r) st(j + r * NS, v[q][r]);
+    }
+  }
+  __syncthreads();
+}
+
+// Shared-memory view of one line: element p at base[p * STRIDE].
+template <typename V, int STRIDE> struct SLine {
+  V* base;
+  __device__ __forceinline__ V get(int p) const { return base[p * STRIDE]; }
+  __device__ __forceinline__ void put(int p, V v) const { base[p * STRIDE] = v; }
+};
+
+// Full transform of one line: stage 0 reads through `first`, the last stage
+// writes through `last`, the stages in between go through the line view.
+template <class P, bool FWD, int T, typename V, int S, class F, class L, class SL>
+__device__ __forceinline__ void run_from(int t, const F& first, const L& last, const SL& sl) {
+  auto sget = [&](int p) { return sl.get(p); };
+  auto sput = [&](int p, V v) { sl.put(p, v); };
+  if constexpr (S == 0 && P::NST == 1) {
+    stage<P, 0, FWD, T, V>(t, first, last);
+  } else if constexpr (S == 0) {
+    stage<P, 0, FWD, T, V>(t, first, sput);
+    run_from<P, FWD, T, V, 1>(t, first, last, sl);
+  } else if constexpr (S == P::NST - 1) {
+    stage<P, S, FWD, T, V>(t, sget, last);
+  } else {
+    stage<P, S, FWD, T, V>(t, sget, sput);
+    run_from<P, FWD, T, V, S + 1>(t, first, last, sl);
+  }
+}
+
+template <class P, bool FWD, int T, typename V, class F, class L, class SL>
+__device__ __forceinline__ void fft_line(int t, const F& first, const L& last, const SL& sl) {
+  run_from<P, FWD, T, V, 0>(t, first, last, sl);
+}
+
+}  // namespace fsa

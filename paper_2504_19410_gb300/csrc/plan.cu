@@ -1,0 +1,454 @@
+// Plans, validation and the single-solve apply path of libfsaconv.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+
+#include "fsa_internal.h"
+
+namespace fsa {
+
+namespace {
+thread_local std::string t_last_error;
+std::mutex g_init_mu;
+std::set<std::pair<int, int>> g_prepared;  // (device, key) pairs already prepared
+std::set<int> g_tw_ready;                  // devices with twiddle tables filled
+}  // namespace
+
+fsa_status set_error(fsa_status st, const std::string& msg) {
+  t_last_error = msg;
+  return st;
+}
+
+fsa_status cuda_error(cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  if (e == cudaErrorMemoryAllocation) return set_error(FSA_ERR_OOM, m);
+  return set_error(FSA_ERR_CUDA, m);
+}
+
+int persistent_grid(const void* func, int threads, int smem, long long tiles) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> occ;
+  static std::map<int, int> sms;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int per_sm = 1, nsm = 1;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(dev, func);
+    auto it = occ.find(key);
+    if (it == occ.end()) {
+      int b = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, func, threads, smem) != cudaSuccess || b < 1) b = 1;
+      it = occ.emplace(key, b).first;
+    }
+    per_sm = it->second;
+    auto is = sms.find(dev);
+    if (is == sms.end()) {
+      int c = 0;
+      if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c < 1) c = 1;
+      is = sms.emplace(dev, c).first;
+    }
+    nsm = is->second;
+  }
+  const long long cap = (long long)per_sm * nsm;
+  const long long g = tiles < cap ? tiles : cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+int& autotune_mode() {
+  static int mode = 1;
+  return mode;
+}
+
+bool supported_n(int n) {
+  if (n < 4 || n > 512 || (n & 1)) return false;
+  int m = n;
+  if (m % 3 == 0) m /= 3;
+  return (m & (m - 1)) == 0;  // power of two
+}
+
+bool supported_M(int M) { return (M % 2 == 0) && supported_n(M / 2); }
+
+// exp(-2 pi i k / 3072) evaluated in long double and rounded once.
+void host_twiddles(double* re, double* im) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int k = 0; k < kTwN; ++k) {
+    const long double a = 2.0L * pi * (long double)k / (long double)kTwN;
+    re[k] = (double)cosl(a);
+    im[k] = -(double)sinl(a);
+  }
+}
+
+}  // namespace fsa
+
+using namespace fsa;
+
+namespace fsa {
+
+// The five passes for `count` solves that share the grid n and the dtype V.
+template <typename V>
+cudaError_t group_passes(const int* n, int count, const void* const* rho, void* const* phi, void* const* X,
+                         void* const* Y, const void* const* S, cudaStream_t s, cudaEvent_t* ev) {
+  const int n0 = n[0], n1 = n[1], n2 = n[2];
+  const long long C = (long long)n1 * n2;
+  const long long rows = (long long)(n0 + 1) * n1;
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < count && e == cudaSuccess; b += kMaxJobs) {
+    const int m = count - b < kMaxJobs ? count - b : kMaxJobs;
+    Jobs j1{}, j2{}, j3{}, j4{}, j5{};
+    j1.count = j2.count = j3.count = j4.count = j5.count = m;
+    for (int i = 0; i < m; ++i) {
+      const int k = b + i;
+      j1.j[i] = Job{rho[k], X[k], nullptr};
+      j2.j[i] = Job{X[k], Y[k], nullptr};
+      j3.j[i] = Job{Y[k], Y[k], S[k]};
+      j4.j[i] = Job{Y[k], X[k], nullptr};
+      j5.j[i] = Job{X[k], phi[k], nullptr};
+    }
+    auto mark = [&](int i) {
+      if (ev && e == cudaSuccess) e = cudaEventRecord(ev[i], s);
+    };
+    mark(0);
+    e = e == cudaSuccess ? Passes<V>::r2c_ax0(2 * n0, j1, C, s) : e;
+    mark(1);
+    if (e == cudaSuccess) e = Passes<V>::row_fwd(2 * n2, j2, rows, s);
+    mark(2);
+    if (e == cudaSuccess) e = Passes<V>::col_mid(2 * n1, j3, 2 * n2, n0 + 1, s);
+    mark(3);
+    if (e == cudaSuccess) e = Passes<V>::row_inv(2 * n2, j4, rows, s);
+    mark(4);
+    if (e == cudaSuccess) e = Passes<V>::c2r_ax0(2 * n0, j5, C, s);
+    mark(5);
+  }
+  return e;
+}
+template cudaError_t group_passes<float2>(const int*, int, const void* const*, void* const*, void* const*,
+                                          void* const*, const void* const*, cudaStream_t, cudaEvent_t*);
+template cudaError_t group_passes<double2>(const int*, int, const void* const*, void* const*, void* const*,
+                                           void* const*, const void* const*, cudaStream_t, cudaEvent_t*);
+
+}  // namespace fsa
+
+namespace {
+
+double appendix_b_bound_impl(double R0, double eps) {
+  // R0^2 f(c), f(c) = (1/(4 pi c^2)) int_c^inf s erfc(s) ds, c = R0/eps (App. B);
+  // int_c^inf s erfc(s) ds = (1/4 - c^2/2) erfc(c) + c exp(-c^2) / (2 sqrt(pi)).
+  const long double c = (long double)R0 / (long double)eps;
+  const long double pi = 3.141592653589793238462643383279502884L;
+  const long double tail = (0.25L - 0.5L * c * c) * erfcl(c) + c * expl(-c * c) / (2.0L * sqrtl(pi));
+  return (double)((long double)R0 * R0 * tail / (4.0L * pi * c * c));
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  cudaError_t set(int dev) {
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev != prev) {
+      e = cudaSetDevice(dev);
+      changed = (e == cudaSuccess);
+    }
+    return e;
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+fsa_status prepare_device(int dev, fsa_dtype dt, const int* n) {
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (!g_tw_ready.count(dev)) {
+    cudaError_t e = Passes<float2>::init_twiddles();
+    if (e == cudaSuccess) e = Passes<double2>::init_twiddles();
+    if (e == cudaSuccess) e = tensorgen_init_twiddles();
+    if (e != cudaSuccess) return cuda_error(e, "twiddle table upload");
+    g_tw_ready.insert(dev);
+  }
+  for (int j = 0; j < 3; ++j) {
+    const int M = 2 * n[j];
+    const int key = M * 4 + (int)dt;
+    if (g_prepared.count({dev, key})) continue;
+    cudaError_t e = (dt == FSA_F32) ? Passes<float2>::prepare(M) : Passes<double2>::prepare(M);
+    if (e == cudaSuccess) e = tensorgen_prepare(M);
+    if (e != cudaSuccess) return cuda_error(e, "kernel shared-memory opt-in");
+    g_prepared.insert({dev, key});
+  }
+  return FSA_OK;
+}
+
+template <typename V>
+cudaError_t apply_passes(const fsa_plan* p, const void* rho, void* phi, void* X, void* Y, cudaStream_t s) {
+  const void* rhos[1] = {rho};
+  void* phis[1] = {phi};
+  void* xs[1] = {X};
+  void* ys[1] = {Y};
+  const void* ss[1] = {p->spectrum};
+  return group_passes<V>(p->n, 1, rhos, phis, xs, ys, ss, s, nullptr);
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+namespace fsa {
+// All five passes of one plan on one stream.
+cudaError_t plan_apply_passes(const fsa_plan* p, const void* rho, void* phi, cudaStream_t s) {
+  void* X = p->ws;
+  void* Y = (char*)p->ws + p->x_bytes;
+  return p->dtype == FSA_F32 ? apply_passes<float2>(p, rho, phi, X, Y, s)
+                             : apply_passes<double2>(p, rho, phi, X, Y, s);
+}
+
+// The same with an event before the first pass and after each pass.
+cudaError_t plan_apply_passes_events(const fsa_plan* p, const void* rho, void* phi, cudaStream_t s,
+                                     cudaEvent_t* ev6) {
+  const void* rhos[1] = {rho};
+  void* phis[1] = {phi};
+  void* xs[1] = {p->ws};
+  void* ys[1] = {(char*)p->ws + p->x_bytes};
+  const void* ss[1] = {p->spectrum};
+  return p->dtype == FSA_F32 ? group_passes<float2>(p->n, 1, rhos, phis, xs, ys, ss, s, ev6)
+                             : group_passes<double2>(p->n, 1, rhos, phis, xs, ys, ss, s, ev6);
+}
+}  // namespace fsa
+
+extern "C" {
+
+const char* fsa_status_string(fsa_status s) {
+  switch (s) {
+    case FSA_OK: return "FSA_OK";
+    case FSA_ERR_INVALID_ARG: return "FSA_ERR_INVALID_ARG";
+    case FSA_ERR_UNSUPPORTED: return "FSA_ERR_UNSUPPORTED";
+    case FSA_ERR_EPS: return "FSA_ERR_EPS";
+    case FSA_ERR_OOM: return "FSA_ERR_OOM";
+    case FSA_ERR_CUDA: return "FSA_ERR_CUDA";
+    case FSA_ERR_NOT_GENERATED: return "FSA_ERR_NOT_GENERATED";
+    case FSA_ERR_BUSY: return "FSA_ERR_BUSY";
+    case FSA_ERR_TIMEOUT: return "FSA_ERR_TIMEOUT";
+    case FSA_ERR_DEVICE_TIMEOUT: return "FSA_ERR_DEVICE_TIMEOUT";
+    case FSA_ERR_NOT_FOUND: return "FSA_ERR_NOT_FOUND";
+  }
+  return "FSA_ERR_UNKNOWN";
+}
+
+const char* fsa_last_error(void) { return t_last_error.c_str(); }
+
+fsa_status fsa_autotune_set(int mode) {
+  if (mode != 0 && mode != 1) return set_error(FSA_ERR_INVALID_ARG, "fsa_autotune_set: mode must be 0 or 1");
+  autotune_mode() = mode;
+  return FSA_OK;
+}
+
+double fsa_appendix_b_bound(double R0, double eps) {
+  if (!(R0 > 0) || !(eps > 0)) return NAN;
+  return appendix_b_bound_impl(R0, eps);
+}
+
+}  // extern "C"
+
+namespace fsa {
+
+size_t plan_workspace_bytes(const int* n, fsa_dtype dt) {
+  const size_t s = dt == FSA_F32 ? 4 : 8;
+  const size_t K0 = n[0] + 1;
+  return K0 * n[1] * n[2] * 2 * s + K0 * n[1] * (2 * (size_t)n[2]) * 2 * s;
+}
+
+// FP32 plans generate in FP64 in a scratch octant; FP64 plans in place.
+size_t plan_gen_scratch_bytes(const int* n, fsa_dtype dt) {
+  return dt == FSA_F64 ? 0 : (size_t)(n[0] + 1) * (n[1] + 1) * (n[2] + 1) * 8;
+}
+
+// Argument checks that need no device.  On success *eps_out / *bound_out
+// hold the eps in use and its App. B bound.
+fsa_status plan_validate(const double* L, const int* n, fsa_dtype dtype, double eps_in, double eps_tol,
+                         double* eps_out, double* bound_out) {
+  if (dtype != FSA_F32 && dtype != FSA_F64) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: bad dtype");
+  for (int j = 0; j < 3; ++j) {
+    if (!supported_n(n[j]))
+      return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: n[" + std::to_string(j) + "] = " +
+                                                std::to_string(n[j]) +
+                                                " unsupported (need even 2^a or 3*2^a in [4, 512])");
+    if (!(L[j] > 0) || !std::isfinite(L[j]))
+      return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: L[" + std::to_string(j) + "] must be > 0");
+  }
+  if (eps_in < 0 || !std::isfinite(eps_in)) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: eps < 0");
+  const double R0 = 2.0 * std::min(L[0], std::min(L[1], L[2]));
+  const double eps = eps_in > 0 ? eps_in : std::min(1.0, R0 / 6.0);
+  const double bound = appendix_b_bound_impl(R0, eps);
+  const double tol = eps_tol == 0 ? 1e-8 : eps_tol;
+  if (tol > 0 && !(bound <= tol)) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "fsa_plan_create: eps = %g fails App. B: R0^2 f(R0/eps) = %.3g > %.3g (R0 = %g)", eps,
+             bound, tol, R0);
+    return set_error(FSA_ERR_EPS, buf);
+  }
+  *eps_out = eps;
+  *bound_out = bound;
+  return FSA_OK;
+}
+
+fsa_status plan_create_internal(fsa_plan** out, const double* L, const int* n, fsa_dtype dtype, double eps_in,
+                                double eps_tol, bool with_workspace) {
+  *out = nullptr;
+  double eps = 0, bound = 0;
+  fsa_status vs = plan_validate(L, n, dtype, eps_in, eps_tol, &eps, &bound);
+  if (vs != FSA_OK) return vs;
+  const double R0 = 2.0 * std::min(L[0], std::min(L[1], L[2]));
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "fsa_plan_create: cudaGetDevice");
+  fsa_status st = prepare_device(dev, dtype, n);
+  if (st != FSA_OK) return st;
+
+  fsa_plan* p = new fsa_plan{};
+  for (int j = 0; j < 3; ++j) {
+    p->n[j] = n[j];
+    p->L[j] = L[j];
+    p->h[j] = 2.0 * L[j] / n[j];
+  }
+  p->eps = eps;
+  p->R0 = R0;
+  p->eps_bound = bound;
+  p->dtype = dtype;
+  p->device = dev;
+  const size_t s = dtype == FSA_F32 ? 4 : 8;
+  p->spectrum_bytes = (size_t)(n[0] + 1) * (n[1] + 1) * (n[2] + 1) * s;
+  p->x_bytes = (size_t)(n[0] + 1) * n[1] * n[2] * 2 * s;
+  p->ws_bytes = with_workspace ? plan_workspace_bytes(n, dtype) : 0;
+  // The workspace always holds the FP64 generation scratch of an FP32 plan.
+  e = cudaMalloc(&p->spectrum, p->spectrum_bytes);
+  if (e == cudaSuccess && with_workspace) e = cudaMalloc(&p->ws, p->ws_bytes);
+  if (e != cudaSuccess) {
+    if (p->spectrum) cudaFree(p->spectrum);
+    delete p;
+    cudaGetLastError();
+    return cuda_error(e, "fsa_plan_create: cudaMalloc");
+  }
+  *out = p;
+  return FSA_OK;
+}
+
+cudaError_t plan_generate_into(fsa_plan* p, void* scratch, cudaStream_t s) {
+  double* oct = p->dtype == FSA_F64 ? (double*)p->spectrum : (double*)scratch;
+  cudaError_t e = tensorgen_run(p->n, p->L, p->eps, oct, p->spectrum, p->dtype, s);
+  if (e == cudaSuccess) p->generated = 1;
+  return e;
+}
+
+}  // namespace fsa
+
+extern "C" {
+
+fsa_status fsa_plan_create(fsa_plan** out, fsa_kernel kernel, int d, const double* L, const int* n,
+                           fsa_dtype dtype, const fsa_plan_opts* opts) {
+  if (!out) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: out is NULL");
+  *out = nullptr;
+  if (kernel != FSA_KERNEL_COULOMB3D) return set_error(FSA_ERR_UNSUPPORTED, "fsa_plan_create: unknown kernel");
+  if (d != 3) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: only d = 3 is implemented");
+  if (!L || !n) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: L or n is NULL");
+  fsa_plan_opts o{};
+  o.device = -1;
+  if (opts) o = *opts;
+  double eps = 0, bound = 0;
+  fsa_status vs = plan_validate(L, n, dtype, o.eps, o.eps_tol, &eps, &bound);
+  if (vs != FSA_OK) return vs;  // no device touched
+  DeviceGuard dg;
+  cudaError_t e = dg.set(o.device);
+  if (e != cudaSuccess) return cuda_error(e, "fsa_plan_create: cudaSetDevice");
+  return plan_create_internal(out, L, n, dtype, o.eps, o.eps_tol, true);
+}
+
+fsa_status fsa_plan_destroy(fsa_plan* p) {
+  if (!p) return FSA_OK;
+  batched_forget_plan(p);
+  DeviceGuard dg;
+  dg.set(p->device);
+  cudaFree(p->spectrum);
+  cudaFree(p->ws);
+  delete p;
+  return FSA_OK;
+}
+
+fsa_status fsa_plan_spectrum_copy(const fsa_plan* p, void* dst, size_t nbytes, fsa_stream_t stream) {
+  if (!p || !dst) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_spectrum_copy: NULL argument");
+  if (nbytes < p->spectrum_bytes) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_spectrum_copy: dst too small");
+  DeviceGuard dg;
+  cudaError_t e = dg.set(p->device);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dst, p->spectrum, p->spectrum_bytes, cudaMemcpyDefault, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "fsa_plan_spectrum_copy");
+  return FSA_OK;
+}
+
+fsa_status fsa_plan_info_get(const fsa_plan* p, fsa_plan_info* info) {
+  if (!p || !info) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_info_get: NULL argument");
+  for (int j = 0; j < 3; ++j) {
+    info->n[j] = p->n[j];
+    info->L[j] = p->L[j];
+    info->h[j] = p->h[j];
+  }
+  info->eps = p->eps;
+  info->R0 = p->R0;
+  info->eps_bound = p->eps_bound;
+  info->dtype = p->dtype;
+  info->device = p->device;
+  info->generated = p->generated;
+  info->workspace_bytes = p->ws_bytes;
+  info->spectrum_bytes = p->spectrum_bytes;
+  info->spectrum = p->spectrum;
+  return FSA_OK;
+}
+
+fsa_status fsa_tensor_generate(fsa_plan* p, fsa_stream_t stream) {
+  if (!p) return set_error(FSA_ERR_INVALID_ARG, "fsa_tensor_generate: plan is NULL");
+  DeviceGuard dg;
+  cudaError_t e = dg.set(p->device);
+  if (e != cudaSuccess) return cuda_error(e, "fsa_tensor_generate: cudaSetDevice");
+  if (!p->ws && p->dtype == FSA_F32)
+    return set_error(FSA_ERR_INVALID_ARG, "fsa_tensor_generate: plan has no workspace for its FP64 scratch");
+  e = plan_generate_into(p, p->ws, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "fsa_tensor_generate: launch");
+  return FSA_OK;
+}
+
+fsa_status fsa_apply(const fsa_plan* p, const void* rho, void* phi, fsa_stream_t stream) {
+  if (!p || !rho || !phi) return set_error(FSA_ERR_INVALID_ARG, "fsa_apply: NULL argument");
+  if (!p->ws) return set_error(FSA_ERR_INVALID_ARG, "fsa_apply: plan has no workspace");
+  if (!p->generated) return set_error(FSA_ERR_NOT_GENERATED, "fsa_apply: call fsa_tensor_generate first");
+  if (!aligned16(rho) || !aligned16(phi))
+    return set_error(FSA_ERR_INVALID_ARG, "fsa_apply: rho and phi must be 16-byte aligned");
+  DeviceGuard dg;
+  cudaError_t e = dg.set(p->device);
+  if (e == cudaSuccess) e = plan_apply_passes(p, rho, phi, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "fsa_apply: launch");
+  return FSA_OK;
+}
+
+fsa_status fsa_apply_host(const fsa_plan* p, const void* rho_host, void* phi_host, fsa_stream_t stream) {
+  if (!p || !rho_host || !phi_host) return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_host: NULL argument");
+  if (!p->ws) return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_host: plan has no workspace");
+  if (!p->generated) return set_error(FSA_ERR_NOT_GENERATED, "fsa_apply_host: call fsa_tensor_generate first");
+  DeviceGuard dg;
+  cudaError_t e = dg.set(p->device);
+  const size_t vbytes = (size_t)p->n[0] * p->n[1] * p->n[2] * (p->dtype == FSA_F32 ? 4 : 8);
+  // rho is staged in the Y region (free until the second pass writes it);
+  // phi is produced there too (Y is dead once the fourth pass has read it).
+  void* X = p->ws;
+  void* Y = (char*)p->ws + p->x_bytes;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Y, rho_host, vbytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = p->dtype == FSA_F32 ? apply_passes<float2>(p, Y, Y, X, Y, s) : apply_passes<double2>(p, Y, Y, X, Y, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(phi_host, Y, vbytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_error(e, "fsa_apply_host");
+  return FSA_OK;
+}
+
+}  // extern "C"

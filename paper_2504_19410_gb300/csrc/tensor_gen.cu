@@ -1,0 +1,159 @@
+// Tensor generation ("Precomp" of Sec. 5, Example 2), in FP64 on the device.
+//
+// The stored spectrum is S[p] = (DFT_{2n}(T^(1))[p] + W(|mu_p|)) / prod_j 2 n_j
+// on the octant p_j in [0, n_j]:
+//   * T^(1)_o = h0 h1 h2 U^eps(|o.h|), U^eps = erf(r/eps)/(4 pi r), with the
+//     limit 1/(2 pi^{3/2} eps) at r = 0 (Sec. 2.1, Eq. Tensor1; Sec. 4,
+//     Eq. KerAppr; Table 1).  T^(1) is even per axis, so its values on the
+//     octant o_j in [0, n_j] define it on the doubled grid.
+//   * The DFT over the doubled grid of an even sequence is a DCT-I per axis
+//     (Sec. 2.3 notes the axis symmetry of T); each axis is done with the
+//     library's FFT kernels on the even extension.
+//   * T^(2) = iDFT(W) (Sec. 2.2, Eq. Tensor2), so its DFT is W itself:
+//     W(k) = (1 - exp(-k^2 eps^2 / 4)) / k^2 (Table 1, 3-D Coulomb), evaluated
+//     with expm1; W(0) = eps^2/4, mu_{p,j} = pi p_j / (2 L_j) (Sec. 2.4, Eq. WkAnis).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "fsa_internal.h"
+#include "passes.cuh"
+
+namespace fsa {
+
+__global__ void k_t1_octant(double* __restrict__ O, int n0, int n1, int n2, double h0, double h1, double h2,
+                            double eps) {
+  const long long total = (long long)(n0 + 1) * (n1 + 1) * (n2 + 1);
+  const double hv = h0 * h1 * h2;
+  const double u0 = 1.0 / (2.0 * 5.5683279968317078453 * eps);  // 1/(2 pi^{3/2} eps)
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p2 = (int)(i % (n2 + 1));
+    const long long r01 = i / (n2 + 1);
+    const int p1 = (int)(r01 % (n1 + 1));
+    const int p0 = (int)(r01 / (n1 + 1));
+    const double x = p0 * h0, y = p1 * h1, z = p2 * h2;
+    const double r = sqrt(x * x + y * y + z * z);
+    const double u = r > 0.0 ? erf(r / eps) / (4.0 * 3.14159265358979323846 * r) : u0;
+    O[i] = hv * u;
+  }
+}
+
+template <typename R>
+__global__ void k_spectrum_finalize(const double* S1, R* S,  // may alias (FP64 plans)
+                                    int n0, int n1, int n2,
+                                    double c0, double c1, double c2, double eps, double inv_norm) {
+  const long long total = (long long)(n0 + 1) * (n1 + 1) * (n2 + 1);
+  const double e2 = eps * eps;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p2 = (int)(i % (n2 + 1));
+    const long long r01 = i / (n2 + 1);
+    const int p1 = (int)(r01 % (n1 + 1));
+    const int p0 = (int)(r01 / (n1 + 1));
+    const double m0 = c0 * p0, m1 = c1 * p1, m2 = c2 * p2;  // mu_j = pi p_j / (2 L_j)
+    const double k2 = m0 * m0 + m1 * m1 + m2 * m2;
+    const double w = k2 > 0.0 ? -expm1(-0.25 * k2 * e2) / k2 : 0.25 * e2;
+    S[i] = (R)((S1[i] + w) * inv_norm);
+  }
+}
+
+namespace {
+
+template <int M> struct DctInst {
+  using P = typename PlanFor<M>::type;
+  static constexpr int W = 8;
+  static constexpr int T = threads_per_line<P, W>();
+  static constexpr int SM = smem_strided<P, double2, W>();
+  static cudaError_t prepare() {
+    return cudaFuncSetAttribute((const void*)k_dct1<P, W, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
+  }
+  static cudaError_t run(double* O, long long nlines, long long inner, long long os, long long is, long long es,
+                         cudaStream_t s) {
+    const long long pairs = (nlines + 1) / 2;
+    const long long tiles = (pairs + W - 1) / W;
+    k_dct1<P, W, T><<<(unsigned)tiles, W * T, SM, s>>>(O, nlines, inner, os, is, es);
+    return cudaGetLastError();
+  }
+};
+
+#define FSA_DCT_DISPATCH(M, CALL)                      \
+  switch (M) {                                         \
+    case 8: return DctInst<8>::CALL;                   \
+    case 12: return DctInst<12>::CALL;                 \
+    case 16: return DctInst<16>::CALL;                 \
+    case 24: return DctInst<24>::CALL;                 \
+    case 32: return DctInst<32>::CALL;                 \
+    case 48: return DctInst<48>::CALL;                 \
+    case 64: return DctInst<64>::CALL;                 \
+    case 96: return DctInst<96>::CALL;                 \
+    case 128: return DctInst<128>::CALL;               \
+    case 192: return DctInst<192>::CALL;               \
+    case 256: return DctInst<256>::CALL;               \
+    case 384: return DctInst<384>::CALL;               \
+    case 512: return DctInst<512>::CALL;               \
+    case 768: return DctInst<768>::CALL;               \
+    case 1024: return DctInst<1024>::CALL;             \
+    default: break;                                    \
+  }
+
+cudaError_t dct_prepare(int M) {
+  FSA_DCT_DISPATCH(M, prepare());
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t dct_run(int M, double* O, long long nlines, long long inner, long long os, long long is, long long es,
+                    cudaStream_t s) {
+  FSA_DCT_DISPATCH(M, run(O, nlines, inner, os, is, es, s));
+  return cudaErrorInvalidValue;
+}
+
+#undef FSA_DCT_DISPATCH
+
+}  // namespace
+
+cudaError_t tensorgen_prepare(int M) { return dct_prepare(M); }
+
+cudaError_t tensorgen_init_twiddles() {
+  std::vector<double> re(kTwN), im(kTwN);
+  host_twiddles(re.data(), im.data());
+  std::vector<double2> t64(kTwN);
+  std::vector<float2> t32(kTwN);
+  for (int k = 0; k < kTwN; ++k) {
+    t64[k] = make_double2(re[k], im[k]);
+    t32[k] = make_float2((float)re[k], (float)im[k]);
+  }
+  cudaError_t e = cudaMemcpyToSymbol(g_tw64, t64.data(), sizeof(double2) * kTwN);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tw32, t32.data(), sizeof(float2) * kTwN);
+  return e;
+}
+
+cudaError_t tensorgen_run(const int n[3], const double L[3], double eps, double* O, void* out, fsa_dtype dtype,
+                          cudaStream_t s) {
+  const int n0 = n[0], n1 = n[1], n2 = n[2];
+  const long long e0 = n0 + 1, e1 = n1 + 1, e2 = n2 + 1;
+  const double h0 = 2.0 * L[0] / n0, h1 = 2.0 * L[1] / n1, h2 = 2.0 * L[2] / n2;
+  const long long total = e0 * e1 * e2;
+  const int threads = 256;
+  const int blocks = (int)std::min<long long>((total + threads - 1) / threads, 152LL * 16);
+  k_t1_octant<<<blocks, threads, 0, s>>>(O, n0, n1, n2, h0, h1, h2, eps);
+  cudaError_t e = cudaGetLastError();
+  // axis 2: lines (p0, p1) contiguous, element stride 1
+  if (e == cudaSuccess) e = dct_run(2 * n2, O, e0 * e1, e1, e1 * e2, e2, 1, s);
+  // axis 1: lines (p0, p2), element stride e2
+  if (e == cudaSuccess) e = dct_run(2 * n1, O, e0 * e2, e2, e1 * e2, 1, e2, s);
+  // axis 0: lines (p1, p2) flattened, element stride e1 * e2
+  if (e == cudaSuccess) e = dct_run(2 * n0, O, e1 * e2, e1 * e2, 0, 1, e1 * e2, s);
+  if (e != cudaSuccess) return e;
+  const double pi = 3.14159265358979323846;
+  const double inv_norm = 1.0 / (8.0 * (double)n0 * n1 * n2);
+  if (dtype == FSA_F64)
+    k_spectrum_finalize<double><<<blocks, threads, 0, s>>>(O, (double*)out, n0, n1, n2, pi / (2 * L[0]),
+                                                           pi / (2 * L[1]), pi / (2 * L[2]), eps, inv_norm);
+  else
+    k_spectrum_finalize<float><<<blocks, threads, 0, s>>>(O, (float*)out, n0, n1, n2, pi / (2 * L[0]),
+                                                          pi / (2 * L[1]), pi / (2 * L[2]), eps, inv_norm);
+  return cudaGetLastError();
+}
+
+}  // namespace fsa

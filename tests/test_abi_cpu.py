@@ -1,0 +1,95 @@
+"""The C-ABI library builds, loads and exports what include/*.h declares;
+host-only logic (argument validation, the App. B bound) is checked without a
+GPU.  No call here launches device work."""
+import glob
+import math
+import os
+import re
+
+import pytest
+
+from tests.conftest import ROOT
+
+
+@pytest.fixture(scope="session")
+def capi():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2504_19410_gb300 import capi as c
+    return c
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(fsa_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("fsa_plan_create", "fsa_tensor_generate", "fsa_apply", "fsa_apply_batched",
+                 "fsa_serve_submit", "fsa_serve_poll", "fsa_plan_destroy", "fsa_status_string"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(capi):
+    lib = capi.lib()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_status_strings(capi):
+    assert capi.fsa_status_string(capi.FSA_OK) == "FSA_OK"
+    assert capi.fsa_status_string(capi.FSA_ERR_EPS) == "FSA_ERR_EPS"
+
+
+def test_appendix_b_bound_matches_oracle(capi):
+    from oracle import fsa
+    for R0, c in [(24.0, 5.85), (24.0, 5.8), (16.0, 6.0), (4.0, 10.0), (2.0, 4.0)]:
+        a = capi.fsa_appendix_b_bound(R0, R0 / c)
+        b = fsa.appendix_b_bound(R0, R0 / c)
+        assert a == pytest.approx(b, rel=1e-8)
+    assert math.isnan(capi.fsa_appendix_b_bound(0.0, 1.0))
+
+
+@pytest.mark.parametrize("n,L,kw,status", [
+    ((4, 4, 5), (1, 1, 1), {}, "FSA_ERR_INVALID_ARG"),        # odd n
+    ((4, 4, 10), (1, 1, 1), {}, "FSA_ERR_INVALID_ARG"),       # 10 = 2 * 5 not 2^a 3^b
+    ((4, 4, 1024), (1, 1, 1), {}, "FSA_ERR_INVALID_ARG"),     # too large
+    ((2, 4, 4), (1, 1, 1), {}, "FSA_ERR_INVALID_ARG"),        # too small
+    ((8, 8, 8), (1, 0, 1), {}, "FSA_ERR_INVALID_ARG"),        # L <= 0
+    ((8, 8, 8), (1, 1, 1), {"eps": -1.0}, "FSA_ERR_INVALID_ARG"),
+    ((8, 8, 8), (8, 8, 8), {"eps": 5.0}, "FSA_ERR_EPS"),      # R0/eps = 3.2: bound ~ 4e-5 > 1e-8
+    ((8, 8, 8), (8, 8, 8), {"eps": 3.0, "eps_tol": 1e-16}, "FSA_ERR_EPS"),
+])
+def test_plan_create_rejects_before_touching_the_device(capi, n, L, kw, status):
+    with pytest.raises(capi.FsaError) as ei:
+        capi.fsa_plan_create(capi.FSA_KERNEL_COULOMB3D, 3, L, n, capi.FSA_F32, **kw)
+    assert capi.fsa_status_string(ei.value.status) == status
+
+
+def test_plan_create_rejects_dimension_and_kernel(capi):
+    with pytest.raises(capi.FsaError) as ei:
+        capi.fsa_plan_create(capi.FSA_KERNEL_COULOMB3D, 2, (1, 1, 1), (8, 8, 8), capi.FSA_F32)
+    assert ei.value.status == capi.FSA_ERR_INVALID_ARG
+    with pytest.raises(capi.FsaError) as ei:
+        capi.fsa_plan_create(7, 3, (1, 1, 1), (8, 8, 8), capi.FSA_F32)
+    assert ei.value.status == capi.FSA_ERR_UNSUPPORTED
+
+
+def test_supported_sizes_match_workloads(capi):
+    import workloads
+    for n in range(2, 600):
+        ok = n in workloads.SUPPORTED_N
+        try:
+            h = capi.fsa_plan_create(capi.FSA_KERNEL_COULOMB3D, 3, (1, 1, 1), (n, 4, 4), capi.FSA_F32,
+                                     eps=0.1, eps_tol=-1)
+            capi.fsa_plan_destroy(h)  # only reached when a device is present
+            accepted = True
+        except capi.FsaError as e:
+            accepted = e.status != capi.FSA_ERR_INVALID_ARG
+        assert accepted == ok, n

@@ -1,0 +1,262 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Tolerances (max-norm relative error of Sec. 5, against the FP64 oracle on the
+same seeded inputs): FP64 path <= 1e-12, FP32 path <= 2e-6 (the FP32 path
+also rounds rho to FP32).  The spectrum the library stores is compared with
+the oracle's literal DFT of T = T^(1) + iDFT(W): <= 1e-13 (FP64) and
+<= 2e-7 (FP32, one rounding).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import closed_forms as cf
+from oracle import fsa as oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 2e-6}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2504_19410_gb300 as fsa
+    return fsa
+
+
+def to_dev(rho, dt):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(rho, dtype=np.float64 if dt == "f64" else np.float32)).cuda()
+
+
+def gpu_solve(lib, L, n, eps, rho, dt):
+    import torch
+    plan = lib.Plan(L, n, dt, eps=eps)
+    out = plan.apply(to_dev(rho, dt))
+    torch.cuda.synchronize()
+    res = out.double().cpu().numpy()
+    plan.close()
+    return res
+
+
+SMALL = [(4, 4, 4), (4, 6, 8), (8, 8, 8), (12, 16, 24), (6, 48, 32), (16, 16, 16), (24, 12, 48),
+         (8, 8, 512), (512, 4, 4), (4, 384, 6), (96, 8, 12), (32, 32, 32)]
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("n", SMALL[:9])
+def test_spectrum_matches_oracle(lib, n, dt):
+    L = (2.0 + 0.1 * n[0] / 4, 3.0, 1.5 + n[2] / 64)
+    eps = min(1.0, 2 * min(L) / 6)
+    plan = lib.Plan(L, n, dt, eps=eps)
+    got = plan.spectrum().double().cpu().numpy()
+    plan.close()
+    want = oracle.spectrum_octant(oracle.tensor_T(L, n, eps), n)
+    err = oracle.rel_error(got, want)
+    assert err <= (1e-13 if dt == "f64" else 2e-7), err
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("n", SMALL)
+def test_apply_random_density_matches_oracle(lib, n, dt):
+    rng = np.random.default_rng(hash(n) % 2 ** 32)
+    L = (1.0 + n[0] / 16, 2.0, 1.0 + n[2] / 32)
+    eps = min(1.0, 2 * min(L) / 6)
+    rho = rng.standard_normal(n)
+    got = gpu_solve(lib, L, n, eps, rho, dt)
+    want = oracle.solve(L, n, eps, rho)
+    err = oracle.rel_error(got, want)
+    assert err <= TOL[dt], err
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_config_c1_iso_gaussian_32(lib, dt):
+    """exp(-|x|^2/2) on [-8,8]^3, 32^3: oracle FFT route, brute force at sampled
+    points, and the erf closed form (reported; bounded by the discretisation)."""
+    d = W.iso_gaussian()
+    rho = d.rho()
+    got = gpu_solve(lib, d.L, d.n, d.eps, rho, dt)
+    T = oracle.tensor_T(d.L, d.n, d.eps)
+    want = oracle.apply_fft(T, rho)
+    assert oracle.rel_error(got, want) <= TOL[dt]
+    rng = np.random.default_rng(1)
+    pts = [tuple(p) for p in rng.integers(0, 32, size=(48, 3))] + [(16, 16, 16), (0, 0, 0), (31, 31, 31)]
+    direct = oracle.apply_direct_at(T, rho, pts)
+    sampled = np.array([got[p] for p in pts])
+    assert np.max(np.abs(sampled - direct)) / np.max(np.abs(want)) <= TOL[dt]
+    exact = cf.density_potential(d)
+    e_exact = oracle.rel_error(got, exact)
+    print(f"C1 {dt}: vs oracle {oracle.rel_error(got, want):.2e}, vs closed form {e_exact:.2e}")
+    assert e_exact < 1e-5
+
+
+@pytest.mark.parametrize("h,printed", [(1.0, 2.0681e-2), (0.5, 2.5036e-6), (0.25, 5.5511e-16)])
+def test_table2_reproduced_by_gpu_fp64(lib, h, printed):
+    """The FP64 GPU path reproduces Table 2's 3-D double isotropic row."""
+    d = W.paper_case1(L=8.0, sigma2=0.8, h_over_gamma=h)
+    got = gpu_solve(lib, d.L, d.n, 1.0, d.rho(), "f64")
+    err = oracle.rel_error(got, cf.density_potential(d))
+    if printed > 1e-10:
+        assert err == pytest.approx(printed, rel=5e-4)
+    else:
+        assert err < 4 * printed
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.25, 0.125])
+def test_table2_case2_and_table3_192_on_gpu(lib, gamma):
+    """Example 1 Case II at h = gamma/8 (n = 192): round-off against the exact
+    potential, as Table 2 (<= 1.2e-15) and Table 3 (3.3394E-16, gamma = 1) print."""
+    c = W.paper_case2(gamma3=gamma, h_over_gamma=0.125)
+    rho = c.rho()
+    exact = cf.case2_potential(c)
+    e64 = oracle.rel_error(gpu_solve(lib, c.L, c.n, c.eps, rho, "f64"), exact)
+    e32 = oracle.rel_error(gpu_solve(lib, c.L, c.n, c.eps, rho, "f32"), exact)
+    print(f"Case II gamma={gamma}: FP64 {e64:.3e}  FP32 {e32:.3e}")
+    assert e64 < 5e-15
+    assert e32 < 2e-6
+
+
+# ---- full sizes, sampled -----------------------------------------------------
+
+def sample_points(n, rng, k, extra=()):
+    pts = [tuple(int(rng.integers(0, n[j])) for j in range(3)) for _ in range(k)]
+    pts += [tuple(x - 1 for x in n), (0, 0, 0), tuple(x // 2 for x in n)]
+    return pts + list(extra)
+
+
+_T_CACHE = {}
+
+
+def oracle_T(d):
+    key = (d.L, d.n, d.eps)
+    if key not in _T_CACHE:
+        _T_CACHE.clear()
+        _T_CACHE[key] = oracle.tensor_T(d.L, d.n, d.eps)
+    return _T_CACHE[key]
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_config_c2_256_sampled(lib, dt):
+    """8-Gaussian sum on [-16,16]^3, 256^3 (the headline workload): sampled
+    outputs against Eq. DiscConv summed directly by the oracle."""
+    d = W.gaussian_sum(seed=2504)
+    rho = d.rho()
+    got = gpu_solve(lib, d.L, d.n, d.eps, rho, dt)
+    amax = np.unravel_index(np.argmax(np.abs(got)), got.shape)
+    pts = sample_points(d.n, np.random.default_rng(5), 24, extra=[amax])
+    T = oracle_T(d)
+    want = oracle.apply_direct_at(T, rho, pts)
+    sampled = np.array([got[p] for p in pts])
+    err = np.max(np.abs(sampled - want)) / np.max(np.abs(want))
+    exact = cf.density_potential_points(d, np.array(pts))
+    print(f"C2 {dt}: sampled vs oracle {err:.2e}, vs closed form "
+          f"{np.max(np.abs(sampled - exact)) / np.max(np.abs(exact)):.2e}")
+    assert err <= TOL[dt]
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("kind", ["cigar", "pancake"])
+def test_config_c3_aniso_sampled(lib, kind, dt):
+    d = W.aniso_gaussian(kind)
+    rho = d.rho()
+    got = gpu_solve(lib, d.L, d.n, d.eps, rho, dt)
+    amax = np.unravel_index(np.argmax(np.abs(got)), got.shape)
+    pts = sample_points(d.n, np.random.default_rng(6), 12, extra=[amax])
+    T = oracle_T(d)
+    want = oracle.apply_direct_at(T, rho, pts)
+    sampled = np.array([got[p] for p in pts])
+    err = np.max(np.abs(sampled - want)) / np.max(np.abs(want))
+    exact = cf.density_potential_points(d, np.array(pts))
+    print(f"{kind} {dt}: sampled vs oracle {err:.2e}, vs closed form "
+          f"{np.max(np.abs(sampled - exact)) / np.max(np.abs(exact)):.2e}")
+    assert err <= TOL[dt]
+
+
+# ---- behaviour -----------------------------------------------------------------
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_in_place_and_deterministic(lib, dt):
+    import torch
+    n, L = (24, 16, 32), (3.0, 2.0, 4.0)
+    rho = np.random.default_rng(2).standard_normal(n)
+    plan = lib.Plan(L, n, dt, eps=0.5)
+    a = plan.apply(to_dev(rho, dt))
+    b = plan.apply(to_dev(rho, dt))
+    x = to_dev(rho, dt)
+    plan.apply(x, x)  # phi == rho
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(a, x)
+    plan.close()
+
+
+def test_linearity_on_gpu(lib):
+    import torch
+    n, L = (16, 24, 12), (2.0, 3.0, 1.5)
+    rng = np.random.default_rng(4)
+    a, b = rng.standard_normal(n), rng.standard_normal(n)
+    plan = lib.Plan(L, n, "f64", eps=0.4)
+    pa = plan.apply(to_dev(a, "f64")).cpu().numpy()
+    pb = plan.apply(to_dev(b, "f64")).cpu().numpy()
+    pc = plan.apply(to_dev(3 * a - 2 * b, "f64")).cpu().numpy()
+    assert oracle.rel_error(pc, 3 * pa - 2 * pb) < 1e-13
+    plan.close()
+
+
+def test_not_generated_and_bad_pointer(lib):
+    import torch
+    from paper_2504_19410_gb300 import capi
+    plan = lib.Plan((1, 1, 1), (8, 8, 8), "f32", eps=0.3, generate=False)
+    x = torch.zeros((8, 8, 8), device="cuda")
+    with pytest.raises(capi.FsaError) as ei:
+        plan.apply(x)
+    assert ei.value.status == capi.FSA_ERR_NOT_GENERATED
+    plan.generate()
+    with pytest.raises(capi.FsaError) as ei:
+        capi.fsa_apply(plan.handle, x.data_ptr() + 4, x.data_ptr(), torch.cuda.current_stream())
+    assert ei.value.status == capi.FSA_ERR_INVALID_ARG
+    plan.close()
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_apply_host_equals_apply(lib, dt):
+    import torch
+    n, L = (32, 48, 16), (4.0, 6.0, 2.0)
+    rho = np.random.default_rng(8).standard_normal(n)
+    plan = lib.Plan(L, n, dt, eps=0.5)
+    dev = plan.apply(to_dev(rho, dt)).cpu()
+    host_in = torch.from_numpy(rho.astype(np.float64 if dt == "f64" else np.float32)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    plan.apply_host(host_in, host_out)
+    torch.cuda.synchronize()
+    assert torch.equal(dev, host_out)
+    plan.close()
+
+
+def test_batched_equals_single(lib):
+    import torch
+    specs = [((16, 16, 16), "f32"), ((24, 24, 24), "f32"), ((16, 16, 16), "f64"), ((16, 16, 16), "f32"),
+             ((8, 48, 16), "f64"), ((32, 32, 32), "f32")]
+    rng = np.random.default_rng(9)
+    plans, rhos, singles = [], [], []
+    for n, dt in specs:
+        L = (2.0 + n[0] / 16, 3.0, 2.5)
+        p = lib.Plan(L, n, dt, eps=0.6)
+        r = to_dev(rng.standard_normal(n), dt)
+        singles.append(p.apply(r).clone())
+        plans.append(p)
+        rhos.append(r)
+    outs = [torch.empty_like(r) for r in rhos]
+    for _ in range(2):  # second call replays the captured graph
+        for o in outs:
+            o.zero_()
+        lib.apply_batched(plans, rhos, outs)
+        torch.cuda.synchronize()
+        for s, o in zip(singles, outs):
+            assert torch.equal(s, o)
+    for p in plans:
+        p.close()
