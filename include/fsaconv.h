@@ -124,6 +124,21 @@ fsa_status fsa_tensor_generate(fsa_plan* plan, fsa_stream_t stream);
  * FSA_ERR_CUDA. */
 fsa_status fsa_apply(const fsa_plan* plan, const void* rho, void* phi, fsa_stream_t stream);
 
+/* fsa_apply for callers that cannot have device memory allocated for them
+ * (the paper has no counterpart: this is a deployment variant).  Same result
+ * as fsa_apply on the same plan, but the two intermediate arrays live in a
+ * 16 MiB static __device__ array of the library instead of the plan's
+ * workspace, and the call allocates nothing.  Size limit: the workspace
+ * 6 (n0+1) n1 n2 s bytes (s = 4 for FP32, 8 for FP64) must fit in 16 MiB,
+ * e.g. grids up to 64^3 in both precisions; larger grids get
+ * FSA_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls on a device share the array and it keeps the
+ * last call's contents; nothing in it needs to start at zero, but calls that
+ * overlap on the GPU race, so order them (one stream, or events).
+ * Errors as fsa_apply. */
+fsa_status fsa_apply_noalloc(const fsa_plan* plan, const void* rho, void* phi, fsa_stream_t stream);
+
 /* fsa_apply with HOST buffers: copies rho_host to the device, applies, copies
  * the result to phi_host, all enqueued on stream (pinned host memory gives
  * asynchronous copies).  The caller must synchronise the stream before

@@ -67,6 +67,7 @@ _PROTOS = {
     "fsa_tensor_generate": (C.c_int, [_VP, _VP]),
     "fsa_apply": (C.c_int, [_VP, _VP, _VP, _VP]),
     "fsa_apply_host": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "fsa_apply_noalloc": (C.c_int, [_VP, _VP, _VP, _VP]),
     "fsa_apply_batched": (C.c_int, [C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), C.c_int, _VP]),
     "fsa_plan_info_get": (C.c_int, [_VP, C.POINTER(PlanInfo)]),
     "fsa_plan_destroy": (C.c_int, [_VP]),
@@ -151,6 +152,10 @@ def fsa_tensor_generate(plan, stream=None):
 
 def fsa_apply(plan, rho, phi, stream=None):
     return check(lib().fsa_apply(plan, _ptr(rho), _ptr(phi), _stream(stream)))
+
+
+def fsa_apply_noalloc(plan, rho, phi, stream=None):
+    return check(lib().fsa_apply_noalloc(plan, _ptr(rho), _ptr(phi), _stream(stream)))
 
 
 def fsa_apply_host(plan, rho_host, phi_host, stream=None):
