@@ -248,9 +248,12 @@ def run_ours(args):
         return res
 
     tiers = {}
-    for dt in ("f32", "f64"):
+    for dt in args.tiers.split(","):
         tiers[dt] = bench_tier(dt)
-    main = tiers["f32"]
+    main = tiers.get("f32") or tiers["f64"]
+
+    batched = None if args.no_batched else bench_batched(args, fsa, W, torch, stream)
+    serving = None if args.no_serve else bench_serving(args, fsa, W, torch, rank)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -260,7 +263,8 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if "f32" in tiers else "f64",
+            "data": "synthetic",
             "config": {"workload": "c2_256: 3-D Coulomb FSA apply, 8-Gaussian density (seed 2504) on "
                                    "[-16,16]^3, 256^3 grid, eps=1, spectrum cached on device",
                        "grid": list(n), "l2": "per-step working set ~0.6 GB (FP32) > 129 MB L2; "
@@ -274,12 +278,135 @@ def run_ours(args):
             "pass_ms": main["pass_ms"],
             "precomp_ms": main["precomp_ms"],
             "step_roofline_frac_27V_model": main["step_roofline_frac_27V_model"],
-            "f64": {k: tiers["f64"][k] for k in ("value", "ms_per_step", "roofline", "pass_ms", "precomp_ms",
-                                                   "step_roofline_frac_27V_model", "e2e", "clocks")},
         }
+        if batched is not None:
+            line["batched"] = batched
+        if serving is not None:
+            line["serving"] = serving
+        if "f64" in tiers and main is not tiers["f64"]:
+            line["f64"] = {k: tiers["f64"][k] for k in ("value", "ms_per_step", "roofline", "pass_ms", "precomp_ms",
+                                                        "step_roofline_frac_27V_model", "e2e", "clocks")}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------- batched (C4) ----
+
+def bench_batched(args, fsa, W, torch, stream):
+    """64 seeded Gaussian-sum densities, cubic n from {64,96,128,192,256},
+    gamma in {1,4,8} (cigar or pancake), FP32, in one batched call (one
+    persistent launch per pass per shape group, captured in a CUDA graph),
+    against the same 64 solves issued one fsa_apply at a time."""
+    dens = W.batch_requests(seed=2504, count=64)
+    plans = [fsa.Plan(d.L, d.n, "f32", eps=d.eps) for d in dens]
+    rhos = [d.rho_torch(torch.float32) for d in dens]
+    phis = [torch.empty_like(r) for r in rhos]
+    for _ in range(2):
+        fsa.apply_batched(plans, rhos, phis)
+    torch.cuda.synchronize()
+    k = max(3, args.steps // 5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        fsa.apply_batched(plans, rhos, phis)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1) / k
+    for p, r, f in zip(plans, rhos, phis):
+        p.apply(r, f)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(k):
+        for p, r, f in zip(plans, rhos, phis):
+            p.apply(r, f)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ts = e0.elapsed_time(e1) / k
+    hist = {}
+    for d in dens:
+        hist[d.n[0]] = hist.get(d.n[0], 0) + 1
+    bytes_model = sum(reference_model_bytes(d.n, 4) for d in dens)
+    hbm_peak, kind = peaks()
+    out = {"workload": "c4: 64 densities, n in {64,96,128,192,256} (counts " + json.dumps(hist) +
+                       "), gamma in {1,4,8}, FP32", "solves_per_batch": len(dens),
+           "value": len(dens) / (tb * 1e-3), "unit": UNIT, "ms_per_batch": tb,
+           "sequential_solves_per_s": len(dens) / (ts * 1e-3), "ms_sequential": ts,
+           "step_roofline_frac_27V_model": bytes_model / (hbm_peak * 1e9) / (tb * 1e-3),
+           "gpu_launches_per_batch": 5 * len(hist) * 1}
+    for p in plans:
+        p.close()
+    del rhos, phis
+    torch.cuda.empty_cache()
+    return out
+
+
+# ------------------------------------------------------- serving (C5) ----
+
+def bench_serving(args, fsa, W, torch, rank):
+    """Poisson-arrival request stream through the serving loop (C5): n
+    log-uniform in [32,512] rounded to supported sizes, 80 % FP32 / 20 % FP64,
+    isotropic [-16,16]^3 8-Gaussian densities; plans cached on the device,
+    admission by free HBM.  Capacity is measured closed loop (all requests
+    queued at once); the open-loop run offers Poisson arrivals at
+    load x capacity and reports p50/p99 latency (submit -> done)."""
+    import numpy as np
+    reqs = W.serve_requests(seed=2504, count=args.serve_n)
+    keys = sorted({(n, dt) for n, dt, _ in reqs})
+    inputs, pools = {}, {}
+    for n, dt in keys:
+        tdt = torch.float32 if dt == "f32" else torch.float64
+        inputs[(n, dt)] = W.gaussian_sum(seed=2504 + n, n=n).rho_torch(tdt)
+        pools[(n, dt)] = [torch.empty_like(inputs[(n, dt)]) for _ in range(4 if n >= 384 else 8)]
+    srv = fsa.Server(max_inflight=32, streams=8)
+
+    def run(arrivals):
+        free = {k: list(v) for k, v in pools.items()}
+        outstanding = {}
+        lat, t0 = [], time.perf_counter()
+
+        def reap(block):
+            for t in list(outstanding):
+                st, tm = srv.poll(t, 0.05 if block else 0.0)
+                if st in (2, 3):
+                    key, buf = outstanding.pop(t)
+                    free[key].append(buf)
+                    lat.append((tm.done_s - tm.submit_s) * 1e3)
+                    if block:
+                        return
+
+        for i, (n, dt, _) in enumerate(reqs):
+            if arrivals is not None:
+                while time.perf_counter() - t0 < arrivals[i]:
+                    reap(False)
+            key = (n, dt)
+            while not free[key]:
+                reap(True)
+            buf = free[key].pop()
+            t = srv.submit((16.0, 16.0, 16.0), (n, n, n), dt, inputs[key], buf, eps=1.0)
+            outstanding[t] = (key, buf)
+            reap(False)
+        while outstanding:
+            reap(True)
+        wall = time.perf_counter() - t0
+        return wall, lat
+
+    run(None)  # warm the plan cache and the workspace pool
+    wall, lat = run(None)
+    capacity = len(reqs) / wall
+    arrivals = W.poisson_arrivals(2504, len(reqs), args.serve_load * capacity)
+    wall2, lat2 = run(arrivals)
+    st = srv.stats()
+    srv.close()
+    torch.cuda.empty_cache()
+    lat2 = np.array(lat2)
+    return {"workload": f"c5: {len(reqs)} requests, n log-uniform in [32,512] (supported sizes), "
+                        "80% FP32 / 20% FP64, [-16,16]^3 8-Gaussian densities",
+            "capacity_solves_per_s": capacity, "offered_load": args.serve_load,
+            "value": len(reqs) / wall2, "unit": UNIT,
+            "p50_ms": float(np.percentile(lat2, 50)), "p99_ms": float(np.percentile(lat2, 99)),
+            "closed_loop_p50_ms": float(np.percentile(lat, 50)),
+            "plan_hit_rate": st.plan_hits / max(1, st.plan_hits + st.plan_misses)}
 
 
 # -------------------------------------------------------------- oracle ----
@@ -343,7 +470,12 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tiers", default="f32,f64", help="apply tiers to time; the first FP32 one is the headline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-n", type=int, default=2000, help="requests in the serving run (C5 uses 10000)")
+    ap.add_argument("--serve-load", type=float, default=0.8, help="offered load as a fraction of capacity")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=128, help="cpu_baseline oracle sample grid (per axis)")
     ap.add_argument("--ref-n", type=int, default=96, help="--impl reference: oracle grid per step")

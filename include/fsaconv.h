@@ -191,9 +191,15 @@ fsa_status fsa_apply_profiled(const fsa_plan* plan, const void* rho, void* phi, 
 fsa_status fsa_profiler_read(fsa_profiler* prof, double* pass_ms, double* step_ms, int* steps);
 fsa_status fsa_profiler_destroy(fsa_profiler* prof);
 
-/* Tuning table for the pass kernels (tile widths), filled by the autotuner
- * on first use of each (pass, length, dtype) unless disabled.  mode: 0 = off
- * (defaults), 1 = tune on first use. */
+/* Kernel selection.  FP32 passes exist in two generations: 1 = Stockham
+ * radix-8 (three shared-memory stages per transform), 2 = two register-resident
+ * steps M = R1 x R2 (one exchange per transform).  mode 1 (default): each new
+ * FP32 plan times both generations for each of its passes on its own workspace
+ * at creation and keeps the faster per (pass, length); choices persist for the
+ * process.  mode 0: untuned passes use generation 2.  mode 2 / 3: force
+ * generation 1 / 2 for every FP32 pass (FP64 always uses generation 1).
+ * FSA_ERR_INVALID_ARG for other modes.  Not thread-safe against concurrent
+ * launches. */
 fsa_status fsa_autotune_set(int mode);
 
 /* ---------------------------------------------------------------- serving -- */

@@ -92,10 +92,49 @@ class Plan:
             pass
 
 
+class Server:
+    """The continuous-batching serving loop (fsa_serve_*).  rho/phi are CUDA
+    tensors owned by the caller until their ticket is DONE or FAILED."""
+
+    def __init__(self, max_inflight=0, streams=0, hbm_fraction=0.0, hbm_budget_bytes=0, plan_cache_max=0,
+                 queue_max=0, device=-1):
+        self.handle = capi.fsa_serve_create(max_inflight, streams, hbm_fraction, hbm_budget_bytes,
+                                            plan_cache_max, queue_max, device)
+
+    def submit(self, L, n, dtype, rho, phi, eps=0.0):
+        return capi.fsa_serve_submit(self.handle, L, n, _DT[dtype], rho, phi, eps)
+
+    def poll(self, ticket, timeout=0.0):
+        """(state, times); times has submit_s, admit_s, done_s, plan_hit, status."""
+        return capi.fsa_serve_poll(self.handle, ticket, timeout)
+
+    def wait(self, ticket, timeout=120.0):
+        state, t = self.poll(ticket, timeout)
+        if state in (capi.FSA_REQ_QUEUED, capi.FSA_REQ_RUNNING):
+            raise FsaError(capi.FSA_ERR_TIMEOUT, f"request {ticket} not done after {timeout} s")
+        if state != capi.FSA_REQ_DONE:
+            raise FsaError(t.status, f"request {ticket} ended in state {state}")
+        return t
+
+    def stats(self):
+        return capi.fsa_serve_stats_get(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            capi.fsa_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def apply_batched(plans, rhos, phis, stream=None):
     """fsa_apply_batched over Plan objects and torch tensors."""
     capi.fsa_apply_batched([p.handle for p in plans], rhos, phis, _cur_stream(stream))
     return phis
 
 
-__all__ = ["Plan", "apply_batched", "capi", "FsaError", "FSA_F32", "FSA_F64"]
+__all__ = ["Plan", "Server", "apply_batched", "capi", "FsaError", "FSA_F32", "FSA_F64"]

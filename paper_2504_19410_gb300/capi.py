@@ -240,10 +240,13 @@ def fsa_serve_submit(server, L, n, dtype, rho, phi, eps=0.0, kernel=FSA_KERNEL_C
 
 
 def fsa_serve_poll(server, ticket, timeout_s=0.0):
-    """Returns (state, ReqTimes); raises FsaError on TIMEOUT / NOT_FOUND."""
+    """Returns (state, ReqTimes).  A wait that runs out (FSA_ERR_TIMEOUT) returns
+    the current state (QUEUED or RUNNING); NOT_FOUND and other errors raise."""
     st = C.c_int()
     tm = ReqTimes()
-    check(lib().fsa_serve_poll(server, C.c_uint64(ticket), float(timeout_s), C.byref(st), C.byref(tm)))
+    rc = lib().fsa_serve_poll(server, C.c_uint64(ticket), float(timeout_s), C.byref(st), C.byref(tm))
+    if rc != FSA_ERR_TIMEOUT:
+        check(rc)
     return st.value, tm
 
 

@@ -21,7 +21,11 @@ struct Geometry {
 };
 
 bool supported_n(int n);
-int& autotune_mode();  // 1 = tune tile variants on first use (fsa_autotune_set)
+int& autotune_mode();  // fsa_autotune_set: 0 defaults, 1 tune per plan, 2 / 3 force generation 1 / 2
+// Kernel generation used for a pass of length M in a dtype: 1 = Stockham
+// radix-8 (passes.cuh), 2 = two-step register kernels (passes2.cuh, FP32).
+int kernel_variant(int pass, int M, fsa_dtype dt);
+void set_kernel_variant(int pass, int M, fsa_dtype dt, int variant);
 bool supported_M(int M);
 
 // Per-precision launchers (passes_f32.cu / passes_f64.cu).  `M` is the

@@ -1,0 +1,231 @@
+// Second-generation apply passes: the same five passes and data flow as
+// passes.cuh (pad + R2C axis 0 -> axis-2 FFT -> axis-1 FFT x spectrum x
+// inverse -> axis-2 inverse -> C2R axis 0 + crop), with every line transformed
+// as M = R1 x R2 in two register-resident steps (fft_reg.cuh).  Shared-memory
+// exchanges per line: R2C 2, row forward 1, middle 2, row inverse 1, C2R 1
+// (the first generation needed 3-5 per pass).
+//
+// Strided passes (axes 0, 1): W lines per CTA, lanes on lines, so each warp
+// access to HBM covers W consecutive elements of the contiguous axis; the
+// shared tile is sm[p * W + l].  Row passes (axis 2): lanes on the R1 threads
+// of a line, so step A's loads x[t + R2 r] and step B's stores X[q + R1 s]
+// are contiguous per half-warp; the shared tile is sm[l * R1 (R2+1) + q (R2+1) + t]
+// (padded rows: conflict-free for both steps).
+#pragma once
+#include "fft_reg.cuh"
+
+namespace fsa {
+
+template <class P> struct Geo2 {
+  static constexpr int W = 16;
+  static constexpr int NT = W * P::T;
+  static constexpr int SM_STRIDED = P::M * W * 8;
+  static constexpr int PITCH = P::R1 * (P::R2 + 1);
+  static constexpr int SM_ROWS = W * PITCH * 8;
+};
+
+// ---------------------------------------------------------------- pass 1 --
+template <class P>
+__global__ void __launch_bounds__(Geo2<P>::NT) k2_r2c_ax0(const Jobs jobs, long long C) {
+  using V = float2;
+  constexpr int M = P::M, n = M / 2, K = n + 1, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int l = threadIdx.x % W, u = threadIdx.x / W;
+  const long long tpj = (C + 2 * W - 1) / (2 * W);
+  for (long long tile = blockIdx.x; tile < tpj * jobs.count; tile += gridDim.x) {
+    const Job& jb = jobs.j[tile / tpj];
+    const float* __restrict__ rho = static_cast<const float*>(jb.in);
+    V* __restrict__ X = static_cast<V*>(jb.out);
+    const long long c = (tile % tpj) * (2 * W) + 2 * l;
+    const bool ok = c < C;
+    stepA_fwd<P, V>(
+        u,
+        [&](int t, int r) {
+          const int p = t + R2 * r;
+          return (p < n && ok) ? *reinterpret_cast<const V*>(rho + (long long)p * C + c) : czero<V>();
+        },
+        [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
+    __syncthreads();
+    V b[R2];
+#pragma unroll
+    for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
+    rfft<R2, true>(b);
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < R2; ++s) sm[(u + R1 * s) * W + l] = b[s];
+    __syncthreads();
+    // Z = DFT(a + i b): A[k] = (Z[k] + conj Z[M-k]) / 2, B[k] = (Z[k] - conj Z[M-k]) / 2i
+    for (int k = u; k < K; k += P::T) {
+      const V zk = sm[k * W + l];
+      const V zm = sm[((M - k) % M) * W + l];
+      if (ok) {
+        X[(long long)k * C + c] = mk(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        X[(long long)k * C + c + 1] = mk(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- pass 2 --
+template <class P>
+__global__ void __launch_bounds__(Geo2<P>::NT) k2_row_fwd(const Jobs jobs, long long rows) {
+  using V = float2;
+  constexpr int M = P::M, n = M / 2, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2, PITCH = Geo2<P>::PITCH;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int u = threadIdx.x % P::T, l = threadIdx.x / P::T;
+  V* line = sm + l * PITCH;
+  const long long tpj = (rows + W - 1) / W;
+  for (long long tile = blockIdx.x; tile < tpj * jobs.count; tile += gridDim.x) {
+    const Job& jb = jobs.j[tile / tpj];
+    const long long row = (tile % tpj) * W + l;
+    const bool ok = row < rows;
+    const V* __restrict__ x = static_cast<const V*>(jb.in) + row * n;
+    V* __restrict__ y = static_cast<V*>(jb.out) + row * M;
+    stepA_fwd<P, V>(
+        u,
+        [&](int t, int r) {
+          const int p = t + R2 * r;
+          return (p < n && ok) ? x[p] : czero<V>();
+        },
+        [&](int q, int t, V v) { line[q * (R2 + 1) + t] = v; });
+    __syncthreads();
+    V b[R2];
+#pragma unroll
+    for (int t = 0; t < R2; ++t) b[t] = line[u * (R2 + 1) + t];
+    rfft<R2, true>(b);
+    if (ok) {
+#pragma unroll
+      for (int s = 0; s < R2; ++s) y[u + R1 * s] = b[s];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- pass 3 --
+template <class P>
+__global__ void __launch_bounds__(Geo2<P>::NT) k2_col_mid(const Jobs jobs, int M2, int planes) {
+  using V = float2;
+  constexpr int M = P::M, n = M / 2, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int l = threadIdx.x % W, u = threadIdx.x / W;
+  const int tiles_per_plane = (M2 + W - 1) / W;
+  const long long tpj = (long long)tiles_per_plane * planes;
+  const int n2 = M2 / 2;
+  for (long long tile = blockIdx.x; tile < tpj * jobs.count; tile += gridDim.x) {
+    const Job& jb = jobs.j[tile / tpj];
+    const int lt = (int)(tile % tpj);
+    const int k0 = lt / tiles_per_plane;
+    const int k2 = (lt % tiles_per_plane) * W + l;
+    const bool ok = k2 < M2;
+    V* __restrict__ col = static_cast<V*>(jb.out) + (long long)k0 * n * M2 + k2;
+    const float* __restrict__ srow =
+        static_cast<const float*>(jb.S) + (long long)k0 * (n + 1) * (n2 + 1) + (ok ? min(k2, M2 - k2) : 0);
+    stepA_fwd<P, V>(
+        u,
+        [&](int t, int r) {
+          const int p = t + R2 * r;
+          return (p < n && ok) ? col[(long long)p * M2] : czero<V>();
+        },
+        [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
+    __syncthreads();
+    V b[R2];
+#pragma unroll
+    for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
+    rfft<R2, true>(b);
+    // b[s] = transform at k1 = u + R1 s: multiply by the spectrum (real, even)
+#pragma unroll
+    for (int s = 0; s < R2; ++s) {
+      const int k1 = u + R1 * s;
+      const float sv = ok ? __ldg(srow + (long long)min(k1, M - k1) * (n2 + 1)) : 0.f;
+      b[s] = cscale(b[s], sv);
+    }
+    // the locations this thread read are the ones it writes: no barrier needed
+    stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
+    __syncthreads();
+    stepA_inv<P, V>(
+        u, [&](int q, int t) { return sm[(q * R2 + t) * W + l]; },
+        [&](int t, int r, V v) {
+          const int p = t + R2 * r;
+          if (p < n && ok) col[(long long)p * M2] = v;
+        });
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- pass 4 --
+template <class P>
+__global__ void __launch_bounds__(Geo2<P>::NT) k2_row_inv(const Jobs jobs, long long rows) {
+  using V = float2;
+  constexpr int M = P::M, n = M / 2, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2, PITCH = Geo2<P>::PITCH;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int u = threadIdx.x % P::T, l = threadIdx.x / P::T;
+  V* line = sm + l * PITCH;
+  const long long tpj = (rows + W - 1) / W;
+  for (long long tile = blockIdx.x; tile < tpj * jobs.count; tile += gridDim.x) {
+    const Job& jb = jobs.j[tile / tpj];
+    const long long row = (tile % tpj) * W + l;
+    const bool ok = row < rows;
+    const V* __restrict__ y = static_cast<const V*>(jb.in) + row * M;
+    V* __restrict__ x = static_cast<V*>(jb.out) + row * n;
+    V b[R2];
+#pragma unroll
+    for (int s = 0; s < R2; ++s) b[s] = ok ? y[u + R1 * s] : czero<V>();
+    stepB_inv<P, V>(u, b, [&](int q, int t, V v) { line[q * (R2 + 1) + t] = v; });
+    __syncthreads();
+    stepA_inv<P, V>(
+        u, [&](int q, int t) { return line[q * (R2 + 1) + t]; },
+        [&](int t, int r, V v) {
+          const int p = t + R2 * r;
+          if (p < n && ok) x[p] = v;
+        });
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- pass 5 --
+template <class P>
+__global__ void __launch_bounds__(Geo2<P>::NT) k2_c2r_ax0(const Jobs jobs, long long C) {
+  using V = float2;
+  constexpr int M = P::M, n = M / 2, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int l = threadIdx.x % W, u = threadIdx.x / W;
+  const long long tpj = (C + 2 * W - 1) / (2 * W);
+  for (long long tile = blockIdx.x; tile < tpj * jobs.count; tile += gridDim.x) {
+    const Job& jb = jobs.j[tile / tpj];
+    const V* __restrict__ X = static_cast<const V*>(jb.in);
+    float* __restrict__ phi = static_cast<float*>(jb.out);
+    const long long c = (tile % tpj) * (2 * W) + 2 * l;
+    const bool ok = c < C;
+    // Z[k] = A[k] + i B[k] with A, B Hermitian: rebuild k > n from M - k.
+    V b[R2];
+#pragma unroll
+    for (int s = 0; s < R2; ++s) {
+      const int k = u + R1 * s;
+      V z = czero<V>();
+      if (ok) {
+        const bool lo = k <= n;
+        const long long kk = lo ? k : M - k;
+        const V a = X[kk * C + c], bb = X[kk * C + c + 1];
+        z = lo ? mk(a.x - bb.y, a.y + bb.x) : mk(a.x + bb.y, bb.x - a.y);
+      }
+      b[s] = z;
+    }
+    stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
+    __syncthreads();
+    stepA_inv<P, V>(
+        u, [&](int q, int t) { return sm[(q * R2 + t) * W + l]; },
+        [&](int t, int r, V v) {
+          const int p = t + R2 * r;
+          if (p < n && ok) *reinterpret_cast<V*>(phi + (long long)p * C + c) = v;
+        });
+    __syncthreads();
+  }
+}
+
+}  // namespace fsa

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <set>
@@ -62,6 +63,25 @@ int persistent_grid(const void* func, int threads, int smem, long long tiles) {
 int& autotune_mode() {
   static int mode = 1;
   return mode;
+}
+
+namespace {
+// Chosen generation per (pass, transform length, dtype); 0 = not chosen yet.
+std::atomic<signed char> g_variant[kNumPass][1025][2];
+std::mutex g_tune_mu;
+}  // namespace
+
+int kernel_variant(int pass, int M, fsa_dtype dt) {
+  const int mode = autotune_mode();
+  if (dt == FSA_F64) return 1;
+  if (mode == 2) return 1;
+  if (mode == 3) return 2;
+  const int v = (M >= 0 && M <= 1024) ? g_variant[pass][M][dt].load(std::memory_order_relaxed) : 0;
+  return v ? v : 2;
+}
+
+void set_kernel_variant(int pass, int M, fsa_dtype dt, int variant) {
+  if (M >= 0 && M <= 1024) g_variant[pass][M][dt].store((signed char)variant, std::memory_order_relaxed);
 }
 
 bool supported_n(int n) {
@@ -240,7 +260,7 @@ const char* fsa_status_string(fsa_status s) {
 const char* fsa_last_error(void) { return t_last_error.c_str(); }
 
 fsa_status fsa_autotune_set(int mode) {
-  if (mode != 0 && mode != 1) return set_error(FSA_ERR_INVALID_ARG, "fsa_autotune_set: mode must be 0 or 1");
+  if (mode < 0 || mode > 3) return set_error(FSA_ERR_INVALID_ARG, "fsa_autotune_set: mode must be 0..3");
   autotune_mode() = mode;
   return FSA_OK;
 }
@@ -264,6 +284,8 @@ size_t plan_workspace_bytes(const int* n, fsa_dtype dt) {
 size_t plan_gen_scratch_bytes(const int* n, fsa_dtype dt) {
   return dt == FSA_F64 ? 0 : (size_t)(n[0] + 1) * (n[1] + 1) * (n[2] + 1) * 8;
 }
+
+cudaError_t tune_plan(const fsa_plan* p);
 
 // Argument checks that need no device.  On success *eps_out / *bound_out
 // hold the eps in use and its App. B bound.
@@ -331,8 +353,78 @@ fsa_status plan_create_internal(fsa_plan** out, const double* L, const int* n, f
     cudaGetLastError();
     return cuda_error(e, "fsa_plan_create: cudaMalloc");
   }
+  e = tune_plan(p);
+  if (e != cudaSuccess) {
+    cudaFree(p->spectrum);
+    if (p->ws) cudaFree(p->ws);
+    delete p;
+    cudaGetLastError();
+    return cuda_error(e, "fsa_plan_create: autotune");
+  }
   *out = p;
   return FSA_OK;
+}
+
+// Autotuner: for an FP32 plan, time both kernel generations of each pass on the
+// plan's own workspace (contents irrelevant: the kernels' cost does not depend
+// on the data) and keep the faster for that pass and length.
+cudaError_t tune_plan(const fsa_plan* p) {
+  if (p->dtype != FSA_F32 || !p->ws || autotune_mode() != 1) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const int n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
+  const int Ms[kNumPass] = {2 * n0, 2 * n2, 2 * n1, 2 * n2, 2 * n0};
+  bool need = false;
+  for (int k = 0; k < kNumPass; ++k) need |= g_variant[k][Ms[k]][FSA_F32].load() == 0;
+  if (!need) return cudaSuccess;
+  cudaStream_t s;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  void* X = p->ws;
+  void* Y = (char*)p->ws + p->x_bytes;
+  const long long C = (long long)n1 * n2, rows = (long long)(n0 + 1) * n1;
+  Jobs j{};
+  j.count = 1;
+  auto run = [&](int k) -> cudaError_t {
+    switch (k) {
+      case kR2C: j.j[0] = Job{Y, X, nullptr}; return Passes<float2>::r2c_ax0(Ms[k], j, C, s);
+      case kRowFwd: j.j[0] = Job{X, Y, nullptr}; return Passes<float2>::row_fwd(Ms[k], j, rows, s);
+      case kColMid: j.j[0] = Job{Y, Y, p->spectrum}; return Passes<float2>::col_mid(Ms[k], j, 2 * n2, n0 + 1, s);
+      case kRowInv: j.j[0] = Job{Y, X, nullptr}; return Passes<float2>::row_inv(Ms[k], j, rows, s);
+      default: j.j[0] = Job{X, Y, nullptr}; return Passes<float2>::c2r_ax0(Ms[k], j, C, s);
+    }
+  };
+  for (int k = 0; k < kNumPass && e == cudaSuccess; ++k) {
+    if (g_variant[k][Ms[k]][FSA_F32].load() != 0) continue;
+    float best = 1e30f;
+    int pick = 2;
+    for (int v = 1; v <= 2 && e == cudaSuccess; ++v) {
+      set_kernel_variant(k, Ms[k], FSA_F32, v);
+      e = run(k);  // warm-up
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, s);
+        e = run(k);
+        cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        tmin = std::min(tmin, ms);
+      }
+      if (tmin < best) {
+        best = tmin;
+        pick = v;
+      }
+    }
+    set_kernel_variant(k, Ms[k], FSA_F32, e == cudaSuccess ? pick : 0);
+  }
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  return e;
 }
 
 cudaError_t plan_generate_into(fsa_plan* p, void* scratch, cudaStream_t s) {

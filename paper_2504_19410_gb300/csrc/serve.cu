@@ -58,6 +58,7 @@ struct PlanKey {
 
 struct CachedPlan {
   fsa_plan* plan = nullptr;
+  cudaEvent_t ready = nullptr;  // recorded after generation, on the generating stream
   int refs = 0;
   size_t bytes = 0;
   std::list<PlanKey>::iterator lru;
@@ -100,17 +101,35 @@ struct fsa_server {
 
 namespace {
 
-// Evict idle plans (LRU) until `need` more bytes fit, or nothing idle is left.
-void make_room(fsa_server* s, size_t need) {
+// Evict idle plans (LRU) other than `keep` until `need` more bytes fit, or
+// nothing idle is left.
+void make_room(fsa_server* s, size_t need, const PlanKey& keep) {
   auto it = s->plan_lru.end();
   while (s->held + need > s->budget && it != s->plan_lru.begin()) {
     --it;
     auto pit = s->plans.find(*it);
-    if (pit->second.refs == 0) {
+    if (pit->second.refs == 0 && std::memcmp(&pit->first, &keep, sizeof keep) != 0) {
       s->held -= pit->second.bytes;
       fsa_plan_destroy(pit->second.plan);
+      cudaEventDestroy(pit->second.ready);
       s->plans.erase(pit);
       it = s->plan_lru.erase(it);
+    }
+  }
+}
+
+// Evict the least recently used idle plan other than `keep`, if any.
+void evict_one(fsa_server* s, const PlanKey& keep) {
+  for (auto it = s->plan_lru.end(); it != s->plan_lru.begin();) {
+    --it;
+    auto pit = s->plans.find(*it);
+    if (pit->second.refs == 0 && std::memcmp(&pit->first, &keep, sizeof keep) != 0) {
+      s->held -= pit->second.bytes;
+      fsa_plan_destroy(pit->second.plan);
+      cudaEventDestroy(pit->second.ready);
+      s->plans.erase(pit);
+      s->plan_lru.erase(it);
+      return;
     }
   }
 }
@@ -119,8 +138,7 @@ void make_room(fsa_server* s, size_t need) {
 bool try_admit(fsa_server* s, uint64_t id) {
   Req& q = s->reqs[id];
   const size_t ws = plan_workspace_bytes(q.r.n, q.r.dtype);
-  auto pit = s->plans.find(q.key);
-  const bool hit = pit != s->plans.end();
+  const bool hit = s->plans.count(q.key) != 0;
   size_t plan_bytes = 0, gen_scratch = 0;
   if (!hit) {
     const size_t so = q.r.dtype == FSA_F32 ? 4 : 8;
@@ -128,8 +146,11 @@ bool try_admit(fsa_server* s, uint64_t id) {
     gen_scratch = plan_gen_scratch_bytes(q.r.n, q.r.dtype);
   }
   const size_t need = ws + plan_bytes + gen_scratch;
-  if (s->held + need > s->budget) make_room(s, need);
+  // make_room never evicts this request's own plan, so `hit` stays valid
+  if (s->held + need > s->budget) make_room(s, need, q.key);
+  if ((int)s->plans.size() >= s->o.plan_cache_max && !hit) evict_one(s, q.key);
   if (s->held + need > s->budget && !(s->inflight.empty() && s->held == 0)) return false;
+  auto pit = s->plans.find(q.key);
 
   cudaStream_t stream = s->streams[s->rr++ % s->streams.size()];
   fsa_status status = FSA_OK;
@@ -139,16 +160,21 @@ bool try_admit(fsa_server* s, uint64_t id) {
     status = plan_create_internal(&p, q.r.L, q.r.n, q.r.dtype, q.r.eps, 0.0, false);
     if (status == FSA_OK) {
       void* scratch = nullptr;
+      cudaEvent_t ready = nullptr;
       if (gen_scratch) e = cudaMallocFromPoolAsync(&scratch, gen_scratch, s->pool, stream);
       if (e == cudaSuccess) e = plan_generate_into(p, scratch, stream);
       if (scratch) cudaFreeAsync(scratch, stream);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(ready, stream);
       if (e != cudaSuccess) {
         fsa_plan_destroy(p);
+        if (ready) cudaEventDestroy(ready);
         status = cuda_error(e, "serve: tensor generation");
       } else {
         s->plan_lru.push_front(q.key);
         CachedPlan cp;
         cp.plan = p;
+        cp.ready = ready;
         cp.bytes = plan_bytes;
         cp.lru = s->plan_lru.begin();
         pit = s->plans.emplace(q.key, cp).first;
@@ -172,7 +198,9 @@ bool try_admit(fsa_server* s, uint64_t id) {
     return true;
   }
   fsa_plan* p = pit->second.plan;
-  e = cudaMallocFromPoolAsync(&q.ws, ws, s->pool, stream);
+  // the spectrum may still be generating on another stream
+  e = cudaStreamWaitEvent(stream, pit->second.ready, 0);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&q.ws, ws, s->pool, stream);
   if (e == cudaSuccess) {
     const void* rho[1] = {q.r.rho};
     void* phi[1] = {q.r.phi};
@@ -400,7 +428,10 @@ fsa_status fsa_serve_destroy(fsa_server* s) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
   }
-  for (auto& kv : s->plans) fsa_plan_destroy(kv.second.plan);
+  for (auto& kv : s->plans) {
+    fsa_plan_destroy(kv.second.plan);
+    cudaEventDestroy(kv.second.ready);
+  }
   for (auto ev : s->free_events) cudaEventDestroy(ev);
   if (s->pool) cudaMemPoolDestroy(s->pool);
   cudaSetDevice(prev);

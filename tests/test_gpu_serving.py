@@ -1,0 +1,130 @@
+"""The serving loop and the batched launcher on the GPU.
+
+Serving is continuous batching: requests submitted while others run are
+admitted as slots and HBM free up and overlap on the device.  Each result
+must equal the same request solved alone (fsa_apply on its own plan) bit for
+bit: every request runs the same kernels on its own workspace, and nothing
+is reduced across requests.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2504_19410_gb300 as fsa
+    return fsa
+
+
+def make_requests(seed, count, sizes=(16, 24, 32, 48, 64)):
+    import torch
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        n = int(rng.choice(sizes))
+        nn = (n, n, int(rng.choice(sizes)))
+        dt = "f64" if rng.uniform() < 0.3 else "f32"
+        L = (4.0, 4.0, 2.0 + nn[2] / 16)
+        tdt = torch.float64 if dt == "f64" else torch.float32
+        rho = torch.from_numpy(rng.standard_normal(nn)).to(tdt).cuda()
+        reqs.append((L, nn, dt, rho))
+    return reqs
+
+
+def alone(lib, L, n, dt, rho):
+    import torch
+    p = lib.Plan(L, n, dt, eps=0.0)
+    out = p.apply(rho)
+    torch.cuda.synchronize()
+    p.close()
+    return out
+
+
+def test_served_results_equal_solved_alone(lib):
+    import torch
+    reqs = make_requests(1, 40)
+    want = [alone(lib, *r) for r in reqs]
+    srv = lib.Server(max_inflight=8, streams=4)
+    outs = [torch.full_like(r[3], float("nan")) for r in reqs]
+    tickets = []
+    for k, (L, n, dt, rho) in enumerate(reqs):
+        tickets.append(srv.submit(L, n, dt, rho, outs[k]))
+        if k % 7 == 3:  # let some finish while more arrive
+            srv.wait(tickets[k - 2])
+    hits = 0
+    for k, t in enumerate(tickets):
+        try:
+            tm = srv.wait(t)
+            hits += tm.plan_hit
+            assert tm.done_s >= tm.admit_s >= tm.submit_s
+        except lib.FsaError as e:
+            if "unknown ticket" not in str(e):  # already reported by the early wait
+                raise
+    torch.cuda.synchronize()
+    for k in range(len(reqs)):
+        assert torch.equal(outs[k], want[k]), k
+    st = srv.stats()
+    assert st.completed == len(reqs) and st.failed == 0 and st.inflight == 0
+    assert st.plan_hits > 0
+    srv.close()
+
+
+def test_tight_hbm_budget_admits_in_turn(lib):
+    """With room for about two workspaces the server still completes every
+    request, admitting new ones only as earlier ones free their memory."""
+    import torch
+    reqs = make_requests(2, 12, sizes=(64,))
+    want = [alone(lib, *r) for r in reqs]
+    ws = 6 * 65 * 64 * 64 * 8
+    srv = lib.Server(max_inflight=16, streams=4, hbm_budget_bytes=2 * ws + 3 * 65 ** 3 * 8)
+    outs = [torch.empty_like(r[3]) for r in reqs]
+    tickets = [srv.submit(L, n, dt, rho, outs[k]) for k, (L, n, dt, rho) in enumerate(reqs)]
+    for t in tickets:
+        srv.wait(t)
+    torch.cuda.synchronize()
+    for k in range(len(reqs)):
+        assert torch.equal(outs[k], want[k]), k
+    srv.close()
+
+
+def test_serving_rejects_bad_requests_and_unknown_tickets(lib):
+    import torch
+    from paper_2504_19410_gb300 import capi
+    srv = lib.Server()
+    x = torch.zeros((8, 8, 8), device="cuda")
+    with pytest.raises(capi.FsaError) as ei:
+        srv.submit((1, 1, 1), (8, 8, 10), "f32", x, x)
+    assert ei.value.status == capi.FSA_ERR_INVALID_ARG
+    with pytest.raises(capi.FsaError) as ei:
+        srv.poll(123456789)
+    assert ei.value.status == capi.FSA_ERR_NOT_FOUND
+    srv.close()
+
+
+def test_batched_c4_mix_equals_single(lib):
+    """The C4-style mix (cubic n from {64,...,256}, gamma in {1,4,8}) in one
+    batched call equals each solve alone."""
+    import torch
+    import workloads as W
+    dens = W.batch_requests(seed=2504, count=10, sizes=(64, 96, 128))
+    plans, rhos, singles = [], [], []
+    for d in dens:
+        p = lib.Plan(d.L, d.n, "f32", eps=d.eps)
+        r = torch.from_numpy(d.rho()).float().cuda()
+        singles.append(p.apply(r).clone())
+        plans.append(p)
+        rhos.append(r)
+    outs = [torch.empty_like(r) for r in rhos]
+    lib.apply_batched(plans, rhos, outs)
+    torch.cuda.synchronize()
+    for s, o in zip(singles, outs):
+        assert torch.equal(s, o)
+    for p in plans:
+        p.close()

@@ -72,6 +72,20 @@ class Density:
             out += g.eval(self.L, self.n)
         return out
 
+    def rho_torch(self, dtype=None, device="cuda"):
+        """The same density evaluated with torch on a device (for large
+        request mixes whose host-side evaluation would be slow)."""
+        import torch
+        dtype = dtype or torch.float64
+        out = torch.zeros(self.n, dtype=torch.float64, device=device)
+        ax = [torch.from_numpy(a).to(device) for a in grid_axes(self.L, self.n)]
+        for g in self.terms:
+            e0 = ((ax[0] - g.center[0]) / g.sigma[0]) ** 2
+            e1 = ((ax[1] - g.center[1]) / g.sigma[1]) ** 2
+            e2 = ((ax[2] - g.center[2]) / g.sigma[2]) ** 2
+            out += g.amp * torch.exp(-0.5 * (e0[:, None, None] + e1[None, :, None] + e2[None, None, :]))
+        return out.to(dtype)
+
     def describe(self):
         return {"name": self.name, "L": list(self.L), "n": list(self.n), "eps": self.eps,
                 "terms": [{"amp": g.amp, "center": list(g.center), "sigma": list(g.sigma)}
