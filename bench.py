@@ -158,6 +158,7 @@ def run_ours(args):
     from paper_2504_19410_gb300 import capi
     import workloads as W
 
+    capi.fsa_autotune_set({"auto": 1, "1": 2, "2": 3, "3": 4}[args.kernel_gen])
     d = W.gaussian_sum(seed=2504)  # 8 Gaussians, [-16,16]^3, 256^3, eps = 1
     n = d.n
     rho64 = d.rho()
@@ -208,6 +209,7 @@ def run_ours(args):
             "value": ws * args.steps / (elapsed * 1e-3),
             "ms_per_step": elapsed / args.steps,
             "precomp_ms": precomp_ms,
+            "arithmetic": ["fp32", "fp64", "double-word"][plan.info.arithmetic],
             "pass_ms": dict(zip(PASSES, [round(x, 5) for x in pass_ms])),
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
                          "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": f"of {peak_kind}",
@@ -285,7 +287,8 @@ def run_ours(args):
             line["serving"] = serving
         if "f64" in tiers and main is not tiers["f64"]:
             line["f64"] = {k: tiers["f64"][k] for k in ("value", "ms_per_step", "roofline", "pass_ms", "precomp_ms",
-                                                        "step_roofline_frac_27V_model", "e2e", "clocks")}
+                                                        "step_roofline_frac_27V_model", "e2e", "clocks",
+                                                        "arithmetic")}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -471,6 +474,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tiers", default="f32,f64", help="apply tiers to time; the first FP32 one is the headline")
+    ap.add_argument("--kernel-gen", choices=["auto", "1", "2", "3"], default="auto",
+                    help="auto: autotuned per plan; 1 / 2 / 3: force one kernel generation "
+                         "(FP64: native for 1, double-word otherwise)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serve", action="store_true")

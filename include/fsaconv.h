@@ -88,6 +88,7 @@ typedef struct {
   fsa_dtype dtype;
   int device;
   int generated;            /* 1 once fsa_tensor_generate has been enqueued           */
+  int arithmetic;           /* 0 FP32; FP64 plans: 1 native FP64, 2 double-word       */
   size_t workspace_bytes;   /* device scratch the plan owns                           */
   size_t spectrum_bytes;    /* device bytes of the stored spectrum octant             */
   const void* spectrum;     /* device pointer: (n0+1) x (n1+1) x (n2+1) dtype, C order */
@@ -191,13 +192,18 @@ fsa_status fsa_apply_profiled(const fsa_plan* plan, const void* rho, void* phi, 
 fsa_status fsa_profiler_read(fsa_profiler* prof, double* pass_ms, double* step_ms, int* steps);
 fsa_status fsa_profiler_destroy(fsa_profiler* prof);
 
-/* Kernel selection.  FP32 passes exist in two generations: 1 = Stockham
+/* Kernel selection.  FP32 passes exist in three generations: 1 = Stockham
  * radix-8 (three shared-memory stages per transform), 2 = two register-resident
- * steps M = R1 x R2 (one exchange per transform).  mode 1 (default): each new
- * FP32 plan times both generations for each of its passes on its own workspace
- * at creation and keeps the faster per (pass, length); choices persist for the
- * process.  mode 0: untuned passes use generation 2.  mode 2 / 3: force
- * generation 1 / 2 for every FP32 pass (FP64 always uses generation 1).
+ * steps M = R1 x R2 (one exchange per transform), 3 = generation 2 with the
+ * middle pass prefetching its next tile asynchronously.  mode 1 (default):
+ * each new FP32 plan times every generation for each of its passes on its own
+ * workspace at creation and keeps the fastest per (pass, length); choices
+ * persist for the process.  mode 0: untuned passes use generation 2.
+ * mode 2 / 3 / 4: force generation 1 / 2 / 3 for every FP32 pass.  FP64 plans compute either in native
+ * FP64 or in double-word arithmetic (two floats, 48-bit significand, on the
+ * FP32 pipes; see fsa_plan_info.arithmetic): one choice per grid shape per
+ * process, timed on the first plan of the shape in mode 1, double-word in
+ * mode 0, native in mode 2, double-word in modes 3 and 4.
  * FSA_ERR_INVALID_ARG for other modes.  Not thread-safe against concurrent
  * launches. */
 fsa_status fsa_autotune_set(int mode);

@@ -34,7 +34,8 @@ class PlanOpts(C.Structure):
 class PlanInfo(C.Structure):
     _fields_ = [("n", C.c_int * 3), ("L", C.c_double * 3), ("h", C.c_double * 3), ("eps", C.c_double),
                 ("R0", C.c_double), ("eps_bound", C.c_double), ("dtype", C.c_int), ("device", C.c_int),
-                ("generated", C.c_int), ("workspace_bytes", C.c_size_t), ("spectrum_bytes", C.c_size_t),
+                ("generated", C.c_int), ("arithmetic", C.c_int), ("workspace_bytes", C.c_size_t),
+                ("spectrum_bytes", C.c_size_t),
                 ("spectrum", C.c_void_p)]
 
 

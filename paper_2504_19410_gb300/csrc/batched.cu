@@ -19,9 +19,9 @@ namespace fsa {
 namespace {
 
 struct GroupKey {
-  int n0, n1, n2, dt;
+  int n0, n1, n2, dt, dw;
   bool operator<(const GroupKey& o) const {
-    return std::tie(n0, n1, n2, dt) < std::tie(o.n0, o.n1, o.n2, o.dt);
+    return std::tie(n0, n1, n2, dt, dw) < std::tie(o.n0, o.n1, o.n2, o.dt, o.dw);
   }
 };
 
@@ -70,12 +70,9 @@ cudaError_t launch_group(const std::vector<int>& idx, const fsa_plan* const* pla
     f.push_back(phi[k]);
     X.push_back(p->ws);
     Y.push_back((char*)p->ws + p->x_bytes);
-    S.push_back(p->spectrum);
+    S.push_back(plan_apply_spectrum(p));
   }
-  const int m = (int)idx.size();
-  return p0->dtype == FSA_F32
-             ? group_passes<float2>(p0->n, m, r.data(), f.data(), X.data(), Y.data(), S.data(), s)
-             : group_passes<double2>(p0->n, m, r.data(), f.data(), X.data(), Y.data(), S.data(), s);
+  return run_group(p0, (int)idx.size(), r.data(), f.data(), X.data(), Y.data(), S.data(), s);
 }
 
 }  // namespace
@@ -99,7 +96,7 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
     if (((uintptr_t)rho[k] | (uintptr_t)phi[k]) & 15u)
       return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched: rho and phi must be 16-byte aligned");
     seen.push_back(p);
-    groups[GroupKey{p->n[0], p->n[1], p->n[2], (int)p->dtype}].push_back(k);
+    groups[GroupKey{p->n[0], p->n[1], p->n[2], (int)p->dtype, p->f64_dw}].push_back(k);
   }
   std::sort(seen.begin(), seen.end());
   if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())

@@ -1,0 +1,77 @@
+// Double-word (float-float) arithmetic for the FP64-accuracy tier.
+//
+// GB300 executes FP64 at a small fraction of its FP32 rate, and the FP64 FFT
+// passes are bound by that rate.  A double-word number hi + lo (two floats,
+// |lo| <= ulp(hi)/2) carries 48 significand bits; its operations run on the
+// FP32 pipes.  Building blocks (Joldes, Muller, Popescu, "Tight and rigorous
+// error bounds for basic building blocks of double-word arithmetic", ACM TOMS
+// 44(2), 2017):
+//   TwoSum (Knuth), Fast2Sum (Dekker), 2Prod via FMA;
+//   addition "SloppyDWPlusDW": error bounded by a small multiple of
+//     u^2 (|x| + |y|), u = 2^-24 — the norm-wise bound an FFT's error
+//     analysis uses (a butterfly's error is relative to its inputs' size);
+//   multiplication "DWTimesDW3" (FMA based), relative error <= 4 u^2.
+// Every float operation here goes through __fadd_rn / __fmul_rn / __fmaf_rn
+// so the compiler can neither contract nor reorder it.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace fsa {
+
+struct dw {
+  float hi, lo;
+  __host__ __device__ constexpr dw() : hi(0.f), lo(0.f) {}
+  __host__ __device__ constexpr dw(float h, float l) : hi(h), lo(l) {}
+  // exact split of a double constant or value (rounded to 48 bits)
+  __host__ __device__ constexpr dw(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ constexpr dw(int i) : hi((float)i), lo(0.f) {}
+};
+
+__device__ __forceinline__ dw dw_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return dw(s, e);
+}
+
+__device__ __forceinline__ dw dw_fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return dw(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ dw operator+(dw x, dw y) {
+  const dw s = dw_two_sum(x.hi, y.hi);
+  const float w = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return dw_fast_two_sum(s.hi, w);
+}
+__device__ __forceinline__ dw operator-(dw x) { return dw(-x.hi, -x.lo); }
+__device__ __forceinline__ dw operator-(dw x, dw y) { return x + dw(-y.hi, -y.lo); }
+
+__device__ __forceinline__ dw operator*(dw x, dw y) {
+  const float ch = __fmul_rn(x.hi, y.hi);
+  const float cl1 = __fmaf_rn(x.hi, y.hi, -ch);
+  const float tl0 = __fmul_rn(x.lo, y.lo);
+  const float tl1 = __fmaf_rn(x.hi, y.lo, tl0);
+  const float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
+  return dw_fast_two_sum(ch, __fadd_rn(cl1, cl2));
+}
+
+__device__ __forceinline__ dw dw_from_double(double d) {
+  const float h = __double2float_rn(d);
+  return dw(h, __double2float_rn(d - (double)h));
+}
+__device__ __forceinline__ double dw_to_double(dw x) { return (double)x.hi + (double)x.lo; }
+
+// complex double-word: 16 bytes, like double2
+struct __align__(16) cdw {
+  dw x, y;
+};
+
+__device__ __forceinline__ cdw mk(dw x, dw y) {
+  cdw r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+
+}  // namespace fsa

@@ -17,6 +17,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
+#include "dw.cuh"
 #include "fsa_consts.h"
 
 namespace fsa {
@@ -28,6 +31,40 @@ __device__ __forceinline__ double2 mk(double x, double y) { return make_double2(
 template <typename V> struct RealOf;
 template <> struct RealOf<float2> { using T = float; };
 template <> struct RealOf<double2> { using T = double; };
+template <> struct RealOf<cdw> { using T = dw; };
+
+// Element types at the pass boundaries: T = the real type of rho and phi in
+// HBM, S = the stored spectrum's element type.  The double-word tier reads and
+// writes FP64 arrays and converts at the boundary.
+template <typename V> struct Io;
+template <> struct Io<float2> { using T = float; using S = float; };
+template <> struct Io<double2> { using T = double; using S = double; };
+template <> struct Io<cdw> { using T = double; using S = dw; };
+
+// two consecutive reals of rho as one complex value (a + i b)
+template <typename V> __device__ __forceinline__ V load_pair(const typename Io<V>::T* p) {
+  if constexpr (std::is_same<V, cdw>::value) {
+    const double2 d = *reinterpret_cast<const double2*>(p);
+    return mk(dw_from_double(d.x), dw_from_double(d.y));
+  } else {
+    return *reinterpret_cast<const V*>(p);
+  }
+}
+template <typename V> __device__ __forceinline__ void store_pair(typename Io<V>::T* p, V v) {
+  if constexpr (std::is_same<V, cdw>::value) {
+    *reinterpret_cast<double2*>(p) = make_double2(dw_to_double(v.x), dw_to_double(v.y));
+  } else {
+    *reinterpret_cast<V*>(p) = v;
+  }
+}
+template <typename V> __device__ __forceinline__ typename RealOf<V>::T load_spec(const typename Io<V>::S* p) {
+  if constexpr (std::is_same<V, cdw>::value) {
+    const float2 f = __ldg(reinterpret_cast<const float2*>(p));
+    return dw(f.x, f.y);
+  } else {
+    return __ldg(p);
+  }
+}
 
 template <typename V> __device__ __forceinline__ V czero() { return mk(typename RealOf<V>::T(0), typename RealOf<V>::T(0)); }
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk(a.x + b.x, a.y + b.y); }
@@ -151,17 +188,24 @@ template <> struct PlanFor<1024> { using type = Plan<1024, 8, 8, 4, 4>; };
 // One copy per translation unit that includes this header.
 static __device__ float2 g_tw32[fsa::kTwN];
 static __device__ double2 g_tw64[fsa::kTwN];
+static __device__ fsa::cdw g_twdw[fsa::kTwN];
 
 namespace fsa {
 
 template <typename V> __device__ __forceinline__ const V* tw_table();
 template <> __device__ __forceinline__ const float2* tw_table<float2>() { return g_tw32; }
 template <> __device__ __forceinline__ const double2* tw_table<double2>() { return g_tw64; }
+template <> __device__ __forceinline__ const cdw* tw_table<cdw>() { return g_twdw; }
 
 // exp(-2 pi i e / L) for 0 <= e < L, L | 3072
 template <typename V, int L> __device__ __forceinline__ V twiddle(int e) {
   static_assert(kTwN % L == 0, "length must divide the twiddle table");
-  return __ldg(tw_table<V>() + e * (kTwN / L));
+  if constexpr (std::is_same<V, cdw>::value) {
+    const float4 f = __ldg(reinterpret_cast<const float4*>(tw_table<V>() + e * (kTwN / L)));
+    return mk(dw(f.x, f.y), dw(f.z, f.w));
+  } else {
+    return __ldg(tw_table<V>() + e * (kTwN / L));
+  }
 }
 
 // One Stockham stage S of plan P over a line, with T threads per line and

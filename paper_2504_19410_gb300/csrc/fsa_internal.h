@@ -21,26 +21,36 @@ struct Geometry {
 };
 
 bool supported_n(int n);
-int& autotune_mode();  // fsa_autotune_set: 0 defaults, 1 tune per plan, 2 / 3 force generation 1 / 2
+int& autotune_mode();  // fsa_autotune_set: 0 defaults, 1 tune per plan, 2 / 3 / 4 force generation 1 / 2 / 3
 // Kernel generation used for a pass of length M in a dtype: 1 = Stockham
 // radix-8 (passes.cuh), 2 = two-step register kernels (passes2.cuh, FP32).
 int kernel_variant(int pass, int M, fsa_dtype dt);
 void set_kernel_variant(int pass, int M, fsa_dtype dt, int variant);
 bool supported_M(int M);
 
-// Per-precision launchers (passes_f32.cu / passes_f64.cu).  `M` is the
-// transform length of the pass's axis; every job of a launch shares the grid.
-// Each returns the launch error.
-template <typename V> struct Passes {
-  static cudaError_t prepare(int M);  // shared-memory opt-in and occupancy, current device
-  static Geometry geometry(PassKind k, int M);
-  static cudaError_t r2c_ax0(int M, const Jobs& jobs, long long C, cudaStream_t s);
-  static cudaError_t row_fwd(int M, const Jobs& jobs, long long rows, cudaStream_t s);
-  static cudaError_t col_mid(int M, const Jobs& jobs, int M2, int planes, cudaStream_t s);
-  static cudaError_t row_inv(int M, const Jobs& jobs, long long rows, cudaStream_t s);
-  static cudaError_t c2r_ax0(int M, const Jobs& jobs, long long C, cudaStream_t s);
-  static cudaError_t init_twiddles();  // fills this TU's table on the current device
+// Launchers of one kernel instance (one arithmetic, one transform length M),
+// registered at library load by the instance translation units (inst_*.cu)
+// and looked up at launch.  Every job of a launch shares the grid.
+struct Jobs;
+struct PassFns {
+  cudaError_t (*prepare)() = nullptr;  // shared-memory opt-in on the current device
+  Geometry (*geometry)(PassKind) = nullptr;
+  cudaError_t (*r2c)(const Jobs&, long long C, cudaStream_t) = nullptr;
+  cudaError_t (*rowf)(const Jobs&, long long rows, cudaStream_t) = nullptr;
+  cudaError_t (*colm)(const Jobs&, int M2, int planes, cudaStream_t) = nullptr;
+  cudaError_t (*rowi)(const Jobs&, long long rows, cudaStream_t) = nullptr;
+  cudaError_t (*c2r)(const Jobs&, long long C, cudaStream_t) = nullptr;
 };
+// FP32 generations: 1 Stockham radix-8, 2 two-step register, 3 = 2 with the
+// middle pass prefetching its next tile (cp.async).
+enum Arith { kArithF32G1 = 0, kArithF32G2 = 1, kArithF64 = 2, kArithDW = 3, kArithF32G3 = 4, kNumArith = 5 };
+void register_pass_fns(int arith, int M, PassFns f);
+const PassFns& pass_fns(int arith, int M);  // prepare == nullptr if absent
+void register_twiddle_init(cudaError_t (*init)());
+cudaError_t init_all_twiddles();  // every instance unit's tables, current device
+
+// Resident CTAs per SM for a kernel (cached per function), times the SM count.
+int persistent_grid(const void* func, int threads, int smem, long long tiles);
 
 // The five apply passes for `count` solves sharing the grid n (plan.cu).
 // With ev != nullptr (count <= kMaxJobs), six events are recorded: before the
@@ -50,11 +60,18 @@ cudaError_t group_passes(const int* n, int count, const void* const* rho, void* 
                          void* const* Y, const void* const* S, cudaStream_t s, cudaEvent_t* ev = nullptr);
 cudaError_t plan_apply_passes(const fsa_plan* p, const void* rho, void* phi, cudaStream_t s);
 
+// The five passes for `count` solves of one plan shape in the plan's
+// arithmetic: FP32, native FP64, or double-word for FP64 plans with f64_dw.
+cudaError_t run_group(const fsa_plan* shape, int count, const void* const* rho, void* const* phi,
+                      void* const* X, void* const* Y, const void* const* S, cudaStream_t s,
+                      cudaEvent_t* ev = nullptr);
+// The spectrum the apply kernels read (the double-word copy for f64_dw plans).
+const void* plan_apply_spectrum(const fsa_plan* p);
+// Converts an FP64 octant to double-word pairs (tensor_gen.cu).
+cudaError_t spectrum_to_dw(const double* src, void* dst, size_t count, cudaStream_t s);
+
 // Drop cached batched graphs that refer to a plan (batched.cu).
 void batched_forget_plan(const fsa_plan* p);
-
-// Resident CTAs per SM for a kernel (cached per function), times the SM count.
-int persistent_grid(const void* func, int threads, int smem, long long tiles);
 
 // Tensor generation (tensor_gen.cu), all FP64.
 cudaError_t tensorgen_prepare(int M);
@@ -83,6 +100,8 @@ struct fsa_plan {
   int generated;
   void* spectrum;
   size_t spectrum_bytes;
+  void* spectrum_dw;  // FP64 plans: the spectrum as double-word pairs
+  int f64_dw;         // FP64 plans: 1 = double-word arithmetic, 0 = native FP64
   void* ws;  // X then Y
   size_t ws_bytes;
   size_t x_bytes;

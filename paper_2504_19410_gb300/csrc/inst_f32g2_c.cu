@@ -1,0 +1,10 @@
+// FP32 two-step register apply passes, lengths 512-1024.
+// Compiled as its own translation unit so that the library's kernel
+// instances build in parallel; registers its launchers at library load.
+#include "passes_impl.cuh"
+
+FSA_REGISTER(
+    FSA_REG_V2(512)
+    FSA_REG_V2(768)
+    FSA_REG_V2(1024)
+)

@@ -77,9 +77,8 @@ extern "C" fsa_status fsa_apply_noalloc(const fsa_plan* p, const void* rho, void
     void* f[1] = {phi};
     void* X[1] = {base};
     void* Y[1] = {static_cast<char*>(base) + x_bytes};
-    const void* S[1] = {p->spectrum};
-    e = p->dtype == FSA_F32 ? group_passes<float2>(p->n, 1, r, f, X, Y, S, (cudaStream_t)stream)
-                            : group_passes<double2>(p->n, 1, r, f, X, Y, S, (cudaStream_t)stream);
+    const void* S[1] = {plan_apply_spectrum(p)};
+    e = run_group(p, 1, r, f, X, Y, S, (cudaStream_t)stream);
   }
   if (prev != p->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return cuda_error(e, "fsa_apply_noalloc");

@@ -33,6 +33,7 @@ namespace fsa {
 
 template <typename V> struct TileW { static constexpr int W = 16; };
 template <> struct TileW<double2> { static constexpr int W = 8; };
+template <> struct TileW<cdw> { static constexpr int W = 8; };
 
 // Threads per line: one butterfly of the largest radix per thread, capped so
 // that a CTA has at most 512 threads.
@@ -59,13 +60,13 @@ __global__ void __launch_bounds__(W * T) k_r2c_ax0(const Jobs jobs, long long C)
   const long long tpj = (C + 2 * W - 1) / (2 * W);
   for (long long tile = blockIdx.x; tile < tpj * jobs.count; tile += gridDim.x) {
   const Job& jb = jobs.j[tile / tpj];
-  const R* __restrict__ rho = static_cast<const R*>(jb.in);
+  const typename Io<V>::T* __restrict__ rho = static_cast<const typename Io<V>::T*>(jb.in);
   V* __restrict__ X = static_cast<V*>(jb.out);
   const long long c = (tile % tpj) * (2 * W) + 2 * l;  // first of the two real columns
   const bool ok = c < C;
   SLine<V, W> sl{sm + l};
   auto first = [&](int p) -> V {
-    return (p < n && ok) ? *reinterpret_cast<const V*>(rho + (long long)p * C + c) : czero<V>();
+    return (p < n && ok) ? load_pair<V>(rho + (long long)p * C + c) : czero<V>();
   };
   auto last = [&](int p, V v) { sl.put(p, v); };
   fft_line<P, true, T, V>(t, first, last, sl);
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(W * T) k_col_mid(const Jobs jobs, int M2, int 
   for (long long tile = blockIdx.x; tile < tpj * jobs.count; tile += gridDim.x) {
   const Job& jb = jobs.j[tile / tpj];
   V* __restrict__ Y = static_cast<V*>(jb.out);
-  const R* __restrict__ S = static_cast<const R*>(jb.S);
+  const typename Io<V>::S* __restrict__ S = static_cast<const typename Io<V>::S*>(jb.S);
   const int lt = (int)(tile % tpj);
   const int k0 = lt / tiles_per_plane;
   const int k2 = (lt % tiles_per_plane) * W + l;
@@ -137,13 +138,13 @@ __global__ void __launch_bounds__(W * T) k_col_mid(const Jobs jobs, int M2, int 
   const int n2 = M2 / 2;
   const int p2 = ok ? min(k2, M2 - k2) : 0;
   V* col = Y + (long long)k0 * n * M2 + k2;
-  const R* srow = S + (long long)k0 * (n + 1) * (n2 + 1) + p2;
+  const typename Io<V>::S* srow = S + (long long)k0 * (n + 1) * (n2 + 1) + p2;
   SLine<V, W> sl{sm + l};
   auto first = [&](int p) -> V { return (p < n && ok) ? col[(long long)p * M2] : czero<V>(); };
   auto to_sm = [&](int p, V v) { sl.put(p, v); };
   fft_line<P, true, T, V>(t, first, to_sm, sl);
   auto mul = [&](int p) -> V {
-    const R s = ok ? __ldg(srow + (long long)min(p, M - p) * (n2 + 1)) : R(0);
+    const R s = ok ? load_spec<V>(srow + (long long)min(p, M - p) * (n2 + 1)) : R(0);
     return cscale(sl.get(p), s);
   };
   auto last = [&](int p, V v) {
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(W * T) k_c2r_ax0(const Jobs jobs, long long C)
   for (long long tile = blockIdx.x; tile < tpj * jobs.count; tile += gridDim.x) {
   const Job& jb = jobs.j[tile / tpj];
   const V* __restrict__ X = static_cast<const V*>(jb.in);
-  R* __restrict__ phi = static_cast<R*>(jb.out);
+  typename Io<V>::T* __restrict__ phi = static_cast<typename Io<V>::T*>(jb.out);
   const long long c = (tile % tpj) * (2 * W) + 2 * l;
   const bool ok = c < C;
   SLine<V, W> sl{sm + l};
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(W * T) k_c2r_ax0(const Jobs jobs, long long C)
     return lo ? mk(a.x - b.y, a.y + b.x) : mk(a.x + b.y, b.x - a.y);
   };
   auto last = [&](int p, V v) {
-    if (p < n && ok) *reinterpret_cast<V*>(phi + (long long)p * C + c) = v;
+    if (p < n && ok) store_pair<V>(phi + (long long)p * C + c, v);
   };
   fft_line<P, false, T, V>(t, first, last, sl);
   }

@@ -19,6 +19,9 @@ namespace fsa {
 template <class P> struct Geo2 {
   static constexpr int W = 16;
   static constexpr int NT = W * P::T;
+  // the middle pass asks for two resident CTAs (<= 128 registers) when a CTA
+  // has at most 256 threads
+  static constexpr int MINB_MID = NT <= 256 ? 2 : 1;
   static constexpr int SM_STRIDED = P::M * W * 8;
   static constexpr int PITCH = P::R1 * (P::R2 + 1);
   static constexpr int SM_ROWS = W * PITCH * 8;
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2_row_fwd(const Jobs jobs, long 
 
 // ---------------------------------------------------------------- pass 3 --
 template <class P>
-__global__ void __launch_bounds__(Geo2<P>::NT) k2_col_mid(const Jobs jobs, int M2, int planes) {
+__global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2_col_mid(const Jobs jobs, int M2, int planes) {
   using V = float2;
   constexpr int M = P::M, n = M / 2, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -154,6 +157,102 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2_col_mid(const Jobs jobs, int M
         });
     __syncthreads();
   }
+}
+
+// ----------------------------------------------- pass 3, prefetching form --
+// Async copy of 8 bytes global -> shared; src_bytes = 0 writes zeros instead
+// (pruned or out-of-range elements).
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// The middle pass with step A's inputs of the next tile copied asynchronously
+// into a staging area while the current tile computes.  Each thread stages
+// and later reads only its own elements (t = u + T i, r < RA), so a thread's
+// own cp.async.wait orders the copy before its reads.
+template <class P> struct Stage2 {
+  static constexpr int RA = (P::R1 + 1) / 2;  // loads per step-A sub-transform (the rest is zero padding)
+  static constexpr int SLOTS = P::PA * RA;
+  static constexpr int BYTES = SLOTS * P::T * Geo2<P>::W * 8;
+};
+
+template <class P>
+__global__ void __launch_bounds__(Geo2<P>::NT) k2p_col_mid(const Jobs jobs, int M2, int planes) {
+  using V = float2;
+  constexpr int M = P::M, n = M / 2, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2, T = P::T;
+  constexpr int RA = Stage2<P>::RA;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  V* stg = sm + M * W;  // staging: [slot][u][l]
+  const int l = threadIdx.x % W, u = threadIdx.x / W;
+  const int tiles_per_plane = (M2 + W - 1) / W;
+  const long long tpj = (long long)tiles_per_plane * planes;
+  const long long total = tpj * jobs.count;
+  const int n2 = M2 / 2;
+  auto issue = [&](long long tile) {
+    const Job& jb = jobs.j[tile / tpj];
+    const int lt = (int)(tile % tpj);
+    const int k0 = lt / tiles_per_plane;
+    const int k2 = (lt % tiles_per_plane) * W + l;
+    const bool ok = k2 < M2;
+    const V* col = static_cast<const V*>(jb.out) + (long long)k0 * n * M2 + (ok ? k2 : 0);
+#pragma unroll
+    for (int i = 0; i < P::PA; ++i) {
+#pragma unroll
+      for (int r = 0; r < RA; ++r) {
+        const int t = u + T * i;
+        const int p = t + R2 * r;
+        const bool live = ok && t < R2 && p < n;
+        cp_async8(&stg[((i * RA + r) * T + u) * W + l], live ? col + (long long)p * M2 : col, live ? 8 : 0);
+      }
+    }
+    cp_async_commit();
+  };
+  if (blockIdx.x < total) issue(blockIdx.x);
+  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const Job& jb = jobs.j[tile / tpj];
+    const int lt = (int)(tile % tpj);
+    const int k0 = lt / tiles_per_plane;
+    const int k2 = (lt % tiles_per_plane) * W + l;
+    const bool ok = k2 < M2;
+    V* __restrict__ col = static_cast<V*>(jb.out) + (long long)k0 * n * M2 + k2;
+    const float* __restrict__ srow =
+        static_cast<const float*>(jb.S) + (long long)k0 * (n + 1) * (n2 + 1) + (ok ? min(k2, M2 - k2) : 0);
+    cp_async_wait_all();
+    stepA_fwd<P, V>(
+        u,
+        [&](int t, int r) {
+          const int i = (t - u) / T;
+          return r < RA ? stg[((i * RA + r) * T + u) * W + l] : czero<V>();
+        },
+        [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
+    // this thread's staged elements are consumed: fetch the next tile's
+    if (tile + gridDim.x < total) issue(tile + gridDim.x);
+    __syncthreads();
+    V b[R2];
+#pragma unroll
+    for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
+    rfft<R2, true>(b);
+#pragma unroll
+    for (int s = 0; s < R2; ++s) {
+      const int k1 = u + R1 * s;
+      const float sv = ok ? __ldg(srow + (long long)min(k1, M - k1) * (n2 + 1)) : 0.f;
+      b[s] = cscale(b[s], sv);
+    }
+    stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
+    __syncthreads();
+    stepA_inv<P, V>(
+        u, [&](int q, int t) { return sm[(q * R2 + t) * W + l]; },
+        [&](int t, int r, V v) {
+          const int p = t + R2 * r;
+          if (p < n && ok) col[(long long)p * M2] = v;
+        });
+    __syncthreads();
+  }
+  cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------- pass 4 --

@@ -1,5 +1,5 @@
-// Host-side launchers of the apply passes for one complex type V, included
-// by passes_f32.cu (V = float2) and passes_f64.cu (V = double2).
+// Host-side launchers of the apply-pass kernel instances, included by the
+// instance translation units (inst_*.cu), which register them at load.
 #pragma once
 #include <mutex>
 #include <type_traits>
@@ -87,6 +87,7 @@ template <int M> struct Inst2 {
     set((const void*)k2_col_mid<P>, G::SM_STRIDED);
     set((const void*)k2_row_inv<P>, G::SM_ROWS);
     set((const void*)k2_c2r_ax0<P>, G::SM_STRIDED);
+    set((const void*)k2p_col_mid<P>, G::SM_STRIDED + Stage2<P>::BYTES);
     return e;
   }
   static Geometry geometry(PassKind k) {
@@ -115,6 +116,13 @@ template <int M> struct Inst2 {
                                                                                                   planes);
     return cudaGetLastError();
   }
+  static cudaError_t colm_p(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
+    const long long tiles = (long long)((M2 + W - 1) / W) * planes * jobs.count;
+    constexpr int smem = G::SM_STRIDED + Stage2<P>::BYTES;
+    auto f = k2p_col_mid<P>;
+    f<<<persistent_grid((const void*)f, G::NT, smem, tiles), G::NT, smem, s>>>(jobs, M2, planes);
+    return cudaGetLastError();
+  }
   static cudaError_t rowi(const Jobs& jobs, long long rows, cudaStream_t s) {
     const long long tiles = (rows + W - 1) / W * jobs.count;
     auto f = k2_row_inv<P>;
@@ -132,111 +140,56 @@ template <int M> struct Inst2 {
 
 }  // namespace detail
 
-#define FSA_DISPATCH(M, CALL)                         \
-  switch (M) {                                        \
-    case 8: return detail::Inst<V, 8>::CALL;          \
-    case 12: return detail::Inst<V, 12>::CALL;        \
-    case 16: return detail::Inst<V, 16>::CALL;        \
-    case 24: return detail::Inst<V, 24>::CALL;        \
-    case 32: return detail::Inst<V, 32>::CALL;        \
-    case 48: return detail::Inst<V, 48>::CALL;        \
-    case 64: return detail::Inst<V, 64>::CALL;        \
-    case 96: return detail::Inst<V, 96>::CALL;        \
-    case 128: return detail::Inst<V, 128>::CALL;      \
-    case 192: return detail::Inst<V, 192>::CALL;      \
-    case 256: return detail::Inst<V, 256>::CALL;      \
-    case 384: return detail::Inst<V, 384>::CALL;      \
-    case 512: return detail::Inst<V, 512>::CALL;      \
-    case 768: return detail::Inst<V, 768>::CALL;      \
-    case 1024: return detail::Inst<V, 1024>::CALL;    \
-    default: break;                                   \
-  }
-
-#define FSA_DISPATCH2(M, CALL)                        \
-  switch (M) {                                        \
-    case 8: return detail::Inst2<8>::CALL;            \
-    case 12: return detail::Inst2<12>::CALL;          \
-    case 16: return detail::Inst2<16>::CALL;          \
-    case 24: return detail::Inst2<24>::CALL;          \
-    case 32: return detail::Inst2<32>::CALL;          \
-    case 48: return detail::Inst2<48>::CALL;          \
-    case 64: return detail::Inst2<64>::CALL;          \
-    case 96: return detail::Inst2<96>::CALL;          \
-    case 128: return detail::Inst2<128>::CALL;        \
-    case 192: return detail::Inst2<192>::CALL;        \
-    case 256: return detail::Inst2<256>::CALL;        \
-    case 384: return detail::Inst2<384>::CALL;        \
-    case 512: return detail::Inst2<512>::CALL;        \
-    case 768: return detail::Inst2<768>::CALL;        \
-    case 1024: return detail::Inst2<1024>::CALL;      \
-    default: break;                                   \
-  }
-
-// FP32 has two kernel generations; the variant table (plan.cu) picks one per
-// pass and length.  FP64 has the first generation only.
-#define FSA_PICK(KIND, M, CALL)                                         \
-  if constexpr (std::is_same<V, float2>::value) {                       \
-    if (kernel_variant(KIND, M, FSA_F32) == 2) { FSA_DISPATCH2(M, CALL); } \
-  }                                                                     \
-  FSA_DISPATCH(M, CALL);
-
-template <typename V> cudaError_t Passes<V>::prepare(int M) {
-  if constexpr (std::is_same<V, float2>::value) {
-    cudaError_t e = [&]() -> cudaError_t {
-      FSA_DISPATCH2(M, prepare());
-      return cudaErrorInvalidValue;
-    }();
-    if (e != cudaSuccess) return e;
-  }
-  FSA_DISPATCH(M, prepare());
-  return cudaErrorInvalidValue;
-}
-template <typename V> Geometry Passes<V>::geometry(PassKind k, int M) {
-  FSA_PICK(k, M, geometry(k));
-  return Geometry{};
-}
-template <typename V>
-cudaError_t Passes<V>::r2c_ax0(int M, const Jobs& jobs, long long C, cudaStream_t s) {
-  FSA_PICK(kR2C, M, r2c(jobs, C, s));
-  return cudaErrorInvalidValue;
-}
-template <typename V>
-cudaError_t Passes<V>::row_fwd(int M, const Jobs& jobs, long long rows, cudaStream_t s) {
-  FSA_PICK(kRowFwd, M, rowf(jobs, rows, s));
-  return cudaErrorInvalidValue;
-}
-template <typename V>
-cudaError_t Passes<V>::col_mid(int M, const Jobs& jobs, int M2, int planes, cudaStream_t s) {
-  FSA_PICK(kColMid, M, colm(jobs, M2, planes, s));
-  return cudaErrorInvalidValue;
-}
-template <typename V>
-cudaError_t Passes<V>::row_inv(int M, const Jobs& jobs, long long rows, cudaStream_t s) {
-  FSA_PICK(kRowInv, M, rowi(jobs, rows, s));
-  return cudaErrorInvalidValue;
-}
-template <typename V>
-cudaError_t Passes<V>::c2r_ax0(int M, const Jobs& jobs, long long C, cudaStream_t s) {
-  FSA_PICK(kC2R, M, c2r(jobs, C, s));
-  return cudaErrorInvalidValue;
+// Launchers of one instance as a function table (see fsa_internal.h).
+template <class I> PassFns fns_of() {
+  PassFns f;
+  f.prepare = &I::prepare;
+  f.geometry = &I::geometry;
+  f.r2c = &I::r2c;
+  f.rowf = &I::rowf;
+  f.colm = &I::colm;
+  f.rowi = &I::rowi;
+  f.c2r = &I::c2r;
+  return f;
 }
 
-template <typename V> cudaError_t Passes<V>::init_twiddles() {
+// Fills this translation unit's copies of the twiddle tables on the current
+// device.  Internal linkage on purpose: every unit has its own tables, and an
+// external-linkage (inline) definition would be merged into one by the linker.
+static cudaError_t init_tu_twiddles() {
   std::vector<double> re(kTwN), im(kTwN);
   host_twiddles(re.data(), im.data());
   std::vector<float2> t32(kTwN);
   std::vector<double2> t64(kTwN);
+  std::vector<cdw> tdw(kTwN);
   for (int k = 0; k < kTwN; ++k) {
     t32[k] = make_float2((float)re[k], (float)im[k]);
     t64[k] = make_double2(re[k], im[k]);
+    tdw[k] = cdw{dw(re[k]), dw(im[k])};
   }
   cudaError_t e = cudaMemcpyToSymbol(g_tw32, t32.data(), sizeof(float2) * kTwN);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tw64, t64.data(), sizeof(double2) * kTwN);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_twdw, tdw.data(), sizeof(cdw) * kTwN);
   return e;
 }
 
-#undef FSA_PICK
-#undef FSA_DISPATCH2
-#undef FSA_DISPATCH
-
 }  // namespace fsa
+
+// Registers the instances of one translation unit at library load.
+#define FSA_REGISTER(...)                                                   \
+  namespace {                                                              \
+  struct Registrar {                                                       \
+    Registrar() {                                                          \
+      fsa::register_twiddle_init(&fsa::init_tu_twiddles);                  \
+      __VA_ARGS__                                                          \
+    }                                                                      \
+  } registrar_instance;                                                    \
+  }
+#define FSA_REG_V1(ARITH, V, M) fsa::register_pass_fns(ARITH, M, fsa::fns_of<fsa::detail::Inst<V, M>>());
+#define FSA_REG_V2(M)                                                                 \
+  fsa::register_pass_fns(fsa::kArithF32G2, M, fsa::fns_of<fsa::detail::Inst2<M>>()); \
+  {                                                                                   \
+    fsa::PassFns f3 = fsa::fns_of<fsa::detail::Inst2<M>>();                           \
+    f3.colm = &fsa::detail::Inst2<M>::colm_p;                                         \
+    fsa::register_pass_fns(fsa::kArithF32G3, M, f3);                                  \
+  }

@@ -4,10 +4,13 @@
 #include <cstring>
 #include <atomic>
 #include <map>
+#include <tuple>
+#include <type_traits>
 #include <mutex>
 #include <set>
 #include <string>
 
+#include "dw.cuh"
 #include "fsa_internal.h"
 
 namespace fsa {
@@ -76,6 +79,7 @@ int kernel_variant(int pass, int M, fsa_dtype dt) {
   if (dt == FSA_F64) return 1;
   if (mode == 2) return 1;
   if (mode == 3) return 2;
+  if (mode == 4) return 3;
   const int v = (M >= 0 && M <= 1024) ? g_variant[pass][M][dt].load(std::memory_order_relaxed) : 0;
   return v ? v : 2;
 }
@@ -110,6 +114,42 @@ using namespace fsa;
 namespace fsa {
 
 // The five passes for `count` solves that share the grid n and the dtype V.
+namespace {
+PassFns g_fns[kNumArith][1025];
+cudaError_t (*g_tw_inits[32])() = {};
+int g_ntw = 0;
+}  // namespace
+
+void register_pass_fns(int arith, int M, PassFns f) {
+  if (arith >= 0 && arith < kNumArith && M >= 0 && M <= 1024) g_fns[arith][M] = f;
+}
+
+const PassFns& pass_fns(int arith, int M) {
+  static const PassFns none{};
+  return (arith >= 0 && arith < kNumArith && M >= 0 && M <= 1024) ? g_fns[arith][M] : none;
+}
+
+void register_twiddle_init(cudaError_t (*init)()) {
+  if (g_ntw < 32) g_tw_inits[g_ntw++] = init;
+}
+
+cudaError_t init_all_twiddles() {
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < g_ntw && e == cudaSuccess; ++i) e = g_tw_inits[i]();
+  return e;
+}
+
+template <typename V> int arith_for(int pass, int M) {
+  if constexpr (std::is_same<V, float2>::value) {
+    const int v = kernel_variant(pass, M, FSA_F32);
+    return v == 3 ? kArithF32G3 : (v == 2 ? kArithF32G2 : kArithF32G1);
+  }
+  else if constexpr (std::is_same<V, double2>::value)
+    return kArithF64;
+  else
+    return kArithDW;
+}
+
 template <typename V>
 cudaError_t group_passes(const int* n, int count, const void* const* rho, void* const* phi, void* const* X,
                          void* const* Y, const void* const* S, cudaStream_t s, cudaEvent_t* ev) {
@@ -133,15 +173,21 @@ cudaError_t group_passes(const int* n, int count, const void* const* rho, void* 
       if (ev && e == cudaSuccess) e = cudaEventRecord(ev[i], s);
     };
     mark(0);
-    e = e == cudaSuccess ? Passes<V>::r2c_ax0(2 * n0, j1, C, s) : e;
+    const PassFns& f1 = pass_fns(arith_for<V>(kR2C, 2 * n0), 2 * n0);
+    const PassFns& f2 = pass_fns(arith_for<V>(kRowFwd, 2 * n2), 2 * n2);
+    const PassFns& f3 = pass_fns(arith_for<V>(kColMid, 2 * n1), 2 * n1);
+    const PassFns& f4 = pass_fns(arith_for<V>(kRowInv, 2 * n2), 2 * n2);
+    const PassFns& f5 = pass_fns(arith_for<V>(kC2R, 2 * n0), 2 * n0);
+    if (!f1.r2c || !f2.rowf || !f3.colm || !f4.rowi || !f5.c2r) return cudaErrorInvalidValue;
+    e = e == cudaSuccess ? f1.r2c(j1, C, s) : e;
     mark(1);
-    if (e == cudaSuccess) e = Passes<V>::row_fwd(2 * n2, j2, rows, s);
+    if (e == cudaSuccess) e = f2.rowf(j2, rows, s);
     mark(2);
-    if (e == cudaSuccess) e = Passes<V>::col_mid(2 * n1, j3, 2 * n2, n0 + 1, s);
+    if (e == cudaSuccess) e = f3.colm(j3, 2 * n2, n0 + 1, s);
     mark(3);
-    if (e == cudaSuccess) e = Passes<V>::row_inv(2 * n2, j4, rows, s);
+    if (e == cudaSuccess) e = f4.rowi(j4, rows, s);
     mark(4);
-    if (e == cudaSuccess) e = Passes<V>::c2r_ax0(2 * n0, j5, C, s);
+    if (e == cudaSuccess) e = f5.c2r(j5, C, s);
     mark(5);
   }
   return e;
@@ -150,6 +196,17 @@ template cudaError_t group_passes<float2>(const int*, int, const void* const*, v
                                           void* const*, const void* const*, cudaStream_t, cudaEvent_t*);
 template cudaError_t group_passes<double2>(const int*, int, const void* const*, void* const*, void* const*,
                                            void* const*, const void* const*, cudaStream_t, cudaEvent_t*);
+template cudaError_t group_passes<cdw>(const int*, int, const void* const*, void* const*, void* const*,
+                                       void* const*, const void* const*, cudaStream_t, cudaEvent_t*);
+
+cudaError_t run_group(const fsa_plan* shape, int count, const void* const* rho, void* const* phi, void* const* X,
+                      void* const* Y, const void* const* S, cudaStream_t s, cudaEvent_t* ev) {
+  if (shape->dtype == FSA_F32) return group_passes<float2>(shape->n, count, rho, phi, X, Y, S, s, ev);
+  if (shape->f64_dw) return group_passes<cdw>(shape->n, count, rho, phi, X, Y, S, s, ev);
+  return group_passes<double2>(shape->n, count, rho, phi, X, Y, S, s, ev);
+}
+
+const void* plan_apply_spectrum(const fsa_plan* p) { return p->f64_dw ? p->spectrum_dw : p->spectrum; }
 
 }  // namespace fsa
 
@@ -184,8 +241,7 @@ struct DeviceGuard {
 fsa_status prepare_device(int dev, fsa_dtype dt, const int* n) {
   std::lock_guard<std::mutex> lk(g_init_mu);
   if (!g_tw_ready.count(dev)) {
-    cudaError_t e = Passes<float2>::init_twiddles();
-    if (e == cudaSuccess) e = Passes<double2>::init_twiddles();
+    cudaError_t e = init_all_twiddles();
     if (e == cudaSuccess) e = tensorgen_init_twiddles();
     if (e != cudaSuccess) return cuda_error(e, "twiddle table upload");
     g_tw_ready.insert(dev);
@@ -194,7 +250,14 @@ fsa_status prepare_device(int dev, fsa_dtype dt, const int* n) {
     const int M = 2 * n[j];
     const int key = M * 4 + (int)dt;
     if (g_prepared.count({dev, key})) continue;
-    cudaError_t e = (dt == FSA_F32) ? Passes<float2>::prepare(M) : Passes<double2>::prepare(M);
+    cudaError_t e = cudaSuccess;
+    const int f32a[3] = {kArithF32G1, kArithF32G2, kArithF32G3};
+    const int f64a[3] = {kArithF64, kArithDW, kArithDW};
+    for (int a : (dt == FSA_F32 ? f32a : f64a)) {
+      const PassFns& f = pass_fns(a, M);
+      if (!f.prepare) return set_error(FSA_ERR_UNSUPPORTED, "no kernels registered for this length");
+      if (e == cudaSuccess) e = f.prepare();
+    }
     if (e == cudaSuccess) e = tensorgen_prepare(M);
     if (e != cudaSuccess) return cuda_error(e, "kernel shared-memory opt-in");
     g_prepared.insert({dev, key});
@@ -202,14 +265,13 @@ fsa_status prepare_device(int dev, fsa_dtype dt, const int* n) {
   return FSA_OK;
 }
 
-template <typename V>
 cudaError_t apply_passes(const fsa_plan* p, const void* rho, void* phi, void* X, void* Y, cudaStream_t s) {
   const void* rhos[1] = {rho};
   void* phis[1] = {phi};
   void* xs[1] = {X};
   void* ys[1] = {Y};
-  const void* ss[1] = {p->spectrum};
-  return group_passes<V>(p->n, 1, rhos, phis, xs, ys, ss, s, nullptr);
+  const void* ss[1] = {plan_apply_spectrum(p)};
+  return run_group(p, 1, rhos, phis, xs, ys, ss, s, nullptr);
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -221,8 +283,7 @@ namespace fsa {
 cudaError_t plan_apply_passes(const fsa_plan* p, const void* rho, void* phi, cudaStream_t s) {
   void* X = p->ws;
   void* Y = (char*)p->ws + p->x_bytes;
-  return p->dtype == FSA_F32 ? apply_passes<float2>(p, rho, phi, X, Y, s)
-                             : apply_passes<double2>(p, rho, phi, X, Y, s);
+  return apply_passes(p, rho, phi, X, Y, s);
 }
 
 // The same with an event before the first pass and after each pass.
@@ -232,9 +293,8 @@ cudaError_t plan_apply_passes_events(const fsa_plan* p, const void* rho, void* p
   void* phis[1] = {phi};
   void* xs[1] = {p->ws};
   void* ys[1] = {(char*)p->ws + p->x_bytes};
-  const void* ss[1] = {p->spectrum};
-  return p->dtype == FSA_F32 ? group_passes<float2>(p->n, 1, rhos, phis, xs, ys, ss, s, ev6)
-                             : group_passes<double2>(p->n, 1, rhos, phis, xs, ys, ss, s, ev6);
+  const void* ss[1] = {plan_apply_spectrum(p)};
+  return run_group(p, 1, rhos, phis, xs, ys, ss, s, ev6);
 }
 }  // namespace fsa
 
@@ -260,7 +320,7 @@ const char* fsa_status_string(fsa_status s) {
 const char* fsa_last_error(void) { return t_last_error.c_str(); }
 
 fsa_status fsa_autotune_set(int mode) {
-  if (mode < 0 || mode > 3) return set_error(FSA_ERR_INVALID_ARG, "fsa_autotune_set: mode must be 0..3");
+  if (mode < 0 || mode > 4) return set_error(FSA_ERR_INVALID_ARG, "fsa_autotune_set: mode must be 0..4");
   autotune_mode() = mode;
   return FSA_OK;
 }
@@ -285,7 +345,7 @@ size_t plan_gen_scratch_bytes(const int* n, fsa_dtype dt) {
   return dt == FSA_F64 ? 0 : (size_t)(n[0] + 1) * (n[1] + 1) * (n[2] + 1) * 8;
 }
 
-cudaError_t tune_plan(const fsa_plan* p);
+cudaError_t tune_plan(fsa_plan* p);
 
 // Argument checks that need no device.  On success *eps_out / *bound_out
 // hold the eps in use and its App. B bound.
@@ -346,9 +406,11 @@ fsa_status plan_create_internal(fsa_plan** out, const double* L, const int* n, f
   p->ws_bytes = with_workspace ? plan_workspace_bytes(n, dtype) : 0;
   // The workspace always holds the FP64 generation scratch of an FP32 plan.
   e = cudaMalloc(&p->spectrum, p->spectrum_bytes);
+  if (e == cudaSuccess && dtype == FSA_F64) e = cudaMalloc(&p->spectrum_dw, p->spectrum_bytes);
   if (e == cudaSuccess && with_workspace) e = cudaMalloc(&p->ws, p->ws_bytes);
   if (e != cudaSuccess) {
     if (p->spectrum) cudaFree(p->spectrum);
+    if (p->spectrum_dw) cudaFree(p->spectrum_dw);
     delete p;
     cudaGetLastError();
     return cuda_error(e, "fsa_plan_create: cudaMalloc");
@@ -356,6 +418,7 @@ fsa_status plan_create_internal(fsa_plan** out, const double* L, const int* n, f
   e = tune_plan(p);
   if (e != cudaSuccess) {
     cudaFree(p->spectrum);
+    if (p->spectrum_dw) cudaFree(p->spectrum_dw);
     if (p->ws) cudaFree(p->ws);
     delete p;
     cudaGetLastError();
@@ -368,8 +431,11 @@ fsa_status plan_create_internal(fsa_plan** out, const double* L, const int* n, f
 // Autotuner: for an FP32 plan, time both kernel generations of each pass on the
 // plan's own workspace (contents irrelevant: the kernels' cost does not depend
 // on the data) and keep the faster for that pass and length.
-cudaError_t tune_plan(const fsa_plan* p) {
-  if (p->dtype != FSA_F32 || !p->ws || autotune_mode() != 1) return cudaSuccess;
+cudaError_t tune_f64(fsa_plan* p);
+
+cudaError_t tune_plan(fsa_plan* p) {
+  if (p->dtype == FSA_F64) return tune_f64(p);
+  if (!p->ws || autotune_mode() != 1) return cudaSuccess;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   const int n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
   const int Ms[kNumPass] = {2 * n0, 2 * n2, 2 * n1, 2 * n2, 2 * n0};
@@ -387,26 +453,26 @@ cudaError_t tune_plan(const fsa_plan* p) {
   const long long C = (long long)n1 * n2, rows = (long long)(n0 + 1) * n1;
   Jobs j{};
   j.count = 1;
-  auto run = [&](int k) -> cudaError_t {
+  auto run = [&](int k, int v) -> cudaError_t {
+    const PassFns& f = pass_fns(v == 3 ? kArithF32G3 : (v == 2 ? kArithF32G2 : kArithF32G1), Ms[k]);
     switch (k) {
-      case kR2C: j.j[0] = Job{Y, X, nullptr}; return Passes<float2>::r2c_ax0(Ms[k], j, C, s);
-      case kRowFwd: j.j[0] = Job{X, Y, nullptr}; return Passes<float2>::row_fwd(Ms[k], j, rows, s);
-      case kColMid: j.j[0] = Job{Y, Y, p->spectrum}; return Passes<float2>::col_mid(Ms[k], j, 2 * n2, n0 + 1, s);
-      case kRowInv: j.j[0] = Job{Y, X, nullptr}; return Passes<float2>::row_inv(Ms[k], j, rows, s);
-      default: j.j[0] = Job{X, Y, nullptr}; return Passes<float2>::c2r_ax0(Ms[k], j, C, s);
+      case kR2C: j.j[0] = Job{Y, X, nullptr}; return f.r2c(j, C, s);
+      case kRowFwd: j.j[0] = Job{X, Y, nullptr}; return f.rowf(j, rows, s);
+      case kColMid: j.j[0] = Job{Y, Y, p->spectrum}; return f.colm(j, 2 * n2, n0 + 1, s);
+      case kRowInv: j.j[0] = Job{Y, X, nullptr}; return f.rowi(j, rows, s);
+      default: j.j[0] = Job{X, Y, nullptr}; return f.c2r(j, C, s);
     }
   };
   for (int k = 0; k < kNumPass && e == cudaSuccess; ++k) {
     if (g_variant[k][Ms[k]][FSA_F32].load() != 0) continue;
     float best = 1e30f;
     int pick = 2;
-    for (int v = 1; v <= 2 && e == cudaSuccess; ++v) {
-      set_kernel_variant(k, Ms[k], FSA_F32, v);
-      e = run(k);  // warm-up
+    for (int v = 1; v <= 3 && e == cudaSuccess; ++v) {
+      e = run(k, v);  // warm-up
       float tmin = 1e30f;
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
         cudaEventRecord(e0, s);
-        e = run(k);
+        e = run(k, v);
         cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0;
@@ -427,9 +493,65 @@ cudaError_t tune_plan(const fsa_plan* p) {
   return e;
 }
 
+// FP64 plans: native FP64 or double-word arithmetic, one choice per grid
+// shape for the whole process (every plan of a shape computes alike, so
+// batched and served results equal single ones).  Mode 1 times one whole
+// apply each way on the first plan of a shape; mode 0 takes double-word;
+// mode 2 / 3 force native / double-word.
+cudaError_t tune_f64(fsa_plan* p) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, int> choice;
+  const int mode = autotune_mode();
+  if (mode >= 2) {
+    p->f64_dw = mode >= 3;
+    return cudaSuccess;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_tuple(p->n[0], p->n[1], p->n[2]);
+  auto it = choice.find(key);
+  if (it != choice.end()) {
+    p->f64_dw = it->second;
+    return cudaSuccess;
+  }
+  if (mode != 1 || !p->ws) {
+    p->f64_dw = 1;
+    return cudaSuccess;
+  }
+  cudaStream_t s;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  void* X = p->ws;
+  void* Y = (char*)p->ws + p->x_bytes;
+  float best[2] = {1e30f, 1e30f};
+  for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    p->f64_dw = v;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      cudaEventRecord(e0, s);
+      e = apply_passes(p, Y, Y, X, Y, s);
+      cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) best[v] = std::min(best[v], ms);
+    }
+  }
+  p->f64_dw = best[1] <= best[0] ? 1 : 0;
+  if (e == cudaSuccess) choice[key] = p->f64_dw;
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  return e;
+}
+
 cudaError_t plan_generate_into(fsa_plan* p, void* scratch, cudaStream_t s) {
   double* oct = p->dtype == FSA_F64 ? (double*)p->spectrum : (double*)scratch;
   cudaError_t e = tensorgen_run(p->n, p->L, p->eps, oct, p->spectrum, p->dtype, s);
+  if (e == cudaSuccess && p->spectrum_dw)
+    e = spectrum_to_dw((const double*)p->spectrum, p->spectrum_dw, p->spectrum_bytes / 8, s);
   if (e == cudaSuccess) p->generated = 1;
   return e;
 }
@@ -463,7 +585,8 @@ fsa_status fsa_plan_destroy(fsa_plan* p) {
   DeviceGuard dg;
   dg.set(p->device);
   cudaFree(p->spectrum);
-  cudaFree(p->ws);
+  if (p->spectrum_dw) cudaFree(p->spectrum_dw);
+  if (p->ws) cudaFree(p->ws);
   delete p;
   return FSA_OK;
 }
@@ -492,6 +615,7 @@ fsa_status fsa_plan_info_get(const fsa_plan* p, fsa_plan_info* info) {
   info->dtype = p->dtype;
   info->device = p->device;
   info->generated = p->generated;
+  info->arithmetic = p->dtype == FSA_F32 ? 0 : (p->f64_dw ? 2 : 1);
   info->workspace_bytes = p->ws_bytes;
   info->spectrum_bytes = p->spectrum_bytes;
   info->spectrum = p->spectrum;
@@ -537,7 +661,7 @@ fsa_status fsa_apply_host(const fsa_plan* p, const void* rho_host, void* phi_hos
   cudaStream_t s = (cudaStream_t)stream;
   if (e == cudaSuccess) e = cudaMemcpyAsync(Y, rho_host, vbytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = p->dtype == FSA_F32 ? apply_passes<float2>(p, Y, Y, X, Y, s) : apply_passes<double2>(p, Y, Y, X, Y, s);
+    e = apply_passes(p, Y, Y, X, Y, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(phi_host, Y, vbytes, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_error(e, "fsa_apply_host");
   return FSA_OK;

@@ -158,6 +158,8 @@ bool try_admit(fsa_server* s, uint64_t id) {
   if (!hit) {
     fsa_plan* p = nullptr;
     status = plan_create_internal(&p, q.r.L, q.r.n, q.r.dtype, q.r.eps, 0.0, false);
+    // server plans have no workspace of their own; FP64 arithmetic follows the
+    // per-shape choice made by earlier plans (double-word by default)
     if (status == FSA_OK) {
       void* scratch = nullptr;
       cudaEvent_t ready = nullptr;
@@ -207,9 +209,8 @@ bool try_admit(fsa_server* s, uint64_t id) {
     void* X[1] = {q.ws};
     const size_t xb = (size_t)(q.r.n[0] + 1) * q.r.n[1] * q.r.n[2] * 2 * (q.r.dtype == FSA_F32 ? 4 : 8);
     void* Y[1] = {(char*)q.ws + xb};
-    const void* S[1] = {p->spectrum};
-    e = q.r.dtype == FSA_F32 ? group_passes<float2>(q.r.n, 1, rho, phi, X, Y, S, stream)
-                             : group_passes<double2>(q.r.n, 1, rho, phi, X, Y, S, stream);
+    const void* S[1] = {plan_apply_spectrum(p)};
+    e = run_group(p, 1, rho, phi, X, Y, S, stream);
     cudaFreeAsync(q.ws, stream);
   }
   if (e == cudaSuccess) {

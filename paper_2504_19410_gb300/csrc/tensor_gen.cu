@@ -58,6 +58,21 @@ __global__ void k_spectrum_finalize(const double* S1, R* S,  // may alias (FP64 
   }
 }
 
+__global__ void k_to_dw(const double* __restrict__ src, float2* __restrict__ dst, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const dw v = dw_from_double(src[i]);
+    dst[i] = make_float2(v.hi, v.lo);
+  }
+}
+
+cudaError_t spectrum_to_dw(const double* src, void* dst, size_t count, cudaStream_t s) {
+  const int threads = 256;
+  const int blocks = (int)std::min<long long>(((long long)count + threads - 1) / threads, 152LL * 16);
+  k_to_dw<<<blocks, threads, 0, s>>>(src, (float2*)dst, (long long)count);
+  return cudaGetLastError();
+}
+
 namespace {
 
 template <int M> struct DctInst {
