@@ -22,6 +22,9 @@ template <class P> struct Geo2 {
   // the middle pass asks for two resident CTAs (<= 128 registers) when a CTA
   // has at most 256 threads
   static constexpr int MINB_MID = NT <= 256 ? 2 : 1;
+  // the R2C pass holds fewer live values: three resident CTAs when small
+  // (measured faster; the row passes and C2R measured slower so capped)
+  static constexpr int MINB = NT <= 256 ? 3 : 1;
   static constexpr int SM_STRIDED = P::M * W * 8;
   static constexpr int PITCH = P::R1 * (P::R2 + 1);
   static constexpr int SM_ROWS = W * PITCH * 8;
@@ -29,7 +32,7 @@ template <class P> struct Geo2 {
 
 // ---------------------------------------------------------------- pass 1 --
 template <class P>
-__global__ void __launch_bounds__(Geo2<P>::NT) k2_r2c_ax0(const Jobs jobs, long long C) {
+__global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB) k2_r2c_ax0(const Jobs jobs, long long C) {
   using V = float2;
   constexpr int M = P::M, n = M / 2, K = n + 1, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -180,7 +183,7 @@ template <class P> struct Stage2 {
 };
 
 template <class P>
-__global__ void __launch_bounds__(Geo2<P>::NT) k2p_col_mid(const Jobs jobs, int M2, int planes) {
+__global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2p_col_mid(const Jobs jobs, int M2, int planes) {
   using V = float2;
   constexpr int M = P::M, n = M / 2, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2, T = P::T;
   constexpr int RA = Stage2<P>::RA;
@@ -249,6 +252,124 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2p_col_mid(const Jobs jobs, int 
         [&](int t, int r, V v) {
           const int p = t + R2 * r;
           if (p < n && ok) col[(long long)p * M2] = v;
+        });
+    __syncthreads();
+  }
+  cp_async_wait_all();
+}
+
+// ------------------------------------------ row passes, prefetching form --
+// WR rows per CTA, lanes on the R1 threads of a row.  Step A (forward) or
+// step B (inverse) inputs of the next tile are copied asynchronously into a
+// per-thread staging area while the current tile computes.
+template <class P, int WR> struct RowGeo {
+  static constexpr int NT = WR * P::T;
+  static constexpr int PITCH = P::R1 * (P::R2 + 1);
+  static constexpr int RA = (P::R1 + 1) / 2;
+  static constexpr int XCH = WR * PITCH * 8;                      // exchange tile
+  static constexpr int STG_FWD = P::PA * RA * P::T * WR * 8;      // step-A inputs
+  static constexpr int STG_INV = P::R2 * P::T * WR * 8;           // step-B inputs
+  static constexpr int SM_FWD = XCH + STG_FWD;
+  static constexpr int SM_INV = XCH + STG_INV;
+};
+
+template <class P, int WR>
+__global__ void __launch_bounds__(RowGeo<P, WR>::NT) k2p_row_fwd(const Jobs jobs, long long rows) {
+  using V = float2;
+  using G = RowGeo<P, WR>;
+  constexpr int M = P::M, n = M / 2, R1 = P::R1, R2 = P::R2, T = P::T, RA = G::RA;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  V* stg = sm + WR * G::PITCH;  // [slot][l][u]
+  const int u = threadIdx.x % T, l = threadIdx.x / T;
+  V* line = sm + l * G::PITCH;
+  const long long tpj = (rows + WR - 1) / WR;
+  const long long total = tpj * jobs.count;
+  auto issue = [&](long long tile) {
+    const Job& jb = jobs.j[tile / tpj];
+    const long long row = (tile % tpj) * WR + l;
+    const bool ok = row < rows;
+    const V* x = static_cast<const V*>(jb.in) + (ok ? row : 0) * n;
+#pragma unroll
+    for (int i = 0; i < P::PA; ++i) {
+#pragma unroll
+      for (int r = 0; r < RA; ++r) {
+        const int t = u + T * i;
+        const int p = t + R2 * r;
+        const bool live = ok && t < R2 && p < n;
+        cp_async8(&stg[((i * RA + r) * WR + l) * T + u], live ? x + p : x, live ? 8 : 0);
+      }
+    }
+    cp_async_commit();
+  };
+  if (blockIdx.x < total) issue(blockIdx.x);
+  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const Job& jb = jobs.j[tile / tpj];
+    const long long row = (tile % tpj) * WR + l;
+    const bool ok = row < rows;
+    V* __restrict__ y = static_cast<V*>(jb.out) + row * M;
+    cp_async_wait_all();
+    stepA_fwd<P, V>(
+        u,
+        [&](int t, int r) {
+          const int i = (t - u) / T;
+          return r < RA ? stg[((i * RA + r) * WR + l) * T + u] : czero<V>();
+        },
+        [&](int q, int t, V v) { line[q * (R2 + 1) + t] = v; });
+    if (tile + gridDim.x < total) issue(tile + gridDim.x);
+    __syncthreads();
+    V b[R2];
+#pragma unroll
+    for (int t = 0; t < R2; ++t) b[t] = line[u * (R2 + 1) + t];
+    rfft<R2, true>(b);
+    if (ok) {
+#pragma unroll
+      for (int s = 0; s < R2; ++s) y[u + R1 * s] = b[s];
+    }
+    __syncthreads();
+  }
+  cp_async_wait_all();
+}
+
+template <class P, int WR>
+__global__ void __launch_bounds__(RowGeo<P, WR>::NT) k2p_row_inv(const Jobs jobs, long long rows) {
+  using V = float2;
+  using G = RowGeo<P, WR>;
+  constexpr int M = P::M, n = M / 2, R1 = P::R1, R2 = P::R2, T = P::T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  V* stg = sm + WR * G::PITCH;  // [s][l][u]
+  const int u = threadIdx.x % T, l = threadIdx.x / T;
+  V* line = sm + l * G::PITCH;
+  const long long tpj = (rows + WR - 1) / WR;
+  const long long total = tpj * jobs.count;
+  auto issue = [&](long long tile) {
+    const Job& jb = jobs.j[tile / tpj];
+    const long long row = (tile % tpj) * WR + l;
+    const bool ok = row < rows;
+    const V* y = static_cast<const V*>(jb.in) + (ok ? row : 0) * M;
+#pragma unroll
+    for (int s = 0; s < R2; ++s) cp_async8(&stg[(s * WR + l) * T + u], y + u + R1 * s, ok ? 8 : 0);
+    cp_async_commit();
+  };
+  if (blockIdx.x < total) issue(blockIdx.x);
+  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const Job& jb = jobs.j[tile / tpj];
+    const long long row = (tile % tpj) * WR + l;
+    const bool ok = row < rows;
+    V* __restrict__ x = static_cast<V*>(jb.out) + row * n;
+    cp_async_wait_all();
+    V b[R2];
+#pragma unroll
+    for (int s = 0; s < R2; ++s) b[s] = stg[(s * WR + l) * T + u];
+    if (tile + gridDim.x < total) issue(tile + gridDim.x);
+    stepB_inv<P, V>(u, b, [&](int q, int t, V v) { line[q * (R2 + 1) + t] = v; });
+    __syncthreads();
+    stepA_inv<P, V>(
+        u, [&](int q, int t) { return line[q * (R2 + 1) + t]; },
+        [&](int t, int r, V v) {
+          const int p = t + R2 * r;
+          if (p < n && ok) x[p] = v;
         });
     __syncthreads();
   }

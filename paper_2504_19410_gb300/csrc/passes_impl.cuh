@@ -88,7 +88,23 @@ template <int M> struct Inst2 {
     set((const void*)k2_row_inv<P>, G::SM_ROWS);
     set((const void*)k2_c2r_ax0<P>, G::SM_STRIDED);
     set((const void*)k2p_col_mid<P>, G::SM_STRIDED + Stage2<P>::BYTES);
+    set((const void*)k2p_row_fwd<P, 16>, RowGeo<P, 16>::SM_FWD);
+    set((const void*)k2p_row_inv<P, 8>, RowGeo<P, 8>::SM_INV);
     return e;
+  }
+  static cudaError_t rowf_p(const Jobs& jobs, long long rows, cudaStream_t s) {
+    using RG = RowGeo<P, 16>;
+    const long long tiles = (rows + 15) / 16 * jobs.count;
+    auto f = k2p_row_fwd<P, 16>;
+    f<<<persistent_grid((const void*)f, RG::NT, RG::SM_FWD, tiles), RG::NT, RG::SM_FWD, s>>>(jobs, rows);
+    return cudaGetLastError();
+  }
+  static cudaError_t rowi_p(const Jobs& jobs, long long rows, cudaStream_t s) {
+    using RG = RowGeo<P, 8>;
+    const long long tiles = (rows + 7) / 8 * jobs.count;
+    auto f = k2p_row_inv<P, 8>;
+    f<<<persistent_grid((const void*)f, RG::NT, RG::SM_INV, tiles), RG::NT, RG::SM_INV, s>>>(jobs, rows);
+    return cudaGetLastError();
   }
   static Geometry geometry(PassKind k) {
     Geometry g;
@@ -191,5 +207,7 @@ static cudaError_t init_tu_twiddles() {
   {                                                                                   \
     fsa::PassFns f3 = fsa::fns_of<fsa::detail::Inst2<M>>();                           \
     f3.colm = &fsa::detail::Inst2<M>::colm_p;                                         \
+    f3.rowf = &fsa::detail::Inst2<M>::rowf_p;                                         \
+    f3.rowi = &fsa::detail::Inst2<M>::rowi_p;                                         \
     fsa::register_pass_fns(fsa::kArithF32G3, M, f3);                                  \
   }
