@@ -181,7 +181,7 @@ def run_ours(args):
         tdt = torch.float32 if dt == "f32" else torch.float64
         s = 4 if dt == "f32" else 8
         t0 = time.perf_counter()
-        plan = fsa.Plan(d.L, n, dt, eps=d.eps, generate=False)  # includes the autotuner's trials
+        plan = fsa.Plan(d.L, n, dt, eps=d.eps, generate=False, l2_chunk_mb=args.l2_chunk_mb)  # + autotuner trials
         torch.cuda.synchronize()
         create_ms = (time.perf_counter() - t0) * 1e3
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -232,7 +232,8 @@ def run_ours(args):
                          "traffic": read_traffic(kname, "c2_256", dt)},
             "step_roofline_frac_27V_model": model_s * 1e3 / (elapsed / args.steps),
             "clocks": clocks,
-            "gpu_launches": 5 * args.steps,
+            "gpu_launches": plan.info.launches_per_apply * args.steps,
+            "launches_per_solve": plan.info.launches_per_apply,
         }
         # e2e through the C-ABI host-buffer entry point: every step copies its rho
         # from pinned host memory and its phi back (both inside the timed
@@ -240,7 +241,7 @@ def run_ours(args):
         # overlap the other's kernels, as a caller streaming solves would run it.
         res["e2e"] = None
         if not args.no_e2e:
-            plan2 = fsa.Plan(d.L, n, dt, eps=d.eps)
+            plan2 = fsa.Plan(d.L, n, dt, eps=d.eps, l2_chunk_mb=args.l2_chunk_mb)
             streams = [torch.cuda.Stream(), torch.cuda.Stream()]
             plans = [plan, plan2]
             hin = [torch.from_numpy(rho64).to(tdt).pin_memory() for _ in range(2)]
@@ -505,6 +506,8 @@ def main():
     ap.add_argument("--kernel-gen", choices=["auto", "1", "2", "3"], default="auto",
                     help="auto: autotuned per plan; 1 / 2 / 3: force one kernel generation "
                          "(FP64: native for 1, double-word otherwise)")
+    ap.add_argument("--l2-chunk-mb", type=int, default=0,
+                    help="plane-slab size of the middle passes in MB (0 = library default, -1 = one slab)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serve", action="store_true")

@@ -73,7 +73,11 @@ typedef struct {
   double eps_tol; /* App. B bound R0^2 f(R0/eps) must not exceed this;         */
                   /* 0 selects 1e-8, a negative value disables the check       */
   int device;     /* CUDA device ordinal; -1 = the calling thread's current one */
-  int reserved;
+  int l2_chunk_mb; /* pass split: run the three middle passes per slab of planes   */
+                   /* whose intermediates take about this many MB, so they stay  */
+                   /* in L2; 0 or negative = one slab (the default: slabs of     */
+                   /* 8-64 MB measured 1.3-3.6x slower at 256^3 on GB300, the    */
+                   /* small slab launches cannot fill the GPU)                   */
 } fsa_plan_opts;
 
 typedef struct fsa_plan fsa_plan;
@@ -89,6 +93,7 @@ typedef struct {
   int device;
   int generated;            /* 1 once fsa_tensor_generate has been enqueued           */
   int arithmetic;           /* 0 FP32; FP64 plans: 1 native FP64, 2 double-word       */
+  int launches_per_apply;   /* kernel launches of one fsa_apply (2 + 3 x plane slabs)  */
   size_t workspace_bytes;   /* device scratch the plan owns                           */
   size_t spectrum_bytes;    /* device bytes of the stored spectrum octant             */
   const void* spectrum;     /* device pointer: (n0+1) x (n1+1) x (n2+1) dtype, C order */
@@ -178,13 +183,14 @@ const char* fsa_last_error(void); /* calling thread's last error message ("" if 
 
 /* ------------------------------------------------------------ profiling -- */
 /* Per-pass timing with CUDA events on the launching stream.  A profiler holds
- * up to max_steps x 6 events (created with cudaEventCreate: no device memory).
- * fsa_apply_profiled is fsa_apply plus an event before the first pass and
- * after each of the five passes; fsa_profiler_read synchronises on the last
- * event and returns, averaged over the recorded steps, the duration of each
- * pass (pass_ms[5]: r2c_ax0, row_fwd, col_mid, row_inv, c2r_ax0) and of the
- * whole step (step_ms), then resets.  FSA_ERR_BUSY if more than max_steps
- * steps are recorded before a read. */
+ * 512 events per step for up to max_steps (1..4096) steps (cudaEventCreate:
+ * no device memory).  fsa_apply_profiled is fsa_apply plus an event before
+ * the first launch and after every launch, each tagged with its pass;
+ * fsa_profiler_read synchronises and returns, averaged over the recorded
+ * steps, the time of each pass (pass_ms[5]: r2c_ax0, row_fwd, col_mid,
+ * row_inv, c2r_ax0; a pass run in several plane slabs is the sum of its
+ * launches) and of the whole step (step_ms), then resets.  FSA_ERR_BUSY if
+ * more than max_steps steps are recorded before a read. */
 typedef struct fsa_profiler fsa_profiler;
 fsa_status fsa_profiler_create(fsa_profiler** out, int max_steps);
 fsa_status fsa_apply_profiled(const fsa_plan* plan, const void* rho, void* phi, fsa_stream_t stream,

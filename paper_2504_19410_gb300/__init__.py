@@ -31,11 +31,13 @@ class Plan:
     'f32' or 'f64'.  eps = 0 picks min(1, R0/6).  The spectrum is generated
     on construction unless generate=False."""
 
-    def __init__(self, L, n, dtype="f32", eps=0.0, eps_tol=0.0, device=-1, generate=True, stream=None):
+    def __init__(self, L, n, dtype="f32", eps=0.0, eps_tol=0.0, device=-1, generate=True, stream=None,
+                 l2_chunk_mb=0):
         self.dtype = _DT[dtype]
         self.n = tuple(int(x) for x in n)
         self.L = tuple(float(x) for x in L)
-        self.handle = capi.fsa_plan_create(FSA_KERNEL_COULOMB3D, 3, self.L, self.n, self.dtype, eps, eps_tol, device)
+        self.handle = capi.fsa_plan_create(FSA_KERNEL_COULOMB3D, 3, self.L, self.n, self.dtype, eps, eps_tol, device,
+                                           l2_chunk_mb)
         if generate:
             self.generate(stream)
 

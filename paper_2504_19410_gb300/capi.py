@@ -28,13 +28,14 @@ class FsaError(RuntimeError):
 
 
 class PlanOpts(C.Structure):
-    _fields_ = [("eps", C.c_double), ("eps_tol", C.c_double), ("device", C.c_int), ("reserved", C.c_int)]
+    _fields_ = [("eps", C.c_double), ("eps_tol", C.c_double), ("device", C.c_int), ("l2_chunk_mb", C.c_int)]
 
 
 class PlanInfo(C.Structure):
     _fields_ = [("n", C.c_int * 3), ("L", C.c_double * 3), ("h", C.c_double * 3), ("eps", C.c_double),
                 ("R0", C.c_double), ("eps_bound", C.c_double), ("dtype", C.c_int), ("device", C.c_int),
-                ("generated", C.c_int), ("arithmetic", C.c_int), ("workspace_bytes", C.c_size_t),
+                ("generated", C.c_int), ("arithmetic", C.c_int), ("launches_per_apply", C.c_int),
+                ("workspace_bytes", C.c_size_t),
                 ("spectrum_bytes", C.c_size_t),
                 ("spectrum", C.c_void_p)]
 
@@ -139,9 +140,9 @@ def _stream(s):
 
 # ---- the C-ABI calls, same names ------------------------------------------------
 
-def fsa_plan_create(kernel, d, L, n, dtype, eps=0.0, eps_tol=0.0, device=-1):
+def fsa_plan_create(kernel, d, L, n, dtype, eps=0.0, eps_tol=0.0, device=-1, l2_chunk_mb=0):
     h = _VP()
-    o = PlanOpts(float(eps), float(eps_tol), int(device), 0)
+    o = PlanOpts(float(eps), float(eps_tol), int(device), int(l2_chunk_mb))
     check(lib().fsa_plan_create(C.byref(h), int(kernel), int(d), (C.c_double * 3)(*[float(x) for x in L]),
                                 (C.c_int * 3)(*[int(x) for x in n]), int(dtype), C.byref(o)))
     return h.value

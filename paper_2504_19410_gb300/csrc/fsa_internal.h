@@ -52,19 +52,27 @@ cudaError_t init_all_twiddles();  // every instance unit's tables, current devic
 // Resident CTAs per SM for a kernel (cached per function), times the SM count.
 int persistent_grid(const void* func, int threads, int smem, long long tiles);
 
+// Per-launch trace for the profiler: an event before the first launch and
+// after every launch, and the pass kind of each launch (intervals i -> i+1).
+struct PassTrace {
+  cudaEvent_t* ev = nullptr;
+  signed char* kind = nullptr;
+  int cap = 0;   // events available
+  int used = 0;  // events recorded
+};
+
 // The five apply passes for `count` solves sharing the grid n (plan.cu).
-// With ev != nullptr (count <= kMaxJobs), six events are recorded: before the
-// first pass and after each pass.
 template <typename V>
 cudaError_t group_passes(const int* n, int count, const void* const* rho, void* const* phi, void* const* X,
-                         void* const* Y, const void* const* S, cudaStream_t s, cudaEvent_t* ev = nullptr);
+                         void* const* Y, const void* const* S, cudaStream_t s, PassTrace* tr = nullptr,
+                         long long chunk_bytes = 0);
 cudaError_t plan_apply_passes(const fsa_plan* p, const void* rho, void* phi, cudaStream_t s);
 
 // The five passes for `count` solves of one plan shape in the plan's
 // arithmetic: FP32, native FP64, or double-word for FP64 plans with f64_dw.
 cudaError_t run_group(const fsa_plan* shape, int count, const void* const* rho, void* const* phi,
                       void* const* X, void* const* Y, const void* const* S, cudaStream_t s,
-                      cudaEvent_t* ev = nullptr);
+                      PassTrace* tr = nullptr);
 // The spectrum the apply kernels read (the double-word copy for f64_dw plans).
 const void* plan_apply_spectrum(const fsa_plan* p);
 // Converts an FP64 octant to double-word pairs (tensor_gen.cu).
@@ -102,6 +110,7 @@ struct fsa_plan {
   size_t spectrum_bytes;
   void* spectrum_dw;  // FP64 plans: the spectrum as double-word pairs
   int f64_dw;         // FP64 plans: 1 = double-word arithmetic, 0 = native FP64
+  long long chunk_bytes;  // pass split: target bytes of one slab's X + Y (<= 0: no split)
   void* ws;  // X then Y
   size_t ws_bytes;
   size_t x_bytes;

@@ -150,9 +150,46 @@ template <typename V> int arith_for(int pass, int M) {
     return kArithDW;
 }
 
+// The three middle passes (row forward, middle, row inverse) of planes
+// [k0s, k0s + pc) of every job: the kernels take any count of rows / planes,
+// so a slab is the same launch with offset pointers.
+cudaError_t trace_mark(PassTrace* tr, int kind, cudaStream_t s) {
+  if (!tr || tr->used >= tr->cap) return cudaSuccess;
+  if (tr->used > 0) tr->kind[tr->used - 1] = (signed char)kind;
+  return cudaEventRecord(tr->ev[tr->used++], s);
+}
+
+template <typename V>
+cudaError_t middle_slab(const int* n, int m, int b, void* const* X, void* const* Y, const void* const* S, int k0s,
+                        int pc, const PassFns& f2, const PassFns& f3, const PassFns& f4, cudaStream_t s,
+                        PassTrace* tr) {
+  const int n1 = n[1], n2 = n[2];
+  const size_t cz = sizeof(V), sz = cz / 2;  // complex and real element sizes
+  Jobs j2{}, j3{}, j4{};
+  j2.count = j3.count = j4.count = m;
+  for (int i = 0; i < m; ++i) {
+    const int k = b + i;
+    char* Xs = (char*)X[k] + (size_t)k0s * n1 * n2 * cz;
+    char* Ys = (char*)Y[k] + (size_t)k0s * n1 * 2 * n2 * cz;
+    const char* Ss = (const char*)S[k] + (size_t)k0s * (n1 + 1) * (n2 + 1) * (std::is_same<V, cdw>::value ? 8 : sz);
+    j2.j[i] = Job{Xs, Ys, nullptr};
+    j3.j[i] = Job{Ys, Ys, Ss};
+    j4.j[i] = Job{Ys, Xs, nullptr};
+  }
+  const long long rows = (long long)pc * n1;
+  cudaError_t e = f2.rowf(j2, rows, s);
+  if (e == cudaSuccess) e = trace_mark(tr, kRowFwd, s);
+  if (e == cudaSuccess) e = f3.colm(j3, 2 * n2, pc, s);
+  if (e == cudaSuccess) e = trace_mark(tr, kColMid, s);
+  if (e == cudaSuccess) e = f4.rowi(j4, rows, s);
+  if (e == cudaSuccess) e = trace_mark(tr, kRowInv, s);
+  return e;
+}
+
 template <typename V>
 cudaError_t group_passes(const int* n, int count, const void* const* rho, void* const* phi, void* const* X,
-                         void* const* Y, const void* const* S, cudaStream_t s, cudaEvent_t* ev) {
+                         void* const* Y, const void* const* S, cudaStream_t s, PassTrace* tr,
+                         long long chunk_bytes) {
   const int n0 = n[0], n1 = n[1], n2 = n[2];
   const long long C = (long long)n1 * n2;
   const long long rows = (long long)(n0 + 1) * n1;
@@ -169,10 +206,7 @@ cudaError_t group_passes(const int* n, int count, const void* const* rho, void* 
       j4.j[i] = Job{Y[k], X[k], nullptr};
       j5.j[i] = Job{X[k], phi[k], nullptr};
     }
-    auto mark = [&](int i) {
-      if (ev && e == cudaSuccess) e = cudaEventRecord(ev[i], s);
-    };
-    mark(0);
+    if (e == cudaSuccess) e = trace_mark(tr, -1, s);
     const PassFns& f1 = pass_fns(arith_for<V>(kR2C, 2 * n0), 2 * n0);
     const PassFns& f2 = pass_fns(arith_for<V>(kRowFwd, 2 * n2), 2 * n2);
     const PassFns& f3 = pass_fns(arith_for<V>(kColMid, 2 * n1), 2 * n1);
@@ -180,30 +214,43 @@ cudaError_t group_passes(const int* n, int count, const void* const* rho, void* 
     const PassFns& f5 = pass_fns(arith_for<V>(kC2R, 2 * n0), 2 * n0);
     if (!f1.r2c || !f2.rowf || !f3.colm || !f4.rowi || !f5.c2r) return cudaErrorInvalidValue;
     e = e == cudaSuccess ? f1.r2c(j1, C, s) : e;
-    mark(1);
-    if (e == cudaSuccess) e = f2.rowf(j2, rows, s);
-    mark(2);
-    if (e == cudaSuccess) e = f3.colm(j3, 2 * n2, n0 + 1, s);
-    mark(3);
-    if (e == cudaSuccess) e = f4.rowi(j4, rows, s);
-    mark(4);
+    if (e == cudaSuccess) e = trace_mark(tr, kR2C, s);
+    // pass split: slabs of planes whose X + Y fit chunk_bytes stay in L2
+    // between the row-forward, middle and row-inverse passes
+    const long long plane = (long long)m * n1 * (n2 + 2 * n2) * (long long)sizeof(V);
+    const int K0 = n0 + 1;
+    int pc = chunk_bytes > 0 ? (int)std::max<long long>(1, chunk_bytes / plane) : K0;
+    if (pc >= K0) {
+      if (e == cudaSuccess) e = f2.rowf(j2, rows, s);
+      if (e == cudaSuccess) e = trace_mark(tr, kRowFwd, s);
+      if (e == cudaSuccess) e = f3.colm(j3, 2 * n2, n0 + 1, s);
+      if (e == cudaSuccess) e = trace_mark(tr, kColMid, s);
+      if (e == cudaSuccess) e = f4.rowi(j4, rows, s);
+      if (e == cudaSuccess) e = trace_mark(tr, kRowInv, s);
+    } else {
+      for (int k0s = 0; k0s < K0 && e == cudaSuccess; k0s += pc) {
+        const int c = std::min(pc, K0 - k0s);
+        e = middle_slab<V>(n, m, b, X, Y, S, k0s, c, f2, f3, f4, s, tr);
+      }
+    }
     if (e == cudaSuccess) e = f5.c2r(j5, C, s);
-    mark(5);
+    if (e == cudaSuccess) e = trace_mark(tr, kC2R, s);
   }
   return e;
 }
 template cudaError_t group_passes<float2>(const int*, int, const void* const*, void* const*, void* const*,
-                                          void* const*, const void* const*, cudaStream_t, cudaEvent_t*);
+                                          void* const*, const void* const*, cudaStream_t, PassTrace*, long long);
 template cudaError_t group_passes<double2>(const int*, int, const void* const*, void* const*, void* const*,
-                                           void* const*, const void* const*, cudaStream_t, cudaEvent_t*);
+                                           void* const*, const void* const*, cudaStream_t, PassTrace*, long long);
 template cudaError_t group_passes<cdw>(const int*, int, const void* const*, void* const*, void* const*,
-                                       void* const*, const void* const*, cudaStream_t, cudaEvent_t*);
+                                       void* const*, const void* const*, cudaStream_t, PassTrace*, long long);
 
 cudaError_t run_group(const fsa_plan* shape, int count, const void* const* rho, void* const* phi, void* const* X,
-                      void* const* Y, const void* const* S, cudaStream_t s, cudaEvent_t* ev) {
-  if (shape->dtype == FSA_F32) return group_passes<float2>(shape->n, count, rho, phi, X, Y, S, s, ev);
-  if (shape->f64_dw) return group_passes<cdw>(shape->n, count, rho, phi, X, Y, S, s, ev);
-  return group_passes<double2>(shape->n, count, rho, phi, X, Y, S, s, ev);
+                      void* const* Y, const void* const* S, cudaStream_t s, PassTrace* tr) {
+  const long long cb = shape->chunk_bytes;
+  if (shape->dtype == FSA_F32) return group_passes<float2>(shape->n, count, rho, phi, X, Y, S, s, tr, cb);
+  if (shape->f64_dw) return group_passes<cdw>(shape->n, count, rho, phi, X, Y, S, s, tr, cb);
+  return group_passes<double2>(shape->n, count, rho, phi, X, Y, S, s, tr, cb);
 }
 
 const void* plan_apply_spectrum(const fsa_plan* p) { return p->f64_dw ? p->spectrum_dw : p->spectrum; }
@@ -286,15 +333,15 @@ cudaError_t plan_apply_passes(const fsa_plan* p, const void* rho, void* phi, cud
   return apply_passes(p, rho, phi, X, Y, s);
 }
 
-// The same with an event before the first pass and after each pass.
-cudaError_t plan_apply_passes_events(const fsa_plan* p, const void* rho, void* phi, cudaStream_t s,
-                                     cudaEvent_t* ev6) {
+// The same with a per-launch event trace.
+cudaError_t plan_apply_passes_trace(const fsa_plan* p, const void* rho, void* phi, cudaStream_t s,
+                                    PassTrace* tr) {
   const void* rhos[1] = {rho};
   void* phis[1] = {phi};
   void* xs[1] = {p->ws};
   void* ys[1] = {(char*)p->ws + p->x_bytes};
   const void* ss[1] = {plan_apply_spectrum(p)};
-  return run_group(p, 1, rhos, phis, xs, ys, ss, s, ev6);
+  return run_group(p, 1, rhos, phis, xs, ys, ss, s, tr);
 }
 }  // namespace fsa
 
@@ -398,6 +445,7 @@ fsa_status plan_create_internal(fsa_plan** out, const double* L, const int* n, f
   p->eps = eps;
   p->R0 = R0;
   p->eps_bound = bound;
+  p->chunk_bytes = 0;  // one slab: measured fastest at 256^3 (see fsa_plan_opts.l2_chunk_mb)
   p->dtype = dtype;
   p->device = dev;
   const size_t s = dtype == FSA_F32 ? 4 : 8;
@@ -576,7 +624,9 @@ fsa_status fsa_plan_create(fsa_plan** out, fsa_kernel kernel, int d, const doubl
   DeviceGuard dg;
   cudaError_t e = dg.set(o.device);
   if (e != cudaSuccess) return cuda_error(e, "fsa_plan_create: cudaSetDevice");
-  return plan_create_internal(out, L, n, dtype, o.eps, o.eps_tol, true);
+  fsa_status st = plan_create_internal(out, L, n, dtype, o.eps, o.eps_tol, true);
+  if (st == FSA_OK && o.l2_chunk_mb != 0) (*out)->chunk_bytes = o.l2_chunk_mb > 0 ? (long long)o.l2_chunk_mb << 20 : 0;
+  return st;
 }
 
 fsa_status fsa_plan_destroy(fsa_plan* p) {
@@ -616,6 +666,13 @@ fsa_status fsa_plan_info_get(const fsa_plan* p, fsa_plan_info* info) {
   info->device = p->device;
   info->generated = p->generated;
   info->arithmetic = p->dtype == FSA_F32 ? 0 : (p->f64_dw ? 2 : 1);
+  {
+    const long long cz = p->dtype == FSA_F32 ? 8 : 16;
+    const long long plane = (long long)p->n[1] * 3 * p->n[2] * cz;
+    const int K0 = p->n[0] + 1;
+    const int pc = p->chunk_bytes > 0 ? (int)std::max<long long>(1, p->chunk_bytes / plane) : K0;
+    info->launches_per_apply = 2 + 3 * ((K0 + std::min(pc, K0) - 1) / std::min(pc, K0));
+  }
   info->workspace_bytes = p->ws_bytes;
   info->spectrum_bytes = p->spectrum_bytes;
   info->spectrum = p->spectrum;
