@@ -423,7 +423,10 @@ def bench_serving(args, fsa, W, torch, rank):
         wall = time.perf_counter() - t0
         return wall, lat
 
-    run(None)  # warm the plan cache and the workspace pool
+    # warm the plan cache and the workspace pool: one request per (n, tier)
+    for key in keys:
+        t = srv.submit((16.0, 16.0, 16.0), (key[0],) * 3, key[1], inputs[key], pools[key][0], eps=1.0)
+        srv.wait(t, timeout=600.0)
     wall, lat = run(None)
     capacity = len(reqs) / wall
     arrivals = W.poisson_arrivals(2504, len(reqs), args.serve_load * capacity)
@@ -432,13 +435,41 @@ def bench_serving(args, fsa, W, torch, rank):
     srv.close()
     torch.cuda.empty_cache()
     lat2 = np.array(lat2)
+
+    # The plain FP64 single-solve path on the same request sizes: one FP64 plan
+    # per size, every request solved alone (fsa_apply, one stream, no overlap),
+    # back to back; a sample of the stream keeps the run short.
+    sample = reqs[: args.serve_fp64_sample]
+    plans64, in64, out64 = {}, {}, {}
+    for n, _, _ in sample:
+        if n not in plans64:
+            plans64[n] = fsa.Plan((16.0, 16.0, 16.0), (n, n, n), "f64", eps=1.0)
+            in64[n] = inputs[(n, "f64")] if (n, "f64") in inputs else \
+                W.gaussian_sum(seed=2504 + n, n=n).rho_torch(torch.float64)
+            out64[n] = torch.empty_like(in64[n])
+    for n in plans64:
+        plans64[n].apply(in64[n], out64[n])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for n, _, _ in sample:
+        plans64[n].apply(in64[n], out64[n])
+    torch.cuda.synchronize()
+    fp64_single = len(sample) / (time.perf_counter() - t0)
+    for p in plans64.values():
+        p.close()
+    del in64, out64
+    torch.cuda.empty_cache()
     return {"workload": f"c5: {len(reqs)} requests, n log-uniform in [32,512] (supported sizes), "
                         "80% FP32 / 20% FP64, [-16,16]^3 8-Gaussian densities",
             "capacity_solves_per_s": capacity, "offered_load": args.serve_load,
             "value": len(reqs) / wall2, "unit": UNIT,
             "p50_ms": float(np.percentile(lat2, 50)), "p99_ms": float(np.percentile(lat2, 99)),
             "closed_loop_p50_ms": float(np.percentile(lat, 50)),
-            "plan_hit_rate": st.plan_hits / max(1, st.plan_hits + st.plan_misses)}
+            "plan_hit_rate": st.plan_hits / max(1, st.plan_hits + st.plan_misses),
+            "fp64_single_solve_solves_per_s": fp64_single,
+            "fp64_single_solve_sample": f"first {len(sample)} requests, each solved alone in FP64 "
+                                        "(the FP64 tier's arithmetic), sequentially",
+            "served_capacity_over_fp64_single": capacity / fp64_single}
 
 
 # -------------------------------------------------------------- oracle ----
@@ -511,7 +542,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-n", type=int, default=2000, help="requests in the serving run (C5 uses 10000)")
+    ap.add_argument("--serve-n", type=int, default=10000, help="requests in the serving run")
+    ap.add_argument("--serve-fp64-sample", type=int, default=1000,
+                    help="requests of the stream re-run through the plain FP64 single-solve path")
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered load as a fraction of capacity")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=128, help="cpu_baseline oracle sample grid (per axis)")

@@ -89,6 +89,45 @@ template <int R, bool FWD, typename V> __device__ __forceinline__ void rfft(V* x
   }
 }
 
+// Forward DFT of x[0..R) whose upper half is zero (only x[0..R/2) is read):
+// X[2j] = DFT_{R/2}(x)[j], X[2j+1] = DFT_{R/2}(x[r] w_R^r)[j].
+template <int R, typename V> __device__ __forceinline__ void rfft_half_in(V* x) {
+  static_assert(R % 2 == 0, "even length");
+  constexpr int H = R / 2;
+  V e[H], o[H];
+  sfor<0, H>([&](auto rc) {
+    constexpr int r = decltype(rc)::value;
+    e[r] = x[r];
+    o[r] = twc<R, r, true>(x[r]);
+  });
+  rfft<H, true>(e);
+  rfft<H, true>(o);
+  sfor<0, H>([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    x[2 * j] = e[j];
+    x[2 * j + 1] = o[j];
+  });
+}
+
+// Inverse DFT of a[0..R) of which only the outputs r < R/2 are wanted (left in
+// a[0..R/2)): x[r] = IDFT_{R/2}(a_even)[r] + w_R^{-r} IDFT_{R/2}(a_odd)[r].
+template <int R, typename V> __device__ __forceinline__ void rifft_half_out(V* a) {
+  static_assert(R % 2 == 0, "even length");
+  constexpr int H = R / 2;
+  V e[H], o[H];
+  sfor<0, H>([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    e[j] = a[2 * j];
+    o[j] = a[2 * j + 1];
+  });
+  rfft<H, false>(e);
+  rfft<H, false>(o);
+  sfor<0, H>([&](auto rc) {
+    constexpr int r = decltype(rc)::value;
+    a[r] = cadd(e[r], twc<R, r, false>(o[r]));
+  });
+}
+
 // Two-factor plan M = R1 * R2 with T = R1 threads per line: step B has one
 // sub-transform per thread, step A ceil(R2 / R1).
 template <int M_, int R1_, int R2_> struct Plan2 {
@@ -116,17 +155,26 @@ template <> struct Plan2For<1024> { using type = Plan2<1024, 32, 32>; };
 
 // Step A, forward: thread u handles t = u, u + T, ... < R2.  ld(t, r) returns
 // x[t + R2 r]; st(q, t, v) stores the twiddled result for (q, t).
-template <class P, typename V, class Ld, class St>
+// With HALF (the pruned passes: x[t + R2 r] = 0 for r >= R1/2), only the
+// lower half is loaded and the half-input transform is used (R1 even).
+template <class P, typename V, bool HALF = false, class Ld, class St>
 __device__ __forceinline__ void stepA_fwd(int u, const Ld& ld, const St& st) {
   constexpr int R1 = P::R1, R2 = P::R2;
+  constexpr bool H = HALF && (R1 % 2 == 0);
 #pragma unroll
   for (int i = 0; i < P::PA; ++i) {
     const int t = u + P::T * i;
     if (P::PA * P::T == R2 || t < R2) {
       V a[R1];
+      if constexpr (H) {
 #pragma unroll
-      for (int r = 0; r < R1; ++r) a[r] = ld(t, r);
-      rfft<R1, true>(a);
+        for (int r = 0; r < R1 / 2; ++r) a[r] = ld(t, r);
+        rfft_half_in<R1>(a);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R1; ++r) a[r] = ld(t, r);
+        rfft<R1, true>(a);
+      }
 #pragma unroll
       for (int q = 1; q < R1; ++q) a[q] = cmul(a[q], twiddle<V, P::M>(t * q));
 #pragma unroll
@@ -136,9 +184,12 @@ __device__ __forceinline__ void stepA_fwd(int u, const Ld& ld, const St& st) {
 }
 
 // Step A, inverse: ld(q, t) returns the (q, t) value; st(t, r, v) stores x[t + R2 r].
-template <class P, typename V, class Ld, class St>
+// With HALF (outputs r >= R1/2 are discarded by the crop), only the lower
+// half of the outputs is computed and stored (R1 even).
+template <class P, typename V, bool HALF = false, class Ld, class St>
 __device__ __forceinline__ void stepA_inv(int u, const Ld& ld, const St& st) {
   constexpr int R1 = P::R1, R2 = P::R2;
+  constexpr bool H = HALF && (R1 % 2 == 0);
 #pragma unroll
   for (int i = 0; i < P::PA; ++i) {
     const int t = u + P::T * i;
@@ -146,9 +197,15 @@ __device__ __forceinline__ void stepA_inv(int u, const Ld& ld, const St& st) {
       V a[R1];
 #pragma unroll
       for (int q = 0; q < R1; ++q) a[q] = ld(q, t);
-      rfft<R1, false>(a);
+      if constexpr (H) {
+        rifft_half_out<R1>(a);
 #pragma unroll
-      for (int r = 0; r < R1; ++r) st(t, r, a[r]);
+        for (int r = 0; r < R1 / 2; ++r) st(t, r, a[r]);
+      } else {
+        rfft<R1, false>(a);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) st(t, r, a[r]);
+      }
     }
   }
 }

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB) k2_r2c_ax0(const J
     V* __restrict__ X = static_cast<V*>(jb.out);
     const long long c = (tile % tpj) * (2 * W) + 2 * l;
     const bool ok = c < C;
-    stepA_fwd<P, V>(
+    stepA_fwd<P, V, true>(
         u,
         [&](int t, int r) {
           const int p = t + R2 * r;
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2_row_fwd(const Jobs jobs, long 
     const bool ok = row < rows;
     const V* __restrict__ x = static_cast<const V*>(jb.in) + row * n;
     V* __restrict__ y = static_cast<V*>(jb.out) + row * M;
-    stepA_fwd<P, V>(
+    stepA_fwd<P, V, true>(
         u,
         [&](int t, int r) {
           const int p = t + R2 * r;
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2_col_mid(con
     V* __restrict__ col = static_cast<V*>(jb.out) + (long long)k0 * n * M2 + k2;
     const float* __restrict__ srow =
         static_cast<const float*>(jb.S) + (long long)k0 * (n + 1) * (n2 + 1) + (ok ? min(k2, M2 - k2) : 0);
-    stepA_fwd<P, V>(
+    stepA_fwd<P, V, true>(
         u,
         [&](int t, int r) {
           const int p = t + R2 * r;
@@ -143,16 +143,22 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2_col_mid(con
     for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
     rfft<R2, true>(b);
     // b[s] = transform at k1 = u + R1 s: multiply by the spectrum (real, even)
+    // k1 = u + R1 s: the even spectrum's index min(k1, M - k1) is k1 for
+    // s < R2/2 and M - k1 from s = R2/2 on (u < R1), decided at compile time
+    {
+      const int st = n2 + 1;
+      const float* lo = srow + u * st;
+      const float* hi = srow + (M - u) * st;
 #pragma unroll
-    for (int s = 0; s < R2; ++s) {
-      const int k1 = u + R1 * s;
-      const float sv = ok ? __ldg(srow + (long long)min(k1, M - k1) * (n2 + 1)) : 0.f;
-      b[s] = cscale(b[s], sv);
+      for (int s = 0; s < R2; ++s) {
+        const float sv = !ok ? 0.f : (2 * s < R2 ? __ldg(lo + (R1 * s) * st) : __ldg(hi - (R1 * s) * st));
+        b[s] = cscale(b[s], sv);
+      }
     }
     // the locations this thread read are the ones it writes: no barrier needed
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
-    stepA_inv<P, V>(
+    stepA_inv<P, V, true>(
         u, [&](int q, int t) { return sm[(q * R2 + t) * W + l]; },
         [&](int t, int r, V v) {
           const int p = t + R2 * r;
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2p_col_mid(co
     const float* __restrict__ srow =
         static_cast<const float*>(jb.S) + (long long)k0 * (n + 1) * (n2 + 1) + (ok ? min(k2, M2 - k2) : 0);
     cp_async_wait_all();
-    stepA_fwd<P, V>(
+    stepA_fwd<P, V, true>(
         u,
         [&](int t, int r) {
           const int i = (t - u) / T;
@@ -239,15 +245,21 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2p_col_mid(co
 #pragma unroll
     for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
     rfft<R2, true>(b);
+    // k1 = u + R1 s: the even spectrum's index min(k1, M - k1) is k1 for
+    // s < R2/2 and M - k1 from s = R2/2 on (u < R1), decided at compile time
+    {
+      const int st = n2 + 1;
+      const float* lo = srow + u * st;
+      const float* hi = srow + (M - u) * st;
 #pragma unroll
-    for (int s = 0; s < R2; ++s) {
-      const int k1 = u + R1 * s;
-      const float sv = ok ? __ldg(srow + (long long)min(k1, M - k1) * (n2 + 1)) : 0.f;
-      b[s] = cscale(b[s], sv);
+      for (int s = 0; s < R2; ++s) {
+        const float sv = !ok ? 0.f : (2 * s < R2 ? __ldg(lo + (R1 * s) * st) : __ldg(hi - (R1 * s) * st));
+        b[s] = cscale(b[s], sv);
+      }
     }
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
-    stepA_inv<P, V>(
+    stepA_inv<P, V, true>(
         u, [&](int q, int t) { return sm[(q * R2 + t) * W + l]; },
         [&](int t, int r, V v) {
           const int p = t + R2 * r;
@@ -309,7 +321,7 @@ __global__ void __launch_bounds__(RowGeo<P, WR>::NT) k2p_row_fwd(const Jobs jobs
     const bool ok = row < rows;
     V* __restrict__ y = static_cast<V*>(jb.out) + row * M;
     cp_async_wait_all();
-    stepA_fwd<P, V>(
+    stepA_fwd<P, V, true>(
         u,
         [&](int t, int r) {
           const int i = (t - u) / T;
@@ -365,7 +377,7 @@ __global__ void __launch_bounds__(RowGeo<P, WR>::NT) k2p_row_inv(const Jobs jobs
     if (tile + gridDim.x < total) issue(tile + gridDim.x);
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { line[q * (R2 + 1) + t] = v; });
     __syncthreads();
-    stepA_inv<P, V>(
+    stepA_inv<P, V, true>(
         u, [&](int q, int t) { return line[q * (R2 + 1) + t]; },
         [&](int t, int r, V v) {
           const int p = t + R2 * r;
@@ -397,7 +409,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2_row_inv(const Jobs jobs, long 
     for (int s = 0; s < R2; ++s) b[s] = ok ? y[u + R1 * s] : czero<V>();
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { line[q * (R2 + 1) + t] = v; });
     __syncthreads();
-    stepA_inv<P, V>(
+    stepA_inv<P, V, true>(
         u, [&](int q, int t) { return line[q * (R2 + 1) + t]; },
         [&](int t, int r, V v) {
           const int p = t + R2 * r;
@@ -438,7 +450,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2_c2r_ax0(const Jobs jobs, long 
     }
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
-    stepA_inv<P, V>(
+    stepA_inv<P, V, true>(
         u, [&](int q, int t) { return sm[(q * R2 + t) * W + l]; },
         [&](int t, int r, V v) {
           const int p = t + R2 * r;
