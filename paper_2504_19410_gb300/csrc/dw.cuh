@@ -59,6 +59,26 @@ __device__ __forceinline__ dw operator*(dw x, dw y) {
   return dw(ch, __fadd_rn(cl1, cl2));
 }
 
+// a * b + c * d: the two leading products exact (2Prod by FMA), summed by
+// TwoSum, with the products' errors and the cross terms a.hi b.lo, a.lo b.hi,
+// c.hi d.lo, c.lo d.hi folded in by FMA (a.lo b.lo and c.lo d.lo, of order
+// u^2 |a b| and u^2 |c d|, are dropped).  16 operations against 20 for two
+// multiplications and an addition; it carries the real and imaginary parts of
+// a complex product.
+__device__ __forceinline__ dw dw_dot2(dw a, dw b, dw c, dw d) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float pe = __fmaf_rn(a.hi, b.hi, -p);
+  const float q = __fmul_rn(c.hi, d.hi);
+  const float qe = __fmaf_rn(c.hi, d.hi, -q);
+  const dw s = dw_two_sum(p, q);
+  float t = __fadd_rn(pe, qe);
+  t = __fmaf_rn(a.hi, b.lo, t);
+  t = __fmaf_rn(a.lo, b.hi, t);
+  t = __fmaf_rn(c.hi, d.lo, t);
+  t = __fmaf_rn(c.lo, d.hi, t);
+  return dw(s.hi, __fadd_rn(s.lo, t));
+}
+
 __device__ __forceinline__ dw dw_from_double(double d) {
   const float h = __double2float_rn(d);
   return dw(h, __double2float_rn(d - (double)h));

@@ -66,6 +66,18 @@ template <typename V> __device__ __forceinline__ typename RealOf<V>::T load_spec
   }
 }
 
+// Canonical form of a value leaving a pass for HBM.  The double-word
+// operations skip their closing renormalisation, so a low part can grow past
+// half an ulp of its high part over many operations; one TwoSum per part at
+// each pass boundary bounds that growth to the operations of one pass.
+template <typename V> __device__ __forceinline__ V canon(V v) {
+  if constexpr (std::is_same<V, cdw>::value) {
+    return mk(dw_two_sum(v.x.hi, v.x.lo), dw_two_sum(v.y.hi, v.y.lo));
+  } else {
+    return v;
+  }
+}
+
 template <typename V> __device__ __forceinline__ V czero() { return mk(typename RealOf<V>::T(0), typename RealOf<V>::T(0)); }
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk(a.x + b.x, a.y + b.y); }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk(a.x - b.x, a.y - b.y); }
@@ -75,6 +87,13 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
 // a * conj(b)
 template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
   return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// double-word complex products: each part is one fused two-term dot product
+__device__ __forceinline__ cdw cmul(cdw a, cdw b) {
+  return mk(dw_dot2(a.x, b.x, -a.y, b.y), dw_dot2(a.x, b.y, a.y, b.x));
+}
+__device__ __forceinline__ cdw cmulc(cdw a, cdw b) {
+  return mk(dw_dot2(a.x, b.x, a.y, b.y), dw_dot2(a.y, b.x, -a.x, b.y));
 }
 template <typename V> __device__ __forceinline__ V cscale(V a, typename RealOf<V>::T s) { return mk(a.x * s, a.y * s); }
 // -i * a for the forward direction, +i * a for the inverse one
@@ -109,16 +128,10 @@ template <bool FWD, typename V> __device__ __forceinline__ void dft4(V* v) {
   v[3] = csub(b, d);
 }
 
-template <bool FWD, typename V> __device__ __forceinline__ void dft8(V* v) {
+// b_k *= w8^k (k = 1, 2, 3), w8 = exp(-+ 2 pi i / 8)
+template <bool FWD, typename V> __device__ __forceinline__ void rot8(V* b) {
   using R = typename RealOf<V>::T;
   const R h = R(0.70710678118654752440084436210485);  // 1/sqrt(2)
-  V a[4], b[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    a[k] = cadd(v[k], v[k + 4]);
-    b[k] = csub(v[k], v[k + 4]);
-  }
-  // b_k *= w8^k, w8 = exp(-+ 2 pi i / 8)
   if (FWD) {
     b[1] = mk(h * (b[1].x + b[1].y), h * (b[1].y - b[1].x));
     b[3] = mk(h * (b[3].y - b[3].x), -h * (b[3].x + b[3].y));
@@ -127,12 +140,77 @@ template <bool FWD, typename V> __device__ __forceinline__ void dft8(V* v) {
     b[3] = mk(-h * (b[3].x + b[3].y), h * (b[3].x - b[3].y));
   }
   b[2] = rot_mi<FWD>(b[2]);
+}
+
+template <bool FWD, typename V> __device__ __forceinline__ void dft8(V* v) {
+  V a[4], b[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    a[k] = cadd(v[k], v[k + 4]);
+    b[k] = csub(v[k], v[k + 4]);
+  }
+  rot8<FWD>(b);
   dft4<FWD>(a);
   dft4<FWD>(b);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     v[2 * q] = a[q];
     v[2 * q + 1] = b[q];
+  }
+}
+
+// Pruned codelets.  dft_half_in: DFT of v[0..R) whose upper half is zero
+// (only v[0..R/2) is read); adding or subtracting the zero half is exact, so
+// the results are those of the full codelet.  dft_half_out: only the outputs
+// v[0..R/2) are formed.  R in {2, 4, 8}.
+template <bool FWD, typename V> __device__ __forceinline__ void dft4_lo2(const V* v, V& o0, V& o1) {
+  const V a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+  const V c = cadd(v[1], v[3]), d = rot_mi<FWD>(csub(v[1], v[3]));
+  o0 = cadd(a, c);
+  o1 = cadd(b, d);
+}
+
+template <int R, bool FWD, typename V> __device__ __forceinline__ void dft_half_in(V* v) {
+  static_assert(R == 2 || R == 4 || R == 8, "pruned codelet radix");
+  if constexpr (R == 2) {
+    v[1] = v[0];
+  } else if constexpr (R == 4) {
+    const V a = v[0], c = v[1], d = rot_mi<FWD>(v[1]);
+    v[0] = cadd(a, c);
+    v[2] = csub(a, c);
+    v[1] = cadd(a, d);
+    v[3] = csub(a, d);
+  } else {
+    V a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] = b[k] = v[k];
+    rot8<FWD>(b);
+    dft4<FWD>(a);
+    dft4<FWD>(b);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      v[2 * q] = a[q];
+      v[2 * q + 1] = b[q];
+    }
+  }
+}
+
+template <int R, bool FWD, typename V> __device__ __forceinline__ void dft_half_out(V* v) {
+  static_assert(R == 2 || R == 4 || R == 8, "pruned codelet radix");
+  if constexpr (R == 2) {
+    v[0] = cadd(v[0], v[1]);
+  } else if constexpr (R == 4) {
+    dft4_lo2<FWD>(v, v[0], v[1]);
+  } else {
+    V a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      a[k] = cadd(v[k], v[k + 4]);
+      b[k] = csub(v[k], v[k + 4]);
+    }
+    rot8<FWD>(b);
+    dft4_lo2<FWD>(a, v[0], v[2]);
+    dft4_lo2<FWD>(b, v[1], v[3]);
   }
 }
 
@@ -212,29 +290,42 @@ template <typename V, int L> __device__ __forceinline__ V twiddle(int e) {
 // thread index t.  `ld(p)` returns element p of the stage input, `st(p, v)`
 // stores element p of the stage output.  All threads of the CTA must call it
 // (it contains two barriers: between loads and stores, and after stores).
-template <class P, int S, bool FWD, int T, typename V, class Ld, class St>
+// ZIN (first stage, even radix): inputs p >= M/2 are zero, i.e. r >= R/2 --
+// they are neither loaded nor transformed.  ZOUT (last stage, even radix):
+// only outputs p < M/2, i.e. r < R/2, are formed and stored.
+template <class P, int S, bool FWD, int T, typename V, bool ZIN, bool ZOUT, class Ld, class St>
 __device__ __forceinline__ void stage(int t, const Ld& ld, const St& st) {
   constexpr int R = P::R[S];
   constexpr int NS = P::ns(S);
   constexpr int M = P::M;
   constexpr int NB = M / R;
   constexpr int PER = (NB + T - 1) / T;
+  constexpr bool HIN = ZIN && S == 0 && R % 2 == 0;
+  constexpr bool HOUT = ZOUT && S == P::NST - 1 && R % 2 == 0;
+  constexpr int RIN = HIN ? R / 2 : R;
+  constexpr int ROUT = HOUT ? R / 2 : R;
   V v[PER][R];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int b = t + q * T;
     if (PER * T == NB || b < NB) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = ld(b + r * NB);
+      for (int r = 0; r < RIN; ++r) v[q][r] = ld(b + r * NB);
       if constexpr (NS > 1) {
         const int k = b % NS;
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
+        for (int r = 1; r < RIN; ++r) {
           const V w = twiddle<V, NS * R>(r * k);
           v[q][r] = FWD ? cmul(v[q][r], w) : cmulc(v[q][r], w);
         }
       }
-      dft<R, FWD>(v[q]);
+      if constexpr (HIN) {
+        dft_half_in<R, FWD>(v[q]);
+      } else if constexpr (HOUT) {
+        dft_half_out<R, FWD>(v[q]);
+      } else {
+        dft<R, FWD>(v[q]);
+      }
     }
   }
   __syncthreads();
@@ -244,7 +335,7 @@ __device__ __forceinline__ void stage(int t, const Ld& ld, const St& st) {
     if (PER * T == NB || b < NB) {
       const int j = (b / NS) * NS * R + (b % NS);
 #pragma unroll
-      for (int r = 0; r < R; ++r) st(j + r * NS, v[q][r]);
+      for (int r = 0; r < ROUT; ++r) st(j + r * NS, v[q][r]);
     }
   }
   __syncthreads();
@@ -259,26 +350,29 @@ template <typename V, int STRIDE> struct SLine {
 
 // Full transform of one line: stage 0 reads through `first`, the last stage
 // writes through `last`, the stages in between go through the line view.
-template <class P, bool FWD, int T, typename V, int S, class F, class L, class SL>
+// HIN: the line's upper half (p >= M/2) is zero and `first` is only asked for
+// p < M/2.  HOUT: only outputs p < M/2 are wanted; `last` sees only those
+// (with an odd radix at that end the full stage runs instead).
+template <class P, bool FWD, int T, typename V, bool HIN, bool HOUT, int S, class F, class L, class SL>
 __device__ __forceinline__ void run_from(int t, const F& first, const L& last, const SL& sl) {
   auto sget = [&](int p) { return sl.get(p); };
   auto sput = [&](int p, V v) { sl.put(p, v); };
   if constexpr (S == 0 && P::NST == 1) {
-    stage<P, 0, FWD, T, V>(t, first, last);
+    stage<P, 0, FWD, T, V, HIN, HOUT>(t, first, last);
   } else if constexpr (S == 0) {
-    stage<P, 0, FWD, T, V>(t, first, sput);
-    run_from<P, FWD, T, V, 1>(t, first, last, sl);
+    stage<P, 0, FWD, T, V, HIN, false>(t, first, sput);
+    run_from<P, FWD, T, V, HIN, HOUT, 1>(t, first, last, sl);
   } else if constexpr (S == P::NST - 1) {
-    stage<P, S, FWD, T, V>(t, sget, last);
+    stage<P, S, FWD, T, V, false, HOUT>(t, sget, last);
   } else {
-    stage<P, S, FWD, T, V>(t, sget, sput);
-    run_from<P, FWD, T, V, S + 1>(t, first, last, sl);
+    stage<P, S, FWD, T, V, false, false>(t, sget, sput);
+    run_from<P, FWD, T, V, HIN, HOUT, S + 1>(t, first, last, sl);
   }
 }
 
-template <class P, bool FWD, int T, typename V, class F, class L, class SL>
+template <class P, bool FWD, int T, typename V, bool HIN = false, bool HOUT = false, class F, class L, class SL>
 __device__ __forceinline__ void fft_line(int t, const F& first, const L& last, const SL& sl) {
-  run_from<P, FWD, T, V, 0>(t, first, last, sl);
+  run_from<P, FWD, T, V, HIN, HOUT, 0>(t, first, last, sl);
 }
 
 }  // namespace fsa

@@ -35,6 +35,11 @@ template <typename V> struct TileW { static constexpr int W = 16; };
 template <> struct TileW<double2> { static constexpr int W = 8; };
 template <> struct TileW<cdw> { static constexpr int W = 8; };
 
+// Resident CTAs per SM the compiler should allow for: double-word passes are
+// bound by the FP32 pipes, so they ask for two (at most 64 registers).
+template <typename V> struct MinB { static constexpr int value = 1; };
+template <> struct MinB<cdw> { static constexpr int value = 2; };
+
 // Threads per line: one butterfly of the largest radix per thread, capped so
 // that a CTA has at most 512 threads.
 template <class P, int W> constexpr int threads_per_line() {
@@ -51,7 +56,7 @@ template <class P, typename V, int W> constexpr int smem_rows() { return W * (P:
 // Every kernel walks the tiles of all jobs of its launch with a grid-strided
 // loop (a persistent grid of a few CTAs per SM).
 template <typename V, class P, int W, int T>
-__global__ void __launch_bounds__(W * T) k_r2c_ax0(const Jobs jobs, long long C) {
+__global__ void __launch_bounds__(W * T, MinB<V>::value) k_r2c_ax0(const Jobs jobs, long long C) {
   using R = typename RealOf<V>::T;
   constexpr int M = P::M, n = M / 2, K = n + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -69,7 +74,7 @@ __global__ void __launch_bounds__(W * T) k_r2c_ax0(const Jobs jobs, long long C)
     return (p < n && ok) ? load_pair<V>(rho + (long long)p * C + c) : czero<V>();
   };
   auto last = [&](int p, V v) { sl.put(p, v); };
-  fft_line<P, true, T, V>(t, first, last, sl);
+  fft_line<P, true, T, V, true, false>(t, first, last, sl);
   // Z = DFT(a + i b): A[k] = (Z[k] + conj Z[M-k]) / 2, B[k] = (Z[k] - conj Z[M-k]) / 2i
   for (int k = t; k < K; k += T) {
     const V zk = sm[k * W + l];
@@ -77,8 +82,8 @@ __global__ void __launch_bounds__(W * T) k_r2c_ax0(const Jobs jobs, long long C)
     const V a = mk(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
     const V b = mk(R(0.5) * (zk.y + zm.y), R(0.5) * (zm.x - zk.x));
     if (ok) {
-      X[(long long)k * C + c] = a;
-      X[(long long)k * C + c + 1] = b;
+      X[(long long)k * C + c] = canon(a);
+      X[(long long)k * C + c + 1] = canon(b);
     }
   }
   __syncthreads();
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(W * T) k_r2c_ax0(const Jobs jobs, long long C)
 
 // ---------------------------------------------------------------- pass 2 --
 template <typename V, class P, int W, int T>
-__global__ void __launch_bounds__(W * T) k_row_fwd(const Jobs jobs, long long rows) {
+__global__ void __launch_bounds__(W * T, MinB<V>::value) k_row_fwd(const Jobs jobs, long long rows) {
   constexpr int M = P::M, n = M / 2, PITCH = M + 1, NT = W * T;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
@@ -107,11 +112,11 @@ __global__ void __launch_bounds__(W * T) k_row_fwd(const Jobs jobs, long long ro
   SLine<V, 1> sl{sm + l * PITCH};
   auto first = [&](int p) -> V { return p < n ? sl.get(p) : czero<V>(); };
   auto last = [&](int p, V v) { sl.put(p, v); };
-  fft_line<P, true, T, V>(t, first, last, sl);
+  fft_line<P, true, T, V, true, false>(t, first, last, sl);
   for (int i = threadIdx.x; i < W * M; i += NT) {
     const int l2 = i / M, p = i - l2 * M;
     const long long row = row0 + l2;
-    if (row < rows) Y[row * M + p] = sm[l2 * PITCH + p];
+    if (row < rows) Y[row * M + p] = canon(sm[l2 * PITCH + p]);
   }
   __syncthreads();
   }
@@ -142,21 +147,21 @@ __global__ void __launch_bounds__(W * T) k_col_mid(const Jobs jobs, int M2, int 
   SLine<V, W> sl{sm + l};
   auto first = [&](int p) -> V { return (p < n && ok) ? col[(long long)p * M2] : czero<V>(); };
   auto to_sm = [&](int p, V v) { sl.put(p, v); };
-  fft_line<P, true, T, V>(t, first, to_sm, sl);
+  fft_line<P, true, T, V, true, false>(t, first, to_sm, sl);
   auto mul = [&](int p) -> V {
     const R s = ok ? load_spec<V>(srow + (long long)min(p, M - p) * (n2 + 1)) : R(0);
     return cscale(sl.get(p), s);
   };
   auto last = [&](int p, V v) {
-    if (p < n && ok) col[(long long)p * M2] = v;
+    if (p < n && ok) col[(long long)p * M2] = canon(v);
   };
-  fft_line<P, false, T, V>(t, mul, last, sl);
+  fft_line<P, false, T, V, false, true>(t, mul, last, sl);
   }
 }
 
 // ---------------------------------------------------------------- pass 4 --
 template <typename V, class P, int W, int T>
-__global__ void __launch_bounds__(W * T) k_row_inv(const Jobs jobs, long long rows) {
+__global__ void __launch_bounds__(W * T, MinB<V>::value) k_row_inv(const Jobs jobs, long long rows) {
   constexpr int M = P::M, n = M / 2, PITCH = M + 1, NT = W * T;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
@@ -176,11 +181,11 @@ __global__ void __launch_bounds__(W * T) k_row_inv(const Jobs jobs, long long ro
   SLine<V, 1> sl{sm + l * PITCH};
   auto first = [&](int p) -> V { return sl.get(p); };
   auto last = [&](int p, V v) { sl.put(p, v); };
-  fft_line<P, false, T, V>(t, first, last, sl);
+  fft_line<P, false, T, V, false, true>(t, first, last, sl);
   for (int i = threadIdx.x; i < W * n; i += NT) {
     const int l2 = i / n, p = i - l2 * n;
     const long long row = row0 + l2;
-    if (row < rows) X[row * n + p] = sm[l2 * PITCH + p];
+    if (row < rows) X[row * n + p] = canon(sm[l2 * PITCH + p]);
   }
   __syncthreads();
   }
@@ -188,7 +193,7 @@ __global__ void __launch_bounds__(W * T) k_row_inv(const Jobs jobs, long long ro
 
 // ---------------------------------------------------------------- pass 5 --
 template <typename V, class P, int W, int T>
-__global__ void __launch_bounds__(W * T) k_c2r_ax0(const Jobs jobs, long long C) {
+__global__ void __launch_bounds__(W * T, MinB<V>::value) k_c2r_ax0(const Jobs jobs, long long C) {
   using R = typename RealOf<V>::T;
   constexpr int M = P::M, n = M / 2;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -213,7 +218,7 @@ __global__ void __launch_bounds__(W * T) k_c2r_ax0(const Jobs jobs, long long C)
   auto last = [&](int p, V v) {
     if (p < n && ok) store_pair<V>(phi + (long long)p * C + c, v);
   };
-  fft_line<P, false, T, V>(t, first, last, sl);
+  fft_line<P, false, T, V, false, true>(t, first, last, sl);
   }
 }
 
