@@ -40,6 +40,14 @@ template <> struct TileW<cdw> { static constexpr int W = 8; };
 template <typename V> struct MinB { static constexpr int value = 1; };
 template <> struct MinB<cdw> { static constexpr int value = 2; };
 
+// The middle pass keeps a whole line's forward transform, multiply and
+// inverse in one CTA; for double-word values it takes half-width tiles so
+// that two CTAs (each up to 128 registers a thread) share an SM and one's
+// barriers and loads overlap the other's arithmetic.
+template <typename V> struct MidW { static constexpr int W = TileW<V>::W; };
+template <> struct MidW<cdw> { static constexpr int W = 4; };
+template <typename V, int NT> constexpr int minb_mid() { return (std::is_same<V, cdw>::value && NT <= 256) ? 2 : 1; }
+
 // Threads per line: one butterfly of the largest radix per thread, capped so
 // that a CTA has at most 512 threads.
 template <class P, int W> constexpr int threads_per_line() {
@@ -124,7 +132,7 @@ __global__ void __launch_bounds__(W * T, MinB<V>::value) k_row_fwd(const Jobs jo
 
 // ---------------------------------------------------------------- pass 3 --
 template <typename V, class P, int W, int T>
-__global__ void __launch_bounds__(W * T) k_col_mid(const Jobs jobs, int M2, int planes) {
+__global__ void __launch_bounds__(W * T, minb_mid<V, W * T>()) k_col_mid(const Jobs jobs, int M2, int planes) {
   using R = typename RealOf<V>::T;
   constexpr int M = P::M, n = M / 2;
   extern __shared__ __align__(16) unsigned char smraw[];

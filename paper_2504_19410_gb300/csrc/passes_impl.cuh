@@ -20,6 +20,10 @@ template <typename V, int M> struct Inst {
   static constexpr int NT = W * T;
   static constexpr int SM_STRIDED = smem_strided<P, V, W>();
   static constexpr int SM_ROWS = smem_rows<P, V, W>();
+  static constexpr int WC = MidW<V>::W;  // middle pass tile
+  static constexpr int TC = threads_per_line<P, WC>();
+  static constexpr int NTC = WC * TC;
+  static constexpr int SM_MID = smem_strided<P, V, WC>();
 
   static cudaError_t prepare() {
     cudaError_t e = cudaSuccess;
@@ -28,16 +32,16 @@ template <typename V, int M> struct Inst {
     };
     set((const void*)k_r2c_ax0<V, P, W, T>, SM_STRIDED);
     set((const void*)k_row_fwd<V, P, W, T>, SM_ROWS);
-    set((const void*)k_col_mid<V, P, W, T>, SM_STRIDED);
+    set((const void*)k_col_mid<V, P, WC, TC>, SM_MID);
     set((const void*)k_row_inv<V, P, W, T>, SM_ROWS);
     set((const void*)k_c2r_ax0<V, P, W, T>, SM_STRIDED);
     return e;
   }
   static Geometry geometry(PassKind k) {
     Geometry g;
-    g.W = W;
-    g.threads = NT;
-    g.smem = (k == kRowFwd || k == kRowInv) ? SM_ROWS : SM_STRIDED;
+    g.W = k == kColMid ? WC : W;
+    g.threads = k == kColMid ? NTC : NT;
+    g.smem = (k == kRowFwd || k == kRowInv) ? SM_ROWS : (k == kColMid ? SM_MID : SM_STRIDED);
     return g;
   }
   static cudaError_t r2c(const Jobs& jobs, long long C, cudaStream_t s) {
@@ -53,9 +57,9 @@ template <typename V, int M> struct Inst {
     return cudaGetLastError();
   }
   static cudaError_t colm(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
-    const long long tiles = (long long)((M2 + W - 1) / W) * planes * jobs.count;
-    auto f = k_col_mid<V, P, W, T>;
-    f<<<persistent_grid((const void*)f, NT, SM_STRIDED, tiles), NT, SM_STRIDED, s>>>(jobs, M2, planes);
+    const long long tiles = (long long)((M2 + WC - 1) / WC) * planes * jobs.count;
+    auto f = k_col_mid<V, P, WC, TC>;
+    f<<<persistent_grid((const void*)f, NTC, SM_MID, tiles), NTC, SM_MID, s>>>(jobs, M2, planes);
     return cudaGetLastError();
   }
   static cudaError_t rowi(const Jobs& jobs, long long rows, cudaStream_t s) {
