@@ -57,6 +57,52 @@ def reference_model_bytes(n, s):
     return (2 * n0 * n1 * n2 + 24 * n0 * n1 * (n2 + 1) + (n0 + 1) * (n1 + 1) * (n2 + 1)) * s
 
 
+# Radix plan of the double-word (first-generation Stockham) line transforms,
+# per line length M = 2n; the same factorisation the kernels are built with.
+DW_RADICES = {8: [8], 12: [4, 3], 16: [4, 4], 24: [8, 3], 32: [8, 4], 48: [4, 4, 3], 64: [8, 8],
+              96: [8, 4, 3], 128: [8, 4, 4], 192: [8, 8, 3], 256: [8, 8, 4], 384: [8, 4, 4, 3],
+              512: [8, 8, 8], 768: [8, 8, 4, 3], 1024: [8, 8, 4, 4]}
+
+
+def dw_mid_ops(n):
+    """FP32 operations of the double-word middle pass for one solve (the pass
+    is bound by the FP32 pipes, not by HBM).  Costs in FP32 operations: a
+    double-word add 8 (TwoSum 6 + 2), multiply 6, complex add 16, complex
+    twiddle product 32 (two fused dot products), complex scale 12.  Codelets:
+    DFT2/3/4/8 = 32/120/128/440; pruned first stage (zero upper half) of radix
+    2/4/8 = 0/64/312; pruned last stage (lower half kept) = 16/96/376.  A
+    column line (length M = 2 n1) is: forward transform (first stage pruned),
+    multiply by the spectrum (M complex scales), inverse transform (last stage
+    pruned), renormalisation of the n1 stored values (12 each); a stage s > 0
+    adds R - 1 twiddle products per radix-R group.  At 256^3 this gives 223,232
+    per line x 257 x 512 lines, equal to the FADD + FMUL + FFMA thread
+    instructions ncu counts for the kernel."""
+    n0, n1, n2 = n
+    M = 2 * n1
+    rad = DW_RADICES[M]
+    full = {2: 32, 3: 120, 4: 128, 8: 440}
+    half_in = {2: 0, 4: 64, 8: 312}
+    half_out = {2: 16, 4: 96, 8: 376}
+
+    def transform(zin, zout):
+        ops = 0
+        for s, R in enumerate(rad):
+            groups = M // R
+            last = s == len(rad) - 1
+            if zin and s == 0 and R % 2 == 0:
+                c = half_in[R]
+            elif zout and last and R % 2 == 0:
+                c = half_out[R]
+            else:
+                c = full[R]
+            tw = (R - 1) * 32 if s > 0 else 0
+            ops += groups * (c + tw)
+        return ops
+
+    per_line = transform(True, False) + 12 * M + transform(False, True) + 12 * n1
+    return per_line * (n0 + 1) * (2 * n2)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -219,17 +265,34 @@ def run_ours(args):
         kname = PASSES[dom]
         achieved = pb[kname] / (pass_ms[dom] * 1e-3) / 1e9
         model_s = reference_model_bytes(n, s) / (hbm_peak * 1e9)
+        arith = ["fp32", "fp64", "double-word"][plan.info.arithmetic]
+        hbm_roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
+                    "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": f"of {peak_kind}",
+                    "alg_bytes_per_launch": pb[kname],
+                    "traffic": read_traffic(kname, "c2_256", dt)}
+        roof = hbm_roof
+        if arith == "double-word" and kname == "col_mid":
+            # bound by the FP32 pipes: FP32 operations per launch over the
+            # FP32 issue peak (SMs x 128 lanes x maximum SM clock)
+            sms = torch.cuda.get_device_properties(local).multi_processor_count
+            max_mhz = clocks.get("sm_max_mhz") or 2070.0
+            alu_peak = sms * 128 * max_mhz * 1e6 / 1e9
+            ops = dw_mid_ops(n)
+            alu = ops / (pass_ms[dom] * 1e-3) / 1e9
+            roof = {"bound": "alu", "kernel": kname, "achieved": alu, "peak": alu_peak,
+                    "unit": "Gop/s (FP32 lane operations)", "frac": alu / alu_peak,
+                    "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz max SM clock",
+                    "alg_ops_per_launch": ops, "traffic": hbm_roof["traffic"],
+                    "hbm": {k: hbm_roof[k] for k in ("achieved", "peak", "unit", "frac", "peak_kind",
+                                                     "alg_bytes_per_launch")}}
         res = {
             "value": ws * args.steps / (elapsed * 1e-3),
             "ms_per_step": elapsed / args.steps,
             "precomp_ms": precomp_ms,
             "plan_create_ms": create_ms,
-            "arithmetic": ["fp32", "fp64", "double-word"][plan.info.arithmetic],
+            "arithmetic": arith,
             "pass_ms": dict(zip(PASSES, [round(x, 5) for x in pass_ms])),
-            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
-                         "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": f"of {peak_kind}",
-                         "alg_bytes_per_launch": pb[kname],
-                         "traffic": read_traffic(kname, "c2_256", dt)},
+            "roofline": roof,
             "step_roofline_frac_27V_model": model_s * 1e3 / (elapsed / args.steps),
             "clocks": clocks,
             "gpu_launches": plan.info.launches_per_apply * args.steps,
