@@ -300,28 +300,29 @@ def run_ours(args):
         }
         # e2e through the C-ABI host-buffer entry point: every step copies its rho
         # from pinned host memory and its phi back (both inside the timed
-        # region).  Two plans on two streams alternate, so one solve's copies
-        # overlap the other's kernels, as a caller streaming solves would run it.
+        # region).  Three plans on three streams rotate -- one solve's input
+        # copy, another's kernels and a third's output copy in flight at once,
+        # the pipeline a caller streaming solves would run.
         res["e2e"] = None
         if not args.no_e2e:
-            plan2 = fsa.Plan(d.L, n, dt, eps=d.eps, l2_chunk_mb=args.l2_chunk_mb)
-            streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-            plans = [plan, plan2]
-            hin = [torch.from_numpy(rho64).to(tdt).pin_memory() for _ in range(2)]
-            hout = [torch.empty_like(hin[0]).pin_memory() for _ in range(2)]
-            for i in range(2):
+            NS = 3
+            plans = [plan] + [fsa.Plan(d.L, n, dt, eps=d.eps, l2_chunk_mb=args.l2_chunk_mb) for _ in range(NS - 1)]
+            streams = [torch.cuda.Stream() for _ in range(NS)]
+            hin = [torch.from_numpy(rho64).to(tdt).pin_memory() for _ in range(NS)]
+            hout = [torch.empty_like(hin[0]).pin_memory() for _ in range(NS)]
+            for i in range(NS):
                 plans[i].apply_host(hin[i], hout[i], streams[i])
             torch.cuda.synchronize()
             barrier()
-            k = max(4, args.steps // 2) // 2 * 2
+            k = max(6, args.steps // 2) // NS * NS
             t0 = time.perf_counter()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for i in range(k):
-                s_i = streams[i % 2]
-                s_i.wait_event(e0) if i < 2 else None
-                plans[i % 2].apply_host(hin[i % 2], hout[i % 2], s_i)
+                s_i = streams[i % NS]
+                s_i.wait_event(e0) if i < NS else None
+                plans[i % NS].apply_host(hin[i % NS], hout[i % NS], s_i)
             for s_i in streams:
                 stream.wait_stream(s_i)
             e1.record(stream)
@@ -332,8 +333,9 @@ def run_ours(args):
             nb = int(np.prod(n)) * s
             res["e2e"] = {"value": ws * k / (et * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nb,
                           "d2h_bytes_per_step": nb, "ms_per_step": et / k, "host_wall_ms_per_step": wall / k,
-                          "how": "fsa_apply_host, pinned host buffers, 2 plans on 2 streams alternating"}
-            plan2.close()
+                          "how": f"fsa_apply_host, pinned host buffers, {NS} plans on {NS} streams rotating"}
+            for p in plans[1:]:
+                p.close()
         plan.close()
         del rhos, phis
         torch.cuda.empty_cache()
