@@ -215,7 +215,7 @@ def run_ours(args):
     from paper_2504_19410_gb300 import capi
     import workloads as W
 
-    capi.fsa_autotune_set({"auto": 1, "1": 2, "2": 3, "3": 4}[args.kernel_gen])
+    capi.fsa_autotune_set({"auto": 1, "1": 2, "2": 3, "3": 4, "4": 5}[args.kernel_gen])
     d = W.gaussian_sum(seed=2504)  # 8 Gaussians, [-16,16]^3, 256^3, eps = 1
     n = d.n
     rho64 = d.rho()
@@ -599,8 +599,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tiers", default="f32,f64", help="apply tiers to time; the first FP32 one is the headline")
-    ap.add_argument("--kernel-gen", choices=["auto", "1", "2", "3"], default="auto",
-                    help="auto: autotuned per plan; 1 / 2 / 3: force one kernel generation "
+    ap.add_argument("--kernel-gen", choices=["auto", "1", "2", "3", "4"], default="auto",
+                    help="auto: autotuned per plan; 1 / 2 / 3 / 4: force one kernel generation "
                          "(FP64: native for 1, double-word otherwise)")
     ap.add_argument("--l2-chunk-mb", type=int, default=0,
                     help="plane-slab size of the middle passes in MB (0 = library default, -1 = one slab)")

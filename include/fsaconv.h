@@ -198,21 +198,34 @@ fsa_status fsa_apply_profiled(const fsa_plan* plan, const void* rho, void* phi, 
 fsa_status fsa_profiler_read(fsa_profiler* prof, double* pass_ms, double* step_ms, int* steps);
 fsa_status fsa_profiler_destroy(fsa_profiler* prof);
 
-/* Kernel selection.  FP32 passes exist in three generations: 1 = Stockham
+/* Kernel selection.  FP32 passes exist in four generations: 1 = Stockham
  * radix-8 (three shared-memory stages per transform), 2 = two register-resident
  * steps M = R1 x R2 (one exchange per transform), 3 = generation 2 with the
- * middle pass prefetching its next tile asynchronously.  mode 1 (default):
- * each new FP32 plan times every generation for each of its passes on its own
- * workspace at creation and keeps the fastest per (pass, length); choices
- * persist for the process.  mode 0: untuned passes use generation 2.
- * mode 2 / 3 / 4: force generation 1 / 2 / 3 for every FP32 pass.  FP64 plans compute either in native
- * FP64 or in double-word arithmetic (two floats, 48-bit significand, on the
- * FP32 pipes; see fsa_plan_info.arithmetic): one choice per grid shape per
- * process, timed on the first plan of the shape in mode 1, double-word in
- * mode 0, native in mode 2, double-word in modes 3 and 4.
- * FSA_ERR_INVALID_ARG for other modes.  Not thread-safe against concurrent
- * launches. */
+ * middle pass prefetching its next tile asynchronously, 4 = generation 3 with
+ * the row passes staging whole tiles by double-buffered bulk asynchronous
+ * copies.  mode 1 (default): each new FP32 plan times every generation for
+ * each of its passes on its own workspace at creation and keeps the fastest
+ * per (pass, length); choices persist for the process.  mode 0: untuned
+ * passes use generation 2.  mode 2 / 3 / 4 / 5: force generation 1 / 2 / 3 / 4
+ * for every FP32 pass.  FP64 plans compute either in native FP64 or in
+ * double-word arithmetic (two floats, 48-bit significand, on the FP32 pipes;
+ * see fsa_plan_info.arithmetic): one choice per grid shape per process, timed
+ * on the first plan of the shape in mode 1, double-word in mode 0, native in
+ * mode 2, double-word in modes 3 to 5.  FSA_ERR_INVALID_ARG for other modes.
+ * Not thread-safe against concurrent launches. */
 fsa_status fsa_autotune_set(int mode);
+
+/* Device-side wait status (no counterpart in the paper: it reports on the
+ * kernels, not on the method).  Kernels that wait on an mbarrier for their own
+ * asynchronous copies bound every wait (about 1 s); a CTA whose wait gives up
+ * records FSA_ERR_DEVICE_TIMEOUT's cause in a per-device word and returns
+ * instead of hanging, leaving its part of that solve's output undefined.
+ * *code receives the word (0 = no wait gave up; bit 0 = an mbarrier wait
+ * timed out) for `device` (-1 = current); clear != 0 resets it.  Read after
+ * the work of interest has completed (e.g. after synchronizing its stream):
+ * the read does not wait for other streams.  Errors: FSA_ERR_INVALID_ARG
+ * (code NULL), FSA_ERR_CUDA. */
+fsa_status fsa_device_fault(int device, unsigned int* code, int clear);
 
 /* ---------------------------------------------------------------- serving -- */
 

@@ -78,6 +78,7 @@ _PROTOS = {
     "fsa_status_string": (C.c_char_p, [C.c_int]),
     "fsa_last_error": (C.c_char_p, []),
     "fsa_autotune_set": (C.c_int, [C.c_int]),
+    "fsa_device_fault": (C.c_int, [C.c_int, C.POINTER(C.c_uint), C.c_int]),
     "fsa_profiler_create": (C.c_int, [C.POINTER(_VP), C.c_int]),
     "fsa_apply_profiled": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "fsa_profiler_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]),
@@ -200,6 +201,13 @@ def fsa_last_error():
 
 def fsa_autotune_set(mode):
     return check(lib().fsa_autotune_set(int(mode)))
+
+
+def fsa_device_fault(device=-1, clear=False):
+    """The device's wait-timeout word (0 = no bounded device wait gave up)."""
+    code = C.c_uint(0)
+    check(lib().fsa_device_fault(int(device), C.byref(code), 1 if clear else 0))
+    return code.value
 
 
 def fsa_profiler_create(max_steps):

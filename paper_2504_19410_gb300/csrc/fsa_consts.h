@@ -15,8 +15,14 @@ struct Job {
 constexpr int kMaxJobs = 64;
 // The jobs of one launch, passed by value as a kernel parameter (about 1.5 KB):
 // no device allocation, and a captured CUDA graph keeps its own copy.
+// `fault` (device word, may be null): kernels with bounded waits OR a code
+// into it when a wait gives up, then return (kWaitTimeout).
 struct Jobs {
   Job j[kMaxJobs];
   int count;
+  unsigned int* fault;
 };
+constexpr unsigned int kWaitTimeout = 1u;
+// Bound of one wait on an mbarrier, in SM clock cycles (about 1 s).
+constexpr long long kWaitLimitCycles = 2000000000LL;
 }  // namespace fsa

@@ -21,7 +21,7 @@ struct Geometry {
 };
 
 bool supported_n(int n);
-int& autotune_mode();  // fsa_autotune_set: 0 defaults, 1 tune per plan, 2 / 3 / 4 force generation 1 / 2 / 3
+int& autotune_mode();  // fsa_autotune_set: 0 defaults, 1 tune per plan, 2..5 force generation 1..4
 // Kernel generation used for a pass of length M in a dtype: 1 = Stockham
 // radix-8 (passes.cuh), 2 = two-step register kernels (passes2.cuh, FP32).
 int kernel_variant(int pass, int M, fsa_dtype dt);
@@ -42,8 +42,19 @@ struct PassFns {
   cudaError_t (*c2r)(const Jobs&, long long C, cudaStream_t) = nullptr;
 };
 // FP32 generations: 1 Stockham radix-8, 2 two-step register, 3 = 2 with the
-// middle pass prefetching its next tile (cp.async).
-enum Arith { kArithF32G1 = 0, kArithF32G2 = 1, kArithF64 = 2, kArithDW = 3, kArithF32G3 = 4, kNumArith = 5 };
+// middle pass prefetching its next tile (cp.async), 4 = 3 with the row passes
+// staging whole tiles by bulk asynchronous copies.
+enum Arith {
+  kArithF32G1 = 0,
+  kArithF32G2 = 1,
+  kArithF64 = 2,
+  kArithDW = 3,
+  kArithF32G3 = 4,
+  kArithF32G4 = 5,
+  kNumArith = 6
+};
+// This device's fault word (Jobs::fault), allocated by prepare_device.
+unsigned int* device_fault_word();
 void register_pass_fns(int arith, int M, PassFns f);
 const PassFns& pass_fns(int arith, int M);  // prepare == nullptr if absent
 void register_twiddle_init(cudaError_t (*init)());

@@ -111,13 +111,70 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2_row_fwd(const Jobs jobs, long 
 }
 
 // ---------------------------------------------------------------- pass 3 --
+// Lanes of the middle pass: l = column (threadIdx % W), u = sub-transform
+// index.  With R1 even, the two half-warps of warp w hold u = w and its
+// mirror R1 - w (warp 0: u = 0 and R1/2, each its own mirror), so that the
+// spectrum values of k1 and M - k1 -- equal, the spectrum is even -- take one
+// load and a shuffle (mid_scale).
+template <class P> __device__ __forceinline__ int mid_u(int tid) {
+  constexpr int R1 = P::R1;
+  if constexpr (R1 % 2 == 0 && P::R2 % 2 == 0 && Geo2<P>::W == 16) {
+    const int w = tid >> 5, h = (tid >> 4) & 1;
+    return h == 0 ? w : (w == 0 ? R1 / 2 : R1 - w);
+  } else {
+    return tid / Geo2<P>::W;
+  }
+}
+
+// b[s] *= S(k1) for k1 = u + R1 s, s < R2, with S(k1) = srow[min(k1, M - k1) st].
+template <class P>
+__device__ __forceinline__ void mid_scale(float2* b, const float* __restrict__ srow, int u, bool ok, int st) {
+  constexpr int M = P::M, R1 = P::R1, R2 = P::R2, H = R2 / 2;
+  if constexpr (R1 % 2 == 0 && R2 % 2 == 0 && Geo2<P>::W == 16) {
+    // k1 < M/2 for s < R2/2: this thread's own loads
+    float v[H];
+    const float* lo = srow + u * st;
+#pragma unroll
+    for (int s = 0; s < H; ++s) v[s] = ok ? __ldg(lo + (R1 * s) * st) : 0.f;
+#pragma unroll
+    for (int s = 0; s < H; ++s) b[s] = cscale(b[s], v[s]);
+    // s >= R2/2: S(M - k1) with M - k1 = (R1 - u) + R1 (R2 - 1 - s) for u > 0
+    if ((threadIdx.x >> 5) == 0) {  // u = 0 (M - k1 = R1 (R2 - s); Nyquist at s = R2/2) or u = R1/2
+      const float nyq = ok ? __ldg(srow + (M / 2) * st) : 0.f;
+      sfor<H, R2>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        float a;
+        if constexpr (s == H) {
+          a = nyq;
+        } else {
+          a = v[R2 - s];
+        }
+        b[s] = cscale(b[s], u == 0 ? a : v[R2 - 1 - s]);
+      });
+    } else {  // the mirror u' = R1 - u is the other half of this warp
+#pragma unroll
+      for (int s = H; s < R2; ++s) b[s] = cscale(b[s], __shfl_xor_sync(0xffffffffu, v[R2 - 1 - s], 16));
+    }
+  } else {
+    // k1 = u + R1 s: the even spectrum's index min(k1, M - k1) is k1 for
+    // s < R2/2 and M - k1 from s = R2/2 on (u < R1), decided at compile time
+    const float* lo = srow + u * st;
+    const float* hi = srow + (M - u) * st;
+#pragma unroll
+    for (int s = 0; s < R2; ++s) {
+      const float sv = !ok ? 0.f : (2 * s < R2 ? __ldg(lo + (R1 * s) * st) : __ldg(hi - (R1 * s) * st));
+      b[s] = cscale(b[s], sv);
+    }
+  }
+}
+
 template <class P>
 __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2_col_mid(const Jobs jobs, int M2, int planes) {
   using V = float2;
   constexpr int M = P::M, n = M / 2, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
-  const int l = threadIdx.x % W, u = threadIdx.x / W;
+  const int l = threadIdx.x % W, u = mid_u<P>(threadIdx.x);
   const int tiles_per_plane = (M2 + W - 1) / W;
   const long long tpj = (long long)tiles_per_plane * planes;
   const int n2 = M2 / 2;
@@ -143,18 +200,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2_col_mid(con
     for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
     rfft<R2, true>(b);
     // b[s] = transform at k1 = u + R1 s: multiply by the spectrum (real, even)
-    // k1 = u + R1 s: the even spectrum's index min(k1, M - k1) is k1 for
-    // s < R2/2 and M - k1 from s = R2/2 on (u < R1), decided at compile time
-    {
-      const int st = n2 + 1;
-      const float* lo = srow + u * st;
-      const float* hi = srow + (M - u) * st;
-#pragma unroll
-      for (int s = 0; s < R2; ++s) {
-        const float sv = !ok ? 0.f : (2 * s < R2 ? __ldg(lo + (R1 * s) * st) : __ldg(hi - (R1 * s) * st));
-        b[s] = cscale(b[s], sv);
-      }
-    }
+    mid_scale<P>(b, srow, u, ok, n2 + 1);
     // the locations this thread read are the ones it writes: no barrier needed
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
@@ -196,7 +242,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2p_col_mid(co
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   V* stg = sm + M * W;  // staging: [slot][u][l]
-  const int l = threadIdx.x % W, u = threadIdx.x / W;
+  const int l = threadIdx.x % W, u = mid_u<P>(threadIdx.x);
   const int tiles_per_plane = (M2 + W - 1) / W;
   const long long tpj = (long long)tiles_per_plane * planes;
   const long long total = tpj * jobs.count;
@@ -245,18 +291,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2p_col_mid(co
 #pragma unroll
     for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
     rfft<R2, true>(b);
-    // k1 = u + R1 s: the even spectrum's index min(k1, M - k1) is k1 for
-    // s < R2/2 and M - k1 from s = R2/2 on (u < R1), decided at compile time
-    {
-      const int st = n2 + 1;
-      const float* lo = srow + u * st;
-      const float* hi = srow + (M - u) * st;
-#pragma unroll
-      for (int s = 0; s < R2; ++s) {
-        const float sv = !ok ? 0.f : (2 * s < R2 ? __ldg(lo + (R1 * s) * st) : __ldg(hi - (R1 * s) * st));
-        b[s] = cscale(b[s], sv);
-      }
-    }
+    mid_scale<P>(b, srow, u, ok, n2 + 1);
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
     stepA_inv<P, V, true>(

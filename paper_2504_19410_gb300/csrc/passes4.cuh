@@ -1,0 +1,196 @@
+// Fourth-generation row passes (FP32): the two-step register transforms of
+// passes2.cuh, with each tile's input rows brought into shared memory by one
+// bulk asynchronous copy (cp.async.bulk, completion counted in bytes on an
+// mbarrier).  A tile's rows are contiguous in HBM (X rows of n complex
+// values, Y rows of M = 2n), so one instruction moves a whole tile and the
+// copy engine, not the threads, generates the addresses.  One staging buffer
+// per CTA: as soon as every thread has taken the tile out of it (into
+// registers or the exchange tile), the next tile's copy is issued into it and
+// runs under the rest of the current tile's work -- the shared memory of a
+// second buffer would cost resident warps.
+//
+// Every wait on an mbarrier is bounded (kWaitLimitCycles).  A CTA whose wait
+// gives up ORs kWaitTimeout into jobs.fault, waits (bounded again) for the
+// copy it still has in flight and returns; the decision is made CTA-wide
+// (__syncthreads_or) so no thread is left at a barrier.
+#pragma once
+#include "passes2.cuh"
+
+namespace fsa {
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+// orders this thread's earlier shared-memory accesses (generic proxy) before
+// later bulk copies into the same memory (async proxy)
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared, `bytes` a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// true once the phase with this parity has completed; false after the bound
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitLimitCycles) return false;
+  }
+  return true;
+}
+
+// Shared-memory plan of a bulk row pass: the staging buffer of WR input rows
+// (ROW complex values each), the exchange tile of the two-step transform, the
+// mbarrier.
+template <class P, int WR, int ROW> struct BulkGeo {
+  static constexpr int NT = WR * P::T;
+  static constexpr int PITCH = P::R1 * (P::R2 + 1);
+  static constexpr int STG = WR * ROW * 8;
+  static constexpr int XCH = WR * PITCH * 8;
+  static constexpr int BAR = STG + XCH;  // byte offset of the mbarrier
+  static constexpr int SMEM = BAR + 16;
+  static_assert(STG % 16 == 0 && BAR % 8 == 0, "staging alignment");
+};
+
+// Issue (one thread) the bulk copy of tile `tile` (rows row0.. of its job,
+// each ROW complex values) into the staging buffer.
+template <int WR, int ROW>
+__device__ __forceinline__ void issue_rows(const Jobs& jobs, long long tpj, long long rows, long long tile, float2* dst,
+                                           unsigned long long* bar) {
+  const Job& jb = jobs.j[tile / tpj];
+  const long long row0 = (tile % tpj) * WR;
+  const long long nr = rows - row0 < WR ? rows - row0 : WR;
+  const unsigned bytes = (unsigned)(nr * ROW * 8);
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(bar, bytes);
+  bulk_g2s(dst, static_cast<const float2*>(jb.in) + row0 * ROW, bytes, bar);
+}
+
+// After a timeout: record it and drain the copy still in flight.
+__device__ __forceinline__ void bulk_abort(const Jobs& jobs, unsigned long long* bar, int it) {
+  if (threadIdx.x == 0) {
+    if (jobs.fault) atomicOr(jobs.fault, kWaitTimeout);
+    mbar_wait(bar, it & 1);
+  }
+  __syncthreads();
+}
+
+template <int WR, int ROW>
+__device__ __forceinline__ void bulk_prologue(const Jobs& jobs, long long tpj, long long rows, long long total,
+                                              float2* stg, unsigned long long* bar) {
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && blockIdx.x < total) issue_rows<WR, ROW>(jobs, tpj, rows, blockIdx.x, stg, bar);
+}
+
+// ------------------------------------------------------------ row forward --
+template <class P, int WR>
+__global__ void __launch_bounds__(BulkGeo<P, WR, P::M / 2>::NT) k4_row_fwd(const Jobs jobs, long long rows) {
+  using V = float2;
+  constexpr int M = P::M, n = M / 2, R1 = P::R1, R2 = P::R2, T = P::T;
+  using G = BulkGeo<P, WR, n>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* stg = reinterpret_cast<V*>(smraw);
+  V* xch = reinterpret_cast<V*>(smraw + G::STG);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smraw + G::BAR);
+  const int u = threadIdx.x % T, l = threadIdx.x / T;
+  V* line = xch + l * G::PITCH;
+  const long long tpj = (rows + WR - 1) / WR;
+  const long long total = tpj * jobs.count;
+  bulk_prologue<WR, n>(jobs, tpj, rows, total, stg, bar);
+  int it = 0;
+  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x, ++it) {
+    const bool late = !mbar_wait(bar, it & 1);
+    const Job& jb = jobs.j[tile / tpj];
+    const long long row = (tile % tpj) * WR + l;
+    const bool ok = row < rows;
+    V* __restrict__ y = static_cast<V*>(jb.out) + row * M;
+    const V* src = stg + l * n;
+    stepA_fwd<P, V, true>(
+        u,
+        [&](int t, int r) {
+          const int p = t + R2 * r;
+          return p < n ? src[p] : czero<V>();
+        },
+        [&](int q, int t, V v) { line[q * (R2 + 1) + t] = v; });
+    if (__syncthreads_or(late)) {
+      bulk_abort(jobs, bar, it);
+      return;
+    }
+    // every thread is done with the staging buffer: refill it
+    if (threadIdx.x == 0 && tile + gridDim.x < total) issue_rows<WR, n>(jobs, tpj, rows, tile + gridDim.x, stg, bar);
+    V bv[R2];
+#pragma unroll
+    for (int t = 0; t < R2; ++t) bv[t] = line[u * (R2 + 1) + t];
+    rfft<R2, true>(bv);
+    if (ok) {
+#pragma unroll
+      for (int s = 0; s < R2; ++s) y[u + R1 * s] = bv[s];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ row inverse --
+template <class P, int WR>
+__global__ void __launch_bounds__(BulkGeo<P, WR, P::M>::NT) k4_row_inv(const Jobs jobs, long long rows) {
+  using V = float2;
+  constexpr int M = P::M, n = M / 2, R1 = P::R1, R2 = P::R2, T = P::T;
+  using G = BulkGeo<P, WR, M>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* stg = reinterpret_cast<V*>(smraw);
+  V* xch = reinterpret_cast<V*>(smraw + G::STG);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smraw + G::BAR);
+  const int u = threadIdx.x % T, l = threadIdx.x / T;
+  V* line = xch + l * G::PITCH;
+  const long long tpj = (rows + WR - 1) / WR;
+  const long long total = tpj * jobs.count;
+  bulk_prologue<WR, M>(jobs, tpj, rows, total, stg, bar);
+  int it = 0;
+  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x, ++it) {
+    const bool late = !mbar_wait(bar, it & 1);
+    const Job& jb = jobs.j[tile / tpj];
+    const long long row = (tile % tpj) * WR + l;
+    const bool ok = row < rows;
+    V* __restrict__ x = static_cast<V*>(jb.out) + row * n;
+    const V* src = stg + l * M;
+    V bv[R2];
+#pragma unroll
+    for (int s = 0; s < R2; ++s) bv[s] = src[u + R1 * s];
+    stepB_inv<P, V>(u, bv, [&](int q, int t, V v) { line[q * (R2 + 1) + t] = v; });
+    if (__syncthreads_or(late)) {
+      bulk_abort(jobs, bar, it);
+      return;
+    }
+    if (threadIdx.x == 0 && tile + gridDim.x < total) issue_rows<WR, M>(jobs, tpj, rows, tile + gridDim.x, stg, bar);
+    stepA_inv<P, V, true>(
+        u, [&](int q, int t) { return line[q * (R2 + 1) + t]; },
+        [&](int t, int r, V v) {
+          const int p = t + R2 * r;
+          if (p < n && ok) x[p] = v;
+        });
+    __syncthreads();
+  }
+}
+
+}  // namespace fsa

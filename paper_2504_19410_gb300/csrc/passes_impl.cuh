@@ -8,6 +8,7 @@
 #include "fsa_internal.h"
 #include "passes.cuh"
 #include "passes2.cuh"
+#include "passes4.cuh"
 
 namespace fsa {
 
@@ -94,7 +95,38 @@ template <int M> struct Inst2 {
     set((const void*)k2p_col_mid<P>, G::SM_STRIDED + Stage2<P>::BYTES);
     set((const void*)k2p_row_fwd<P, 16>, RowGeo<P, 16>::SM_FWD);
     set((const void*)k2p_row_inv<P, 8>, RowGeo<P, 8>::SM_INV);
+    set((const void*)k4_row_fwd<P, WRF>, GF::SMEM);
+    set((const void*)k4_row_inv<P, WRI>, GI::SMEM);
     return e;
+  }
+  // bulk-copy row passes: rows per tile, fewer for the longest lines
+  static constexpr int WRF = 4;
+  static constexpr int WRI = M >= 1024 ? 4 : 8;
+  using GF = BulkGeo<P, WRF, M / 2>;
+  using GI = BulkGeo<P, WRI, M>;
+  // bulk copies need 16-byte aligned sources (row offsets are: n is even)
+  static bool inputs_aligned(const Jobs& jobs) {
+    for (int i = 0; i < jobs.count; ++i)
+      if (reinterpret_cast<uintptr_t>(jobs.j[i].in) % 16 != 0) return false;
+    return true;
+  }
+  static cudaError_t rowf_b(const Jobs& jobs, long long rows, cudaStream_t s) {
+    if (!inputs_aligned(jobs)) return rowf_p(jobs, rows, s);
+    Jobs jj = jobs;
+    jj.fault = device_fault_word();
+    const long long tiles = (rows + WRF - 1) / WRF * jobs.count;
+    auto f = k4_row_fwd<P, WRF>;
+    f<<<persistent_grid((const void*)f, GF::NT, GF::SMEM, tiles), GF::NT, GF::SMEM, s>>>(jj, rows);
+    return cudaGetLastError();
+  }
+  static cudaError_t rowi_b(const Jobs& jobs, long long rows, cudaStream_t s) {
+    if (!inputs_aligned(jobs)) return rowi_p(jobs, rows, s);
+    Jobs jj = jobs;
+    jj.fault = device_fault_word();
+    const long long tiles = (rows + WRI - 1) / WRI * jobs.count;
+    auto f = k4_row_inv<P, WRI>;
+    f<<<persistent_grid((const void*)f, GI::NT, GI::SMEM, tiles), GI::NT, GI::SMEM, s>>>(jj, rows);
+    return cudaGetLastError();
   }
   static cudaError_t rowf_p(const Jobs& jobs, long long rows, cudaStream_t s) {
     using RG = RowGeo<P, 16>;
@@ -214,4 +246,7 @@ static cudaError_t init_tu_twiddles() {
     f3.rowf = &fsa::detail::Inst2<M>::rowf_p;                                         \
     f3.rowi = &fsa::detail::Inst2<M>::rowi_p;                                         \
     fsa::register_pass_fns(fsa::kArithF32G3, M, f3);                                  \
+    f3.rowf = &fsa::detail::Inst2<M>::rowf_b;                                         \
+    f3.rowi = &fsa::detail::Inst2<M>::rowi_b;                                         \
+    fsa::register_pass_fns(fsa::kArithF32G4, M, f3);                                  \
   }

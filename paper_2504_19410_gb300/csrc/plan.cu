@@ -20,7 +20,15 @@ thread_local std::string t_last_error;
 std::mutex g_init_mu;
 std::set<std::pair<int, int>> g_prepared;  // (device, key) pairs already prepared
 std::set<int> g_tw_ready;                  // devices with twiddle tables filled
+constexpr int kMaxDevices = 64;
+unsigned int* g_fault[kMaxDevices] = {};    // per-device fault word (Jobs::fault)
 }  // namespace
+
+unsigned int* device_fault_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  return g_fault[dev];
+}
 
 fsa_status set_error(fsa_status st, const std::string& msg) {
   t_last_error = msg;
@@ -80,6 +88,7 @@ int kernel_variant(int pass, int M, fsa_dtype dt) {
   if (mode == 2) return 1;
   if (mode == 3) return 2;
   if (mode == 4) return 3;
+  if (mode == 5) return 4;
   const int v = (M >= 0 && M <= 1024) ? g_variant[pass][M][dt].load(std::memory_order_relaxed) : 0;
   return v ? v : 2;
 }
@@ -142,7 +151,7 @@ cudaError_t init_all_twiddles() {
 template <typename V> int arith_for(int pass, int M) {
   if constexpr (std::is_same<V, float2>::value) {
     const int v = kernel_variant(pass, M, FSA_F32);
-    return v == 3 ? kArithF32G3 : (v == 2 ? kArithF32G2 : kArithF32G1);
+    return v == 4 ? kArithF32G4 : (v == 3 ? kArithF32G3 : (v == 2 ? kArithF32G2 : kArithF32G1));
   }
   else if constexpr (std::is_same<V, double2>::value)
     return kArithF64;
@@ -291,6 +300,13 @@ fsa_status prepare_device(int dev, fsa_dtype dt, const int* n) {
     cudaError_t e = init_all_twiddles();
     if (e == cudaSuccess) e = tensorgen_init_twiddles();
     if (e != cudaSuccess) return cuda_error(e, "twiddle table upload");
+    if (dev >= 0 && dev < kMaxDevices && !g_fault[dev]) {
+      unsigned int* w = nullptr;
+      e = cudaMalloc(&w, sizeof(unsigned int));
+      if (e == cudaSuccess) e = cudaMemset(w, 0, sizeof(unsigned int));
+      if (e != cudaSuccess) return cuda_error(e, "fault word");
+      g_fault[dev] = w;
+    }
     g_tw_ready.insert(dev);
   }
   for (int j = 0; j < 3; ++j) {
@@ -298,8 +314,8 @@ fsa_status prepare_device(int dev, fsa_dtype dt, const int* n) {
     const int key = M * 4 + (int)dt;
     if (g_prepared.count({dev, key})) continue;
     cudaError_t e = cudaSuccess;
-    const int f32a[3] = {kArithF32G1, kArithF32G2, kArithF32G3};
-    const int f64a[3] = {kArithF64, kArithDW, kArithDW};
+    const int f32a[4] = {kArithF32G1, kArithF32G2, kArithF32G3, kArithF32G4};
+    const int f64a[4] = {kArithF64, kArithDW, kArithDW, kArithDW};
     for (int a : (dt == FSA_F32 ? f32a : f64a)) {
       const PassFns& f = pass_fns(a, M);
       if (!f.prepare) return set_error(FSA_ERR_UNSUPPORTED, "no kernels registered for this length");
@@ -366,8 +382,28 @@ const char* fsa_status_string(fsa_status s) {
 
 const char* fsa_last_error(void) { return t_last_error.c_str(); }
 
+fsa_status fsa_device_fault(int device, unsigned int* code, int clear) {
+  if (!code) return set_error(FSA_ERR_INVALID_ARG, "fsa_device_fault: NULL code");
+  *code = 0;
+  if (device < 0) {
+    if (cudaGetDevice(&device) != cudaSuccess) return set_error(FSA_ERR_CUDA, "fsa_device_fault: no device");
+  }
+  unsigned int* w = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    if (device < kMaxDevices) w = g_fault[device];
+  }
+  if (!w) return FSA_OK;  // nothing ran on this device yet
+  DeviceGuard dg;
+  cudaError_t e = dg.set(device);
+  if (e == cudaSuccess) e = cudaMemcpy(code, w, sizeof(unsigned int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && clear && *code) e = cudaMemset(w, 0, sizeof(unsigned int));
+  if (e != cudaSuccess) return cuda_error(e, "fsa_device_fault");
+  return FSA_OK;
+}
+
 fsa_status fsa_autotune_set(int mode) {
-  if (mode < 0 || mode > 4) return set_error(FSA_ERR_INVALID_ARG, "fsa_autotune_set: mode must be 0..4");
+  if (mode < 0 || mode > 5) return set_error(FSA_ERR_INVALID_ARG, "fsa_autotune_set: mode must be 0..5");
   autotune_mode() = mode;
   return FSA_OK;
 }
@@ -502,7 +538,7 @@ cudaError_t tune_plan(fsa_plan* p) {
   Jobs j{};
   j.count = 1;
   auto run = [&](int k, int v) -> cudaError_t {
-    const PassFns& f = pass_fns(v == 3 ? kArithF32G3 : (v == 2 ? kArithF32G2 : kArithF32G1), Ms[k]);
+    const PassFns& f = pass_fns(v == 4 ? kArithF32G4 : (v == 3 ? kArithF32G3 : (v == 2 ? kArithF32G2 : kArithF32G1)), Ms[k]);
     switch (k) {
       case kR2C: j.j[0] = Job{Y, X, nullptr}; return f.r2c(j, C, s);
       case kRowFwd: j.j[0] = Job{X, Y, nullptr}; return f.rowf(j, rows, s);
@@ -515,7 +551,7 @@ cudaError_t tune_plan(fsa_plan* p) {
     if (g_variant[k][Ms[k]][FSA_F32].load() != 0) continue;
     float best = 1e30f;
     int pick = 2;
-    for (int v = 1; v <= 3 && e == cudaSuccess; ++v) {
+    for (int v = 1; v <= 4 && e == cudaSuccess; ++v) {
       e = run(k, v);  // warm-up
       float tmin = 1e30f;
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {

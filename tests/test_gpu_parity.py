@@ -29,15 +29,21 @@ def lib():
     return fsa
 
 
-@pytest.fixture(params=["gen1", "gen2", "gen3"])
+@pytest.fixture(params=["gen1", "gen2", "gen3", "gen4"])
 def gen(request, lib):
     """Force one kernel generation for a test: gen1 = Stockham radix-8 (FP32) and
     native FP64; gen2 = two-step register kernels (FP32) and double-word FP64;
-    gen3 = gen2 with the prefetching middle pass (FP32) and double-word FP64."""
+    gen3 = gen2 with the prefetching middle pass (FP32) and double-word FP64;
+    gen4 = gen3 with bulk-copy row passes (FP32) and double-word FP64.  No
+    bounded device wait may have given up during the test."""
+    import torch
     from paper_2504_19410_gb300 import capi
-    capi.fsa_autotune_set({"gen1": 2, "gen2": 3, "gen3": 4}[request.param])
+    capi.fsa_device_fault(clear=True)
+    capi.fsa_autotune_set({"gen1": 2, "gen2": 3, "gen3": 4, "gen4": 5}[request.param])
     yield request.param
     capi.fsa_autotune_set(1)
+    torch.cuda.synchronize()
+    assert capi.fsa_device_fault(clear=True) == 0
 
 
 def to_dev(rho, dt):
