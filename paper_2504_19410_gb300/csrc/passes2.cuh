@@ -126,45 +126,52 @@ template <class P> __device__ __forceinline__ int mid_u(int tid) {
   }
 }
 
-// b[s] *= S(k1) for k1 = u + R1 s, s < R2, with S(k1) = srow[min(k1, M - k1) st].
+// The spectrum values S(k1) of one thread, k1 = u + R1 s (s < R2), with
+// S(k1) = srow[min(k1, M - k1) st].  mid_load issues the loads (so their
+// latency can pass under the forward transform), mid_apply multiplies.
+template <class P> struct MidSpec {
+  static constexpr bool PAIRED = P::R1 % 2 == 0 && P::R2 % 2 == 0 && Geo2<P>::W == 16;
+  static constexpr int NV = PAIRED ? P::R2 / 2 + 1 : P::R2;  // paired: s < R2/2, then the Nyquist value
+  float v[NV];
+};
+
 template <class P>
-__device__ __forceinline__ void mid_scale(float2* b, const float* __restrict__ srow, int u, bool ok, int st) {
+__device__ __forceinline__ void mid_load(MidSpec<P>& sp, const float* __restrict__ srow, int u, bool ok, int st) {
   constexpr int M = P::M, R1 = P::R1, R2 = P::R2, H = R2 / 2;
-  if constexpr (R1 % 2 == 0 && R2 % 2 == 0 && Geo2<P>::W == 16) {
-    // k1 < M/2 for s < R2/2: this thread's own loads
-    float v[H];
-    const float* lo = srow + u * st;
+  const float* lo = srow + u * st;
+  if constexpr (MidSpec<P>::PAIRED) {
+    // k1 < M/2 for s < R2/2: this thread's own loads; v[H] = S(M/2) for u = 0
 #pragma unroll
-    for (int s = 0; s < H; ++s) v[s] = ok ? __ldg(lo + (R1 * s) * st) : 0.f;
+    for (int s = 0; s < H; ++s) sp.v[s] = ok ? __ldg(lo + (R1 * s) * st) : 0.f;
+    sp.v[H] = (ok && (threadIdx.x >> 5) == 0) ? __ldg(srow + (M / 2) * st) : 0.f;
+  } else {
+    // the even spectrum's index min(k1, M - k1) is k1 for s < R2/2 and M - k1
+    // from s = R2/2 on (u < R1), decided at compile time
+    const float* hi = srow + (M - u) * st;
 #pragma unroll
-    for (int s = 0; s < H; ++s) b[s] = cscale(b[s], v[s]);
+    for (int s = 0; s < R2; ++s) sp.v[s] = !ok ? 0.f : (2 * s < R2 ? __ldg(lo + (R1 * s) * st) : __ldg(hi - (R1 * s) * st));
+  }
+}
+
+template <class P> __device__ __forceinline__ void mid_apply(float2* b, const MidSpec<P>& sp, int u) {
+  constexpr int R1 = P::R1, R2 = P::R2, H = R2 / 2;
+  if constexpr (MidSpec<P>::PAIRED) {
+#pragma unroll
+    for (int s = 0; s < H; ++s) b[s] = cscale(b[s], sp.v[s]);
     // s >= R2/2: S(M - k1) with M - k1 = (R1 - u) + R1 (R2 - 1 - s) for u > 0
     if ((threadIdx.x >> 5) == 0) {  // u = 0 (M - k1 = R1 (R2 - s); Nyquist at s = R2/2) or u = R1/2
-      const float nyq = ok ? __ldg(srow + (M / 2) * st) : 0.f;
       sfor<H, R2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
-        float a;
-        if constexpr (s == H) {
-          a = nyq;
-        } else {
-          a = v[R2 - s];
-        }
-        b[s] = cscale(b[s], u == 0 ? a : v[R2 - 1 - s]);
+        const float a = sp.v[s == H ? H : R2 - s];
+        b[s] = cscale(b[s], u == 0 ? a : sp.v[R2 - 1 - s]);
       });
     } else {  // the mirror u' = R1 - u is the other half of this warp
 #pragma unroll
-      for (int s = H; s < R2; ++s) b[s] = cscale(b[s], __shfl_xor_sync(0xffffffffu, v[R2 - 1 - s], 16));
+      for (int s = H; s < R2; ++s) b[s] = cscale(b[s], __shfl_xor_sync(0xffffffffu, sp.v[R2 - 1 - s], 16));
     }
   } else {
-    // k1 = u + R1 s: the even spectrum's index min(k1, M - k1) is k1 for
-    // s < R2/2 and M - k1 from s = R2/2 on (u < R1), decided at compile time
-    const float* lo = srow + u * st;
-    const float* hi = srow + (M - u) * st;
 #pragma unroll
-    for (int s = 0; s < R2; ++s) {
-      const float sv = !ok ? 0.f : (2 * s < R2 ? __ldg(lo + (R1 * s) * st) : __ldg(hi - (R1 * s) * st));
-      b[s] = cscale(b[s], sv);
-    }
+    for (int s = 0; s < R2; ++s) b[s] = cscale(b[s], sp.v[s]);
   }
 }
 
@@ -195,12 +202,14 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2_col_mid(con
         },
         [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
+    MidSpec<P> sp;
+    mid_load<P>(sp, srow, u, ok, n2 + 1);
     V b[R2];
 #pragma unroll
     for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
     rfft<R2, true>(b);
     // b[s] = transform at k1 = u + R1 s: multiply by the spectrum (real, even)
-    mid_scale<P>(b, srow, u, ok, n2 + 1);
+    mid_apply<P>(b, sp, u);
     // the locations this thread read are the ones it writes: no barrier needed
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
@@ -287,11 +296,13 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2p_col_mid(co
     // this thread's staged elements are consumed: fetch the next tile's
     if (tile + gridDim.x < total) issue(tile + gridDim.x);
     __syncthreads();
+    MidSpec<P> sp;
+    mid_load<P>(sp, srow, u, ok, n2 + 1);
     V b[R2];
 #pragma unroll
     for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
     rfft<R2, true>(b);
-    mid_scale<P>(b, srow, u, ok, n2 + 1);
+    mid_apply<P>(b, sp, u);
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
     stepA_inv<P, V, true>(
