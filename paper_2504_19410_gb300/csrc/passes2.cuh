@@ -66,8 +66,9 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB) k2_r2c_ax0(const J
       const V zk = sm[k * W + l];
       const V zm = sm[((M - k) % M) * W + l];
       if (ok) {
-        X[(long long)k * C + c] = mk(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-        X[(long long)k * C + c + 1] = mk(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+        // columns c and c + 1 are adjacent (c even, C even): one 16-byte store
+        *reinterpret_cast<float4*>(X + (long long)k * C + c) =
+            make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y), 0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
       }
     }
     __syncthreads();
@@ -489,8 +490,9 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2_c2r_ax0(const Jobs jobs, long 
       if (ok) {
         const bool lo = k <= n;
         const long long kk = lo ? k : M - k;
-        const V a = X[kk * C + c], bb = X[kk * C + c + 1];
-        z = lo ? mk(a.x - bb.y, a.y + bb.x) : mk(a.x + bb.y, bb.x - a.y);
+        // columns c and c + 1 are adjacent (c even, C even): one 16-byte load
+        const float4 ab = *reinterpret_cast<const float4*>(X + kk * C + c);
+        z = lo ? mk(ab.x - ab.w, ab.y + ab.z) : mk(ab.x + ab.w, ab.z - ab.y);
       }
       b[s] = z;
     }
