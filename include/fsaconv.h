@@ -227,6 +227,16 @@ fsa_status fsa_autotune_set(int mode);
  * (code NULL), FSA_ERR_CUDA. */
 fsa_status fsa_device_fault(int device, unsigned int* code, int clear);
 
+/* Self-test of the bounded device-side wait (no counterpart in the paper: it
+ * checks the library's own safeguard).  On `device` (-1 = current) one CTA
+ * waits, with a bound of about 1 ms, on an mbarrier that nothing completes,
+ * takes the give-up path of the bulk-copy row passes (records the timeout in
+ * the device's fault word, returns) and the host reads the word: *code = 1
+ * (bit 0, an mbarrier wait timed out) when the safeguard works.  The word is
+ * cleared again before return.  Synchronous; nothing faults or hangs.
+ * Errors: FSA_ERR_INVALID_ARG (code NULL), FSA_ERR_CUDA. */
+fsa_status fsa_wait_selftest(int device, unsigned int* code);
+
 /* ---------------------------------------------------------------- serving -- */
 
 typedef struct fsa_server fsa_server;

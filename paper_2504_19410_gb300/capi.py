@@ -79,6 +79,7 @@ _PROTOS = {
     "fsa_last_error": (C.c_char_p, []),
     "fsa_autotune_set": (C.c_int, [C.c_int]),
     "fsa_device_fault": (C.c_int, [C.c_int, C.POINTER(C.c_uint), C.c_int]),
+    "fsa_wait_selftest": (C.c_int, [C.c_int, C.POINTER(C.c_uint)]),
     "fsa_profiler_create": (C.c_int, [C.POINTER(_VP), C.c_int]),
     "fsa_apply_profiled": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "fsa_profiler_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]),
@@ -207,6 +208,14 @@ def fsa_device_fault(device=-1, clear=False):
     """The device's wait-timeout word (0 = no bounded device wait gave up)."""
     code = C.c_uint(0)
     check(lib().fsa_device_fault(int(device), C.byref(code), 1 if clear else 0))
+    return code.value
+
+
+def fsa_wait_selftest(device=-1):
+    """Runs one bounded device wait that nothing completes; returns the fault
+    word it left (1 = the wait gave up and was recorded)."""
+    code = C.c_uint(0)
+    check(lib().fsa_wait_selftest(int(device), C.byref(code)))
     return code.value
 
 

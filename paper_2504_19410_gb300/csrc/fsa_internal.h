@@ -53,8 +53,10 @@ enum Arith {
   kArithF32G4 = 5,
   kNumArith = 6
 };
-// This device's fault word (Jobs::fault), allocated by prepare_device.
+// This device's fault word (Jobs::fault), allocated by prepare_device;
+// ensure_device_fault_word allocates it if needed (current device).
 unsigned int* device_fault_word();
+unsigned int* ensure_device_fault_word();
 void register_pass_fns(int arith, int M, PassFns f);
 const PassFns& pass_fns(int arith, int M);  // prepare == nullptr if absent
 void register_twiddle_init(cudaError_t (*init)());

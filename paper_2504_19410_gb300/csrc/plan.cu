@@ -24,6 +24,25 @@ constexpr int kMaxDevices = 64;
 unsigned int* g_fault[kMaxDevices] = {};    // per-device fault word (Jobs::fault)
 }  // namespace
 
+// Allocates the device's fault word once (device current, g_init_mu held).
+cudaError_t ensure_fault_word_locked(int dev) {
+  if (dev < 0 || dev >= kMaxDevices || g_fault[dev]) return cudaSuccess;
+  unsigned int* w = nullptr;
+  cudaError_t e = cudaMalloc(&w, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(w, 0, sizeof(unsigned int));
+  if (e != cudaSuccess) return e;
+  g_fault[dev] = w;
+  return cudaSuccess;
+}
+
+unsigned int* ensure_device_fault_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (ensure_fault_word_locked(dev) != cudaSuccess) return nullptr;
+  return g_fault[dev];
+}
+
 unsigned int* device_fault_word() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
@@ -300,13 +319,8 @@ fsa_status prepare_device(int dev, fsa_dtype dt, const int* n) {
     cudaError_t e = init_all_twiddles();
     if (e == cudaSuccess) e = tensorgen_init_twiddles();
     if (e != cudaSuccess) return cuda_error(e, "twiddle table upload");
-    if (dev >= 0 && dev < kMaxDevices && !g_fault[dev]) {
-      unsigned int* w = nullptr;
-      e = cudaMalloc(&w, sizeof(unsigned int));
-      if (e == cudaSuccess) e = cudaMemset(w, 0, sizeof(unsigned int));
-      if (e != cudaSuccess) return cuda_error(e, "fault word");
-      g_fault[dev] = w;
-    }
+    e = ensure_fault_word_locked(dev);
+    if (e != cudaSuccess) return cuda_error(e, "fault word");
     g_tw_ready.insert(dev);
   }
   for (int j = 0; j < 3; ++j) {
