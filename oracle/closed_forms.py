@@ -1,4 +1,5 @@
-"""Exact Coulomb potentials (kernel 1/(4 pi r)) of the synthetic densities.
+"""Exact potentials of the synthetic densities: Coulomb (kernel 1/(4 pi r)) and
+3-D biharmonic (kernel r/(8 pi)).
 
 Test infrastructure.  These are not steps of the FSA method: they are the
 exact answers the method approximates, derived from the densities'
@@ -18,6 +19,17 @@ print them).
 * Example 1 Case II: rho = -Laplacian(Phi0) + shifted copy, so
   Phi = Phi0(x) + Phi0(x - x0) exactly (the Coulomb kernel is the Green's
   function of -Laplacian in 3-D).
+
+Exact biharmonic potentials (kernel r/(8 pi), Example 4):
+* Isotropic Gaussian a exp(-|x-c|^2/(2 w^2)) = q times the N(c, w^2 I)
+  density, q = a (2 pi w^2)^{3/2}, so Phi(x) = q/(8 pi) E|x - c - w Z| with Z
+  a standard normal 3-vector.  |x - c - w Z| / w is a non-central chi variable
+  with 3 degrees of freedom and parameter lam = |x - c| / w, whose mean is
+      sqrt(2/pi) exp(-lam^2/2) + (lam + 1/lam) erf(lam/sqrt2)
+  (value 2 sqrt(2/pi) at lam = 0).  Pinned in the tests by the radial
+  integral Phi(r) = (a/4) int_0^inf t^2 exp(-t^2/(2 w^2))
+  ((r+t)^3 - |r-t|^3) / (3 r t) dt (the angular mean of |x - y| over the
+  sphere |y| = t, done by hand), evaluated by quadrature.
 """
 from __future__ import annotations
 
@@ -116,4 +128,30 @@ def case2_potential(c):
         Y = (x[1] - ctr[1])[None, :, None]
         Z = (x[2] - ctr[2])[None, None, :]
         out += np.exp(-(X ** 2 + Y ** 2 + Z ** 2 / c.gamma3 ** 2) / c.sigma2)
+    return out
+
+
+def biharmonic_iso_gaussian_r(amp, w, r):
+    """Biharmonic potential of amp exp(-|x|^2/(2 w^2)) at distances r (array)."""
+    r = np.asarray(r, dtype=np.float64)
+    q = amp * (2.0 * math.pi * w * w) ** 1.5
+    lam = r / w
+    mean = np.empty_like(lam)
+    nz = lam > 1e-8
+    ln = lam[nz]
+    mean[nz] = math.sqrt(2.0 / math.pi) * np.exp(-0.5 * ln * ln) + (ln + 1.0 / ln) * sp.erf(ln / math.sqrt(2.0))
+    mean[~nz] = 2.0 * math.sqrt(2.0 / math.pi)
+    return q * w * mean / (8.0 * math.pi)
+
+
+def biharmonic_density_potential(d):
+    """Exact biharmonic potential of a workloads.Density of isotropic terms."""
+    x = grid_axes(d.L, d.n)
+    out = np.zeros(d.n)
+    for g in d.terms:
+        s = g.sigma
+        assert s[0] == s[1] == s[2], "isotropic terms only"
+        r = np.sqrt((x[0] - g.center[0])[:, None, None] ** 2 + (x[1] - g.center[1])[None, :, None] ** 2
+                    + (x[2] - g.center[2])[None, None, :] ** 2)
+        out += biharmonic_iso_gaussian_r(g.amp, s[0], r)
     return out

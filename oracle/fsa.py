@@ -65,10 +65,81 @@ def What_by_quadrature(k, eps):
     return val
 
 
-def appendix_b_bound(R0, eps):
-    """App. B: int_{R0}^inf |U - U^eps| r^2 dr = R0^2 f(c), c = R0/eps,
-    f(c) = (1/(4 pi c^2)) int_c^inf s erfc(s) ds (3-D Coulomb)."""
+def biharmonic3d_U(r):
+    """3-D biharmonic kernel U(r) = r/(8 pi) (Table 1; Example 4)."""
+    return r / (8.0 * math.pi)
+
+
+def biharmonic3d_Ueps(r, eps):
+    """Far-field smooth approximation U^eps(r) = r erf(r/eps)/(8 pi) (Table 1,
+    3-D biharmonic row).  It vanishes at r = 0."""
+    r = np.asarray(r, dtype=np.float64)
+    return r * sp.erf(r / eps) / (8.0 * math.pi)
+
+
+def biharmonic3d_What(k, eps):
+    """Whole-space Fourier transform of U - U^eps (Table 1, 3-D biharmonic
+    row): (-8 + exp(-k^2 eps^2/4) (8 + 2 k^2 eps^2 + k^4 eps^4)) / (8 k^4).
+    With x = k^2 eps^2 / 4 this is (eps^4/16) g(x),
+    g(x) = (exp(-x) (1 + x + 2 x^2) - 1) / x^2, which loses all its digits to
+    cancellation as x -> 0.  For x < 1 g is summed from its Taylor series
+    g(x) = sum_{j>=2} c_j x^(j-2), c_j = (-1)^j (1/j! - 1/(j-1)! + 2/(j-2)!)
+    (the product of the exponential series with 1 + x + 2 x^2), 30 terms;
+    g(0) = 3/2, so the k = 0 value is 3 eps^4 / 32.  The paper gives only the
+    closed form."""
+    k = np.asarray(k, dtype=np.float64)
+    x = (k * eps) ** 2 / 4.0
+    g = np.empty_like(x)
+    small = x < 1.0
+    xs = x[small]
+    acc = np.zeros_like(xs)
+    for j in range(31, 1, -1):  # Horner, highest power first
+        cj = (-1) ** j * (1.0 / math.factorial(j) - 1.0 / math.factorial(j - 1) + 2.0 / math.factorial(j - 2))
+        acc = acc * xs + cj
+    g[small] = acc
+    xl = x[~small]
+    g[~small] = (np.exp(-xl) * (1.0 + xl + 2.0 * xl * xl) - 1.0) / (xl * xl)
+    return eps ** 4 / 16.0 * g
+
+
+# kernel name -> names of its (U^eps, What) of Table 1, looked up at call time
+KERNELS = {
+    "coulomb3d": ("coulomb3d_Ueps", "coulomb3d_What"),
+    "biharmonic3d": ("biharmonic3d_Ueps", "biharmonic3d_What"),
+}
+
+
+def kernel_fns(kernel):
+    """(U^eps, What) of a kernel of Table 1."""
+    u, w = KERNELS[kernel]
+    return globals()[u], globals()[w]
+
+
+def What_by_quadrature_kernel(k, eps, kernel):
+    """Eq. (Fourier-Symmetric), d = 3, by adaptive quadrature for either
+    kernel: 4 pi int_0^inf (U - U^eps)(r) sin(kr)/(kr) r^2 dr with
+    (U - U^eps)(r) = erfc(r/eps) / (4 pi r) (Coulomb) or
+    r erfc(r/eps) / (8 pi) (biharmonic).  Pins the closed forms."""
+    if kernel == "coulomb3d":
+        return What_by_quadrature(k, eps)
+    if k == 0:
+        f = lambda r: 0.5 * sp.erfc(r / eps) * r ** 3
+    else:
+        f = lambda r: 0.5 * sp.erfc(r / eps) * r * r * math.sin(k * r) / k
+    val, _ = si.quad(f, 0.0, 12.0 * eps, limit=400, epsabs=0.0, epsrel=1e-13)
+    return val
+
+
+def appendix_b_bound(R0, eps, kernel="coulomb3d"):
+    """App. B: the far-field condition int_{R0}^inf |U - U^eps| r^2 dr.
+    3-D Coulomb: R0^2 f(c), c = R0/eps, f(c) = (1/(4 pi c^2)) int_c^inf
+    s erfc(s) ds, as App. B states it.  3-D biharmonic (App. B does not treat
+    it; the same integral of its U - U^eps = r erfc(r/eps)/(8 pi)):
+    (eps^4 / (8 pi)) int_c^inf s^3 erfc(s) ds."""
     c = R0 / eps
+    if kernel == "biharmonic3d":
+        tail, _ = si.quad(lambda s: s ** 3 * sp.erfc(s), c, np.inf, epsabs=0.0, epsrel=1e-12, limit=200)
+        return eps ** 4 * tail / (8.0 * math.pi)
     tail, _ = si.quad(lambda s: s * sp.erfc(s), c, np.inf, epsabs=0.0, epsrel=1e-12, limit=200)
     return R0 * R0 * tail / (4.0 * math.pi * c * c)
 
@@ -86,39 +157,39 @@ def mesh_steps(L, n):
     return [2.0 * L[j] / n[j] for j in range(3)]
 
 
-def tensor_T1(L, n, eps):
+def tensor_T1(L, n, eps, kernel="coulomb3d"):
     """T^(1) on the doubled grid: T^(1)_o = h_0 h_1 h_2 U^eps(|(o_0 h_0, o_1 h_1,
     o_2 h_2)|) (Sec. 2.1, Eq. Tensor1; Sec. 2.4, Eq. TensorAnis first term)."""
     h = mesh_steps(L, n)
     x = [_offsets(n[j]) * h[j] for j in range(3)]
     r = np.sqrt(x[0][:, None, None] ** 2 + x[1][None, :, None] ** 2 + x[2][None, None, :] ** 2)
-    return h[0] * h[1] * h[2] * coulomb3d_Ueps(r, eps)
+    return h[0] * h[1] * h[2] * kernel_fns(kernel)[0](r, eps)
 
 
-def fourier_W(L, n, eps):
+def fourier_W(L, n, eps, kernel="coulomb3d"):
     """W on the Fourier mesh Lambda: mu_{p,j} = pi p_j / (2 L_j),
     p_j = -n_j .. n_j - 1 (Sec. 2.2, Eqs. DisFourierSeries, Wk; Sec. 2.4,
     Eq. WkAnis), with the bounded-domain transform replaced by the whole-space
     one (Eq. FouTran), i.e. W(mu) = What(|mu|).  Stored in FFT order."""
     mu = [math.pi * _offsets(n[j]) / (2.0 * L[j]) for j in range(3)]
     k = np.sqrt(mu[0][:, None, None] ** 2 + mu[1][None, :, None] ** 2 + mu[2][None, None, :] ** 2)
-    return coulomb3d_What(k, eps)
+    return kernel_fns(kernel)[1](k, eps)
 
 
-def tensor_T2(L, n, eps, return_imag=False):
+def tensor_T2(L, n, eps, return_imag=False, kernel="coulomb3d"):
     """T^(2)_o = (2N)^{-d} sum_p W(mu_p) exp(2 pi i p.o / 2N) (Sec. 2.2,
     Eq. Tensor2; Eq. TensorAnis second term): numpy's ifftn carries exactly
     this sign and normalisation.  The imaginary part vanishes in exact
     arithmetic (W is real and even); its max is returned on request."""
-    T2 = np.fft.ifftn(fourier_W(L, n, eps))
+    T2 = np.fft.ifftn(fourier_W(L, n, eps, kernel))
     if return_imag:
         return T2.real.copy(), float(np.abs(T2.imag).max())
     return T2.real.copy()
 
 
-def tensor_T(L, n, eps):
+def tensor_T(L, n, eps, kernel="coulomb3d"):
     """T = T^(1) + T^(2) (Sec. 2.3, Eq. DiscConv)."""
-    return tensor_T1(L, n, eps) + tensor_T2(L, n, eps)
+    return tensor_T1(L, n, eps, kernel) + tensor_T2(L, n, eps, kernel=kernel)
 
 
 def spectrum(T):
@@ -188,6 +259,6 @@ def rel_error(a, b):
     return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(b)))
 
 
-def solve(L, n, eps, rho):
+def solve(L, n, eps, rho, kernel="coulomb3d"):
     """Tensor generation followed by the FFT route: the whole method."""
-    return apply_fft(tensor_T(L, n, eps), rho)
+    return apply_fft(tensor_T(L, n, eps, kernel), rho)

@@ -28,6 +28,13 @@ def pins_pass():
     d = W.paper_case1(L=8.0, sigma2=1.2, gamma3=0.25, h_over_gamma=0.25)
     if fsa.rel_error(fsa.solve(d.L, d.n, 0.5, d.rho()), cf.density_potential(d)) > 6e-15:
         return False
+    # Table 5, 3-D biharmonic, h = 1 and 1/2 (printed 2.6307E-04, 1.1065E-10)
+    for h, want in ((1.0, 2.6307e-4), (0.5, 1.1065e-10)):
+        d = W.paper_case1(L=12.0, sigma2=1.2, h_over_gamma=h)
+        e = fsa.rel_error(fsa.solve(d.L, d.n, 1.0, d.rho(), kernel="biharmonic3d"),
+                          cf.biharmonic_density_potential(d))
+        if abs(e - want) > 5e-4 * want:
+            return False
     # brute force
     n, L = (4, 6, 8), (3.0, 4.0, 2.5)
     T = fsa.tensor_T(L, n, 0.6)
@@ -64,29 +71,48 @@ def _ueps_erfc(r, eps):
     return np.where(r > 0, sp.erfc(r / eps) / (4 * math.pi * np.where(r > 0, r, 1)), 0.0)
 
 
-fsa_orig = {k: getattr(fsa, k) for k in ("coulomb3d_What", "coulomb3d_Ueps", "tensor_T",
-                                         "tensor_T1", "tensor_T2", "fourier_W", "apply_fft")}
+fsa_orig = {k: getattr(fsa, k) for k in ("coulomb3d_What", "coulomb3d_Ueps", "biharmonic3d_What",
+                                         "biharmonic3d_Ueps", "tensor_T", "tensor_T1", "tensor_T2",
+                                         "fourier_W", "apply_fft")}
 
 
-def _mu_wrong_scale(L, n, eps):
-    return fsa_orig["fourier_W"](tuple(2 * l for l in L), n, eps)
+def _mu_wrong_scale(L, n, eps, kernel="coulomb3d"):
+    return fsa_orig["fourier_W"](tuple(2 * l for l in L), n, eps, kernel)
 
 
-def _W_axes_transposed(L, n, eps):
-    return fsa_orig["fourier_W"](tuple(L[::-1]), n, eps)
+def _W_axes_transposed(L, n, eps, kernel="coulomb3d"):
+    return fsa_orig["fourier_W"](tuple(L[::-1]), n, eps, kernel)
 
 
-def _T1_no_h(L, n, eps):
+def _T1_no_h(L, n, eps, kernel="coulomb3d"):
     h = fsa.mesh_steps(L, n)
-    return fsa_orig["tensor_T1"](L, n, eps) / (h[0] * h[1] * h[2])
+    return fsa_orig["tensor_T1"](L, n, eps, kernel) / (h[0] * h[1] * h[2])
 
 
-def _T_no_T2(L, n, eps):
-    return fsa_orig["tensor_T1"](L, n, eps)
+def _T_no_T2(L, n, eps, kernel="coulomb3d"):
+    return fsa_orig["tensor_T1"](L, n, eps, kernel)
 
 
-def _T_no_T1(L, n, eps):
-    return fsa_orig["tensor_T2"](L, n, eps)
+def _T_no_T1(L, n, eps, kernel="coulomb3d"):
+    return fsa_orig["tensor_T2"](L, n, eps, kernel=kernel)
+
+
+def _bh_what_coefficient(k, eps):
+    # Table 1's 2 k^2 eps^2 term read as k^2 eps^2
+    k = np.asarray(k, dtype=np.float64)
+    kk = np.where(k > 0, k, 1.0)
+    v = (-8 + np.exp(-(kk * eps) ** 2 / 4) * (8 + (kk * eps) ** 2 + (kk * eps) ** 4)) / (8 * kk ** 4)
+    return np.where(k > 0, v, 3 * eps ** 4 / 32)
+
+
+def _bh_ueps_coulomb_scale(r, eps):
+    # 1/(4 pi) instead of 1/(8 pi)
+    return 2.0 * fsa_orig["biharmonic3d_Ueps"](r, eps)
+
+
+def _bh_what_limit_dropped(k, eps):
+    k = np.asarray(k, dtype=np.float64)
+    return np.where(k > 0, fsa_orig["biharmonic3d_What"](k, eps), 0.0)
 
 
 def _apply_wrong_crop(T, rho):
@@ -118,6 +144,9 @@ MUTATIONS = {
     "T1 dropped": ("tensor_T", _T_no_T1),
     "crop shifted": ("apply_fft", _apply_wrong_crop),
     "pad on the wrong side": ("apply_fft", _apply_pad_at_end),
+    "biharmonic What 2k^2eps^2 -> k^2eps^2": ("biharmonic3d_What", _bh_what_coefficient),
+    "biharmonic Ueps 1/(4 pi)": ("biharmonic3d_Ueps", _bh_ueps_coulomb_scale),
+    "biharmonic What limit at k=0 dropped": ("biharmonic3d_What", _bh_what_limit_dropped),
 }
 
 

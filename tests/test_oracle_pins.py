@@ -53,6 +53,84 @@ def test_Ueps_limit_and_far_field():
     assert u[3] == pytest.approx(1 / (4 * math.pi * r[3]), rel=1e-16)
 
 
+# ---- Table 1, 3-D biharmonic row -------------------------------------------------
+
+@pytest.mark.parametrize("eps", [0.4, 1.0])
+@pytest.mark.parametrize("k", [0.0, 1e-5, 0.05, 0.3, 1.0, 1.9, 2.1, 3.0, 10.0])
+def test_biharmonic_What_equals_radial_fourier_integral(k, eps):
+    """Table 1's biharmonic closed form (series below x = 1) equals Eq.
+    (Fourier-Symmetric) d=3 of r erfc(r/eps)/(8 pi) by quadrature."""
+    a = fsa.biharmonic3d_What(np.array([k]), eps)[0]
+    b = fsa.What_by_quadrature_kernel(k, eps, "biharmonic3d")
+    assert abs(a - b) <= 1e-14 * abs(b) + 1e-20
+
+
+def test_biharmonic_What_series_meets_closed_form():
+    """The two evaluations agree where both are accurate (x near 1) and the
+    k = 0 value is 3 eps^4 / 32."""
+    eps = 0.8
+    for x in (0.7, 0.95, 0.999):
+        k = 2.0 * math.sqrt(x) / eps
+        direct = eps ** 4 / 16 * (math.exp(-x) * (1 + x + 2 * x * x) - 1) / (x * x)
+        assert fsa.biharmonic3d_What(np.array([k]), eps)[0] == pytest.approx(direct, rel=1e-14)
+    assert fsa.biharmonic3d_What(np.array([0.0]), eps)[0] == 3 * eps ** 4 / 32
+
+
+def test_biharmonic_Ueps_zero_and_far_field():
+    eps = 0.7
+    r = np.array([0.0, 6 * eps, 9 * eps])
+    u = fsa.biharmonic3d_Ueps(r, eps)
+    assert u[0] == 0.0
+    assert u[1] == pytest.approx(r[1] / (8 * math.pi), rel=1e-15)
+    assert u[2] == pytest.approx(r[2] / (8 * math.pi), rel=1e-16)
+
+
+@pytest.mark.parametrize("r", [1e-3, 0.5, 2.0, 7.0])
+def test_biharmonic_closed_form_equals_radial_integral(r):
+    """The non-central-chi mean form of the Gaussian's biharmonic potential
+    equals the radial integral of |x - y| against the density."""
+    import scipy.integrate as si
+    w = math.sqrt(0.6)
+    f = lambda t: t * t * math.exp(-t * t / (2 * w * w)) * ((r + t) ** 3 - abs(r - t) ** 3) / (3 * r * t)
+    v, _ = si.quad(f, 0, np.inf, epsabs=0, epsrel=1e-13, limit=400)
+    assert cf.biharmonic_iso_gaussian_r(1.0, w, np.array([r]))[0] == pytest.approx(v / 4, rel=1e-12)
+
+
+@pytest.mark.parametrize("h,n,printed", [tuple(r) for r in read_golden("table5_biharmonic3d_iso_double.txt")])
+def test_table5_biharmonic3d(h, n, printed):
+    """Table 5, 3-D biharmonic (L = 12, sigma^2 = 1.2, eps = 1): the printed
+    discretisation errors at h = 2, 1, 1/2 to 4 digits, round-off at 1/4."""
+    d = W.paper_case1(L=12.0, sigma2=1.2, gamma3=1.0, h_over_gamma=float(h))
+    assert d.n[0] == int(n)
+    err = fsa.rel_error(fsa.solve(d.L, d.n, 1.0, d.rho(), kernel="biharmonic3d"),
+                        cf.biharmonic_density_potential(d))
+    printed = float(printed)
+    if printed > 1e-10:
+        assert err == pytest.approx(printed, rel=5e-4)
+    else:
+        assert err < 4 * printed
+
+
+def test_biharmonic_fft_route_equals_brute_force():
+    rng = np.random.default_rng(9)
+    n, L = (6, 4, 8), (2.0, 3.0, 2.5)
+    T = fsa.tensor_T(L, n, 0.5, kernel="biharmonic3d")
+    rho = rng.standard_normal(n)
+    assert fsa.rel_error(fsa.apply_fft(T, rho), fsa.apply_direct(T, rho)) < 1e-13
+
+
+def test_biharmonic_appendix_b_bound_closed_form():
+    """The App. B integral of the biharmonic U - U^eps against its closed
+    form (eps^4/(8 pi)) [erfc(c) (3/16 - c^4/4) + exp(-c^2) (c^3/2 + 3c/4)/(2 sqrt(pi))],
+    from integrating by parts (the library evaluates this closed form)."""
+    for R0, eps in ((24.0, 1.0), (8.0, 1.0), (4.0, 0.9), (2.0, 0.5)):
+        c = R0 / eps
+        closed = eps ** 4 / (8 * math.pi) * (math.erfc(c) * (3 / 16 - c ** 4 / 4)
+                                            + math.exp(-c * c) * (c ** 3 / 2 + 3 * c / 4) / (2 * math.sqrt(math.pi)))
+        q = fsa.appendix_b_bound(R0, eps, kernel="biharmonic3d")
+        assert closed == pytest.approx(q, rel=1e-9, abs=1e-300)
+
+
 # ---- App. B: eps thresholds ---------------------------------------------------
 
 def test_appendix_b_thresholds():
