@@ -36,6 +36,7 @@ if ROOT not in sys.path:
 METRIC = "solves/s and HBM-roofline % at 256^3 FP64/FP32; p50/p99 latency under serving"
 UNIT = "solves/s"
 PASSES = ["r2c_ax0", "row_fwd", "col_mid", "row_inv", "c2r_ax0"]
+KERNEL_TEXT = {"coulomb3d": "3-D Coulomb", "biharmonic3d": "3-D biharmonic"}
 
 
 def pass_bytes(n, s):
@@ -227,7 +228,8 @@ def run_ours(args):
         tdt = torch.float32 if dt == "f32" else torch.float64
         s = 4 if dt == "f32" else 8
         t0 = time.perf_counter()
-        plan = fsa.Plan(d.L, n, dt, eps=d.eps, generate=False, l2_chunk_mb=args.l2_chunk_mb)  # + autotuner trials
+        plan = fsa.Plan(d.L, n, dt, eps=d.eps, generate=False, l2_chunk_mb=args.l2_chunk_mb,
+                        kernel=args.kernel)  # + autotuner trials
         torch.cuda.synchronize()
         create_ms = (time.perf_counter() - t0) * 1e3
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -306,7 +308,8 @@ def run_ours(args):
         res["e2e"] = None
         if not args.no_e2e:
             NS = 3
-            plans = [plan] + [fsa.Plan(d.L, n, dt, eps=d.eps, l2_chunk_mb=args.l2_chunk_mb) for _ in range(NS - 1)]
+            plans = [plan] + [fsa.Plan(d.L, n, dt, eps=d.eps, l2_chunk_mb=args.l2_chunk_mb, kernel=args.kernel)
+                              for _ in range(NS - 1)]
             streams = [torch.cuda.Stream() for _ in range(NS)]
             hin = [torch.from_numpy(rho64).to(tdt).pin_memory() for _ in range(NS)]
             hout = [torch.empty_like(hin[0]).pin_memory() for _ in range(NS)]
@@ -359,7 +362,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if "f32" in tiers else "f64",
             "data": "synthetic",
-            "config": {"workload": "c2_256: 3-D Coulomb FSA apply, 8-Gaussian density (seed 2504) on "
+            "config": {"workload": f"c2_256: {KERNEL_TEXT[args.kernel]} FSA apply, 8-Gaussian density (seed 2504) on "
                                    "[-16,16]^3, 256^3 grid, eps=1, spectrum cached on device",
                        "grid": list(n), "l2": "per-step working set ~0.6 GB (FP32) > 129 MB L2; "
                                              "4 rotating rho/phi buffers",
@@ -599,6 +602,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tiers", default="f32,f64", help="apply tiers to time; the first FP32 one is the headline")
+    ap.add_argument("--kernel", choices=["coulomb3d", "biharmonic3d"], default="coulomb3d",
+                    help="kernel of Table 1 for the single-solve tiers (batched and serving legs use Coulomb)")
     ap.add_argument("--kernel-gen", choices=["auto", "1", "2", "3", "4"], default="auto",
                     help="auto: autotuned per plan; 1 / 2 / 3 / 4: force one kernel generation "
                          "(FP64: native for 1, double-word otherwise)")

@@ -60,7 +60,9 @@ typedef enum {
 } fsa_status;
 
 typedef enum {
-  FSA_KERNEL_COULOMB3D = 0 /* U = 1/(4 pi r), U^eps = U erf(r/eps) (Table 1) */
+  FSA_KERNEL_COULOMB3D = 0,   /* U = 1/(4 pi r), U^eps = U erf(r/eps) (Table 1) */
+  FSA_KERNEL_BIHARMONIC3D = 1 /* U = r/(8 pi), U^eps = U erf(r/eps) (Table 1;    */
+                              /* Example 4)                                      */
 } fsa_kernel;
 
 typedef enum {
@@ -97,15 +99,18 @@ typedef struct {
   size_t workspace_bytes;   /* device scratch the plan owns                           */
   size_t spectrum_bytes;    /* device bytes of the stored spectrum octant             */
   const void* spectrum;     /* device pointer: (n0+1) x (n1+1) x (n2+1) dtype, C order */
+  fsa_kernel kernel;        /* the plan's kernel                                      */
 } fsa_plan_info;
 
 /* Create a plan (the "Precomp" object of Sec. 5, Example 2) for the grid
  * n[0..d-1] on the box prod_j [-L_j, L_j].  d must be 3.  The plan owns,
  * on the chosen device, the spectrum octant and the apply workspace
  * (fsa_plan_info.workspace_bytes); both are freed by fsa_plan_destroy.
- * eps follows Remark 2.1 / App. B: the plan computes R0^2 f(R0/eps) with
- * f(c) = (1/(4 pi c^2)) int_c^inf s erfc(s) ds and rejects eps with
- * FSA_ERR_EPS when it exceeds opts->eps_tol.  opts may be NULL.
+ * kernel: FSA_KERNEL_COULOMB3D or FSA_KERNEL_BIHARMONIC3D (Table 1); the apply
+ * path is the same for both, only the generated spectrum differs.
+ * eps follows Remark 2.1 / App. B: the plan computes the far-field integral
+ * int_{R0}^inf |U - U^eps| r^2 dr (fsa_appendix_b_bound_kernel) and rejects
+ * eps with FSA_ERR_EPS when it exceeds opts->eps_tol.  opts may be NULL.
  * Errors: FSA_ERR_INVALID_ARG (out == NULL, d != 3, unsupported n_j,
  * L_j <= 0, eps < 0), FSA_ERR_UNSUPPORTED (kernel), FSA_ERR_EPS,
  * FSA_ERR_OOM, FSA_ERR_CUDA.  On error *out is set to NULL. */
@@ -177,6 +182,14 @@ fsa_status fsa_plan_spectrum_copy(const fsa_plan* plan, void* dst, size_t nbytes
  * f(c) = (1/(4 pi c^2)) int_c^inf s erfc(s) ds (host-only; NaN for
  * non-positive arguments).  fsa_plan_create checks it against eps_tol. */
 double fsa_appendix_b_bound(double R0, double eps);
+
+/* The same far-field integral int_{R0}^inf |U - U^eps| r^2 dr for a kernel of
+ * Table 1: Coulomb as above; 3-D biharmonic (App. B works out only Coulomb;
+ * the same integral of r erfc(r/eps)/(8 pi)) =
+ * (eps^4 / (8 pi)) int_c^inf s^3 erfc(s) ds, c = R0/eps, in closed form
+ * erfc(c) (3/16 - c^4/4) + exp(-c^2) (c^3/2 + 3c/4) / (2 sqrt(pi)).
+ * Host-only; NaN for non-positive arguments or an unknown kernel. */
+double fsa_appendix_b_bound_kernel(fsa_kernel kernel, double R0, double eps);
 
 const char* fsa_status_string(fsa_status s);
 const char* fsa_last_error(void); /* calling thread's last error message ("" if none) */

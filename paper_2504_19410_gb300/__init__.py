@@ -9,7 +9,7 @@ there is no CPU path.  Build the library with ``__graft_entry__.build()``
 from __future__ import annotations
 
 from . import capi
-from .capi import FSA_F32, FSA_F64, FSA_KERNEL_COULOMB3D, FsaError
+from .capi import FSA_F32, FSA_F64, FSA_KERNEL_BIHARMONIC3D, FSA_KERNEL_COULOMB3D, KERNELS, FsaError
 
 _DT = {"f32": FSA_F32, "f64": FSA_F64, FSA_F32: FSA_F32, FSA_F64: FSA_F64}
 
@@ -28,15 +28,17 @@ def _cur_stream(stream):
 
 class Plan:
     """A device-resident FSA plan: grid n (3 ints), box half-widths L, dtype
-    'f32' or 'f64'.  eps = 0 picks min(1, R0/6).  The spectrum is generated
-    on construction unless generate=False."""
+    'f32' or 'f64', kernel 'coulomb3d' or 'biharmonic3d' (Table 1).  eps = 0
+    picks min(1, R0/6).  The spectrum is generated on construction unless
+    generate=False."""
 
     def __init__(self, L, n, dtype="f32", eps=0.0, eps_tol=0.0, device=-1, generate=True, stream=None,
-                 l2_chunk_mb=0):
+                 l2_chunk_mb=0, kernel="coulomb3d"):
         self.dtype = _DT[dtype]
         self.n = tuple(int(x) for x in n)
         self.L = tuple(float(x) for x in L)
-        self.handle = capi.fsa_plan_create(FSA_KERNEL_COULOMB3D, 3, self.L, self.n, self.dtype, eps, eps_tol, device,
+        self.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        self.handle = capi.fsa_plan_create(self.kernel, 3, self.L, self.n, self.dtype, eps, eps_tol, device,
                                            l2_chunk_mb)
         if generate:
             self.generate(stream)
@@ -103,8 +105,9 @@ class Server:
         self.handle = capi.fsa_serve_create(max_inflight, streams, hbm_fraction, hbm_budget_bytes,
                                             plan_cache_max, queue_max, device)
 
-    def submit(self, L, n, dtype, rho, phi, eps=0.0):
-        return capi.fsa_serve_submit(self.handle, L, n, _DT[dtype], rho, phi, eps)
+    def submit(self, L, n, dtype, rho, phi, eps=0.0, kernel="coulomb3d"):
+        k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        return capi.fsa_serve_submit(self.handle, L, n, _DT[dtype], rho, phi, eps, k)
 
     def poll(self, ticket, timeout=0.0):
         """(state, times); times has submit_s, admit_s, done_s, plan_hit, status."""

@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libfsaconv.so")
 FSA_OK, FSA_ERR_INVALID_ARG, FSA_ERR_UNSUPPORTED, FSA_ERR_EPS, FSA_ERR_OOM, FSA_ERR_CUDA, \
     FSA_ERR_NOT_GENERATED, FSA_ERR_BUSY, FSA_ERR_TIMEOUT, FSA_ERR_DEVICE_TIMEOUT, FSA_ERR_NOT_FOUND = range(11)
 FSA_KERNEL_COULOMB3D = 0
+FSA_KERNEL_BIHARMONIC3D = 1
+KERNELS = {"coulomb3d": FSA_KERNEL_COULOMB3D, "biharmonic3d": FSA_KERNEL_BIHARMONIC3D}
 FSA_F32, FSA_F64 = 0, 1
 FSA_REQ_QUEUED, FSA_REQ_RUNNING, FSA_REQ_DONE, FSA_REQ_FAILED = range(4)
 
@@ -37,7 +39,7 @@ class PlanInfo(C.Structure):
                 ("generated", C.c_int), ("arithmetic", C.c_int), ("launches_per_apply", C.c_int),
                 ("workspace_bytes", C.c_size_t),
                 ("spectrum_bytes", C.c_size_t),
-                ("spectrum", C.c_void_p)]
+                ("spectrum", C.c_void_p), ("kernel", C.c_int)]
 
 
 class ServeOpts(C.Structure):
@@ -75,6 +77,7 @@ _PROTOS = {
     "fsa_plan_destroy": (C.c_int, [_VP]),
     "fsa_plan_spectrum_copy": (C.c_int, [_VP, _VP, C.c_size_t, _VP]),
     "fsa_appendix_b_bound": (C.c_double, [C.c_double, C.c_double]),
+    "fsa_appendix_b_bound_kernel": (C.c_double, [C.c_int, C.c_double, C.c_double]),
     "fsa_status_string": (C.c_char_p, [C.c_int]),
     "fsa_last_error": (C.c_char_p, []),
     "fsa_autotune_set": (C.c_int, [C.c_int]),
@@ -190,6 +193,10 @@ def fsa_plan_destroy(plan):
 
 def fsa_appendix_b_bound(R0, eps):
     return lib().fsa_appendix_b_bound(float(R0), float(eps))
+
+
+def fsa_appendix_b_bound_kernel(kernel, R0, eps):
+    return lib().fsa_appendix_b_bound_kernel(int(kernel), float(R0), float(eps))
 
 
 def fsa_status_string(s):

@@ -97,7 +97,7 @@ void batched_forget_plan(const fsa_plan* p);
 // Tensor generation (tensor_gen.cu), all FP64.
 cudaError_t tensorgen_prepare(int M);
 cudaError_t tensorgen_init_twiddles();
-cudaError_t tensorgen_run(const int n[3], const double L[3], double eps, double* oct64, void* out,
+cudaError_t tensorgen_run(fsa_kernel kernel, const int n[3], const double L[3], double eps, double* oct64, void* out,
                           fsa_dtype dtype, cudaStream_t s);
 
 // Twiddle table exp(-2 pi i k / 3072), k < 3072, computed on the host.
@@ -116,6 +116,7 @@ struct fsa_plan {
   double eps;
   double R0;
   double eps_bound;
+  fsa_kernel kernel;
   fsa_dtype dtype;
   int device;
   int generated;

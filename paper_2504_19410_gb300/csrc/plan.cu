@@ -287,6 +287,22 @@ const void* plan_apply_spectrum(const fsa_plan* p) { return p->f64_dw ? p->spect
 
 namespace {
 
+double appendix_b_bound_impl(double R0, double eps);
+
+// The far-field integral for a kernel of Table 1 (see fsa_appendix_b_bound_kernel).
+double appendix_b_bound_kernel_impl(fsa_kernel kernel, double R0, double eps) {
+  if (kernel == FSA_KERNEL_COULOMB3D) return appendix_b_bound_impl(R0, eps);
+  if (kernel != FSA_KERNEL_BIHARMONIC3D) return NAN;
+  // (eps^4/(8 pi)) int_c^inf s^3 erfc(s) ds; by parts,
+  // int_c^inf s^3 erfc(s) ds = erfc(c) (3/16 - c^4/4) + exp(-c^2) (c^3/2 + 3c/4) / (2 sqrt(pi))
+  const long double c = (long double)R0 / (long double)eps;
+  const long double pi = 3.141592653589793238462643383279502884L;
+  const long double e4 = (long double)eps * eps * eps * eps;
+  const long double tail =
+      erfcl(c) * (3.0L / 16.0L - c * c * c * c / 4.0L) + expl(-c * c) * (c * c * c / 2.0L + 0.75L * c) / (2.0L * sqrtl(pi));
+  return (double)(e4 * tail / (8.0L * pi));
+}
+
 double appendix_b_bound_impl(double R0, double eps) {
   // R0^2 f(c), f(c) = (1/(4 pi c^2)) int_c^inf s erfc(s) ds, c = R0/eps (App. B);
   // int_c^inf s erfc(s) ds = (1/4 - c^2/2) erfc(c) + c exp(-c^2) / (2 sqrt(pi)).
@@ -427,6 +443,11 @@ double fsa_appendix_b_bound(double R0, double eps) {
   return appendix_b_bound_impl(R0, eps);
 }
 
+double fsa_appendix_b_bound_kernel(fsa_kernel kernel, double R0, double eps) {
+  if (!(R0 > 0) || !(eps > 0)) return NAN;
+  return appendix_b_bound_kernel_impl(kernel, R0, eps);
+}
+
 }  // extern "C"
 
 namespace fsa {
@@ -446,8 +467,10 @@ cudaError_t tune_plan(fsa_plan* p);
 
 // Argument checks that need no device.  On success *eps_out / *bound_out
 // hold the eps in use and its App. B bound.
-fsa_status plan_validate(const double* L, const int* n, fsa_dtype dtype, double eps_in, double eps_tol,
-                         double* eps_out, double* bound_out) {
+fsa_status plan_validate(fsa_kernel kernel, const double* L, const int* n, fsa_dtype dtype, double eps_in,
+                         double eps_tol, double* eps_out, double* bound_out) {
+  if (kernel != FSA_KERNEL_COULOMB3D && kernel != FSA_KERNEL_BIHARMONIC3D)
+    return set_error(FSA_ERR_UNSUPPORTED, "fsa_plan_create: unknown kernel");
   if (dtype != FSA_F32 && dtype != FSA_F64) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: bad dtype");
   for (int j = 0; j < 3; ++j) {
     if (!supported_n(n[j]))
@@ -460,12 +483,12 @@ fsa_status plan_validate(const double* L, const int* n, fsa_dtype dtype, double 
   if (eps_in < 0 || !std::isfinite(eps_in)) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: eps < 0");
   const double R0 = 2.0 * std::min(L[0], std::min(L[1], L[2]));
   const double eps = eps_in > 0 ? eps_in : std::min(1.0, R0 / 6.0);
-  const double bound = appendix_b_bound_impl(R0, eps);
+  const double bound = appendix_b_bound_kernel_impl(kernel, R0, eps);
   const double tol = eps_tol == 0 ? 1e-8 : eps_tol;
   if (tol > 0 && !(bound <= tol)) {
     char buf[256];
-    snprintf(buf, sizeof buf, "fsa_plan_create: eps = %g fails App. B: R0^2 f(R0/eps) = %.3g > %.3g (R0 = %g)", eps,
-             bound, tol, R0);
+    snprintf(buf, sizeof buf, "fsa_plan_create: eps = %g fails App. B: int_R0^inf |U - U^eps| r^2 dr = %.3g > %.3g (R0 = %g)",
+             eps, bound, tol, R0);
     return set_error(FSA_ERR_EPS, buf);
   }
   *eps_out = eps;
@@ -473,11 +496,11 @@ fsa_status plan_validate(const double* L, const int* n, fsa_dtype dtype, double 
   return FSA_OK;
 }
 
-fsa_status plan_create_internal(fsa_plan** out, const double* L, const int* n, fsa_dtype dtype, double eps_in,
-                                double eps_tol, bool with_workspace) {
+fsa_status plan_create_internal(fsa_plan** out, fsa_kernel kernel, const double* L, const int* n, fsa_dtype dtype,
+                                double eps_in, double eps_tol, bool with_workspace) {
   *out = nullptr;
   double eps = 0, bound = 0;
-  fsa_status vs = plan_validate(L, n, dtype, eps_in, eps_tol, &eps, &bound);
+  fsa_status vs = plan_validate(kernel, L, n, dtype, eps_in, eps_tol, &eps, &bound);
   if (vs != FSA_OK) return vs;
   const double R0 = 2.0 * std::min(L[0], std::min(L[1], L[2]));
   int dev = 0;
@@ -495,6 +518,7 @@ fsa_status plan_create_internal(fsa_plan** out, const double* L, const int* n, f
   p->eps = eps;
   p->R0 = R0;
   p->eps_bound = bound;
+  p->kernel = kernel;
   p->chunk_bytes = 0;  // one slab: measured fastest at 256^3 (see fsa_plan_opts.l2_chunk_mb)
   p->dtype = dtype;
   p->device = dev;
@@ -647,7 +671,7 @@ cudaError_t tune_f64(fsa_plan* p) {
 
 cudaError_t plan_generate_into(fsa_plan* p, void* scratch, cudaStream_t s) {
   double* oct = p->dtype == FSA_F64 ? (double*)p->spectrum : (double*)scratch;
-  cudaError_t e = tensorgen_run(p->n, p->L, p->eps, oct, p->spectrum, p->dtype, s);
+  cudaError_t e = tensorgen_run(p->kernel, p->n, p->L, p->eps, oct, p->spectrum, p->dtype, s);
   if (e == cudaSuccess && p->spectrum_dw)
     e = spectrum_to_dw((const double*)p->spectrum, p->spectrum_dw, p->spectrum_bytes / 8, s);
   if (e == cudaSuccess) p->generated = 1;
@@ -662,19 +686,20 @@ fsa_status fsa_plan_create(fsa_plan** out, fsa_kernel kernel, int d, const doubl
                            fsa_dtype dtype, const fsa_plan_opts* opts) {
   if (!out) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: out is NULL");
   *out = nullptr;
-  if (kernel != FSA_KERNEL_COULOMB3D) return set_error(FSA_ERR_UNSUPPORTED, "fsa_plan_create: unknown kernel");
+  if (kernel != FSA_KERNEL_COULOMB3D && kernel != FSA_KERNEL_BIHARMONIC3D)
+    return set_error(FSA_ERR_UNSUPPORTED, "fsa_plan_create: unknown kernel");
   if (d != 3) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: only d = 3 is implemented");
   if (!L || !n) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: L or n is NULL");
   fsa_plan_opts o{};
   o.device = -1;
   if (opts) o = *opts;
   double eps = 0, bound = 0;
-  fsa_status vs = plan_validate(L, n, dtype, o.eps, o.eps_tol, &eps, &bound);
+  fsa_status vs = plan_validate(kernel, L, n, dtype, o.eps, o.eps_tol, &eps, &bound);
   if (vs != FSA_OK) return vs;  // no device touched
   DeviceGuard dg;
   cudaError_t e = dg.set(o.device);
   if (e != cudaSuccess) return cuda_error(e, "fsa_plan_create: cudaSetDevice");
-  fsa_status st = plan_create_internal(out, L, n, dtype, o.eps, o.eps_tol, true);
+  fsa_status st = plan_create_internal(out, kernel, L, n, dtype, o.eps, o.eps_tol, true);
   if (st == FSA_OK && o.l2_chunk_mb != 0) (*out)->chunk_bytes = o.l2_chunk_mb > 0 ? (long long)o.l2_chunk_mb << 20 : 0;
   return st;
 }
@@ -726,6 +751,7 @@ fsa_status fsa_plan_info_get(const fsa_plan* p, fsa_plan_info* info) {
   info->workspace_bytes = p->ws_bytes;
   info->spectrum_bytes = p->spectrum_bytes;
   info->spectrum = p->spectrum;
+  info->kernel = p->kernel;
   return FSA_OK;
 }
 

@@ -30,8 +30,8 @@
 #include "fsa_internal.h"
 
 namespace fsa {
-fsa_status plan_create_internal(fsa_plan** out, const double* L, const int* n, fsa_dtype dtype, double eps,
-                                double eps_tol, bool with_workspace);
+fsa_status plan_create_internal(fsa_plan** out, fsa_kernel kernel, const double* L, const int* n, fsa_dtype dtype,
+                                double eps, double eps_tol, bool with_workspace);
 cudaError_t plan_generate_into(fsa_plan* p, void* scratch, cudaStream_t s);
 size_t plan_workspace_bytes(const int* n, fsa_dtype dt);
 size_t plan_gen_scratch_bytes(const int* n, fsa_dtype dt);
@@ -48,6 +48,7 @@ double now_s() {
 
 struct PlanKey {
   int n[3];
+  int kernel;
   double L[3];
   int dt;
   double eps;
@@ -157,7 +158,7 @@ bool try_admit(fsa_server* s, uint64_t id) {
   cudaError_t e = cudaSuccess;
   if (!hit) {
     fsa_plan* p = nullptr;
-    status = plan_create_internal(&p, q.r.L, q.r.n, q.r.dtype, q.r.eps, 0.0, false);
+    status = plan_create_internal(&p, q.r.kernel, q.r.L, q.r.n, q.r.dtype, q.r.eps, 0.0, false);
     // server plans have no workspace of their own; FP64 arithmetic follows the
     // per-shape choice made by earlier plans (double-word by default)
     if (status == FSA_OK) {
@@ -290,7 +291,7 @@ void loop(fsa_server* s) {
 }
 
 bool valid_request(const fsa_request* r) {
-  if (!r || r->kernel != FSA_KERNEL_COULOMB3D || r->d != 3) return false;
+  if (!r || (r->kernel != FSA_KERNEL_COULOMB3D && r->kernel != FSA_KERNEL_BIHARMONIC3D) || r->d != 3) return false;
   if (r->dtype != FSA_F32 && r->dtype != FSA_F64) return false;
   if (!r->rho || !r->phi || (((uintptr_t)r->rho | (uintptr_t)r->phi) & 15u)) return false;
   if (!(r->eps >= 0)) return false;
@@ -370,6 +371,7 @@ fsa_status fsa_serve_submit(fsa_server* s, const fsa_request* req, uint64_t* tic
     q.key.n[j] = req->n[j];
     q.key.L[j] = req->L[j];
   }
+  q.key.kernel = req->kernel;
   q.key.dt = req->dtype;
   q.key.eps = req->eps;
   s->queue.push_back(id);

@@ -2,16 +2,22 @@
 //
 // The stored spectrum is S[p] = (DFT_{2n}(T^(1))[p] + W(|mu_p|)) / prod_j 2 n_j
 // on the octant p_j in [0, n_j]:
-//   * T^(1)_o = h0 h1 h2 U^eps(|o.h|), U^eps = erf(r/eps)/(4 pi r), with the
-//     limit 1/(2 pi^{3/2} eps) at r = 0 (Sec. 2.1, Eq. Tensor1; Sec. 4,
-//     Eq. KerAppr; Table 1).  T^(1) is even per axis, so its values on the
-//     octant o_j in [0, n_j] define it on the doubled grid.
+//   * T^(1)_o = h0 h1 h2 U^eps(|o.h|) (Sec. 2.1, Eq. Tensor1; Sec. 4,
+//     Eq. KerAppr; Table 1): 3-D Coulomb U^eps = erf(r/eps)/(4 pi r), with the
+//     limit 1/(2 pi^{3/2} eps) at r = 0; 3-D biharmonic U^eps = r erf(r/eps)/(8 pi),
+//     0 at r = 0.  T^(1) is even per axis, so its values on the octant
+//     o_j in [0, n_j] define it on the doubled grid.
 //   * The DFT over the doubled grid of an even sequence is a DCT-I per axis
 //     (Sec. 2.3 notes the axis symmetry of T); each axis is done with the
 //     library's FFT kernels on the even extension.
-//   * T^(2) = iDFT(W) (Sec. 2.2, Eq. Tensor2), so its DFT is W itself:
-//     W(k) = (1 - exp(-k^2 eps^2 / 4)) / k^2 (Table 1, 3-D Coulomb), evaluated
-//     with expm1; W(0) = eps^2/4, mu_{p,j} = pi p_j / (2 L_j) (Sec. 2.4, Eq. WkAnis).
+//   * T^(2) = iDFT(W) (Sec. 2.2, Eq. Tensor2), so its DFT is W itself, at
+//     k = |mu_p|, mu_{p,j} = pi p_j / (2 L_j) (Sec. 2.4, Eq. WkAnis).  Table 1:
+//     3-D Coulomb W(k) = (1 - exp(-k^2 eps^2 / 4)) / k^2, evaluated with expm1,
+//     W(0) = eps^2/4; 3-D biharmonic
+//     W(k) = (-8 + exp(-k^2 eps^2/4) (8 + 2 k^2 eps^2 + k^4 eps^4)) / (8 k^4)
+//          = (eps^4/16) g(x), x = k^2 eps^2 / 4, g(x) = (exp(-x)(1 + x + 2x^2) - 1)/x^2,
+//     summed from the Taylor series of g below x = 1 (the closed form cancels
+//     there), W(0) = 3 eps^4 / 32.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -21,8 +27,45 @@
 
 namespace fsa {
 
-__global__ void k_t1_octant(double* __restrict__ O, int n0, int n1, int n2, double h0, double h1, double h2,
-                            double eps) {
+// Taylor coefficients of g(x) = (exp(-x)(1 + x + 2x^2) - 1)/x^2: the
+// coefficient of x^m is c_{m+2}, c_j = (-1)^j (1/j! - 1/(j-1)! + 2/(j-2)!)
+// (the exponential series times 1 + x + 2x^2).
+struct BihSeries {
+  double c[30];
+};
+constexpr BihSeries bih_series() {
+  BihSeries s{};
+  double f[33] = {};
+  f[0] = 1.0;
+  for (int i = 1; i < 33; ++i) f[i] = f[i - 1] * i;
+  for (int m = 0; m < 30; ++m) {
+    const int j = m + 2;
+    const double sign = (j % 2 == 0) ? 1.0 : -1.0;
+    s.c[m] = sign * (1.0 / f[j] - 1.0 / f[j - 1] + 2.0 / f[j - 2]);
+  }
+  return s;
+}
+__constant__ BihSeries c_bih = bih_series();
+
+// W(k) of Table 1 at k^2 (see the file comment)
+__device__ __forceinline__ double singular_W(int kernel, double k2, double e2) {
+  if (kernel == FSA_KERNEL_BIHARMONIC3D) {
+    const double x = 0.25 * k2 * e2;
+    double g;
+    if (x < 1.0) {
+      g = 0.0;
+#pragma unroll
+      for (int m = 29; m >= 0; --m) g = g * x + c_bih.c[m];
+    } else {
+      g = (exp(-x) * (1.0 + x + 2.0 * x * x) - 1.0) / (x * x);
+    }
+    return e2 * e2 / 16.0 * g;
+  }
+  return k2 > 0.0 ? -expm1(-0.25 * k2 * e2) / k2 : 0.25 * e2;
+}
+
+__global__ void k_t1_octant(double* __restrict__ O, int kernel, int n0, int n1, int n2, double h0, double h1,
+                            double h2, double eps) {
   const long long total = (long long)(n0 + 1) * (n1 + 1) * (n2 + 1);
   const double hv = h0 * h1 * h2;
   const double u0 = 1.0 / (2.0 * 5.5683279968317078453 * eps);  // 1/(2 pi^{3/2} eps)
@@ -34,14 +77,16 @@ __global__ void k_t1_octant(double* __restrict__ O, int n0, int n1, int n2, doub
     const int p0 = (int)(r01 / (n1 + 1));
     const double x = p0 * h0, y = p1 * h1, z = p2 * h2;
     const double r = sqrt(x * x + y * y + z * z);
-    const double u = r > 0.0 ? erf(r / eps) / (4.0 * 3.14159265358979323846 * r) : u0;
+    const double u = kernel == FSA_KERNEL_BIHARMONIC3D
+                         ? r * erf(r / eps) / (8.0 * 3.14159265358979323846)
+                         : (r > 0.0 ? erf(r / eps) / (4.0 * 3.14159265358979323846 * r) : u0);
     O[i] = hv * u;
   }
 }
 
 template <typename R>
 __global__ void k_spectrum_finalize(const double* S1, R* S,  // may alias (FP64 plans)
-                                    int n0, int n1, int n2,
+                                    int kernel, int n0, int n1, int n2,
                                     double c0, double c1, double c2, double eps, double inv_norm) {
   const long long total = (long long)(n0 + 1) * (n1 + 1) * (n2 + 1);
   const double e2 = eps * eps;
@@ -53,7 +98,7 @@ __global__ void k_spectrum_finalize(const double* S1, R* S,  // may alias (FP64 
     const int p0 = (int)(r01 / (n1 + 1));
     const double m0 = c0 * p0, m1 = c1 * p1, m2 = c2 * p2;  // mu_j = pi p_j / (2 L_j)
     const double k2 = m0 * m0 + m1 * m1 + m2 * m2;
-    const double w = k2 > 0.0 ? -expm1(-0.25 * k2 * e2) / k2 : 0.25 * e2;
+    const double w = singular_W(kernel, k2, e2);
     S[i] = (R)((S1[i] + w) * inv_norm);
   }
 }
@@ -143,15 +188,15 @@ cudaError_t tensorgen_init_twiddles() {
   return e;
 }
 
-cudaError_t tensorgen_run(const int n[3], const double L[3], double eps, double* O, void* out, fsa_dtype dtype,
-                          cudaStream_t s) {
+cudaError_t tensorgen_run(fsa_kernel kernel, const int n[3], const double L[3], double eps, double* O, void* out,
+                          fsa_dtype dtype, cudaStream_t s) {
   const int n0 = n[0], n1 = n[1], n2 = n[2];
   const long long e0 = n0 + 1, e1 = n1 + 1, e2 = n2 + 1;
   const double h0 = 2.0 * L[0] / n0, h1 = 2.0 * L[1] / n1, h2 = 2.0 * L[2] / n2;
   const long long total = e0 * e1 * e2;
   const int threads = 256;
   const int blocks = (int)std::min<long long>((total + threads - 1) / threads, 152LL * 16);
-  k_t1_octant<<<blocks, threads, 0, s>>>(O, n0, n1, n2, h0, h1, h2, eps);
+  k_t1_octant<<<blocks, threads, 0, s>>>(O, (int)kernel, n0, n1, n2, h0, h1, h2, eps);
   cudaError_t e = cudaGetLastError();
   // axis 2: lines (p0, p1) contiguous, element stride 1
   if (e == cudaSuccess) e = dct_run(2 * n2, O, e0 * e1, e1, e1 * e2, e2, 1, s);
@@ -163,10 +208,10 @@ cudaError_t tensorgen_run(const int n[3], const double L[3], double eps, double*
   const double pi = 3.14159265358979323846;
   const double inv_norm = 1.0 / (8.0 * (double)n0 * n1 * n2);
   if (dtype == FSA_F64)
-    k_spectrum_finalize<double><<<blocks, threads, 0, s>>>(O, (double*)out, n0, n1, n2, pi / (2 * L[0]),
+    k_spectrum_finalize<double><<<blocks, threads, 0, s>>>(O, (double*)out, (int)kernel, n0, n1, n2, pi / (2 * L[0]),
                                                            pi / (2 * L[1]), pi / (2 * L[2]), eps, inv_norm);
   else
-    k_spectrum_finalize<float><<<blocks, threads, 0, s>>>(O, (float*)out, n0, n1, n2, pi / (2 * L[0]),
+    k_spectrum_finalize<float><<<blocks, threads, 0, s>>>(O, (float*)out, (int)kernel, n0, n1, n2, pi / (2 * L[0]),
                                                           pi / (2 * L[1]), pi / (2 * L[2]), eps, inv_norm);
   return cudaGetLastError();
 }

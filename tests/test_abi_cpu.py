@@ -56,6 +56,26 @@ def test_appendix_b_bound_matches_oracle(capi):
     assert math.isnan(capi.fsa_appendix_b_bound(0.0, 1.0))
 
 
+def test_appendix_b_bound_per_kernel_matches_oracle(capi):
+    """The library's closed forms of the far-field integral per kernel against
+    the oracle's quadrature of the same integral."""
+    from oracle import fsa
+    for name, k in (("coulomb3d", capi.FSA_KERNEL_COULOMB3D), ("biharmonic3d", capi.FSA_KERNEL_BIHARMONIC3D)):
+        for R0, eps in [(24.0, 1.0), (24.0, 4.1), (16.0, 2.7), (4.0, 0.9), (2.0, 0.5), (8.0, 2.0)]:
+            a = capi.fsa_appendix_b_bound_kernel(k, R0, eps)
+            b = fsa.appendix_b_bound(R0, eps, kernel=name)
+            assert a == pytest.approx(b, rel=1e-8, abs=1e-300), (name, R0, eps)
+    assert math.isnan(capi.fsa_appendix_b_bound_kernel(9, 24.0, 1.0))
+    assert math.isnan(capi.fsa_appendix_b_bound_kernel(capi.FSA_KERNEL_BIHARMONIC3D, 24.0, 0.0))
+
+
+def test_plan_create_checks_the_biharmonic_bound(capi):
+    # R0 = 16, eps = 5: (eps^4/(8 pi)) int_{3.2}^inf s^3 erfc(s) ds ~ 1e-4 > 1e-8
+    with pytest.raises(capi.FsaError) as ei:
+        capi.fsa_plan_create(capi.FSA_KERNEL_BIHARMONIC3D, 3, (8, 8, 8), (8, 8, 8), capi.FSA_F32, eps=5.0)
+    assert ei.value.status == capi.FSA_ERR_EPS
+
+
 @pytest.mark.parametrize("n,L,kw,status", [
     ((4, 4, 5), (1, 1, 1), {}, "FSA_ERR_INVALID_ARG"),        # odd n
     ((4, 4, 10), (1, 1, 1), {}, "FSA_ERR_INVALID_ARG"),       # 10 = 2 * 5 not 2^a 3^b

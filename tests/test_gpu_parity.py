@@ -12,6 +12,7 @@ import pytest
 import workloads as W
 from oracle import closed_forms as cf
 from oracle import fsa as oracle
+from tests.conftest import read_golden
 
 pytestmark = pytest.mark.gpu
 
@@ -284,3 +285,76 @@ def test_batched_equals_single(lib):
             assert torch.equal(s, o)
     for p in plans:
         p.close()
+
+
+# ---- 3-D biharmonic kernel (Table 1; Example 4): same apply path, own spectrum ----
+
+BIH_SIZES = [(8, 8, 8), (12, 16, 24), (24, 12, 48), (32, 32, 32), (6, 48, 32)]
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("n", BIH_SIZES[:3])
+def test_biharmonic_spectrum_matches_oracle(lib, n, dt):
+    L = (2.0 + 0.1 * n[0] / 4, 3.0, 1.5 + n[2] / 64)
+    eps = min(1.0, 2 * min(L) / 6)
+    plan = lib.Plan(L, n, dt, eps=eps, kernel="biharmonic3d")
+    assert plan.info.kernel == lib.FSA_KERNEL_BIHARMONIC3D
+    got = plan.spectrum().double().cpu().numpy()
+    plan.close()
+    want = oracle.spectrum_octant(oracle.tensor_T(L, n, eps, kernel="biharmonic3d"), n)
+    err = oracle.rel_error(got, want)
+    assert err <= (1e-13 if dt == "f64" else 2e-7), err
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("n", BIH_SIZES)
+def test_biharmonic_apply_matches_oracle(lib, n, dt, gen):
+    rng = np.random.default_rng(sum(n))
+    L = (1.0 + n[0] / 16, 2.0, 1.0 + n[2] / 32)
+    eps = min(1.0, 2 * min(L) / 6)
+    rho = rng.standard_normal(n)
+    import torch
+    plan = lib.Plan(L, n, dt, eps=eps, kernel="biharmonic3d")
+    out = plan.apply(to_dev(rho, dt))
+    torch.cuda.synchronize()
+    got = out.double().cpu().numpy()
+    plan.close()
+    want = oracle.solve(L, n, eps, rho, kernel="biharmonic3d")
+    err = oracle.rel_error(got, want)
+    assert err <= TOL[dt], err
+
+
+@pytest.mark.parametrize("h,n,printed", [tuple(r) for r in read_golden("table5_biharmonic3d_iso_double.txt")])
+def test_table5_biharmonic_reproduced_by_gpu(lib, h, n, printed):
+    """Table 5, 3-D biharmonic (L = 12, sigma^2 = 1.2, eps = 1) on the GPU:
+    the printed discretisation errors at h = 2, 1, 1/2 to 4 digits (FP64 and
+    FP32, whose round-off is far below them at h >= 1/2 except 1/2 in FP32),
+    round-off at h = 1/4 (FP64 tier)."""
+    import torch
+    from paper_2504_19410_gb300 import capi
+    d = W.paper_case1(L=12.0, sigma2=1.2, gamma3=1.0, h_over_gamma=float(h))
+    exact = cf.biharmonic_density_potential(d)
+    printed = float(printed)
+    errs = {}
+    # FP64 tier in each arithmetic: native FP64 (mode 2) and double-word (mode 3)
+    for name, mode in (("native", 2), ("double-word", 3)):
+        capi.fsa_autotune_set(mode)
+        try:
+            plan = lib.Plan(d.L, d.n, "f64", eps=1.0, kernel="biharmonic3d")
+            out = plan.apply(to_dev(d.rho(), "f64"))
+            torch.cuda.synchronize()
+            errs[name] = oracle.rel_error(out.double().cpu().numpy(), exact)
+            plan.close()
+        finally:
+            capi.fsa_autotune_set(1)
+    print(f"Table 5 biharmonic h={h}: FP64 native {errs['native']:.4e}, double-word "
+          f"{errs['double-word']:.4e} (printed {printed:.4e})")
+    if printed > 1e-10:
+        for e in errs.values():
+            assert e == pytest.approx(printed, rel=5e-4)
+    else:
+        # round-off: native FP64 at the paper's level; double-word (unit
+        # round-off 2^-48) at its own, amplified by the biharmonic spectrum's
+        # large low-frequency values
+        assert errs["native"] < 4 * printed
+        assert errs["double-word"] < 1e-13

@@ -128,3 +128,31 @@ def test_batched_c4_mix_equals_single(lib):
         assert torch.equal(s, o)
     for p in plans:
         p.close()
+
+
+def test_served_kernels_do_not_share_plans(lib):
+    """Coulomb and biharmonic requests on the same grid, box and eps are
+    cached as different plans; each result equals its kernel's plan alone."""
+    import torch
+    rng = np.random.default_rng(5)
+    L, n = (3.0, 3.0, 2.5), (16, 24, 16)
+    rho = torch.from_numpy(rng.standard_normal(n)).cuda()
+    want = {}
+    for k in ("coulomb3d", "biharmonic3d"):
+        p = lib.Plan(L, n, "f64", eps=0.0, kernel=k)
+        want[k] = p.apply(rho)
+        torch.cuda.synchronize()
+        p.close()
+    srv = lib.Server(max_inflight=4, streams=2)
+    outs, tickets = {}, {}
+    for rep in range(2):
+        for k in ("coulomb3d", "biharmonic3d"):
+            outs[(k, rep)] = torch.full_like(rho, float("nan"))
+            tickets[(k, rep)] = srv.submit(L, n, "f64", rho, outs[(k, rep)], kernel=k)
+    for key, t in tickets.items():
+        srv.wait(t)
+    torch.cuda.synchronize()
+    srv.close()
+    for (k, rep), o in outs.items():
+        assert torch.equal(o, want[k]), (k, rep)
+    assert not torch.equal(want["coulomb3d"], want["biharmonic3d"])
