@@ -155,3 +155,64 @@ def biharmonic_density_potential(d):
                     + (x[2] - g.center[2])[None, None, :] ** 2)
         out += biharmonic_iso_gaussian_r(g.amp, s[0], r)
     return out
+
+
+# ---- 2-D kernels (Table 1), radial Gaussian rho = amp exp(-r^2/s2), s2 = sigma^2 ----
+
+def coulomb2d_gaussian_r(amp, s2, r):
+    """2-D Coulomb (1/(2 pi r)) potential of amp exp(-r^2/s2): from the
+    transform pi s2 exp(-k^2 s2/4)/k and int_0^inf exp(-a k^2) J0(b k) dk =
+    sqrt(pi/(4a)) exp(-b^2/(8a)) I0(b^2/(8a)):
+    Phi(r) = amp (sqrt(pi s2)/2) exp(-x) I0(x), x = r^2/(2 s2)."""
+    x = np.asarray(r, dtype=np.float64) ** 2 / (2.0 * s2)
+    return amp * 0.5 * math.sqrt(math.pi * s2) * sp.i0e(x)
+
+
+def poisson2d_gaussian_r(amp, s2, r):
+    """2-D Poisson (-ln(r)/(2 pi)) potential of amp exp(-r^2/s2): the angular
+    mean of ln|x - y| over |y| = t is ln max(r, t), so
+    Phi(r) = -amp int_0^inf t exp(-t^2/s2) ln max(r, t) dt
+           = -amp (s2/4) (2 ln r + E1(r^2/s2)),
+    with 2 ln r + E1(u) = ln s2 - gamma - sum_{k>=1} (-u)^k/(k k!) for u < 1."""
+    r = np.asarray(r, dtype=np.float64)
+    u = r * r / s2
+    br = np.empty_like(u)
+    small = u < 1.0
+    us = u[small]
+    acc = np.zeros_like(us)
+    for k in range(40, 0, -1):
+        acc = acc * (-us) + 1.0 / (k * math.factorial(k))
+    acc = acc * (-us)
+    br[small] = math.log(s2) - 0.57721566490153286060651209008240243 - acc
+    br[~small] = 2.0 * np.log(r[~small]) + sp.exp1(u[~small])
+    return -amp * s2 / 4.0 * br
+
+
+def biharmonic2d_gaussian_r(amp, s2, r):
+    """2-D biharmonic (-r^2 (ln r - 1)/(8 pi)) potential of amp exp(-r^2/s2) by
+    a 1-D integral: over the circle |y| = t the mean of |x-y|^2 is r^2 + t^2
+    and that of |x-y|^2 ln|x-y| is (r^2 + t^2) ln max(r,t) + min(r,t)^2 (from
+    ln|x-y| = ln R - sum_m (q^m/m) cos(m theta), q = min/max), so
+    Phi(r) = -(amp/4) int_0^inf t exp(-t^2/s2) [(r^2+t^2)(ln max(r,t) - 1) + min(r,t)^2] dt,
+    evaluated by adaptive quadrature split at t = r."""
+    import scipy.integrate as si
+    r = np.atleast_1d(np.asarray(r, dtype=np.float64))
+    out = np.empty_like(r)
+    for i, ri in enumerate(r):
+        f_in = lambda t: t * math.exp(-t * t / s2) * ((ri * ri + t * t) * (math.log(ri) - 1.0) + t * t)
+        f_out = lambda t: t * math.exp(-t * t / s2) * ((ri * ri + t * t) * (math.log(t) - 1.0) + ri * ri)
+        a = si.quad(f_in, 0.0, ri, epsabs=0.0, epsrel=1e-13, limit=200)[0] if ri > 0 else 0.0
+        b = si.quad(f_out, ri, np.inf, epsabs=0.0, epsrel=1e-13, limit=400)[0] if ri > 0 else \
+            si.quad(lambda t: t * math.exp(-t * t / s2) * t * t * (math.log(t) - 1.0), 0.0, np.inf,
+                    epsabs=0.0, epsrel=1e-13, limit=400)[0]
+        out[i] = -amp / 4.0 * (a + b)
+    return out
+
+
+def radial_on_grid_2d(fn, amp, s2, L, n):
+    """A radial 2-D potential fn(amp, s2, r) on the mesh of Sec. 2 (centred
+    density), evaluated once per distinct radius."""
+    x = grid_axes(L, n)
+    r = np.sqrt(x[0][:, None] ** 2 + x[1][None, :] ** 2)
+    ru, inv = np.unique(r, return_inverse=True)
+    return fn(amp, s2, ru)[inv].reshape(r.shape)

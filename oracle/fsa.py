@@ -7,7 +7,8 @@ scipy's erf / erfc / quad.  There is no pruning, blocking or symmetry trick:
 the convolution tensor T is built on the full doubled grid and the
 convolution is a full-size complex FFT product, as Sec. 2.3 states it.
 
-Index convention.  A tensor on the doubled grid has shape (2 n_0, 2 n_1,
+Index convention (d = 3 shown; the d = 2 kernels use the same with two
+axes).  A tensor on the doubled grid has shape (2 n_0, 2 n_1,
 2 n_2); entry k_j holds the offset o_j = k_j for k_j < n_j and
 o_j = k_j - 2 n_j otherwise, i.e. offsets -n_j .. n_j - 1 in FFT order (the
 index set I_{2N} of Sec. 2.2).  Densities and potentials are n_0 x n_1 x n_2
@@ -102,11 +103,105 @@ def biharmonic3d_What(k, eps):
     return eps ** 4 / 16.0 * g
 
 
+# ---- 2-D kernels of Table 1 -------------------------------------------------
+
+_EULER_GAMMA = 0.57721566490153286060651209008240243
+
+
+def _log_plus_half_E1(r, eps):
+    """ln(r) + E1(r^2/eps^2)/2, the bracket of the 2-D Poisson and biharmonic
+    U^eps (Eq. lnrAppr).  With u = r^2/eps^2 and the series
+    E1(u) = -gamma - ln(u) - sum_{k>=1} (-u)^k / (k k!) (Abramowitz & Stegun
+    5.1.11) the logarithms cancel exactly:
+    ln(eps) - gamma/2 - (1/2) sum_{k>=1} (-u)^k / (k k!), used for u < 1 (40
+    terms); for u >= 1 the two terms are summed directly.  At r = 0 the value
+    is ln(eps) - gamma/2, the limit the paper leaves implicit."""
+    r = np.asarray(r, dtype=np.float64)
+    u = (r / eps) ** 2
+    out = np.empty_like(u)
+    small = u < 1.0
+    us = u[small]
+    acc = np.zeros_like(us)
+    for k in range(40, 0, -1):
+        acc = acc * (-us) + 1.0 / (k * math.factorial(k))
+    acc = acc * (-us)  # sum_{k>=1} (-u)^k / (k k!)
+    out[small] = math.log(eps) - 0.5 * _EULER_GAMMA - 0.5 * acc
+    ul = u[~small]
+    out[~small] = np.log(r[~small]) + 0.5 * sp.exp1(ul)
+    return out
+
+
+def poisson2d_Ueps(r, eps):
+    """2-D Poisson U^eps(r) = -(1/(2 pi)) [ln r + E1(r^2/eps^2)/2] (Eq. lnrAppr;
+    Table 1); -(ln eps - gamma/2)/(2 pi) at r = 0."""
+    return -_log_plus_half_E1(r, eps) / (2.0 * math.pi)
+
+
+def poisson2d_What(k, eps):
+    """Table 1, 2-D Poisson row: (1 - exp(-k^2 eps^2/4)) / k^2, the 3-D
+    Coulomb form (limit eps^2/4)."""
+    return coulomb3d_What(k, eps)
+
+
+def coulomb2d_Ueps(r, eps):
+    """2-D Coulomb U^eps(r) = erf(r/eps)/(2 pi r) (Table 1); limit
+    1/(pi^{3/2} eps) at r = 0."""
+    r = np.asarray(r, dtype=np.float64)
+    out = np.empty_like(r)
+    nz = r > 0
+    out[nz] = sp.erf(r[nz] / eps) / (2.0 * math.pi * r[nz])
+    out[~nz] = 1.0 / (math.pi ** 1.5 * eps)
+    return out
+
+
+def coulomb2d_What(k, eps):
+    """Table 1, 2-D Coulomb row: erf(k eps/2) / k; limit eps/sqrt(pi) at k = 0."""
+    k = np.asarray(k, dtype=np.float64)
+    out = np.empty_like(k)
+    nz = k > 0
+    out[nz] = sp.erf(k[nz] * eps / 2.0) / k[nz]
+    out[~nz] = eps / math.sqrt(math.pi)
+    return out
+
+
+def biharmonic2d_Ueps(r, eps):
+    """2-D biharmonic U^eps(r) = -(r^2/(8 pi)) [ln r + E1(r^2/eps^2)/2 - 1]
+    (Table 1); 0 at r = 0."""
+    r = np.asarray(r, dtype=np.float64)
+    return -(r * r) / (8.0 * math.pi) * (_log_plus_half_E1(r, eps) - 1.0)
+
+
+def biharmonic2d_What(k, eps):
+    """Table 1, 2-D biharmonic row:
+    (-16 + exp(-k^2 eps^2/4) (16 + 4 k^2 eps^2 + k^4 eps^4)) / (16 k^4)
+    = (eps^4/16) h(x), x = k^2 eps^2 / 4, h(x) = (exp(-x)(1 + x + x^2) - 1)/x^2.
+    For x < 1 h is summed from its Taylor series, coefficient of x^(j-2)
+    (-1)^j (1/j! - 1/(j-1)! + 1/(j-2)!), 30 terms; h(0) = 1/2, so the k = 0
+    value is eps^4/32."""
+    k = np.asarray(k, dtype=np.float64)
+    x = (k * eps) ** 2 / 4.0
+    h = np.empty_like(x)
+    small = x < 1.0
+    xs = x[small]
+    acc = np.zeros_like(xs)
+    for j in range(31, 1, -1):
+        cj = (-1) ** j * (1.0 / math.factorial(j) - 1.0 / math.factorial(j - 1) + 1.0 / math.factorial(j - 2))
+        acc = acc * xs + cj
+    h[small] = acc
+    xl = x[~small]
+    h[~small] = (np.exp(-xl) * (1.0 + xl + xl * xl) - 1.0) / (xl * xl)
+    return eps ** 4 / 16.0 * h
+
+
 # kernel name -> names of its (U^eps, What) of Table 1, looked up at call time
 KERNELS = {
     "coulomb3d": ("coulomb3d_Ueps", "coulomb3d_What"),
     "biharmonic3d": ("biharmonic3d_Ueps", "biharmonic3d_What"),
+    "poisson2d": ("poisson2d_Ueps", "poisson2d_What"),
+    "coulomb2d": ("coulomb2d_Ueps", "coulomb2d_What"),
+    "biharmonic2d": ("biharmonic2d_Ueps", "biharmonic2d_What"),
 }
+KERNEL_DIM = {"coulomb3d": 3, "biharmonic3d": 3, "poisson2d": 2, "coulomb2d": 2, "biharmonic2d": 2}
 
 
 def kernel_fns(kernel):
@@ -116,12 +211,22 @@ def kernel_fns(kernel):
 
 
 def What_by_quadrature_kernel(k, eps, kernel):
-    """Eq. (Fourier-Symmetric), d = 3, by adaptive quadrature for either
-    kernel: 4 pi int_0^inf (U - U^eps)(r) sin(kr)/(kr) r^2 dr with
-    (U - U^eps)(r) = erfc(r/eps) / (4 pi r) (Coulomb) or
-    r erfc(r/eps) / (8 pi) (biharmonic).  Pins the closed forms."""
+    """Eq. (Fourier-Symmetric) by adaptive quadrature.  d = 3:
+    4 pi int_0^inf (U - U^eps)(r) sin(kr)/(kr) r^2 dr with
+    (U - U^eps)(r) = erfc(r/eps) / (4 pi r) (Coulomb) or r erfc(r/eps) / (8 pi)
+    (biharmonic).  d = 2: 2 pi int_0^inf (U - U^eps)(r) J0(kr) r dr with
+    U - U^eps = E1(r^2/eps^2)/(4 pi) (Poisson), erfc(r/eps)/(2 pi r) (Coulomb),
+    r^2 E1(r^2/eps^2)/(16 pi) (biharmonic).  Pins the closed forms."""
     if kernel == "coulomb3d":
         return What_by_quadrature(k, eps)
+    if kernel in ("poisson2d", "coulomb2d", "biharmonic2d"):
+        diff = {"poisson2d": lambda r: sp.exp1((r / eps) ** 2) / (4.0 * math.pi),
+                "coulomb2d": lambda r: sp.erfc(r / eps) / (2.0 * math.pi * r),
+                "biharmonic2d": lambda r: r * r * sp.exp1((r / eps) ** 2) / (16.0 * math.pi)}[kernel]
+        f = lambda r: 2.0 * math.pi * diff(r) * sp.j0(k * r) * r
+        pts = [eps * 1e-6, eps * 1e-3, eps] if kernel == "poisson2d" else None
+        val, _ = si.quad(f, 0.0, 12.0 * eps, limit=800, epsabs=0.0, epsrel=1e-13, points=pts)
+        return val
     if k == 0:
         f = lambda r: 0.5 * sp.erfc(r / eps) * r ** 3
     else:
@@ -135,8 +240,17 @@ def appendix_b_bound(R0, eps, kernel="coulomb3d"):
     3-D Coulomb: R0^2 f(c), c = R0/eps, f(c) = (1/(4 pi c^2)) int_c^inf
     s erfc(s) ds, as App. B states it.  3-D biharmonic (App. B does not treat
     it; the same integral of its U - U^eps = r erfc(r/eps)/(8 pi)):
-    (eps^4 / (8 pi)) int_c^inf s^3 erfc(s) ds."""
+    (eps^4 / (8 pi)) int_c^inf s^3 erfc(s) ds.  2-D kernels: the integral
+    int_{R0}^inf |U - U^eps| r dr of App. B's general bound with d = 2 (the
+    paper gives its thresholds R0/5.64 for Coulomb and R0/5.75 for Poisson)."""
     c = R0 / eps
+    if KERNEL_DIM.get(kernel) == 2:
+        # d = 2: int_{R0}^inf |U - U^eps| r dr
+        diff = {"poisson2d": lambda r: sp.exp1((r / eps) ** 2) / (4.0 * math.pi),
+                "coulomb2d": lambda r: sp.erfc(r / eps) / (2.0 * math.pi * r),
+                "biharmonic2d": lambda r: r * r * sp.exp1((r / eps) ** 2) / (16.0 * math.pi)}[kernel]
+        val, _ = si.quad(lambda r: diff(r) * r, R0, np.inf, epsabs=0.0, epsrel=1e-12, limit=200)
+        return val
     if kernel == "biharmonic3d":
         tail, _ = si.quad(lambda s: s ** 3 * sp.erfc(s), c, np.inf, epsabs=0.0, epsrel=1e-12, limit=200)
         return eps ** 4 * tail / (8.0 * math.pi)
@@ -154,16 +268,21 @@ def _offsets(n):
 
 def mesh_steps(L, n):
     """h_j = 2 L_j / n_j (Sec. 2; Sec. 2.4 for the anisotropic box)."""
-    return [2.0 * L[j] / n[j] for j in range(3)]
+    return [2.0 * L[j] / n[j] for j in range(len(n))]
+
+
+def _radius(axes):
+    """|(x_0, ..., x_{d-1})| on the tensor grid of the given per-axis values."""
+    g = np.meshgrid(*axes, indexing="ij", sparse=True)
+    return np.sqrt(sum(a * a for a in g))
 
 
 def tensor_T1(L, n, eps, kernel="coulomb3d"):
     """T^(1) on the doubled grid: T^(1)_o = h_0 h_1 h_2 U^eps(|(o_0 h_0, o_1 h_1,
     o_2 h_2)|) (Sec. 2.1, Eq. Tensor1; Sec. 2.4, Eq. TensorAnis first term)."""
     h = mesh_steps(L, n)
-    x = [_offsets(n[j]) * h[j] for j in range(3)]
-    r = np.sqrt(x[0][:, None, None] ** 2 + x[1][None, :, None] ** 2 + x[2][None, None, :] ** 2)
-    return h[0] * h[1] * h[2] * kernel_fns(kernel)[0](r, eps)
+    r = _radius([_offsets(n[j]) * h[j] for j in range(len(n))])
+    return float(np.prod(h)) * kernel_fns(kernel)[0](r, eps)
 
 
 def fourier_W(L, n, eps, kernel="coulomb3d"):
@@ -171,8 +290,7 @@ def fourier_W(L, n, eps, kernel="coulomb3d"):
     p_j = -n_j .. n_j - 1 (Sec. 2.2, Eqs. DisFourierSeries, Wk; Sec. 2.4,
     Eq. WkAnis), with the bounded-domain transform replaced by the whole-space
     one (Eq. FouTran), i.e. W(mu) = What(|mu|).  Stored in FFT order."""
-    mu = [math.pi * _offsets(n[j]) / (2.0 * L[j]) for j in range(3)]
-    k = np.sqrt(mu[0][:, None, None] ** 2 + mu[1][None, :, None] ** 2 + mu[2][None, None, :] ** 2)
+    k = _radius([math.pi * _offsets(n[j]) / (2.0 * L[j]) for j in range(len(n))])
     return kernel_fns(kernel)[1](k, eps)
 
 
@@ -202,7 +320,7 @@ def spectrum(T):
 
 def spectrum_octant(T, n):
     """The spectrum on p_j in [0, n_j]: all of it, since it is even per axis."""
-    return spectrum(T)[: n[0] + 1, : n[1] + 1, : n[2] + 1].copy()
+    return spectrum(T)[tuple(slice(0, nj + 1) for nj in n)].copy()
 
 
 # ----------------------------------------------------------- convolution ----
@@ -212,46 +330,40 @@ def apply_fft(T, rho):
     """Phi_m = sum_i T_{m-i} rho_i (Eq. DiscConv) by the route of Sec. 2.3:
     zero-pad rho to the doubled grid, FFT, multiply by the FFT of T, inverse
     FFT, keep the first n_j entries per axis."""
-    n = rho.shape
+    box = tuple(slice(0, nj) for nj in rho.shape)
     pad = np.zeros(T.shape)
-    pad[: n[0], : n[1], : n[2]] = rho
+    pad[box] = rho
     out = np.fft.ifftn(np.fft.fftn(T) * np.fft.fftn(pad))
-    return out.real[: n[0], : n[1], : n[2]].copy()
+    return out.real[box].copy()
 
 
 def apply_spectrum(S, rho):
     """Same as apply_fft with the spectrum of T (from ``spectrum``) cached:
     the 'Execution' phase of Example 2."""
-    n = rho.shape
+    box = tuple(slice(0, nj) for nj in rho.shape)
     pad = np.zeros(S.shape)
-    pad[: n[0], : n[1], : n[2]] = rho
+    pad[box] = rho
     out = np.fft.ifftn(S * S.size * np.fft.fftn(pad))
-    return out.real[: n[0], : n[1], : n[2]].copy()
+    return out.real[box].copy()
 
 
 def T_at(T, o):
-    """T at signed offsets o = (o0, o1, o2) (arrays), |o_j| < n_j."""
-    return T[o[0] % T.shape[0], o[1] % T.shape[1], o[2] % T.shape[2]]
+    """T at signed offsets o = (o_0, ..., o_{d-1}) (arrays), |o_j| < n_j."""
+    return T[tuple(o[j] % T.shape[j] for j in range(T.ndim))]
 
 
 def apply_direct(T, rho):
     """Eq. DiscConv by brute force, O(V^2): for every output point m, the
     sum over all source points i of T_{m-i} rho_i.  Small grids only."""
-    n = rho.shape
-    i0, i1, i2 = np.meshgrid(*[np.arange(n[j]) for j in range(3)], indexing="ij")
-    i0, i1, i2, r = i0.ravel(), i1.ravel(), i2.ravel(), rho.ravel()
-    out = np.empty(rho.size)
-    for m, (m0, m1, m2) in enumerate(np.ndindex(*n)):
-        out[m] = np.dot(T_at(T, (m0 - i0, m1 - i1, m2 - i2)), r)
-    return out.reshape(n)
+    return apply_direct_at(T, rho, list(np.ndindex(*rho.shape))).reshape(rho.shape)
 
 
 def apply_direct_at(T, rho, points):
     """Eq. DiscConv by brute force at selected output indices only."""
     n = rho.shape
-    i0, i1, i2 = np.meshgrid(*[np.arange(n[j]) for j in range(3)], indexing="ij")
-    i0, i1, i2, r = i0.ravel(), i1.ravel(), i2.ravel(), rho.ravel()
-    return np.array([np.dot(T_at(T, (m0 - i0, m1 - i1, m2 - i2)), r) for (m0, m1, m2) in points])
+    idx = [a.ravel() for a in np.meshgrid(*[np.arange(nj) for nj in n], indexing="ij")]
+    r = rho.ravel()
+    return np.array([np.dot(T_at(T, tuple(m[j] - idx[j] for j in range(len(n)))), r) for m in points])
 
 
 def rel_error(a, b):

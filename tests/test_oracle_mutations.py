@@ -73,7 +73,8 @@ def _ueps_erfc(r, eps):
 
 fsa_orig = {k: getattr(fsa, k) for k in ("coulomb3d_What", "coulomb3d_Ueps", "biharmonic3d_What",
                                          "biharmonic3d_Ueps", "tensor_T", "tensor_T1", "tensor_T2",
-                                         "fourier_W", "apply_fft")}
+                                         "fourier_W", "apply_fft", "poisson2d_Ueps", "coulomb2d_What",
+                                         "coulomb2d_Ueps", "biharmonic2d_What", "biharmonic2d_Ueps")}
 
 
 def _mu_wrong_scale(L, n, eps, kernel="coulomb3d"):
@@ -155,3 +156,78 @@ def test_pins_catch_mutation(name, monkeypatch):
     attr, fn = MUTATIONS[name]
     monkeypatch.setattr(fsa, attr, fn)
     assert not pins_pass(), f"pins missed the planted mistake: {name}"
+
+
+# ---- d = 2 -------------------------------------------------------------------
+
+def pins_pass_2d():
+    """The 2-D discretisation-error rows of Tables 2, 4 and 5 (h = 1 and 1/2)
+    and brute force on a small plane."""
+    from workloads import grid_axes
+    rows = (("coulomb2d", 8.0, 0.8, cf.coulomb2d_gaussian_r, ((1.0, 1.3856e-2), (0.5, 2.9648e-6))),
+            ("poisson2d", 8.0, 1.2, cf.poisson2d_gaussian_r, ((1.0, 1.3761e-3), (0.5, 5.5617e-9))),
+            ("biharmonic2d", 12.0, 1.2, cf.biharmonic2d_gaussian_r, ((1.0, 2.6558e-5), (0.5, 5.8860e-12))))
+    for kernel, L, s2, fn, tab in rows:
+        for h, want in tab:
+            n = int(round(2 * L / h))
+            x = grid_axes((L, L), (n, n))
+            rho = np.exp(-(x[0][:, None] ** 2 + x[1][None, :] ** 2) / s2)
+            e = fsa.rel_error(fsa.solve((L, L), (n, n), 1.0, rho, kernel=kernel),
+                              cf.radial_on_grid_2d(fn, 1.0, s2, (L, L), (n, n)))
+            if abs(e - want) > 5e-4 * want:
+                return False
+    n, L = (6, 8), (3.0, 2.5)
+    T = fsa.tensor_T(L, n, 0.6, kernel="poisson2d")
+    rho = np.random.default_rng(3).standard_normal(n)
+    return fsa.rel_error(fsa.apply_fft(T, rho), fsa.apply_direct(T, rho)) < 1e-13
+
+
+def test_unmutated_2d_pins_pass():
+    assert pins_pass_2d()
+
+
+def _p2_full_E1(r, eps):
+    # E1(r^2/eps^2) without the factor 1/2 of Eq. lnrAppr
+    import scipy.special as sp
+    r = np.asarray(r, dtype=np.float64)
+    rr = np.where(r > 0, r, 1.0)
+    return np.where(r > 0, -(np.log(rr) + sp.exp1((rr / eps) ** 2)) / (2 * math.pi), 0.0)
+
+
+def _c2_what_no_half(k, eps):
+    # erf(k eps) / k instead of erf(k eps / 2) / k
+    return np.where(np.asarray(k) > 0, sp.erf(np.asarray(k) * eps) / np.where(np.asarray(k) > 0, k, 1.0), eps / math.sqrt(math.pi))
+
+
+def _c2_ueps_3d_scale(r, eps):
+    # 1/(4 pi r) instead of 1/(2 pi r)
+    return 0.5 * fsa_orig["coulomb2d_Ueps"](r, eps)
+
+
+def _b2_what_coefficient(k, eps):
+    # Table 1's 4 k^2 eps^2 term read as 2 k^2 eps^2
+    k = np.asarray(k, dtype=np.float64)
+    kk = np.where(k > 0, k, 1.0)
+    v = (-16 + np.exp(-(kk * eps) ** 2 / 4) * (16 + 2 * (kk * eps) ** 2 + (kk * eps) ** 4)) / (16 * kk ** 4)
+    return np.where(k > 0, v, eps ** 4 / 32)
+
+
+def _b2_ueps_no_minus_one(r, eps):
+    # the "- 1" in the bracket dropped
+    return fsa_orig["biharmonic2d_Ueps"](r, eps) - np.asarray(r, dtype=np.float64) ** 2 / (8 * math.pi)
+
+
+MUTATIONS_2D = {
+    "2-D Poisson Ueps with E1 instead of E1/2": ("poisson2d_Ueps", _p2_full_E1),
+    "2-D Coulomb What erf(k eps)": ("coulomb2d_What", _c2_what_no_half),
+    "2-D Coulomb Ueps 1/(4 pi r)": ("coulomb2d_Ueps", _c2_ueps_3d_scale),
+    "2-D biharmonic What 4k^2eps^2 -> 2k^2eps^2": ("biharmonic2d_What", _b2_what_coefficient),
+    "2-D biharmonic Ueps without -1": ("biharmonic2d_Ueps", _b2_ueps_no_minus_one),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS_2D))
+def test_2d_pins_catch_mutation(name, monkeypatch):
+    attr, fn = MUTATIONS_2D[name]
+    monkeypatch.setattr(fsa, attr, fn)
+    assert not pins_pass_2d(), f"pins missed the planted mistake: {name}"

@@ -311,3 +311,143 @@ def test_case2_density_is_minus_laplacian():
     inner = rho[2:-2, 2:-2, 2:-2]
     # second-order stencil: O(h^2) agreement
     assert np.max(np.abs(-lap - inner)) < 0.05 * np.max(np.abs(inner))
+
+
+# ---- d = 2: the kernels of Table 1 on the plane ---------------------------------
+
+def _case1_2d(L, s2, h):
+    from workloads import grid_axes
+    n = int(round(2 * L / h))
+    x = grid_axes((L, L), (n, n))
+    return (L, L), (n, n), np.exp(-(x[0][:, None] ** 2 + x[1][None, :] ** 2) / s2)
+
+
+@pytest.mark.parametrize("kernel", ["poisson2d", "coulomb2d", "biharmonic2d"])
+@pytest.mark.parametrize("eps", [0.4, 1.0])
+def test_2d_What_equals_hankel_integral(kernel, eps):
+    """Table 1's 2-D closed forms equal Eq. (Fourier-Symmetric), d = 2
+    (2 pi int (U - U^eps) J0(kr) r dr), by quadrature."""
+    for k in [0.0, 1e-5, 0.05, 0.3, 1.0, 1.9, 2.1, 3.0, 10.0]:
+        a = fsa.kernel_fns(kernel)[1](np.array([k]), eps)[0]
+        b = fsa.What_by_quadrature_kernel(k, eps, kernel)
+        assert abs(a - b) <= 1e-14 * abs(b) + 1e-20, (k, a, b)
+
+
+@pytest.mark.parametrize("kernel", ["poisson2d", "biharmonic2d"])
+def test_2d_log_Ueps_series_meets_direct(kernel):
+    """ln r + E1(r^2/eps^2)/2 from its series (u < 1) against the direct sum
+    near u = 1, and the r = 0 limits."""
+    import scipy.special as sp
+    eps = 0.8
+    for u in (0.9, 0.999):
+        r = math.sqrt(u) * eps
+        br = math.log(r) + 0.5 * sp.exp1(u)
+        want = -br / (2 * math.pi) if kernel == "poisson2d" else -(r * r) / (8 * math.pi) * (br - 1)
+        assert fsa.kernel_fns(kernel)[0](np.array([r]), eps)[0] == pytest.approx(want, rel=2e-15)
+    u0 = fsa.kernel_fns(kernel)[0](np.array([0.0]), eps)[0]
+    if kernel == "poisson2d":
+        assert u0 == pytest.approx(-(math.log(eps) - 0.5 * 0.5772156649015329) / (2 * math.pi), rel=1e-15)
+    else:
+        assert u0 == 0.0
+
+
+def test_2d_appendix_b_thresholds():
+    for kernel, R0, c, tol in read_golden("appendix_b_thresholds_2d.txt"):
+        R0, c, tol = float(R0), float(c), float(tol)
+        assert fsa.appendix_b_bound(R0, R0 / c, kernel) <= tol
+        assert fsa.appendix_b_bound(R0, R0 / (c - 0.05), kernel) > tol
+
+
+@pytest.mark.parametrize("fn,args", [
+    ("coulomb2d", (0.8, [1e-3, 0.7, 2.5, 6.0])),
+    ("poisson2d", (0.8, [1e-3, 0.7, 2.5, 6.0])),
+])
+def test_2d_closed_forms_equal_radial_integrals(fn, args):
+    """2-D Coulomb: the Bessel form against the angular mean of 1/|x-y| over
+    a circle, (2/pi) K(m)/(r+t), m = 4rt/(r+t)^2, integrated in t.  2-D
+    Poisson: the E1 form against the integral of t rho(t) ln max(r, t)."""
+    import scipy.integrate as si
+    import scipy.special as sp
+    s2, rs = args
+    for r in rs:
+        if fn == "coulomb2d":
+            g = lambda t: t * math.exp(-t * t / s2) * (2 / math.pi) * sp.ellipk(min(4 * r * t / (r + t) ** 2, 1 - 1e-16)) / (r + t)
+            want = cf.coulomb2d_gaussian_r(1.0, s2, np.array([r]))[0]
+        else:
+            g = lambda t: -t * math.exp(-t * t / s2) * math.log(max(r, t))
+            want = cf.poisson2d_gaussian_r(1.0, s2, np.array([r]))[0]
+        v = si.quad(g, 0, r, limit=400, epsabs=0, epsrel=1e-12)[0] + si.quad(g, r, np.inf, limit=400, epsabs=0, epsrel=1e-12)[0]
+        assert want == pytest.approx(v, rel=1e-10)
+
+
+def test_2d_biharmonic_angular_mean_and_closed_form():
+    """The angular mean of |x-y|^2 ln|x-y| over |y| = t used by the 2-D
+    biharmonic closed form, against quadrature over the circle; and the 1-D
+    integral form against a direct polar double integral at one point."""
+    import scipy.integrate as si
+    for r, t in ((0.7, 1.3), (2.0, 0.5), (1.0, 1.0)):
+        m = si.quad(lambda th: (r * r + t * t - 2 * r * t * math.cos(th)) * 0.5
+                    * math.log(r * r + t * t - 2 * r * t * math.cos(th) + 1e-300), 0, 2 * math.pi, limit=400)[0] / (2 * math.pi)
+        assert m == pytest.approx((r * r + t * t) * math.log(max(r, t)) + min(r, t) ** 2, rel=1e-10)
+    s2, r = 0.8, 1.1
+    U = lambda s: -s * s * (math.log(s) - 1) / (8 * math.pi) if s > 0 else 0.0
+    val = si.dblquad(lambda th, t: t * math.exp(-t * t / s2) * U(math.sqrt(max(r * r + t * t - 2 * r * t * math.cos(th), 0.0))),
+                     0, 12, 0, 2 * math.pi, epsabs=1e-12, epsrel=1e-10)[0]
+    assert cf.biharmonic2d_gaussian_r(1.0, s2, np.array([r]))[0] == pytest.approx(val, rel=1e-9)
+
+
+def _check_table_row(err, printed):
+    if printed > 1e-10:
+        assert err == pytest.approx(printed, rel=5e-4)
+    else:
+        assert err < 4 * printed
+
+
+@pytest.mark.parametrize("h,n,printed,taken", [tuple(r) for r in read_golden("table2_coulomb2d_iso_double.txt")])
+def test_table2_coulomb2d(h, n, printed, taken):
+    L, nn, rho = _case1_2d(8.0, 0.8, float(h))
+    assert nn[0] == int(n)
+    err = fsa.rel_error(fsa.solve(L, nn, 1.0, rho, kernel="coulomb2d"),
+                        cf.radial_on_grid_2d(cf.coulomb2d_gaussian_r, 1.0, 0.8, L, nn))
+    _check_table_row(err, float(taken))
+
+
+@pytest.mark.parametrize("case,hg,printed", [tuple(r) for r in read_golden("table4_poisson2d_double.txt")])
+def test_table4_poisson2d(case, hg, printed):
+    from workloads import grid_axes
+    hg, printed = float(hg), float(printed)
+    if case == "iso":
+        L, nn, rho = _case1_2d(8.0, 1.2, hg)
+        exact = cf.radial_on_grid_2d(cf.poisson2d_gaussian_r, 1.0, 1.2, L, nn)
+        err = fsa.rel_error(fsa.solve(L, nn, 1.0, rho, kernel="poisson2d"), exact)
+    else:
+        g, s2 = hg, 1.2 ** 2
+        L, nn = (10.0, 10.0 * g), (160, 160)
+        x = grid_axes(L, nn)
+        X, Y = x[0][:, None], x[1][None, :]
+        exact = np.exp(-(X ** 2 + Y ** 2 / g ** 2) / s2)
+        rho = exact * (-4 * X ** 2 / s2 ** 2 - 4 * Y ** 2 / (g ** 4 * s2 ** 2) + 2 / s2 + 2 / (g ** 2 * s2))
+        err = fsa.rel_error(fsa.solve(L, nn, 0.4, rho, kernel="poisson2d"), exact)
+    if case == "iso":
+        _check_table_row(err, printed)
+    else:  # round-off level
+        assert err < max(1e-15, 2 * printed)
+
+
+@pytest.mark.parametrize("h,n,printed", [tuple(r) for r in read_golden("table5_biharmonic2d_iso_double.txt")])
+def test_table5_biharmonic2d(h, n, printed):
+    L, nn, rho = _case1_2d(12.0, 1.2, float(h))
+    assert nn[0] == int(n)
+    err = fsa.rel_error(fsa.solve(L, nn, 1.0, rho, kernel="biharmonic2d"),
+                        cf.radial_on_grid_2d(cf.biharmonic2d_gaussian_r, 1.0, 1.2, L, nn))
+    _check_table_row(err, float(printed))
+
+
+@pytest.mark.parametrize("n", [(4, 6), (8, 8), (6, 12)])
+@pytest.mark.parametrize("kernel", ["poisson2d", "coulomb2d", "biharmonic2d"])
+def test_2d_fft_route_equals_brute_force(n, kernel):
+    rng = np.random.default_rng(3)
+    L = (3.0, 2.5)
+    T = fsa.tensor_T(L, n, 0.6, kernel=kernel)
+    rho = rng.standard_normal(n)
+    assert fsa.rel_error(fsa.apply_fft(T, rho), fsa.apply_direct(T, rho)) < 1e-13
