@@ -60,9 +60,13 @@ typedef enum {
 } fsa_status;
 
 typedef enum {
-  FSA_KERNEL_COULOMB3D = 0,   /* U = 1/(4 pi r), U^eps = U erf(r/eps) (Table 1) */
-  FSA_KERNEL_BIHARMONIC3D = 1 /* U = r/(8 pi), U^eps = U erf(r/eps) (Table 1;    */
-                              /* Example 4)                                      */
+  FSA_KERNEL_COULOMB3D = 0,    /* d = 3: U = 1/(4 pi r), U^eps = U erf(r/eps) (Table 1)      */
+  FSA_KERNEL_BIHARMONIC3D = 1, /* d = 3: U = r/(8 pi), U^eps = U erf(r/eps) (Table 1; Ex. 4) */
+  FSA_KERNEL_POISSON2D = 2,    /* d = 2: U = -ln(r)/(2 pi),                                  */
+                               /* U^eps = -(ln r + E1(r^2/eps^2)/2)/(2 pi) (Eq. lnrAppr)      */
+  FSA_KERNEL_COULOMB2D = 3,    /* d = 2: U = 1/(2 pi r), U^eps = U erf(r/eps) (Table 1)       */
+  FSA_KERNEL_BIHARMONIC2D = 4  /* d = 2: U = -r^2 (ln r - 1)/(8 pi),                           */
+                               /* U^eps = -r^2 (ln r + E1(r^2/eps^2)/2 - 1)/(8 pi) (Table 1)  */
 } fsa_kernel;
 
 typedef enum {
@@ -100,10 +104,15 @@ typedef struct {
   size_t spectrum_bytes;    /* device bytes of the stored spectrum octant             */
   const void* spectrum;     /* device pointer: (n0+1) x (n1+1) x (n2+1) dtype, C order */
   fsa_kernel kernel;        /* the plan's kernel                                      */
+  int d;                    /* 3, or 2 for the plane kernels (then n[2] = 1, the      */
+                            /* spectrum octant is (n0+1) x (n1+1), 3 launches/apply)  */
 } fsa_plan_info;
 
 /* Create a plan (the "Precomp" object of Sec. 5, Example 2) for the grid
- * n[0..d-1] on the box prod_j [-L_j, L_j].  d must be 3.  The plan owns,
+ * n[0..d-1] on the box prod_j [-L_j, L_j].  d is the kernel's dimension: 3
+ * for the 3-D kernels, 2 for the plane kernels (Poisson, Coulomb, biharmonic
+ * of Table 1), whose solves run R2C along axis 0, one middle pass along
+ * axis 1 (forward, multiply, inverse) and C2R (Sec. 2.3 with d = 2).  The plan owns,
  * on the chosen device, the spectrum octant and the apply workspace
  * (fsa_plan_info.workspace_bytes); both are freed by fsa_plan_destroy.
  * kernel: FSA_KERNEL_COULOMB3D or FSA_KERNEL_BIHARMONIC3D (Table 1); the apply

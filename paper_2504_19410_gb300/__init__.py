@@ -27,10 +27,11 @@ def _cur_stream(stream):
 
 
 class Plan:
-    """A device-resident FSA plan: grid n (3 ints), box half-widths L, dtype
-    'f32' or 'f64', kernel 'coulomb3d' or 'biharmonic3d' (Table 1).  eps = 0
-    picks min(1, R0/6).  The spectrum is generated on construction unless
-    generate=False."""
+    """A device-resident FSA plan: grid n (3 ints, or 2 for a plane kernel),
+    box half-widths L, dtype 'f32' or 'f64', kernel 'coulomb3d',
+    'biharmonic3d', 'poisson2d', 'coulomb2d' or 'biharmonic2d' (Table 1).
+    eps = 0 picks min(1, R0/6).  The spectrum is generated on construction
+    unless generate=False."""
 
     def __init__(self, L, n, dtype="f32", eps=0.0, eps_tol=0.0, device=-1, generate=True, stream=None,
                  l2_chunk_mb=0, kernel="coulomb3d"):
@@ -38,8 +39,8 @@ class Plan:
         self.n = tuple(int(x) for x in n)
         self.L = tuple(float(x) for x in L)
         self.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
-        self.handle = capi.fsa_plan_create(self.kernel, 3, self.L, self.n, self.dtype, eps, eps_tol, device,
-                                           l2_chunk_mb)
+        self.handle = capi.fsa_plan_create(self.kernel, len(self.n), self.L, self.n, self.dtype, eps, eps_tol,
+                                           device, l2_chunk_mb)
         if generate:
             self.generate(stream)
 

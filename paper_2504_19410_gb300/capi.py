@@ -18,7 +18,14 @@ FSA_OK, FSA_ERR_INVALID_ARG, FSA_ERR_UNSUPPORTED, FSA_ERR_EPS, FSA_ERR_OOM, FSA_
     FSA_ERR_NOT_GENERATED, FSA_ERR_BUSY, FSA_ERR_TIMEOUT, FSA_ERR_DEVICE_TIMEOUT, FSA_ERR_NOT_FOUND = range(11)
 FSA_KERNEL_COULOMB3D = 0
 FSA_KERNEL_BIHARMONIC3D = 1
-KERNELS = {"coulomb3d": FSA_KERNEL_COULOMB3D, "biharmonic3d": FSA_KERNEL_BIHARMONIC3D}
+FSA_KERNEL_POISSON2D = 2
+FSA_KERNEL_COULOMB2D = 3
+FSA_KERNEL_BIHARMONIC2D = 4
+KERNELS = {"coulomb3d": FSA_KERNEL_COULOMB3D, "biharmonic3d": FSA_KERNEL_BIHARMONIC3D,
+           "poisson2d": FSA_KERNEL_POISSON2D, "coulomb2d": FSA_KERNEL_COULOMB2D,
+           "biharmonic2d": FSA_KERNEL_BIHARMONIC2D}
+KERNEL_DIM = {FSA_KERNEL_COULOMB3D: 3, FSA_KERNEL_BIHARMONIC3D: 3, FSA_KERNEL_POISSON2D: 2,
+              FSA_KERNEL_COULOMB2D: 2, FSA_KERNEL_BIHARMONIC2D: 2}
 FSA_F32, FSA_F64 = 0, 1
 FSA_REQ_QUEUED, FSA_REQ_RUNNING, FSA_REQ_DONE, FSA_REQ_FAILED = range(4)
 
@@ -39,7 +46,7 @@ class PlanInfo(C.Structure):
                 ("generated", C.c_int), ("arithmetic", C.c_int), ("launches_per_apply", C.c_int),
                 ("workspace_bytes", C.c_size_t),
                 ("spectrum_bytes", C.c_size_t),
-                ("spectrum", C.c_void_p), ("kernel", C.c_int)]
+                ("spectrum", C.c_void_p), ("kernel", C.c_int), ("d", C.c_int)]
 
 
 class ServeOpts(C.Structure):
@@ -258,7 +265,7 @@ def fsa_serve_create(max_inflight=0, streams=0, hbm_fraction=0.0, hbm_budget_byt
 
 
 def fsa_serve_submit(server, L, n, dtype, rho, phi, eps=0.0, kernel=FSA_KERNEL_COULOMB3D):
-    req = Request(kernel, 3, (C.c_double * 3)(*map(float, L)), (C.c_int * 3)(*map(int, n)), int(dtype),
+    req = Request(kernel, len(n), (C.c_double * 3)(*map(float, L)), (C.c_int * 3)(*map(int, n)), int(dtype),
                   float(eps), _ptr(rho), _ptr(phi))
     t = C.c_uint64()
     check(lib().fsa_serve_submit(server, C.byref(req), C.byref(t)))

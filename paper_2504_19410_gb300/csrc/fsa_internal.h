@@ -11,6 +11,11 @@
 
 namespace fsa {
 
+// Dimension of a kernel of Table 1 (2 for the plane kernels, else 3).
+inline int kernel_dim(fsa_kernel k) {
+  return (k == FSA_KERNEL_POISSON2D || k == FSA_KERNEL_COULOMB2D || k == FSA_KERNEL_BIHARMONIC2D) ? 2 : 3;
+}
+
 enum PassKind { kR2C = 0, kRowFwd = 1, kColMid = 2, kRowInv = 3, kC2R = 4, kNumPass = 5 };
 
 // Tile geometry of one pass instance (lines per CTA, threads, shared bytes).
@@ -40,6 +45,8 @@ struct PassFns {
   cudaError_t (*colm)(const Jobs&, int M2, int planes, cudaStream_t) = nullptr;
   cudaError_t (*rowi)(const Jobs&, long long rows, cudaStream_t) = nullptr;
   cudaError_t (*c2r)(const Jobs&, long long C, cudaStream_t) = nullptr;
+  // d = 2 middle pass (first generation only; nullptr for the others)
+  cudaError_t (*rowm)(const Jobs&, long long rows, cudaStream_t) = nullptr;
 };
 // FP32 generations: 1 Stockham radix-8, 2 two-step register, 3 = 2 with the
 // middle pass prefetching its next tile (cp.async), 4 = 3 with the row passes
@@ -117,6 +124,7 @@ struct fsa_plan {
   double R0;
   double eps_bound;
   fsa_kernel kernel;
+  int d;  // 3, or 2 for the plane kernels (then n[2] = 1 and the octant is (n0+1)(n1+1))
   fsa_dtype dtype;
   int device;
   int generated;

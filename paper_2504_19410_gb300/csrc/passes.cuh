@@ -167,6 +167,52 @@ __global__ void __launch_bounds__(W * T, minb_mid<V, W * T>()) k_col_mid(const J
   }
 }
 
+// ------------------------------------------------- middle pass, d = 2 --
+// The 2-D path's middle pass (Sec. 2.3 with d = 2): after the R2C pass along
+// axis 0, each row k0 of X (n1 = M/2 complex values, contiguous) is padded to
+// M, transformed, multiplied by the spectrum S[k0][min(k1, M - k1)] (real,
+// even; row stride n1 + 1), transformed back and cropped to n1 values, in
+// place.  W rows per CTA in an odd-pitch shared tile, as the row passes.
+template <typename V, class P, int W, int T>
+__global__ void __launch_bounds__(W * T, MinB<V>::value) k_row_mid(const Jobs jobs, long long rows) {
+  using R = typename RealOf<V>::T;
+  constexpr int M = P::M, n = M / 2, PITCH = M + 1, NT = W * T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const long long tpj = (rows + W - 1) / W;
+  for (long long tile = blockIdx.x; tile < tpj * jobs.count; tile += gridDim.x) {
+  const Job& jb = jobs.j[tile / tpj];
+  V* __restrict__ X = static_cast<V*>(jb.out);
+  const typename Io<V>::S* __restrict__ S = static_cast<const typename Io<V>::S*>(jb.S);
+  const long long row0 = (tile % tpj) * W;
+  for (int i = threadIdx.x; i < W * n; i += NT) {
+    const int l = i / n, p = i - l * n;
+    const long long row = row0 + l;
+    sm[l * PITCH + p] = row < rows ? X[row * n + p] : czero<V>();
+  }
+  __syncthreads();
+  const int l = threadIdx.x % W, t = threadIdx.x / W;
+  const long long row = row0 + l;
+  const bool ok = row < rows;
+  const typename Io<V>::S* srow = S + (ok ? row : 0) * (n + 1);
+  SLine<V, 1> sl{sm + l * PITCH};
+  auto first = [&](int p) -> V { return p < n ? sl.get(p) : czero<V>(); };
+  auto to_sm = [&](int p, V v) { sl.put(p, v); };
+  fft_line<P, true, T, V, true, false>(t, first, to_sm, sl);
+  auto mul = [&](int p) -> V {
+    const R sv = ok ? load_spec<V>(srow + min(p, M - p)) : R(0);
+    return cscale(sl.get(p), sv);
+  };
+  fft_line<P, false, T, V, false, true>(t, mul, to_sm, sl);
+  for (int i = threadIdx.x; i < W * n; i += NT) {
+    const int l2 = i / n, p = i - l2 * n;
+    const long long r2 = row0 + l2;
+    if (r2 < rows) X[r2 * n + p] = canon(sm[l2 * PITCH + p]);
+  }
+  __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- pass 4 --
 template <typename V, class P, int W, int T>
 __global__ void __launch_bounds__(W * T, MinB<V>::value) k_row_inv(const Jobs jobs, long long rows) {

@@ -35,6 +35,7 @@ template <typename V, int M> struct Inst {
     set((const void*)k_row_fwd<V, P, W, T>, SM_ROWS);
     set((const void*)k_col_mid<V, P, WC, TC>, SM_MID);
     set((const void*)k_row_inv<V, P, W, T>, SM_ROWS);
+    set((const void*)k_row_mid<V, P, W, T>, SM_ROWS);
     set((const void*)k_c2r_ax0<V, P, W, T>, SM_STRIDED);
     return e;
   }
@@ -61,6 +62,13 @@ template <typename V, int M> struct Inst {
     const long long tiles = (long long)((M2 + WC - 1) / WC) * planes * jobs.count;
     auto f = k_col_mid<V, P, WC, TC>;
     f<<<persistent_grid((const void*)f, NTC, SM_MID, tiles), NTC, SM_MID, s>>>(jobs, M2, planes);
+    return cudaGetLastError();
+  }
+  // the d = 2 middle pass: rows of the R2C output, in place
+  static cudaError_t rowm(const Jobs& jobs, long long rows, cudaStream_t s) {
+    const long long tiles = (rows + W - 1) / W * jobs.count;
+    auto f = k_row_mid<V, P, W, T>;
+    f<<<persistent_grid((const void*)f, NT, SM_ROWS, tiles), NT, SM_ROWS, s>>>(jobs, rows);
     return cudaGetLastError();
   }
   static cudaError_t rowi(const Jobs& jobs, long long rows, cudaStream_t s) {
@@ -193,8 +201,12 @@ template <int M> struct Inst2 {
 }  // namespace detail
 
 // Launchers of one instance as a function table (see fsa_internal.h).
+template <class I, class = void> struct HasRowm : std::false_type {};
+template <class I> struct HasRowm<I, std::void_t<decltype(&I::rowm)>> : std::true_type {};
+
 template <class I> PassFns fns_of() {
   PassFns f;
+  if constexpr (HasRowm<I>::value) f.rowm = &I::rowm;
   f.prepare = &I::prepare;
   f.geometry = &I::geometry;
   f.r2c = &I::r2c;

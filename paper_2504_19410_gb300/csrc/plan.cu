@@ -273,8 +273,53 @@ template cudaError_t group_passes<double2>(const int*, int, const void* const*, 
 template cudaError_t group_passes<cdw>(const int*, int, const void* const*, void* const*, void* const*,
                                        void* const*, const void* const*, cudaStream_t, PassTrace*, long long);
 
+// The d = 2 path (Sec. 2.3 with two axes): R2C along axis 0 over the n1
+// real columns, the row middle pass (axis 1 forward, multiply, inverse) in
+// place on X, C2R along axis 0.  n = (n0, n1, 1); Y is not used.
+template <typename V> int first_gen_arith() {
+  if constexpr (std::is_same<V, float2>::value) return kArithF32G1;
+  else if constexpr (std::is_same<V, double2>::value) return kArithF64;
+  else return kArithDW;
+}
+
+template <typename V>
+cudaError_t group_passes_2d(const int* n, int count, const void* const* rho, void* const* phi, void* const* X,
+                            const void* const* S, cudaStream_t s, PassTrace* tr) {
+  const int n0 = n[0], n1 = n[1];
+  const long long C = n1, rows = n0 + 1;
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < count && e == cudaSuccess; b += kMaxJobs) {
+    const int m = count - b < kMaxJobs ? count - b : kMaxJobs;
+    Jobs j1{}, j2{}, j3{};
+    j1.count = j2.count = j3.count = m;
+    for (int i = 0; i < m; ++i) {
+      const int k = b + i;
+      j1.j[i] = Job{rho[k], X[k], nullptr};
+      j2.j[i] = Job{X[k], X[k], S[k]};
+      j3.j[i] = Job{X[k], phi[k], nullptr};
+    }
+    const PassFns& f1 = pass_fns(arith_for<V>(kR2C, 2 * n0), 2 * n0);
+    const PassFns& f2 = pass_fns(first_gen_arith<V>(), 2 * n1);
+    const PassFns& f3 = pass_fns(arith_for<V>(kC2R, 2 * n0), 2 * n0);
+    if (!f1.r2c || !f2.rowm || !f3.c2r) return cudaErrorInvalidValue;
+    e = trace_mark(tr, -1, s);
+    if (e == cudaSuccess) e = f1.r2c(j1, C, s);
+    if (e == cudaSuccess) e = trace_mark(tr, kR2C, s);
+    if (e == cudaSuccess) e = f2.rowm(j2, rows, s);
+    if (e == cudaSuccess) e = trace_mark(tr, kColMid, s);
+    if (e == cudaSuccess) e = f3.c2r(j3, C, s);
+    if (e == cudaSuccess) e = trace_mark(tr, kC2R, s);
+  }
+  return e;
+}
+
 cudaError_t run_group(const fsa_plan* shape, int count, const void* const* rho, void* const* phi, void* const* X,
                       void* const* Y, const void* const* S, cudaStream_t s, PassTrace* tr) {
+  if (shape->d == 2) {
+    if (shape->dtype == FSA_F32) return group_passes_2d<float2>(shape->n, count, rho, phi, X, S, s, tr);
+    if (shape->f64_dw) return group_passes_2d<cdw>(shape->n, count, rho, phi, X, S, s, tr);
+    return group_passes_2d<double2>(shape->n, count, rho, phi, X, S, s, tr);
+  }
   const long long cb = shape->chunk_bytes;
   if (shape->dtype == FSA_F32) return group_passes<float2>(shape->n, count, rho, phi, X, Y, S, s, tr, cb);
   if (shape->f64_dw) return group_passes<cdw>(shape->n, count, rho, phi, X, Y, S, s, tr, cb);
@@ -290,13 +335,51 @@ namespace {
 double appendix_b_bound_impl(double R0, double eps);
 
 // The far-field integral for a kernel of Table 1 (see fsa_appendix_b_bound_kernel).
+// E1(x), x > 0, in long double: series (Abramowitz & Stegun 5.1.11) below 1,
+// continued fraction (Press et al., Numerical Recipes, expint; modified
+// Lentz) above.
+long double expint_e1(long double x) {
+  if (x < 1.0L) {
+    long double sum = 0.0L, term = 1.0L;
+    for (int k = 1; k < 60; ++k) {
+      term *= -x / k;
+      sum += term / k;  // (-x)^k / (k k!)
+    }
+    return -0.577215664901532860606512090082402431L - logl(x) - sum;
+  }
+  long double b = x + 1.0L, c = 1.0e300L, d = 1.0L / b, h = d;
+  for (int i = 1; i < 400; ++i) {
+    const long double an = -(long double)i * i;
+    b += 2.0L;
+    d = 1.0L / (an * d + b);
+    c = b + an / c;
+    const long double del = c * d;
+    h *= del;
+    if (fabsl(del - 1.0L) < 1e-19L) break;
+  }
+  return h * expl(-x);
+}
+
 double appendix_b_bound_kernel_impl(fsa_kernel kernel, double R0, double eps) {
   if (kernel == FSA_KERNEL_COULOMB3D) return appendix_b_bound_impl(R0, eps);
+  const long double c = (long double)R0 / (long double)eps, e = eps;
+  const long double pi = 3.141592653589793238462643383279502884L;
+  // d = 2: int_{R0}^inf |U - U^eps| r dr, a = c^2:
+  //   Coulomb    (eps/(2 pi)) int_c^inf erfc(s) ds = (eps/(2 pi)) (exp(-c^2)/sqrt(pi) - c erfc(c))
+  //   Poisson    (eps^2/(8 pi)) int_a^inf E1(u) du = (eps^2/(8 pi)) (exp(-a) - a E1(a))
+  //   biharmonic (eps^4/(32 pi)) int_a^inf u E1(u) du = (eps^4/(64 pi)) ((1 + a) exp(-a) - a^2 E1(a))
+  if (kernel == FSA_KERNEL_COULOMB2D) return (double)(e / (2 * pi) * (expl(-c * c) / sqrtl(pi) - c * erfcl(c)));
+  if (kernel == FSA_KERNEL_POISSON2D) {
+    const long double a = c * c;
+    return (double)(e * e / (8 * pi) * (expl(-a) - a * expint_e1(a)));
+  }
+  if (kernel == FSA_KERNEL_BIHARMONIC2D) {
+    const long double a = c * c;
+    return (double)(e * e * e * e / (64 * pi) * ((1 + a) * expl(-a) - a * a * expint_e1(a)));
+  }
   if (kernel != FSA_KERNEL_BIHARMONIC3D) return NAN;
   // (eps^4/(8 pi)) int_c^inf s^3 erfc(s) ds; by parts,
   // int_c^inf s^3 erfc(s) ds = erfc(c) (3/16 - c^4/4) + exp(-c^2) (c^3/2 + 3c/4) / (2 sqrt(pi))
-  const long double c = (long double)R0 / (long double)eps;
-  const long double pi = 3.141592653589793238462643383279502884L;
   const long double e4 = (long double)eps * eps * eps * eps;
   const long double tail =
       erfcl(c) * (3.0L / 16.0L - c * c * c * c / 4.0L) + expl(-c * c) * (c * c * c / 2.0L + 0.75L * c) / (2.0L * sqrtl(pi));
@@ -329,7 +412,7 @@ struct DeviceGuard {
   }
 };
 
-fsa_status prepare_device(int dev, fsa_dtype dt, const int* n) {
+fsa_status prepare_device(int dev, fsa_dtype dt, const int* n, int d) {
   std::lock_guard<std::mutex> lk(g_init_mu);
   if (!g_tw_ready.count(dev)) {
     cudaError_t e = init_all_twiddles();
@@ -339,7 +422,7 @@ fsa_status prepare_device(int dev, fsa_dtype dt, const int* n) {
     if (e != cudaSuccess) return cuda_error(e, "fault word");
     g_tw_ready.insert(dev);
   }
-  for (int j = 0; j < 3; ++j) {
+  for (int j = 0; j < d; ++j) {  // a plane's unit third axis has no kernels
     const int M = 2 * n[j];
     const int key = M * 4 + (int)dt;
     if (g_prepared.count({dev, key})) continue;
@@ -469,10 +552,11 @@ cudaError_t tune_plan(fsa_plan* p);
 // hold the eps in use and its App. B bound.
 fsa_status plan_validate(fsa_kernel kernel, const double* L, const int* n, fsa_dtype dtype, double eps_in,
                          double eps_tol, double* eps_out, double* bound_out) {
-  if (kernel != FSA_KERNEL_COULOMB3D && kernel != FSA_KERNEL_BIHARMONIC3D)
+  if (kernel < FSA_KERNEL_COULOMB3D || kernel > FSA_KERNEL_BIHARMONIC2D)
     return set_error(FSA_ERR_UNSUPPORTED, "fsa_plan_create: unknown kernel");
   if (dtype != FSA_F32 && dtype != FSA_F64) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: bad dtype");
-  for (int j = 0; j < 3; ++j) {
+  const int d = kernel_dim(kernel);
+  for (int j = 0; j < d; ++j) {
     if (!supported_n(n[j]))
       return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: n[" + std::to_string(j) + "] = " +
                                                 std::to_string(n[j]) +
@@ -481,7 +565,7 @@ fsa_status plan_validate(fsa_kernel kernel, const double* L, const int* n, fsa_d
       return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: L[" + std::to_string(j) + "] must be > 0");
   }
   if (eps_in < 0 || !std::isfinite(eps_in)) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: eps < 0");
-  const double R0 = 2.0 * std::min(L[0], std::min(L[1], L[2]));
+  const double R0 = 2.0 * (d == 2 ? std::min(L[0], L[1]) : std::min(L[0], std::min(L[1], L[2])));
   const double eps = eps_in > 0 ? eps_in : std::min(1.0, R0 / 6.0);
   const double bound = appendix_b_bound_kernel_impl(kernel, R0, eps);
   const double tol = eps_tol == 0 ? 1e-8 : eps_tol;
@@ -502,11 +586,12 @@ fsa_status plan_create_internal(fsa_plan** out, fsa_kernel kernel, const double*
   double eps = 0, bound = 0;
   fsa_status vs = plan_validate(kernel, L, n, dtype, eps_in, eps_tol, &eps, &bound);
   if (vs != FSA_OK) return vs;
-  const double R0 = 2.0 * std::min(L[0], std::min(L[1], L[2]));
+  const int d = kernel_dim(kernel);
+  const double R0 = 2.0 * (d == 2 ? std::min(L[0], L[1]) : std::min(L[0], std::min(L[1], L[2])));
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "fsa_plan_create: cudaGetDevice");
-  fsa_status st = prepare_device(dev, dtype, n);
+  fsa_status st = prepare_device(dev, dtype, n, d);
   if (st != FSA_OK) return st;
 
   fsa_plan* p = new fsa_plan{};
@@ -519,11 +604,12 @@ fsa_status plan_create_internal(fsa_plan** out, fsa_kernel kernel, const double*
   p->R0 = R0;
   p->eps_bound = bound;
   p->kernel = kernel;
+  p->d = d;
   p->chunk_bytes = 0;  // one slab: measured fastest at 256^3 (see fsa_plan_opts.l2_chunk_mb)
   p->dtype = dtype;
   p->device = dev;
   const size_t s = dtype == FSA_F32 ? 4 : 8;
-  p->spectrum_bytes = (size_t)(n[0] + 1) * (n[1] + 1) * (n[2] + 1) * s;
+  p->spectrum_bytes = (size_t)(n[0] + 1) * (n[1] + 1) * (d == 2 ? 1 : n[2] + 1) * s;
   p->x_bytes = (size_t)(n[0] + 1) * n[1] * n[2] * 2 * s;
   p->ws_bytes = with_workspace ? plan_workspace_bytes(n, dtype) : 0;
   // The workspace always holds the FP64 generation scratch of an FP32 plan.
@@ -557,7 +643,7 @@ cudaError_t tune_f64(fsa_plan* p);
 
 cudaError_t tune_plan(fsa_plan* p) {
   if (p->dtype == FSA_F64) return tune_f64(p);
-  if (!p->ws || autotune_mode() != 1) return cudaSuccess;
+  if (!p->ws || autotune_mode() != 1 || p->d == 2) return cudaSuccess;  // d = 2: defaults
   std::lock_guard<std::mutex> lk(g_tune_mu);
   const int n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
   const int Ms[kNumPass] = {2 * n0, 2 * n2, 2 * n1, 2 * n2, 2 * n0};
@@ -686,10 +772,17 @@ fsa_status fsa_plan_create(fsa_plan** out, fsa_kernel kernel, int d, const doubl
                            fsa_dtype dtype, const fsa_plan_opts* opts) {
   if (!out) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: out is NULL");
   *out = nullptr;
-  if (kernel != FSA_KERNEL_COULOMB3D && kernel != FSA_KERNEL_BIHARMONIC3D)
+  if (kernel < FSA_KERNEL_COULOMB3D || kernel > FSA_KERNEL_BIHARMONIC2D)
     return set_error(FSA_ERR_UNSUPPORTED, "fsa_plan_create: unknown kernel");
-  if (d != 3) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: only d = 3 is implemented");
+  if (d != kernel_dim(kernel))
+    return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: d = " + std::to_string(d) + " does not match the kernel (d = " +
+                                              std::to_string(kernel_dim(kernel)) + ")");
   if (!L || !n) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: L or n is NULL");
+  // internally every plan has three axes; a plane (d = 2) has n[2] = 1
+  const double L3[3] = {L[0], L[1], d == 3 ? L[2] : 1.0};
+  const int n3[3] = {n[0], n[1], d == 3 ? n[2] : 1};
+  L = L3;
+  n = n3;
   fsa_plan_opts o{};
   o.device = -1;
   if (opts) o = *opts;
@@ -746,12 +839,13 @@ fsa_status fsa_plan_info_get(const fsa_plan* p, fsa_plan_info* info) {
     const long long plane = (long long)p->n[1] * 3 * p->n[2] * cz;
     const int K0 = p->n[0] + 1;
     const int pc = p->chunk_bytes > 0 ? (int)std::max<long long>(1, p->chunk_bytes / plane) : K0;
-    info->launches_per_apply = 2 + 3 * ((K0 + std::min(pc, K0) - 1) / std::min(pc, K0));
+    info->launches_per_apply = p->d == 2 ? 3 : 2 + 3 * ((K0 + std::min(pc, K0) - 1) / std::min(pc, K0));
   }
   info->workspace_bytes = p->ws_bytes;
   info->spectrum_bytes = p->spectrum_bytes;
   info->spectrum = p->spectrum;
   info->kernel = p->kernel;
+  info->d = p->d;
   return FSA_OK;
 }
 

@@ -291,11 +291,12 @@ void loop(fsa_server* s) {
 }
 
 bool valid_request(const fsa_request* r) {
-  if (!r || (r->kernel != FSA_KERNEL_COULOMB3D && r->kernel != FSA_KERNEL_BIHARMONIC3D) || r->d != 3) return false;
+  if (!r || r->kernel < FSA_KERNEL_COULOMB3D || r->kernel > FSA_KERNEL_BIHARMONIC2D) return false;
+  if (r->d != kernel_dim(r->kernel)) return false;
   if (r->dtype != FSA_F32 && r->dtype != FSA_F64) return false;
   if (!r->rho || !r->phi || (((uintptr_t)r->rho | (uintptr_t)r->phi) & 15u)) return false;
   if (!(r->eps >= 0)) return false;
-  for (int j = 0; j < 3; ++j)
+  for (int j = 0; j < r->d; ++j)
     if (!supported_n(r->n[j]) || !(r->L[j] > 0)) return false;
   return true;
 }
@@ -365,11 +366,15 @@ fsa_status fsa_serve_submit(fsa_server* s, const fsa_request* req, uint64_t* tic
   const uint64_t id = s->next++;
   Req& q = s->reqs[id];
   q.r = *req;
+  if (q.r.d == 2) {  // a plane is held as three axes with n[2] = 1
+    q.r.n[2] = 1;
+    q.r.L[2] = 1.0;
+  }
   q.t.submit_s = now_s();
   std::memset(&q.key, 0, sizeof q.key);
   for (int j = 0; j < 3; ++j) {
-    q.key.n[j] = req->n[j];
-    q.key.L[j] = req->L[j];
+    q.key.n[j] = q.r.n[j];
+    q.key.L[j] = q.r.L[j];
   }
   q.key.kernel = req->kernel;
   q.key.dt = req->dtype;

@@ -18,6 +18,17 @@
 //          = (eps^4/16) g(x), x = k^2 eps^2 / 4, g(x) = (exp(-x)(1 + x + 2x^2) - 1)/x^2,
 //     summed from the Taylor series of g below x = 1 (the closed form cancels
 //     there), W(0) = 3 eps^4 / 32.
+//   * d = 2 (the plane kernels, Table 1): the same with two axes (the octant
+//     is (n0+1) x (n1+1), the normalisation 1/(4 n0 n1)).  U^eps: Poisson
+//     -(ln r + E1(r^2/eps^2)/2)/(2 pi) (Eq. lnrAppr), Coulomb erf(r/eps)/(2 pi r)
+//     (limit 1/(pi^{3/2} eps)), biharmonic -r^2 (ln r + E1(r^2/eps^2)/2 - 1)/(8 pi).
+//     The bracket ln r + E1(u)/2, u = r^2/eps^2, is ln eps - gamma/2 -
+//     (1/2) sum_{k>=1} (-u)^k/(k k!) for u < 1 (the logarithms cancel; the E1
+//     series of Abramowitz & Stegun 5.1.11) and ln r + E1(u)/2 with E1 from the
+//     continued fraction of Press et al. (Numerical Recipes, expint; modified
+//     Lentz) for u >= 1.  W: Poisson (1 - exp(-k^2 eps^2/4))/k^2, Coulomb
+//     erf(k eps/2)/k (limit eps/sqrt(pi)), biharmonic (eps^4/16) h(x),
+//     h(x) = (exp(-x)(1 + x + x^2) - 1)/x^2 from its Taylor series below x = 1.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -27,13 +38,14 @@
 
 namespace fsa {
 
-// Taylor coefficients of g(x) = (exp(-x)(1 + x + 2x^2) - 1)/x^2: the
-// coefficient of x^m is c_{m+2}, c_j = (-1)^j (1/j! - 1/(j-1)! + 2/(j-2)!)
-// (the exponential series times 1 + x + 2x^2).
+// Taylor coefficients of (exp(-x)(1 + x + a x^2) - 1)/x^2 (a = 2: 3-D
+// biharmonic g; a = 1: 2-D biharmonic h): the coefficient of x^m is c_{m+2},
+// c_j = (-1)^j (1/j! - 1/(j-1)! + a/(j-2)!) (the exponential series times
+// 1 + x + a x^2).
 struct BihSeries {
   double c[30];
 };
-constexpr BihSeries bih_series() {
+constexpr BihSeries bih_series(double a) {
   BihSeries s{};
   double f[33] = {};
   f[0] = 1.0;
@@ -41,34 +53,98 @@ constexpr BihSeries bih_series() {
   for (int m = 0; m < 30; ++m) {
     const int j = m + 2;
     const double sign = (j % 2 == 0) ? 1.0 : -1.0;
-    s.c[m] = sign * (1.0 / f[j] - 1.0 / f[j - 1] + 2.0 / f[j - 2]);
+    s.c[m] = sign * (1.0 / f[j] - 1.0 / f[j - 1] + a / f[j - 2]);
   }
   return s;
 }
-__constant__ BihSeries c_bih = bih_series();
+__constant__ BihSeries c_bih = bih_series(2.0);
+__constant__ BihSeries c_bih2 = bih_series(1.0);
+
+// 1/(k k!) for k = 0..40 (entry 0 unused): the E1 series
+struct E1Series {
+  double c[41];
+};
+constexpr E1Series e1_series() {
+  E1Series s{};
+  double f = 1.0;
+  for (int k = 1; k <= 40; ++k) {
+    f *= k;
+    s.c[k] = 1.0 / (k * f);
+  }
+  return s;
+}
+__constant__ E1Series c_e1 = e1_series();
+
+// E1(x) for x >= 1: continued fraction (Press et al., Numerical Recipes,
+// expint), evaluated by the modified Lentz method; at most 200 terms.
+__device__ double e1_cfrac(double x) {
+  double b = x + 1.0, c = 1.0e300, d = 1.0 / b, h = d;
+  for (int i = 1; i < 200; ++i) {
+    const double an = -(double)i * i;
+    b += 2.0;
+    d = 1.0 / (an * d + b);
+    c = b + an / c;
+    const double del = c * d;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-16) break;
+  }
+  return h * exp(-x);
+}
+
+// ln(r) + E1(r^2/eps^2)/2, the bracket of Eq. lnrAppr (see the file comment)
+__device__ double log_half_e1(double r, double eps) {
+  const double u = (r / eps) * (r / eps);
+  if (u < 1.0) {
+    double acc = 0.0;
+    for (int k = 40; k >= 1; --k) acc = acc * (-u) + c_e1.c[k];
+    acc *= -u;
+    return log(eps) - 0.5 * 0.57721566490153286060651209008240243 - 0.5 * acc;
+  }
+  return log(r) + 0.5 * e1_cfrac(u);
+}
+
+// Sum of c.c[m] x^m, m < 30 (Horner)
+__device__ __forceinline__ double series30(const BihSeries& c, double x) {
+  double g = 0.0;
+#pragma unroll
+  for (int m = 29; m >= 0; --m) g = g * x + c.c[m];
+  return g;
+}
 
 // W(k) of Table 1 at k^2 (see the file comment)
 __device__ __forceinline__ double singular_W(int kernel, double k2, double e2) {
-  if (kernel == FSA_KERNEL_BIHARMONIC3D) {
+  if (kernel == FSA_KERNEL_BIHARMONIC3D || kernel == FSA_KERNEL_BIHARMONIC2D) {
+    const bool d3 = kernel == FSA_KERNEL_BIHARMONIC3D;
+    const double a = d3 ? 2.0 : 1.0;
     const double x = 0.25 * k2 * e2;
-    double g;
-    if (x < 1.0) {
-      g = 0.0;
-#pragma unroll
-      for (int m = 29; m >= 0; --m) g = g * x + c_bih.c[m];
-    } else {
-      g = (exp(-x) * (1.0 + x + 2.0 * x * x) - 1.0) / (x * x);
-    }
+    const double g = x < 1.0 ? series30(d3 ? c_bih : c_bih2, x) : (exp(-x) * (1.0 + x + a * x * x) - 1.0) / (x * x);
     return e2 * e2 / 16.0 * g;
   }
-  return k2 > 0.0 ? -expm1(-0.25 * k2 * e2) / k2 : 0.25 * e2;
+  if (kernel == FSA_KERNEL_COULOMB2D) {
+    const double k = sqrt(k2);
+    return k > 0.0 ? erf(0.5 * k * sqrt(e2)) / k : sqrt(e2) / 1.7724538509055160272981674833411452;
+  }
+  return k2 > 0.0 ? -expm1(-0.25 * k2 * e2) / k2 : 0.25 * e2;  // 3-D Coulomb and 2-D Poisson
+}
+
+// U^eps of Table 1 at r
+__device__ __forceinline__ double smooth_U(int kernel, double r, double eps) {
+  const double pi = 3.14159265358979323846;
+  switch (kernel) {
+    case FSA_KERNEL_BIHARMONIC3D: return r * erf(r / eps) / (8.0 * pi);
+    case FSA_KERNEL_POISSON2D: return -log_half_e1(r, eps) / (2.0 * pi);
+    case FSA_KERNEL_COULOMB2D:
+      return r > 0.0 ? erf(r / eps) / (2.0 * pi * r) : 1.0 / (5.5683279968317078453 * eps);  // 1/(pi^{3/2} eps)
+    case FSA_KERNEL_BIHARMONIC2D: return -(r * r) / (8.0 * pi) * (log_half_e1(r, eps) - 1.0);
+    default:
+      return r > 0.0 ? erf(r / eps) / (4.0 * pi * r) : 1.0 / (2.0 * 5.5683279968317078453 * eps);
+  }
 }
 
 __global__ void k_t1_octant(double* __restrict__ O, int kernel, int n0, int n1, int n2, double h0, double h1,
                             double h2, double eps) {
   const long long total = (long long)(n0 + 1) * (n1 + 1) * (n2 + 1);
   const double hv = h0 * h1 * h2;
-  const double u0 = 1.0 / (2.0 * 5.5683279968317078453 * eps);  // 1/(2 pi^{3/2} eps)
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const int p2 = (int)(i % (n2 + 1));
@@ -77,10 +153,7 @@ __global__ void k_t1_octant(double* __restrict__ O, int kernel, int n0, int n1, 
     const int p0 = (int)(r01 / (n1 + 1));
     const double x = p0 * h0, y = p1 * h1, z = p2 * h2;
     const double r = sqrt(x * x + y * y + z * z);
-    const double u = kernel == FSA_KERNEL_BIHARMONIC3D
-                         ? r * erf(r / eps) / (8.0 * 3.14159265358979323846)
-                         : (r > 0.0 ? erf(r / eps) / (4.0 * 3.14159265358979323846 * r) : u0);
-    O[i] = hv * u;
+    O[i] = hv * smooth_U(kernel, r, eps);
   }
 }
 
@@ -190,29 +263,32 @@ cudaError_t tensorgen_init_twiddles() {
 
 cudaError_t tensorgen_run(fsa_kernel kernel, const int n[3], const double L[3], double eps, double* O, void* out,
                           fsa_dtype dtype, cudaStream_t s) {
-  const int n0 = n[0], n1 = n[1], n2 = n[2];
+  // d = 2: a single plane of the octant (n2 = 0 here, unit h2), no axis-2 DCT
+  const bool plane = kernel_dim(kernel) == 2;
+  const int n0 = n[0], n1 = n[1], n2 = plane ? 0 : n[2];
   const long long e0 = n0 + 1, e1 = n1 + 1, e2 = n2 + 1;
-  const double h0 = 2.0 * L[0] / n0, h1 = 2.0 * L[1] / n1, h2 = 2.0 * L[2] / n2;
+  const double h0 = 2.0 * L[0] / n0, h1 = 2.0 * L[1] / n1, h2 = plane ? 1.0 : 2.0 * L[2] / n2;
   const long long total = e0 * e1 * e2;
   const int threads = 256;
   const int blocks = (int)std::min<long long>((total + threads - 1) / threads, 152LL * 16);
   k_t1_octant<<<blocks, threads, 0, s>>>(O, (int)kernel, n0, n1, n2, h0, h1, h2, eps);
   cudaError_t e = cudaGetLastError();
   // axis 2: lines (p0, p1) contiguous, element stride 1
-  if (e == cudaSuccess) e = dct_run(2 * n2, O, e0 * e1, e1, e1 * e2, e2, 1, s);
+  if (e == cudaSuccess && !plane) e = dct_run(2 * n2, O, e0 * e1, e1, e1 * e2, e2, 1, s);
   // axis 1: lines (p0, p2), element stride e2
   if (e == cudaSuccess) e = dct_run(2 * n1, O, e0 * e2, e2, e1 * e2, 1, e2, s);
   // axis 0: lines (p1, p2) flattened, element stride e1 * e2
   if (e == cudaSuccess) e = dct_run(2 * n0, O, e1 * e2, e1 * e2, 0, 1, e1 * e2, s);
   if (e != cudaSuccess) return e;
   const double pi = 3.14159265358979323846;
-  const double inv_norm = 1.0 / (8.0 * (double)n0 * n1 * n2);
+  const double inv_norm = plane ? 1.0 / (4.0 * (double)n0 * n1) : 1.0 / (8.0 * (double)n0 * n1 * n2);
+  const double c2 = plane ? 0.0 : pi / (2 * L[2]);
   if (dtype == FSA_F64)
     k_spectrum_finalize<double><<<blocks, threads, 0, s>>>(O, (double*)out, (int)kernel, n0, n1, n2, pi / (2 * L[0]),
-                                                           pi / (2 * L[1]), pi / (2 * L[2]), eps, inv_norm);
+                                                           pi / (2 * L[1]), c2, eps, inv_norm);
   else
     k_spectrum_finalize<float><<<blocks, threads, 0, s>>>(O, (float*)out, (int)kernel, n0, n1, n2, pi / (2 * L[0]),
-                                                          pi / (2 * L[1]), pi / (2 * L[2]), eps, inv_norm);
+                                                          pi / (2 * L[1]), c2, eps, inv_norm);
   return cudaGetLastError();
 }
 

@@ -65,6 +65,12 @@ def test_appendix_b_bound_per_kernel_matches_oracle(capi):
             a = capi.fsa_appendix_b_bound_kernel(k, R0, eps)
             b = fsa.appendix_b_bound(R0, eps, kernel=name)
             assert a == pytest.approx(b, rel=1e-8, abs=1e-300), (name, R0, eps)
+    for name, k in (("poisson2d", capi.FSA_KERNEL_POISSON2D), ("coulomb2d", capi.FSA_KERNEL_COULOMB2D),
+                    ("biharmonic2d", capi.FSA_KERNEL_BIHARMONIC2D)):
+        for R0, eps in [(24.0, 24.0 / 5.64), (24.0, 24.0 / 5.75), (16.0, 2.7), (4.0, 0.9), (2.0, 0.5), (8.0, 2.0)]:
+            a = capi.fsa_appendix_b_bound_kernel(k, R0, eps)
+            b = fsa.appendix_b_bound(R0, eps, kernel=name)
+            assert a == pytest.approx(b, rel=1e-8, abs=1e-300), (name, R0, eps)
     assert math.isnan(capi.fsa_appendix_b_bound_kernel(9, 24.0, 1.0))
     assert math.isnan(capi.fsa_appendix_b_bound_kernel(capi.FSA_KERNEL_BIHARMONIC3D, 24.0, 0.0))
 
@@ -113,3 +119,17 @@ def test_supported_sizes_match_workloads(capi):
         except capi.FsaError as e:
             accepted = e.status != capi.FSA_ERR_INVALID_ARG
         assert accepted == ok, n
+
+
+def test_plan_create_checks_dimension_against_kernel(capi):
+    for k, d in ((capi.FSA_KERNEL_POISSON2D, 3), (capi.FSA_KERNEL_COULOMB2D, 3), (capi.FSA_KERNEL_COULOMB3D, 2)):
+        with pytest.raises(capi.FsaError) as ei:
+            capi.fsa_plan_create(k, d, (1, 1, 1), (8, 8, 8), capi.FSA_F32)
+        assert ei.value.status == capi.FSA_ERR_INVALID_ARG
+    # plane kernels validate only their two axes
+    with pytest.raises(capi.FsaError) as ei:
+        capi.fsa_plan_create(capi.FSA_KERNEL_POISSON2D, 2, (1, 1), (8, 10), capi.FSA_F32)
+    assert ei.value.status == capi.FSA_ERR_INVALID_ARG
+    with pytest.raises(capi.FsaError) as ei:
+        capi.fsa_plan_create(capi.FSA_KERNEL_COULOMB2D, 2, (8, 8), (8, 8), capi.FSA_F32, eps=5.0)
+    assert ei.value.status == capi.FSA_ERR_EPS

@@ -156,3 +156,36 @@ def test_served_kernels_do_not_share_plans(lib):
     for (k, rep), o in outs.items():
         assert torch.equal(o, want[k]), (k, rep)
     assert not torch.equal(want["coulomb3d"], want["biharmonic3d"])
+
+
+def test_served_plane_requests_equal_solved_alone(lib):
+    """Plane (d = 2) requests are served beside 3-D ones; each equals its plan
+    solved alone."""
+    import torch
+    rng = np.random.default_rng(8)
+    reqs = [("poisson2d", (4.0, 4.0), (32, 48), "f32"), ("coulomb3d", (3.0, 3.0, 3.0), (16, 16, 16), "f64"),
+            ("biharmonic2d", (5.0, 3.0), (64, 32), "f64"), ("coulomb2d", (4.0, 4.0), (48, 48), "f32")]
+    want, outs, tickets, rhos = [], [], [], []
+    srv = lib.Server(max_inflight=4, streams=2)
+    for kernel, L, n, dt in reqs:
+        tdt = torch.float64 if dt == "f64" else torch.float32
+        rho = torch.from_numpy(rng.standard_normal(n)).to(tdt).cuda()
+        rhos.append(rho)
+        p = lib.Plan(L, n, dt, eps=0.0, kernel=kernel)
+        want.append(p.apply(rho))
+        torch.cuda.synchronize()
+        p.close()
+        outs.append(torch.full_like(rho, float("nan")))
+        tickets.append(srv.submit(L, n, dt, rho, outs[-1], kernel=kernel))
+    for t in tickets:
+        srv.wait(t)
+    torch.cuda.synchronize()
+    srv.close()
+    from oracle import fsa as oracle
+    for i, (o, w) in enumerate(zip(outs, want)):
+        kernel, L, n, dt = reqs[i]
+        ref = oracle.solve(L, n, min(1.0, 2 * min(L) / 6), rhos[i].double().cpu().numpy(), kernel=kernel)
+        e_srv = oracle.rel_error(o.double().cpu().numpy(), ref)
+        e_alone = oracle.rel_error(w.double().cpu().numpy(), ref)
+        assert torch.equal(o, w), (reqs[i], e_srv, e_alone)
+        assert e_srv <= (1e-12 if dt == "f64" else 2e-6), (reqs[i], e_srv)
