@@ -36,7 +36,21 @@ if ROOT not in sys.path:
 METRIC = "solves/s and HBM-roofline % at 256^3 FP64/FP32; p50/p99 latency under serving"
 UNIT = "solves/s"
 PASSES = ["r2c_ax0", "row_fwd", "col_mid", "row_inv", "c2r_ax0"]
-KERNEL_TEXT = {"coulomb3d": "3-D Coulomb", "biharmonic3d": "3-D biharmonic"}
+KERNEL_TEXT = {"coulomb3d": "3-D Coulomb", "biharmonic3d": "3-D biharmonic", "poisson2d": "2-D Poisson",
+               "coulomb2d": "2-D Coulomb", "biharmonic2d": "2-D biharmonic"}
+PLANE_KERNELS = ("poisson2d", "coulomb2d", "biharmonic2d")
+
+
+def plane_pass_bytes(n, s):
+    """Algorithmic HBM bytes of the three passes of a plane solve (s = bytes
+    per real): R2C reads rho and writes X = (n0+1) n1 complex; the middle pass
+    reads and writes X and reads the (n0+1)(n1+1) octant; C2R reads X and
+    writes phi."""
+    n0, n1 = n
+    V = n0 * n1
+    X = (n0 + 1) * n1 * 2
+    S = (n0 + 1) * (n1 + 1)
+    return {"r2c_ax0": (V + X) * s, "row_fwd": 0, "col_mid": (2 * X + S) * s, "row_inv": 0, "c2r_ax0": (X + V) * s}
 
 
 def pass_bytes(n, s):
@@ -217,7 +231,9 @@ def run_ours(args):
     import workloads as W
 
     capi.fsa_autotune_set({"auto": 1, "1": 2, "2": 3, "3": 4, "4": 5}[args.kernel_gen])
-    d = W.gaussian_sum(seed=2504)  # 8 Gaussians, [-16,16]^3, 256^3, eps = 1
+    plane = args.kernel in PLANE_KERNELS
+    # 8 Gaussians, [-16,16]^3 at 256^3 (or [-16,16]^2 at 512^2 for a plane kernel), eps = 1
+    d = W.gaussian_sum_2d(seed=2504) if plane else W.gaussian_sum(seed=2504)
     n = d.n
     rho64 = d.rho()
     hbm_peak, peak_kind = peaks()
@@ -262,18 +278,19 @@ def run_ours(args):
         elapsed = allreduce_max(elapsed, dist, "cuda")
         pass_ms, step_ms, steps = capi.fsa_profiler_read(prof)
         capi.fsa_profiler_destroy(prof)
-        pb = pass_bytes(n, s)
+        pb = plane_pass_bytes(n, s) if plane else pass_bytes(n, s)
         dom = max(range(5), key=lambda i: pass_ms[i])
         kname = PASSES[dom]
         achieved = pb[kname] / (pass_ms[dom] * 1e-3) / 1e9
-        model_s = reference_model_bytes(n, s) / (hbm_peak * 1e9)
+        # 3-D: the reference 27V byte model; plane: the sum of the three passes' bytes
+        model_s = (sum(pb.values()) if plane else reference_model_bytes(n, s)) / (hbm_peak * 1e9)
         arith = ["fp32", "fp64", "double-word"][plan.info.arithmetic]
         hbm_roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
                     "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": f"of {peak_kind}",
                     "alg_bytes_per_launch": pb[kname],
-                    "traffic": read_traffic(kname, "c2_256", dt)}
+                    "traffic": None if plane else read_traffic(kname, "c2_256", dt)}
         roof = hbm_roof
-        if arith == "double-word" and kname == "col_mid":
+        if arith == "double-word" and kname == "col_mid" and not plane:
             # bound by the FP32 pipes: FP32 operations per launch over the
             # FP32 issue peak (SMs x 128 lanes x maximum SM clock)
             sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -362,10 +379,15 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if "f32" in tiers else "f64",
             "data": "synthetic",
-            "config": {"workload": f"c2_256: {KERNEL_TEXT[args.kernel]} FSA apply, 8-Gaussian density (seed 2504) on "
-                                   "[-16,16]^3, 256^3 grid, eps=1, spectrum cached on device",
-                       "grid": list(n), "l2": "per-step working set ~0.6 GB (FP32) > 129 MB L2; "
-                                             "4 rotating rho/phi buffers",
+            "config": {"workload": (f"plane_512: {KERNEL_TEXT[args.kernel]} FSA apply, 8-Gaussian plane density "
+                                    "(seed 2504) on [-16,16]^2, 512^2 grid, eps=1, spectrum cached on device")
+                                   if args.kernel in PLANE_KERNELS else
+                                   (f"c2_256: {KERNEL_TEXT[args.kernel]} FSA apply, 8-Gaussian density (seed 2504) on "
+                                    "[-16,16]^3, 256^3 grid, eps=1, spectrum cached on device"),
+                       "grid": list(n),
+                       "l2": ("plane: per-step working set ~12 MB (FP32) < 129 MB L2, L2-resident, not flushed"
+                              if args.kernel in PLANE_KERNELS else
+                              "per-step working set ~0.6 GB (FP32) > 129 MB L2; 4 rotating rho/phi buffers"),
                        "parallelism": f"replicas x{ws}"},
             "roofline": main["roofline"],
             "cpu_baseline": cpu,
@@ -602,7 +624,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tiers", default="f32,f64", help="apply tiers to time; the first FP32 one is the headline")
-    ap.add_argument("--kernel", choices=["coulomb3d", "biharmonic3d"], default="coulomb3d",
+    ap.add_argument("--kernel", choices=list(KERNEL_TEXT), default="coulomb3d",
                     help="kernel of Table 1 for the single-solve tiers (batched and serving legs use Coulomb)")
     ap.add_argument("--kernel-gen", choices=["auto", "1", "2", "3", "4"], default="auto",
                     help="auto: autotuned per plan; 1 / 2 / 3 / 4: force one kernel generation "

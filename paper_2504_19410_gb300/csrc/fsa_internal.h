@@ -45,8 +45,11 @@ struct PassFns {
   cudaError_t (*colm)(const Jobs&, int M2, int planes, cudaStream_t) = nullptr;
   cudaError_t (*rowi)(const Jobs&, long long rows, cudaStream_t) = nullptr;
   cudaError_t (*c2r)(const Jobs&, long long C, cudaStream_t) = nullptr;
-  // d = 2 middle pass (first generation only; nullptr for the others)
+  // d = 2: middle pass and narrow-tile R2C / C2R (first generation only;
+  // nullptr for the others)
   cudaError_t (*rowm)(const Jobs&, long long rows, cudaStream_t) = nullptr;
+  cudaError_t (*r2c_plane)(const Jobs&, long long C, cudaStream_t) = nullptr;
+  cudaError_t (*c2r_plane)(const Jobs&, long long C, cudaStream_t) = nullptr;
 };
 // FP32 generations: 1 Stockham radix-8, 2 two-step register, 3 = 2 with the
 // middle pass prefetching its next tile (cp.async), 4 = 3 with the row passes

@@ -35,7 +35,9 @@ template <typename V, int M> struct Inst {
     set((const void*)k_row_fwd<V, P, W, T>, SM_ROWS);
     set((const void*)k_col_mid<V, P, WC, TC>, SM_MID);
     set((const void*)k_row_inv<V, P, W, T>, SM_ROWS);
-    set((const void*)k_row_mid<V, P, W, T>, SM_ROWS);
+    set((const void*)k_row_mid<V, P, WM, TM>, SM_ROWM);
+    set((const void*)k_r2c_ax0<V, P, WM, TM>, SM_STRM);
+    set((const void*)k_c2r_ax0<V, P, WM, TM>, SM_STRM);
     set((const void*)k_c2r_ax0<V, P, W, T>, SM_STRIDED);
     return e;
   }
@@ -64,11 +66,31 @@ template <typename V, int M> struct Inst {
     f<<<persistent_grid((const void*)f, NTC, SM_MID, tiles), NTC, SM_MID, s>>>(jobs, M2, planes);
     return cudaGetLastError();
   }
-  // the d = 2 middle pass: rows of the R2C output, in place
+  // the d = 2 middle pass: rows of the R2C output, in place.  A plane has
+  // only n0 + 1 rows, so its tiles are narrower than the 3-D row passes'
+  // (more CTAs for one solve).
+  static constexpr int WM = std::is_same<V, float2>::value ? 4 : 2;
+  static constexpr int TM = threads_per_line<P, WM>();
+  static constexpr int NTM = WM * TM;
+  static constexpr int SM_ROWM = smem_rows<P, V, WM>();
   static cudaError_t rowm(const Jobs& jobs, long long rows, cudaStream_t s) {
-    const long long tiles = (rows + W - 1) / W * jobs.count;
-    auto f = k_row_mid<V, P, W, T>;
-    f<<<persistent_grid((const void*)f, NT, SM_ROWS, tiles), NT, SM_ROWS, s>>>(jobs, rows);
+    const long long tiles = (rows + WM - 1) / WM * jobs.count;
+    auto f = k_row_mid<V, P, WM, TM>;
+    f<<<persistent_grid((const void*)f, NTM, SM_ROWM, tiles), NTM, SM_ROWM, s>>>(jobs, rows);
+    return cudaGetLastError();
+  }
+  // the plane's R2C / C2R passes: its n1 real columns are few, so narrow tiles
+  static constexpr int SM_STRM = smem_strided<P, V, WM>();
+  static cudaError_t r2c_plane(const Jobs& jobs, long long C, cudaStream_t s) {
+    const long long tiles = (C + 2 * WM - 1) / (2 * WM) * jobs.count;
+    auto f = k_r2c_ax0<V, P, WM, TM>;
+    f<<<persistent_grid((const void*)f, NTM, SM_STRM, tiles), NTM, SM_STRM, s>>>(jobs, C);
+    return cudaGetLastError();
+  }
+  static cudaError_t c2r_plane(const Jobs& jobs, long long C, cudaStream_t s) {
+    const long long tiles = (C + 2 * WM - 1) / (2 * WM) * jobs.count;
+    auto f = k_c2r_ax0<V, P, WM, TM>;
+    f<<<persistent_grid((const void*)f, NTM, SM_STRM, tiles), NTM, SM_STRM, s>>>(jobs, C);
     return cudaGetLastError();
   }
   static cudaError_t rowi(const Jobs& jobs, long long rows, cudaStream_t s) {
@@ -206,7 +228,11 @@ template <class I> struct HasRowm<I, std::void_t<decltype(&I::rowm)>> : std::tru
 
 template <class I> PassFns fns_of() {
   PassFns f;
-  if constexpr (HasRowm<I>::value) f.rowm = &I::rowm;
+  if constexpr (HasRowm<I>::value) {
+    f.rowm = &I::rowm;
+    f.r2c_plane = &I::r2c_plane;
+    f.c2r_plane = &I::c2r_plane;
+  }
   f.prepare = &I::prepare;
   f.geometry = &I::geometry;
   f.r2c = &I::r2c;

@@ -275,7 +275,8 @@ template cudaError_t group_passes<cdw>(const int*, int, const void* const*, void
 
 // The d = 2 path (Sec. 2.3 with two axes): R2C along axis 0 over the n1
 // real columns, the row middle pass (axis 1 forward, multiply, inverse) in
-// place on X, C2R along axis 0.  n = (n0, n1, 1); Y is not used.
+// place on X, C2R along axis 0, all first-generation kernels with narrow
+// tiles (a plane is small: more CTAs per solve).  n = (n0, n1, 1); Y unused.
 template <typename V> int first_gen_arith() {
   if constexpr (std::is_same<V, float2>::value) return kArithF32G1;
   else if constexpr (std::is_same<V, double2>::value) return kArithF64;
@@ -298,16 +299,16 @@ cudaError_t group_passes_2d(const int* n, int count, const void* const* rho, voi
       j2.j[i] = Job{X[k], X[k], S[k]};
       j3.j[i] = Job{X[k], phi[k], nullptr};
     }
-    const PassFns& f1 = pass_fns(arith_for<V>(kR2C, 2 * n0), 2 * n0);
+    const PassFns& f1 = pass_fns(first_gen_arith<V>(), 2 * n0);
     const PassFns& f2 = pass_fns(first_gen_arith<V>(), 2 * n1);
-    const PassFns& f3 = pass_fns(arith_for<V>(kC2R, 2 * n0), 2 * n0);
-    if (!f1.r2c || !f2.rowm || !f3.c2r) return cudaErrorInvalidValue;
+    const PassFns& f3 = f1;
+    if (!f1.r2c_plane || !f2.rowm || !f3.c2r_plane) return cudaErrorInvalidValue;
     e = trace_mark(tr, -1, s);
-    if (e == cudaSuccess) e = f1.r2c(j1, C, s);
+    if (e == cudaSuccess) e = f1.r2c_plane(j1, C, s);
     if (e == cudaSuccess) e = trace_mark(tr, kR2C, s);
     if (e == cudaSuccess) e = f2.rowm(j2, rows, s);
     if (e == cudaSuccess) e = trace_mark(tr, kColMid, s);
-    if (e == cudaSuccess) e = f3.c2r(j3, C, s);
+    if (e == cudaSuccess) e = f3.c2r_plane(j3, C, s);
     if (e == cudaSuccess) e = trace_mark(tr, kC2R, s);
   }
   return e;

@@ -116,6 +116,38 @@ def gaussian_sum(seed=2504, L=16.0, n=256, count=8, center_box=4.0,
     return Density(LL, nn, terms, eps, f"gaussian_sum_{count}_{nn[0]}x{nn[1]}x{nn[2]}_s{seed}")
 
 
+@dataclass
+class Plane:
+    """A sum of isotropic Gaussians a exp(-|x-c|^2/(2 w^2)) on the plane box
+    [-L_0, L_0] x [-L_1, L_1] with n_j points per axis (the d = 2 kernels)."""
+    L: tuple
+    n: tuple
+    terms: list
+    eps: float = 1.0
+    name: str = ""
+
+    def rho(self):
+        x = grid_axes(self.L, self.n)
+        out = np.zeros(self.n, dtype=np.float64)
+        for a, c, w in self.terms:
+            out += a * np.exp(-((x[0] - c[0])[:, None] ** 2 + (x[1] - c[1])[None, :] ** 2) / (2.0 * w * w))
+        return out
+
+
+def gaussian_sum_2d(seed=2504, L=16.0, n=512, count=8, center_box=4.0, width=(0.5, 1.5), amp=(-1.0, 1.0),
+                    eps=1.0):
+    """The plane analogue of C2: ``count`` Gaussians, centres U[-4,4]^2, widths
+    U[0.5,1.5], amplitudes U[-1,1], on [-L, L]^2 with n x n points."""
+    rng = np.random.default_rng(seed)
+    terms = []
+    for _ in range(count):
+        c = rng.uniform(-center_box, center_box, 2)
+        w = rng.uniform(*width)
+        a = rng.uniform(*amp)
+        terms.append((float(a), (float(c[0]), float(c[1])), float(w)))
+    return Plane((L, L), (n, n), terms, eps, f"plane_gaussian_sum_{count}_{n}x{n}_s{seed}")
+
+
 def aniso_gaussian(kind="cigar", gamma=8.0, eps=0.4):
     """C3: cigar exp(-(g^2 (x^2+y^2) + z^2)/2) on [-2,2]^2 x [-16,16], 128x128x512,
     or pancake exp(-(x^2+y^2+g^2 z^2)/2) on [-16,16]^2 x [-2,2], 512x512x128."""
