@@ -216,3 +216,64 @@ def radial_on_grid_2d(fn, amp, s2, L, n):
     r = np.sqrt(x[0][:, None] ** 2 + x[1][None, :] ** 2)
     ru, inv = np.unique(r, return_inverse=True)
     return fn(amp, s2, ru)[inv].reshape(r.shape)
+
+
+# ---- 3-D DDI (Example 4), rho = exp(-|x|^2/s2) ----------------------------
+
+def _erf_over_r_derivs(a, r):
+    """For F(r) = erf(a r) / r: g1 = F'(r)/r and g2 = (F''(r) - F'(r)/r)/r^2.
+    Closed forms
+        g1 = (2a/sqrt(pi)) e^{-a^2 r^2} / r^2 - erf(a r) / r^3,
+        g2 = 3 erf(a r) / r^5 - (6a/sqrt(pi)) e^{-a^2 r^2} / r^4
+             - (4 a^3/sqrt(pi)) e^{-a^2 r^2} / r^2,
+    and for u = a^2 r^2 < 1 (where they cancel) the Maclaurin series of
+    F = (2a/sqrt(pi)) sum_k c_k a^{2k} r^{2k}, c_k = (-1)^k / (k! (2k+1)):
+        g1 = (2a/sqrt(pi)) a^2 sum_{k>=1} 2k c_k u^{k-1},
+        g2 = (2a/sqrt(pi)) a^4 sum_{k>=2} 4k(k-1) c_k u^{k-2}."""
+    r = np.asarray(r, dtype=np.float64)
+    u = (a * r) ** 2
+    g1 = np.empty_like(r)
+    g2 = np.empty_like(r)
+    small = u < 1.0
+    pre = 2.0 * a / math.sqrt(math.pi)
+    us = u[small]
+    s1 = np.zeros_like(us)
+    s2 = np.zeros_like(us)
+    for k in range(40, 0, -1):
+        ck = (-1) ** k / (math.factorial(k) * (2 * k + 1))
+        s1 = s1 * us + 2 * k * ck
+        if k >= 2:
+            s2 = s2 * us + 4 * k * (k - 1) * ck
+    g1[small] = pre * a * a * s1
+    g2[small] = pre * a ** 4 * s2
+    rl = r[~small]
+    e = np.exp(-(a * rl) ** 2)
+    erf = sp.erf(a * rl)
+    g1[~small] = pre * e / rl ** 2 - erf / rl ** 3
+    g2[~small] = 3.0 * erf / rl ** 5 - 3.0 * pre * e / rl ** 4 - 2.0 * pre * a * a * e / rl ** 2
+    return g1, g2
+
+
+def ddi3d_gaussian_points(s2, pts, nvec, mvec):
+    """Exact 3-D DDI potential of rho = exp(-|x|^2/s2) at points pts (..., 3),
+    in Example 4's reformulation Phi = -(m.n) rho - 3 d_n d_m Phi_C with the
+    Coulomb potential Phi_C(r) = q erf(r/s) / (4 pi r), q = (pi s2)^{3/2}
+    (the isotropic Gaussian above).  For radial Phi_C,
+    d_n d_m Phi_C = (n.m) Phi_C'/r + (n.x)(m.x) (Phi_C'' - Phi_C'/r) / r^2."""
+    pts = np.asarray(pts, dtype=np.float64)
+    r = np.sqrt(np.sum(pts * pts, axis=-1))
+    a = 1.0 / math.sqrt(s2)
+    q = (math.pi * s2) ** 1.5
+    g1, g2 = _erf_over_r_derivs(a, r)
+    nm = float(np.dot(nvec, mvec))
+    xn = pts @ np.asarray(nvec, dtype=np.float64)
+    xm = pts @ np.asarray(mvec, dtype=np.float64)
+    dnm = q / (4.0 * math.pi) * (nm * g1 + xn * xm * g2)
+    return -nm * np.exp(-r * r / s2) - 3.0 * dnm
+
+
+def ddi3d_gaussian_grid(s2, L, n, nvec, mvec):
+    """ddi3d_gaussian_points on the mesh of workloads.grid_axes(L, n)."""
+    x = grid_axes(L, n)
+    X = np.stack(np.meshgrid(*x, indexing="ij"), axis=-1)
+    return ddi3d_gaussian_points(s2, X, nvec, mvec)

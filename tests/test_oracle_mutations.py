@@ -231,3 +231,77 @@ def test_2d_pins_catch_mutation(name, monkeypatch):
     attr, fn = MUTATIONS_2D[name]
     monkeypatch.setattr(fsa, attr, fn)
     assert not pins_pass_2d(), f"pins missed the planted mistake: {name}"
+
+
+# ---- 3-D DDI -----------------------------------------------------------------
+
+def pins_pass_ddi():
+    """Table 5's 3-D DDI row (grid reading, h = 2, 1, 1/2 to the printed
+    digits; h = 1/4 round-off) and the kernel reading's round-off at h = 1/4."""
+    s2 = 1.2
+    for h, want in ((2.0, 2.2087), (1.0, 3.3668e-2), (0.5, 8.5098e-7), (0.25, None)):
+        d = W.paper_case1(L=8.0, sigma2=s2, h_over_gamma=h)
+        exact = cf.ddi3d_gaussian_grid(s2, d.L, d.n, W.DDI_N, W.DDI_M)
+        e = fsa.rel_error(fsa.ddi3d_solve(d.L, d.n, 1.0, d.rho(), W.DDI_N, W.DDI_M, "grid"), exact)
+        if (want is None and e > 3e-14) or (want is not None and abs(e - want) > 5e-4 * want):
+            return False
+        if h == 0.25:
+            e = fsa.rel_error(fsa.ddi3d_solve(d.L, d.n, 1.0, d.rho(), W.DDI_N, W.DDI_M, "kernel"), exact)
+            if e > 3e-14:
+                return False
+    return True
+
+
+def test_unmutated_ddi_pins_pass():
+    assert pins_pass_ddi()
+
+
+def _dnm_double_period(F, periods, nvec, mvec):
+    return fsa_orig_ddi["spectral_dnm_of_dft"](F, [2 * p for p in periods], nvec, mvec)
+
+
+def _dnm_sign(F, periods, nvec, mvec):
+    return -fsa_orig_ddi["spectral_dnm_of_dft"](F, periods, nvec, mvec)
+
+
+def _dnm_n_twice(F, periods, nvec, mvec):
+    return fsa_orig_ddi["spectral_dnm_of_dft"](F, periods, nvec, nvec)
+
+
+def _dnm_nyquist_diagonal_only(F, periods, nvec, mvec):
+    # mixed Nyquist terms of -(k.n)(k.m) dropped, diagonal ones kept
+    k0, nq = [], []
+    for N, P in zip(F.shape, periods):
+        k = 2.0 * math.pi * np.fft.fftfreq(N, d=1.0 / N) / P
+        z = k.copy()
+        z[N // 2] = 0.0
+        k0.append(z)
+        nq.append(k - z)
+    K0 = np.meshgrid(*k0, indexing="ij", sparse=True)
+    NQ = np.meshgrid(*nq, indexing="ij", sparse=True)
+    D = -sum(nvec[j] * K0[j] for j in range(3)) * sum(mvec[j] * K0[j] for j in range(3)) \
+        - sum(nvec[j] * mvec[j] * NQ[j] ** 2 for j in range(3))
+    return np.fft.ifftn(D * F).real
+
+
+def _ddi_local_sign(L, n, eps, rho, nvec, mvec, derivative="grid"):
+    nm = float(np.dot(nvec, mvec))
+    return fsa_orig_ddi["ddi3d_solve"](L, n, eps, rho, nvec, mvec, derivative) + 2 * nm * rho
+
+
+fsa_orig_ddi = {k: getattr(fsa, k) for k in ("spectral_dnm_of_dft", "ddi3d_solve")}
+
+MUTATIONS_DDI = {
+    "DDI derivative with twice the period": ("spectral_dnm_of_dft", _dnm_double_period),
+    "DDI derivative sign": ("spectral_dnm_of_dft", _dnm_sign),
+    "DDI derivative d_n d_n": ("spectral_dnm_of_dft", _dnm_n_twice),
+    "DDI Nyquist mixed terms dropped": ("spectral_dnm_of_dft", _dnm_nyquist_diagonal_only),
+    "DDI local term +(m.n) rho": ("ddi3d_solve", _ddi_local_sign),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS_DDI))
+def test_ddi_pins_catch_mutation(name, monkeypatch):
+    attr, fn = MUTATIONS_DDI[name]
+    monkeypatch.setattr(fsa, attr, fn)
+    assert not pins_pass_ddi(), f"pins missed the planted mistake: {name}"

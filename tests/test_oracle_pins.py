@@ -451,3 +451,150 @@ def test_2d_fft_route_equals_brute_force(n, kernel):
     T = fsa.tensor_T(L, n, 0.6, kernel=kernel)
     rho = rng.standard_normal(n)
     assert fsa.rel_error(fsa.apply_fft(T, rho), fsa.apply_direct(T, rho)) < 1e-13
+
+
+# ---- 3-D DDI (Example 4, Table 5) -------------------------------------------
+
+DDI_S2, DDI_L = 1.2, 8.0
+
+
+def _ddi_case(h):
+    d = W.paper_case1(L=DDI_L, sigma2=DDI_S2, h_over_gamma=h)
+    return d.L, d.n, d.rho()
+
+
+@pytest.mark.parametrize("h,n,printed", [tuple(r) for r in read_golden("table5_ddi3d_double.txt")])
+def test_table5_ddi3d_grid_reading(h, n, printed):
+    """Table 5, 3-D DDI (L = 8, sigma^2 = 1.2, eps = 1, the printed n and m):
+    the grid reading of d_n d_m rho reproduces h = 2, 1, 1/2 to the printed
+    digits and reaches round-off at h = 1/4."""
+    L, nn, rho = _ddi_case(float(h))
+    assert nn[0] == int(n)
+    err = fsa.rel_error(fsa.ddi3d_solve(L, nn, 1.0, rho, W.DDI_N, W.DDI_M, "grid"),
+                        cf.ddi3d_gaussian_grid(DDI_S2, L, nn, W.DDI_N, W.DDI_M))
+    _check_table_row(err, float(printed))
+
+
+@pytest.mark.parametrize("h,n,printed", [tuple(r) for r in read_golden("table5_ddi3d_double.txt")])
+def test_table5_ddi3d_kernel_reading(h, n, printed):
+    """The kernel reading is as accurate as the printed row: round-off at
+    h = 1/4 and within 10% of the printed discretisation error at h <= 1
+    (the two readings differ only in the coarse-grid aliasing)."""
+    L, nn, rho = _ddi_case(float(h))
+    err = fsa.rel_error(fsa.ddi3d_solve(L, nn, 1.0, rho, W.DDI_N, W.DDI_M, "kernel"),
+                        cf.ddi3d_gaussian_grid(DDI_S2, L, nn, W.DDI_N, W.DDI_M))
+    printed = float(printed)
+    if printed < 1e-10:
+        assert err < 4 * printed
+    else:
+        assert 0.9 * printed < err < 1.1 * printed or float(h) == 2.0
+        assert err < 1.1 * max(printed, 2.2087)
+
+
+def test_ddi3d_nyquist_convention_matters_at_h2():
+    """The printed h = 2 value fixes the Nyquist rule of the grid reading:
+    with the mixed Nyquist terms of -(k.n)(k.m) dropped it is 2.30, not 2.2087."""
+    L, nn, rho = _ddi_case(2.0)
+    exact = cf.ddi3d_gaussian_grid(DDI_S2, L, nn, W.DDI_N, W.DDI_M)
+    n = nn[0]
+    k = 2 * math.pi * np.fft.fftfreq(n, d=1.0 / n) / (2 * L[0])
+    k0 = k.copy()
+    k0[n // 2] = 0
+    nyq = k - k0
+    K0 = np.meshgrid(k0, k0, k0, indexing="ij")
+    NQ = np.meshgrid(nyq, nyq, nyq, indexing="ij")
+    D = -sum(W.DDI_N[i] * K0[i] for i in range(3)) * sum(W.DDI_M[i] * K0[i] for i in range(3)) \
+        - sum(W.DDI_N[i] * W.DDI_M[i] * NQ[i] ** 2 for i in range(3))
+    drho = np.fft.ifftn(D * np.fft.fftn(rho)).real
+    nm = float(np.dot(W.DDI_N, W.DDI_M))
+    other = fsa.rel_error(-nm * rho - 3 * fsa.apply_fft(fsa.tensor_T(L, nn, 1.0), drho), exact)
+    assert abs(other - 2.2087) > 0.05
+
+
+def test_ddi3d_closed_form_far_field_is_the_kernel():
+    """Far from the density the exact potential is q U(x) with Example 4's
+    kernel U (q = (pi s2)^{3/2}, the total charge): erf(r/s) = 1 and
+    exp(-r^2/s2) = 0 to double precision at r >= 8 s."""
+    rng = np.random.default_rng(11)
+    d = rng.standard_normal((200, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    s = math.sqrt(DDI_S2)
+    pts = d * rng.uniform(8 * s, 30 * s, (200, 1))
+    for nv, mv in ((W.DDI_N, W.DDI_M), W.ddi_dipoles(5), ((0, 0, 1.0), (0, 0, 1.0))):
+        got = cf.ddi3d_gaussian_points(DDI_S2, pts, nv, mv)
+        want = (math.pi * DDI_S2) ** 1.5 * fsa.ddi3d_U(pts, nv, mv)
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
+
+
+def test_ddi3d_closed_form_is_traceless():
+    """sum_i Phi(n = m = e_i) = -3 rho - 3 Laplacian(Phi_C) = 0 (the Coulomb
+    kernel is the Green's function of -Laplacian), everywhere including the
+    series region near r = 0."""
+    rng = np.random.default_rng(12)
+    pts = rng.uniform(-3, 3, (500, 3))
+    pts[:5] *= 1e-3
+    tot = sum(cf.ddi3d_gaussian_points(DDI_S2, pts, e, e) for e in np.eye(3))
+    scale = np.max(np.abs(cf.ddi3d_gaussian_points(DDI_S2, pts, np.eye(3)[0], np.eye(3)[0])))
+    assert np.max(np.abs(tot)) < 1e-14 * scale
+
+
+def test_ddi3d_closed_form_series_meets_closed_form():
+    """The small-r series and the closed forms of the radial derivatives agree
+    where they meet (u = a^2 r^2 = 1) and against central differences of
+    erf(ar)/r."""
+    a = 1 / math.sqrt(DDI_S2)
+    for u in (0.999999, 1.000001):
+        r = np.array([math.sqrt(u) / a])
+        g = cf._erf_over_r_derivs(a, r)
+        r2 = np.array([math.sqrt(2 - u) / a])
+        g_other = cf._erf_over_r_derivs(a, r2)
+        # both sides of u = 1 use different formulas; neighbouring points agree smoothly
+        assert abs(g[0][0] - g_other[0][0]) < 1e-5 * abs(g[0][0])
+    F = lambda r: math.erf(a * r) / r
+    for r in (0.3, 0.9, 1.1, 2.0, 4.0):
+        hh = 1e-3
+        d1 = (-F(r + 2 * hh) + 8 * F(r + hh) - 8 * F(r - hh) + F(r - 2 * hh)) / (12 * hh)
+        d2 = (-F(r + 2 * hh) + 16 * F(r + hh) - 30 * F(r) + 16 * F(r - hh) - F(r - 2 * hh)) / (12 * hh * hh)
+        g1, g2 = cf._erf_over_r_derivs(a, np.array([r]))
+        assert g1[0] == pytest.approx(d1 / r, rel=1e-8)
+        assert g2[0] == pytest.approx((d2 - d1 / r) / r ** 2, rel=2e-5)
+
+
+@pytest.mark.parametrize("shape", [(8, 6, 4), (4, 8, 6)])
+def test_spectral_dnm_exact_on_trig_polynomials(shape):
+    """d_n d_m of cos(k.x + phi) is -(k.n)(k.m) cos(k.x + phi) for grid
+    frequencies below Nyquist; a Nyquist cosine along one axis j takes
+    -n_j m_j (pi/h_j)^2 (its mixed terms vanish on the grid)."""
+    rng = np.random.default_rng(4)
+    P = (3.0, 5.0, 2.0)
+    axes = [np.arange(N) * (Pj / N) for N, Pj in zip(shape, P)]
+    X = np.meshgrid(*axes, indexing="ij")
+    nv, mv = W.ddi_dipoles(9)
+    for _ in range(4):
+        q = [int(rng.integers(-(N // 2) + 1, N // 2)) for N in shape]
+        k = [2 * math.pi * q[j] / P[j] for j in range(3)]
+        ph = rng.uniform(0, 2 * math.pi)
+        f = np.cos(sum(k[j] * X[j] for j in range(3)) + ph)
+        want = -np.dot(k, nv) * np.dot(k, mv) * f
+        np.testing.assert_allclose(fsa.spectral_dnm(f, P, nv, mv), want, atol=1e-11 * max(1, np.abs(want).max()))
+    for j in range(3):
+        kn = math.pi * shape[j] / P[j]
+        f = np.cos(kn * X[j])
+        np.testing.assert_allclose(fsa.spectral_dnm(f, P, nv, mv), -nv[j] * mv[j] * kn * kn * f, atol=1e-10 * kn * kn)
+
+
+def test_ddi3d_readings_equal_brute_force():
+    """Both readings as brute-force sums (Eq. DiscConv): the grid reading is
+    the Coulomb sum over spectral_dnm(rho); the kernel reading is the sum
+    over rho with the doubled-grid spectral derivative of T (a Fourier
+    multiplier commutes with the circular convolution)."""
+    rng = np.random.default_rng(21)
+    n, L = (4, 6, 8), (3.0, 4.0, 2.5)
+    rho = rng.standard_normal(n)
+    nv, mv = W.ddi_dipoles(3)
+    nm = float(np.dot(nv, mv))
+    T = fsa.tensor_T(L, n, 0.6)
+    want_grid = -nm * rho - 3 * fsa.apply_direct(T, fsa.spectral_dnm(rho, [2 * l for l in L], nv, mv))
+    want_kernel = -nm * rho - 3 * fsa.apply_direct(fsa.spectral_dnm(T, [4 * l for l in L], nv, mv), rho)
+    assert fsa.rel_error(fsa.ddi3d_solve(L, n, 0.6, rho, nv, mv, "grid"), want_grid) < 1e-13
+    assert fsa.rel_error(fsa.ddi3d_solve(L, n, 0.6, rho, nv, mv, "kernel"), want_kernel) < 1e-13

@@ -261,3 +261,16 @@ def poisson_arrivals(seed, count, rate_per_s):
     """Arrival times (s) of a Poisson process with the given rate."""
     rng = np.random.default_rng(seed)
     return np.cumsum(rng.exponential(1.0 / rate_per_s, count))
+
+
+# Dipole orientations of Example 4's 3-D DDI run (Sec. 5): n and m as printed.
+DDI_N = (0.82778, 0.41505, -0.37751)
+DDI_M = (0.3118, 0.9378, -0.15214)
+
+
+def ddi_dipoles(seed):
+    """A random pair of unit dipole orientations (n, m), for parity tests."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((2, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return tuple(v[0]), tuple(v[1])
