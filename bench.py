@@ -37,7 +37,7 @@ METRIC = "solves/s and HBM-roofline % at 256^3 FP64/FP32; p50/p99 latency under 
 UNIT = "solves/s"
 PASSES = ["r2c_ax0", "row_fwd", "col_mid", "row_inv", "c2r_ax0"]
 KERNEL_TEXT = {"coulomb3d": "3-D Coulomb", "biharmonic3d": "3-D biharmonic", "poisson2d": "2-D Poisson",
-               "coulomb2d": "2-D Coulomb", "biharmonic2d": "2-D biharmonic"}
+               "coulomb2d": "2-D Coulomb", "biharmonic2d": "2-D biharmonic", "ddi3d": "3-D DDI (Example 4)"}
 PLANE_KERNELS = ("poisson2d", "coulomb2d", "biharmonic2d")
 
 
@@ -64,6 +64,21 @@ def pass_bytes(n, s):
     S = (n0 + 1) * (n1 + 1) * (n2 + 1)
     return {"r2c_ax0": (V + X) * s, "row_fwd": (X + Y) * s, "col_mid": (2 * Y + S) * s,
             "row_inv": (Y + X) * s, "c2r_ax0": (X + V) * s}
+
+
+def ddi_grid_pass_bytes(n, s):
+    """The DDI grid reading's passes, summed per kind as the profiler does:
+    the Coulomb passes, the five unpadded passes of d_n d_m rho (Xn =
+    (n0/2+1) n1 n2 complex: R2C reads rho and writes Xn, the row and middle
+    passes read and write Xn, C2R reads Xn and writes V reals) and the final
+    C2R's read of rho for the local term."""
+    n0, n1, n2 = n
+    V = n0 * n1 * n2
+    Xn = (n0 // 2 + 1) * n1 * n2 * 2
+    b = pass_bytes(n, s)
+    extra = {"r2c_ax0": (V + Xn) * s, "row_fwd": 2 * Xn * s, "col_mid": 2 * Xn * s, "row_inv": 2 * Xn * s,
+             "c2r_ax0": (Xn + V) * s + V * s}
+    return {k: b[k] + extra[k] for k in b}
 
 
 def reference_model_bytes(n, s):
@@ -232,6 +247,8 @@ def run_ours(args):
 
     capi.fsa_autotune_set({"auto": 1, "1": 2, "2": 3, "3": 4, "4": 5}[args.kernel_gen])
     plane = args.kernel in PLANE_KERNELS
+    ddi_kw = ({"dipoles": (W.DDI_N, W.DDI_M), "ddi_derivative": args.ddi_derivative}
+              if args.kernel == "ddi3d" else {})
     # 8 Gaussians, [-16,16]^3 at 256^3 (or [-16,16]^2 at 512^2 for a plane kernel), eps = 1
     d = W.gaussian_sum_2d(seed=2504) if plane else W.gaussian_sum(seed=2504)
     n = d.n
@@ -245,7 +262,7 @@ def run_ours(args):
         s = 4 if dt == "f32" else 8
         t0 = time.perf_counter()
         plan = fsa.Plan(d.L, n, dt, eps=d.eps, generate=False, l2_chunk_mb=args.l2_chunk_mb,
-                        kernel=args.kernel)  # + autotuner trials
+                        kernel=args.kernel, **ddi_kw)  # + autotuner trials
         torch.cuda.synchronize()
         create_ms = (time.perf_counter() - t0) * 1e3
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -278,7 +295,9 @@ def run_ours(args):
         elapsed = allreduce_max(elapsed, dist, "cuda")
         pass_ms, step_ms, steps = capi.fsa_profiler_read(prof)
         capi.fsa_profiler_destroy(prof)
-        pb = plane_pass_bytes(n, s) if plane else pass_bytes(n, s)
+        pb = (plane_pass_bytes(n, s) if plane else
+              ddi_grid_pass_bytes(n, s) if args.kernel == "ddi3d" and args.ddi_derivative == "grid" else
+              pass_bytes(n, s))
         dom = max(range(5), key=lambda i: pass_ms[i])
         kname = PASSES[dom]
         achieved = pb[kname] / (pass_ms[dom] * 1e-3) / 1e9
@@ -288,7 +307,7 @@ def run_ours(args):
         hbm_roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
                     "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": f"of {peak_kind}",
                     "alg_bytes_per_launch": pb[kname],
-                    "traffic": None if plane else read_traffic(kname, "c2_256", dt)}
+                    "traffic": None if plane or args.kernel == "ddi3d" else read_traffic(kname, "c2_256", dt)}
         roof = hbm_roof
         if arith == "double-word" and kname == "col_mid" and not plane:
             # bound by the FP32 pipes: FP32 operations per launch over the
@@ -325,8 +344,8 @@ def run_ours(args):
         res["e2e"] = None
         if not args.no_e2e:
             NS = 3
-            plans = [plan] + [fsa.Plan(d.L, n, dt, eps=d.eps, l2_chunk_mb=args.l2_chunk_mb, kernel=args.kernel)
-                              for _ in range(NS - 1)]
+            plans = [plan] + [fsa.Plan(d.L, n, dt, eps=d.eps, l2_chunk_mb=args.l2_chunk_mb, kernel=args.kernel,
+                                       **ddi_kw) for _ in range(NS - 1)]
             streams = [torch.cuda.Stream() for _ in range(NS)]
             hin = [torch.from_numpy(rho64).to(tdt).pin_memory() for _ in range(NS)]
             hout = [torch.empty_like(hin[0]).pin_memory() for _ in range(NS)]
@@ -383,7 +402,9 @@ def run_ours(args):
                                     "(seed 2504) on [-16,16]^2, 512^2 grid, eps=1, spectrum cached on device")
                                    if args.kernel in PLANE_KERNELS else
                                    (f"c2_256: {KERNEL_TEXT[args.kernel]} FSA apply, 8-Gaussian density (seed 2504) on "
-                                    "[-16,16]^3, 256^3 grid, eps=1, spectrum cached on device"),
+                                    "[-16,16]^3, 256^3 grid, eps=1, spectrum cached on device"
+                                    + (f"; dipoles n, m of Example 4, {args.ddi_derivative} reading of d_n d_m rho"
+                                       if args.kernel == "ddi3d" else "")),
                        "grid": list(n),
                        "l2": ("plane: per-step working set ~12 MB (FP32) < 129 MB L2, L2-resident, not flushed"
                               if args.kernel in PLANE_KERNELS else
@@ -626,6 +647,9 @@ def main():
     ap.add_argument("--tiers", default="f32,f64", help="apply tiers to time; the first FP32 one is the headline")
     ap.add_argument("--kernel", choices=list(KERNEL_TEXT), default="coulomb3d",
                     help="kernel of Table 1 for the single-solve tiers (batched and serving legs use Coulomb)")
+    ap.add_argument("--ddi-derivative", choices=["grid", "kernel"], default="grid",
+                    help="--kernel ddi3d: d_n d_m rho on the computational grid (the paper's Table 5) or "
+                         "fused into the middle multiply")
     ap.add_argument("--kernel-gen", choices=["auto", "1", "2", "3", "4"], default="auto",
                     help="auto: autotuned per plan; 1 / 2 / 3 / 4: force one kernel generation "
                          "(FP64: native for 1, double-word otherwise)")

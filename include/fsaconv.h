@@ -65,9 +65,27 @@ typedef enum {
   FSA_KERNEL_POISSON2D = 2,    /* d = 2: U = -ln(r)/(2 pi),                                  */
                                /* U^eps = -(ln r + E1(r^2/eps^2)/2)/(2 pi) (Eq. lnrAppr)      */
   FSA_KERNEL_COULOMB2D = 3,    /* d = 2: U = 1/(2 pi r), U^eps = U erf(r/eps) (Table 1)       */
-  FSA_KERNEL_BIHARMONIC2D = 4  /* d = 2: U = -r^2 (ln r - 1)/(8 pi),                           */
+  FSA_KERNEL_BIHARMONIC2D = 4, /* d = 2: U = -r^2 (ln r - 1)/(8 pi),                          */
                                /* U^eps = -r^2 (ln r + E1(r^2/eps^2)/2 - 1)/(8 pi) (Table 1)  */
+  FSA_KERNEL_DDI3D = 5         /* d = 3: the dipole-dipole kernel of Sec. 5, Example 4,       */
+                               /* through the Coulomb kernel; see fsa_plan_create_ddi3d      */
 } fsa_kernel;
+
+/* How a 3-D DDI plan discretises d_n d_m rho (Sec. 5, Example 4, which
+ * computes the DDI potential as Phi = -(m.n) rho - 3 (1/(4 pi |x|)) * (d_n d_m rho),
+ * d_n = n . grad, and does not say how d_n d_m rho is formed). */
+typedef enum {
+  FSA_DDI_GRID = 0,  /* spectral d_n d_m rho on the n-point grid (period 2 L_j,             */
+                     /* multiplier -(k.n)(k.m), k_j = pi q_j / L_j, Nyquist q_j = -n_j/2,  */
+                     /* real part), then the Coulomb solve: reproduces Table 5's 3-D row.  */
+                     /* Ten passes: five of length n_j, five of the Coulomb solve         */
+  FSA_DDI_KERNEL = 1 /* the same derivative taken of the Coulomb convolution on the       */
+                     /* doubled grid (period 4 L_j, k_j = pi q_j / (2 L_j)): the multiplier */
+                     /* -3 S(k) (-(k.n)(k.m)) - (m.n) / (8 n0 n1 n2) in the middle pass,   */
+                     /* the five passes of a Coulomb solve.  Same accuracy as FSA_DDI_GRID */
+                     /* (round-off at h = 1/4 in Table 5's case), different coarse-grid   */
+                     /* aliasing                                                           */
+} fsa_ddi_derivative;
 
 typedef enum {
   FSA_F32 = 0, /* rho, phi, stored spectrum and FFT arithmetic in FP32 */
@@ -106,6 +124,9 @@ typedef struct {
   fsa_kernel kernel;        /* the plan's kernel                                      */
   int d;                    /* 3, or 2 for the plane kernels (then n[2] = 1, the      */
                             /* spectrum octant is (n0+1) x (n1+1), 3 launches/apply)  */
+  int ddi_derivative;       /* FSA_KERNEL_DDI3D plans: their fsa_ddi_derivative; -1   */
+  double dipole_n[3];       /* FSA_KERNEL_DDI3D plans: n and m; zero otherwise        */
+  double dipole_m[3];
 } fsa_plan_info;
 
 /* Create a plan (the "Precomp" object of Sec. 5, Example 2) for the grid
@@ -115,8 +136,9 @@ typedef struct {
  * axis 1 (forward, multiply, inverse) and C2R (Sec. 2.3 with d = 2).  The plan owns,
  * on the chosen device, the spectrum octant and the apply workspace
  * (fsa_plan_info.workspace_bytes); both are freed by fsa_plan_destroy.
- * kernel: FSA_KERNEL_COULOMB3D or FSA_KERNEL_BIHARMONIC3D (Table 1); the apply
- * path is the same for both, only the generated spectrum differs.
+ * kernel: one of Table 1's kernels (FSA_KERNEL_DDI3D plans come from
+ * fsa_plan_create_ddi3d); the apply path is the same for all kernels of one
+ * dimension, only the generated spectrum differs.
  * eps follows Remark 2.1 / App. B: the plan computes the far-field integral
  * int_{R0}^inf |U - U^eps| r^2 dr (fsa_appendix_b_bound_kernel) and rejects
  * eps with FSA_ERR_EPS when it exceeds opts->eps_tol.  opts may be NULL.
@@ -125,6 +147,23 @@ typedef struct {
  * FSA_ERR_OOM, FSA_ERR_CUDA.  On error *out is set to NULL. */
 fsa_status fsa_plan_create(fsa_plan** out, fsa_kernel kernel, int d, const double* L,
                            const int* n, fsa_dtype dtype, const fsa_plan_opts* opts);
+
+/* A plan for the 3-D dipole-dipole potential of Sec. 5, Example 4:
+ *   Phi = -(m.n) rho - 3 (1/(4 pi |x|)) * (d_n d_m rho),
+ * the kernel U(x) = (3/(4 pi)) (m.n - 3 (x.m)(x.n)/|x|^2) / |x|^3 applied through
+ * the 3-D Coulomb kernel's FSA tensor (same spectrum, eps rule and App. B
+ * check as FSA_KERNEL_COULOMB3D).  dipole_n, dipole_m: 3 doubles each (host),
+ * finite (the paper takes unit vectors; any vectors are accepted, the
+ * potential is bilinear in them).  derivative: see fsa_ddi_derivative; the
+ * grid reading needs n_j >= 8.  fsa_tensor_generate, fsa_apply,
+ * fsa_apply_host, fsa_apply_noalloc and fsa_apply_batched then compute the
+ * DDI potential; the plan's workspace holds n0 n1 n2 more dtype elements
+ * (fsa_apply_host stages rho there).  Serving requests do not take DDI
+ * plans.  Errors as fsa_plan_create; FSA_ERR_INVALID_ARG also for NULL or
+ * non-finite dipoles, an unknown derivative, or n_j < 8 with FSA_DDI_GRID. */
+fsa_status fsa_plan_create_ddi3d(fsa_plan** out, const double* L, const int* n, fsa_dtype dtype,
+                                 const double* dipole_n, const double* dipole_m,
+                                 fsa_ddi_derivative derivative, const fsa_plan_opts* opts);
 
 /* Generate the kernel tensor's spectrum on the device, in FP64, and store it
  * in the plan's dtype (Sec. 2.1-2.3: T^(1) by the trapezoid rule, T^(2) from

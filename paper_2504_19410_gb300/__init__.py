@@ -29,18 +29,26 @@ def _cur_stream(stream):
 class Plan:
     """A device-resident FSA plan: grid n (3 ints, or 2 for a plane kernel),
     box half-widths L, dtype 'f32' or 'f64', kernel 'coulomb3d',
-    'biharmonic3d', 'poisson2d', 'coulomb2d' or 'biharmonic2d' (Table 1).
-    eps = 0 picks min(1, R0/6).  The spectrum is generated on construction
-    unless generate=False."""
+    'biharmonic3d', 'poisson2d', 'coulomb2d' or 'biharmonic2d' (Table 1), or
+    'ddi3d' (Sec. 5, Example 4: dipoles = (n, m), two 3-vectors, and
+    ddi_derivative 'grid' or 'kernel').  eps = 0 picks min(1, R0/6).  The
+    spectrum is generated on construction unless generate=False."""
 
     def __init__(self, L, n, dtype="f32", eps=0.0, eps_tol=0.0, device=-1, generate=True, stream=None,
-                 l2_chunk_mb=0, kernel="coulomb3d"):
+                 l2_chunk_mb=0, kernel="coulomb3d", dipoles=None, ddi_derivative="grid"):
         self.dtype = _DT[dtype]
         self.n = tuple(int(x) for x in n)
         self.L = tuple(float(x) for x in L)
         self.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
-        self.handle = capi.fsa_plan_create(self.kernel, len(self.n), self.L, self.n, self.dtype, eps, eps_tol,
-                                           device, l2_chunk_mb)
+        if self.kernel == capi.FSA_KERNEL_DDI3D:
+            if dipoles is None:
+                raise ValueError("the ddi3d kernel needs dipoles=(n, m)")
+            der = capi.DDI_DERIVATIVES[ddi_derivative] if isinstance(ddi_derivative, str) else int(ddi_derivative)
+            self.handle = capi.fsa_plan_create_ddi3d(self.L, self.n, self.dtype, dipoles[0], dipoles[1], der, eps,
+                                                     eps_tol, device)
+        else:
+            self.handle = capi.fsa_plan_create(self.kernel, len(self.n), self.L, self.n, self.dtype, eps, eps_tol,
+                                               device, l2_chunk_mb)
         if generate:
             self.generate(stream)
 

@@ -21,11 +21,14 @@ FSA_KERNEL_BIHARMONIC3D = 1
 FSA_KERNEL_POISSON2D = 2
 FSA_KERNEL_COULOMB2D = 3
 FSA_KERNEL_BIHARMONIC2D = 4
+FSA_KERNEL_DDI3D = 5
 KERNELS = {"coulomb3d": FSA_KERNEL_COULOMB3D, "biharmonic3d": FSA_KERNEL_BIHARMONIC3D,
            "poisson2d": FSA_KERNEL_POISSON2D, "coulomb2d": FSA_KERNEL_COULOMB2D,
-           "biharmonic2d": FSA_KERNEL_BIHARMONIC2D}
+           "biharmonic2d": FSA_KERNEL_BIHARMONIC2D, "ddi3d": FSA_KERNEL_DDI3D}
 KERNEL_DIM = {FSA_KERNEL_COULOMB3D: 3, FSA_KERNEL_BIHARMONIC3D: 3, FSA_KERNEL_POISSON2D: 2,
-              FSA_KERNEL_COULOMB2D: 2, FSA_KERNEL_BIHARMONIC2D: 2}
+              FSA_KERNEL_COULOMB2D: 2, FSA_KERNEL_BIHARMONIC2D: 2, FSA_KERNEL_DDI3D: 3}
+FSA_DDI_GRID, FSA_DDI_KERNEL = 0, 1
+DDI_DERIVATIVES = {"grid": FSA_DDI_GRID, "kernel": FSA_DDI_KERNEL}
 FSA_F32, FSA_F64 = 0, 1
 FSA_REQ_QUEUED, FSA_REQ_RUNNING, FSA_REQ_DONE, FSA_REQ_FAILED = range(4)
 
@@ -46,7 +49,8 @@ class PlanInfo(C.Structure):
                 ("generated", C.c_int), ("arithmetic", C.c_int), ("launches_per_apply", C.c_int),
                 ("workspace_bytes", C.c_size_t),
                 ("spectrum_bytes", C.c_size_t),
-                ("spectrum", C.c_void_p), ("kernel", C.c_int), ("d", C.c_int)]
+                ("spectrum", C.c_void_p), ("kernel", C.c_int), ("d", C.c_int), ("ddi_derivative", C.c_int),
+                ("dipole_n", C.c_double * 3), ("dipole_m", C.c_double * 3)]
 
 
 class ServeOpts(C.Structure):
@@ -75,6 +79,8 @@ _VP = C.c_void_p
 _PROTOS = {
     "fsa_plan_create": (C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
                                   C.c_int, C.POINTER(PlanOpts)]),
+    "fsa_plan_create_ddi3d": (C.c_int, [C.POINTER(_VP), C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int,
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.POINTER(PlanOpts)]),
     "fsa_tensor_generate": (C.c_int, [_VP, _VP]),
     "fsa_apply": (C.c_int, [_VP, _VP, _VP, _VP]),
     "fsa_apply_host": (C.c_int, [_VP, _VP, _VP, _VP]),
@@ -157,6 +163,15 @@ def fsa_plan_create(kernel, d, L, n, dtype, eps=0.0, eps_tol=0.0, device=-1, l2_
     o = PlanOpts(float(eps), float(eps_tol), int(device), int(l2_chunk_mb))
     check(lib().fsa_plan_create(C.byref(h), int(kernel), int(d), (C.c_double * 3)(*[float(x) for x in L]),
                                 (C.c_int * 3)(*[int(x) for x in n]), int(dtype), C.byref(o)))
+    return h.value
+
+
+def fsa_plan_create_ddi3d(L, n, dtype, dipole_n, dipole_m, derivative, eps=0.0, eps_tol=0.0, device=-1):
+    h = _VP()
+    o = PlanOpts(float(eps), float(eps_tol), int(device), 0)
+    d3 = lambda v: (C.c_double * 3)(*[float(x) for x in v])
+    check(lib().fsa_plan_create_ddi3d(C.byref(h), d3(L), (C.c_int * 3)(*[int(x) for x in n]), int(dtype),
+                                      d3(dipole_n), d3(dipole_m), int(derivative), C.byref(o)))
     return h.value
 
 

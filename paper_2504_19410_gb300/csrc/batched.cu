@@ -19,9 +19,9 @@ namespace fsa {
 namespace {
 
 struct GroupKey {
-  int n0, n1, n2, dt, dw;
+  int n0, n1, n2, dt, dw, ddi;
   bool operator<(const GroupKey& o) const {
-    return std::tie(n0, n1, n2, dt, dw) < std::tie(o.n0, o.n1, o.n2, o.dt, o.dw);
+    return std::tie(n0, n1, n2, dt, dw, ddi) < std::tie(o.n0, o.n1, o.n2, o.dt, o.dw, o.ddi);
   }
 };
 
@@ -64,6 +64,7 @@ cudaError_t launch_group(const std::vector<int>& idx, const fsa_plan* const* pla
   const fsa_plan* p0 = plans[idx[0]];
   std::vector<const void*> r, S;
   std::vector<void*> f, X, Y;
+  std::vector<const double*> par;
   for (int k : idx) {
     const fsa_plan* p = plans[k];
     r.push_back(rho[k]);
@@ -71,8 +72,9 @@ cudaError_t launch_group(const std::vector<int>& idx, const fsa_plan* const* pla
     X.push_back(p->ws);
     Y.push_back((char*)p->ws + p->x_bytes);
     S.push_back(plan_apply_spectrum(p));
+    par.push_back(p->ddi_par);
   }
-  return run_group(p0, (int)idx.size(), r.data(), f.data(), X.data(), Y.data(), S.data(), s);
+  return run_group(p0, (int)idx.size(), r.data(), f.data(), X.data(), Y.data(), S.data(), s, nullptr, par.data());
 }
 
 }  // namespace
@@ -96,7 +98,7 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
     if (((uintptr_t)rho[k] | (uintptr_t)phi[k]) & 15u)
       return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched: rho and phi must be 16-byte aligned");
     seen.push_back(p);
-    groups[GroupKey{p->n[0], p->n[1], p->n[2], (int)p->dtype, p->f64_dw}].push_back(k);
+    groups[GroupKey{p->n[0], p->n[1], p->n[2], (int)p->dtype, p->f64_dw, p->ddi}].push_back(k);
   }
   std::sort(seen.begin(), seen.end());
   if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())

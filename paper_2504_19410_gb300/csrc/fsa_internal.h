@@ -50,6 +50,16 @@ struct PassFns {
   cudaError_t (*rowm)(const Jobs&, long long rows, cudaStream_t) = nullptr;
   cudaError_t (*r2c_plane)(const Jobs&, long long C, cudaStream_t) = nullptr;
   cudaError_t (*c2r_plane)(const Jobs&, long long C, cudaStream_t) = nullptr;
+  // 3-D DDI (Sec. 5, Example 4): the kernel reading's middle pass and the
+  // grid reading's C2R with the local term (every generation), and the grid
+  // reading's unpadded passes of length M (first generation only)
+  cudaError_t (*colm_ddi)(const Jobs&, int M2, int planes, cudaStream_t) = nullptr;
+  cudaError_t (*c2r_epi)(const Jobs&, long long C, cudaStream_t) = nullptr;
+  cudaError_t (*r2c_per)(const Jobs&, long long C, cudaStream_t) = nullptr;
+  cudaError_t (*rowf_per)(const Jobs&, long long rows, cudaStream_t) = nullptr;
+  cudaError_t (*colm_per)(const Jobs&, int M2, int planes, cudaStream_t) = nullptr;
+  cudaError_t (*rowi_per)(const Jobs&, long long rows, cudaStream_t) = nullptr;
+  cudaError_t (*c2r_per)(const Jobs&, long long C, cudaStream_t) = nullptr;
 };
 // FP32 generations: 1 Stockham radix-8, 2 two-step register, 3 = 2 with the
 // middle pass prefetching its next tile (cp.async), 4 = 3 with the row passes
@@ -93,9 +103,10 @@ cudaError_t plan_apply_passes(const fsa_plan* p, const void* rho, void* phi, cud
 
 // The five passes for `count` solves of one plan shape in the plan's
 // arithmetic: FP32, native FP64, or double-word for FP64 plans with f64_dw.
+// par[k]: solve k's DDI parameter block (3-D DDI plans; may be null otherwise).
 cudaError_t run_group(const fsa_plan* shape, int count, const void* const* rho, void* const* phi,
                       void* const* X, void* const* Y, const void* const* S, cudaStream_t s,
-                      PassTrace* tr = nullptr);
+                      PassTrace* tr = nullptr, const double* const* par = nullptr);
 // The spectrum the apply kernels read (the double-word copy for f64_dw plans).
 const void* plan_apply_spectrum(const fsa_plan* p);
 // Converts an FP64 octant to double-word pairs (tensor_gen.cu).
@@ -136,7 +147,11 @@ struct fsa_plan {
   void* spectrum_dw;  // FP64 plans: the spectrum as double-word pairs
   int f64_dw;         // FP64 plans: 1 = double-word arithmetic, 0 = native FP64
   long long chunk_bytes;  // pass split: target bytes of one slab's X + Y (<= 0: no split)
-  void* ws;  // X then Y
+  void* ws;  // X then Y (then, for DDI plans, the host path's staging of rho)
   size_t ws_bytes;
   size_t x_bytes;
+  // 3-D DDI (Sec. 5, Example 4): -1 = not a DDI plan, else the fsa_ddi_derivative
+  int ddi;
+  double* ddi_par;  // device: kDdiParCount doubles (fsa_consts.h)
+  double dipole_n[3], dipole_m[3];
 };

@@ -1,4 +1,4 @@
-// FP32 first-generation (Stockham radix-8) apply passes, every supported length.
+// FP32 first-generation (Stockham radix-8) apply passes, lengths 8-128.
 // Compiled as its own translation unit so that the library's kernel
 // instances build in parallel; registers its launchers at library load.
 #include "passes_impl.cuh"
@@ -13,10 +13,4 @@ FSA_REGISTER(
     FSA_REG_V1(fsa::kArithF32G1, float2, 64)
     FSA_REG_V1(fsa::kArithF32G1, float2, 96)
     FSA_REG_V1(fsa::kArithF32G1, float2, 128)
-    FSA_REG_V1(fsa::kArithF32G1, float2, 192)
-    FSA_REG_V1(fsa::kArithF32G1, float2, 256)
-    FSA_REG_V1(fsa::kArithF32G1, float2, 384)
-    FSA_REG_V1(fsa::kArithF32G1, float2, 512)
-    FSA_REG_V1(fsa::kArithF32G1, float2, 768)
-    FSA_REG_V1(fsa::kArithF32G1, float2, 1024)
 )

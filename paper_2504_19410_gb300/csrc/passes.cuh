@@ -27,6 +27,7 @@
 // pitch: lanes on different rows hit different banks), transform them with
 // lanes mapped to rows, and copy them out coalesced.
 #pragma once
+#include "ddi.cuh"
 #include "fft_core.cuh"
 
 namespace fsa {
@@ -63,10 +64,12 @@ template <class P, typename V, int W> constexpr int smem_rows() { return W * (P:
 // ---------------------------------------------------------------- pass 1 --
 // Every kernel walks the tiles of all jobs of its launch with a grid-strided
 // loop (a persistent grid of a few CTAs per SM).
-template <typename V, class P, int W, int T>
+// PAD = false: the unpadded transform of length M over all M inputs (the DDI
+// grid reading's derivative, Sec. 5 Example 4); the same K = M/2 + 1 outputs.
+template <typename V, class P, int W, int T, bool PAD = true>
 __global__ void __launch_bounds__(W * T, MinB<V>::value) k_r2c_ax0(const Jobs jobs, long long C) {
   using R = typename RealOf<V>::T;
-  constexpr int M = P::M, n = M / 2, K = n + 1;
+  constexpr int M = P::M, NV = PAD ? M / 2 : M, K = M / 2 + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int l = threadIdx.x % W, t = threadIdx.x / W;
@@ -79,10 +82,10 @@ __global__ void __launch_bounds__(W * T, MinB<V>::value) k_r2c_ax0(const Jobs jo
   const bool ok = c < C;
   SLine<V, W> sl{sm + l};
   auto first = [&](int p) -> V {
-    return (p < n && ok) ? load_pair<V>(rho + (long long)p * C + c) : czero<V>();
+    return (p < NV && ok) ? load_pair<V>(rho + (long long)p * C + c) : czero<V>();
   };
   auto last = [&](int p, V v) { sl.put(p, v); };
-  fft_line<P, true, T, V, true, false>(t, first, last, sl);
+  fft_line<P, true, T, V, PAD, false>(t, first, last, sl);
   // Z = DFT(a + i b): A[k] = (Z[k] + conj Z[M-k]) / 2, B[k] = (Z[k] - conj Z[M-k]) / 2i
   for (int k = t; k < K; k += T) {
     const V zk = sm[k * W + l];
@@ -99,9 +102,9 @@ __global__ void __launch_bounds__(W * T, MinB<V>::value) k_r2c_ax0(const Jobs jo
 }
 
 // ---------------------------------------------------------------- pass 2 --
-template <typename V, class P, int W, int T>
+template <typename V, class P, int W, int T, bool PAD = true>
 __global__ void __launch_bounds__(W * T, MinB<V>::value) k_row_fwd(const Jobs jobs, long long rows) {
-  constexpr int M = P::M, n = M / 2, PITCH = M + 1, NT = W * T;
+  constexpr int M = P::M, n = PAD ? M / 2 : M, PITCH = M + 1, NT = W * T;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const long long tpj = (rows + W - 1) / W;
@@ -120,7 +123,7 @@ __global__ void __launch_bounds__(W * T, MinB<V>::value) k_row_fwd(const Jobs jo
   SLine<V, 1> sl{sm + l * PITCH};
   auto first = [&](int p) -> V { return p < n ? sl.get(p) : czero<V>(); };
   auto last = [&](int p, V v) { sl.put(p, v); };
-  fft_line<P, true, T, V, true, false>(t, first, last, sl);
+  fft_line<P, true, T, V, PAD, false>(t, first, last, sl);
   for (int i = threadIdx.x; i < W * M; i += NT) {
     const int l2 = i / M, p = i - l2 * M;
     const long long row = row0 + l2;
@@ -131,10 +134,14 @@ __global__ void __launch_bounds__(W * T, MinB<V>::value) k_row_fwd(const Jobs jo
 }
 
 // ---------------------------------------------------------------- pass 3 --
-template <typename V, class P, int W, int T>
+// MODE (ddi.cuh): kMulSpectrum multiplies by the stored spectrum; the DDI
+// modes by the multiplier of jb.par, kMulDdiGrid on the unpadded grid (all
+// M entries of a column live, transform length M along every axis).
+template <typename V, class P, int W, int T, int MODE = kMulSpectrum>
 __global__ void __launch_bounds__(W * T, minb_mid<V, W * T>()) k_col_mid(const Jobs jobs, int M2, int planes) {
   using R = typename RealOf<V>::T;
-  constexpr int M = P::M, n = M / 2;
+  constexpr bool PAD = MODE != kMulDdiGrid;
+  constexpr int M = P::M, n = PAD ? M / 2 : M;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int l = threadIdx.x % W, t = threadIdx.x / W;
@@ -151,19 +158,23 @@ __global__ void __launch_bounds__(W * T, minb_mid<V, W * T>()) k_col_mid(const J
   const int n2 = M2 / 2;
   const int p2 = ok ? min(k2, M2 - k2) : 0;
   V* col = Y + (long long)k0 * n * M2 + k2;
-  const typename Io<V>::S* srow = S + (long long)k0 * (n + 1) * (n2 + 1) + p2;
+  const typename Io<V>::S* srow = PAD ? S + (long long)k0 * (n + 1) * (n2 + 1) + p2 : S;
+  DdiLine<typename DdiReal<V>::T> ddi;
+  if constexpr (MODE != kMulSpectrum) ddi.init(jb.par, k0, ok ? k2 : 0, M2);
   SLine<V, W> sl{sm + l};
   auto first = [&](int p) -> V { return (p < n && ok) ? col[(long long)p * M2] : czero<V>(); };
   auto to_sm = [&](int p, V v) { sl.put(p, v); };
-  fft_line<P, true, T, V, true, false>(t, first, to_sm, sl);
+  fft_line<P, true, T, V, PAD, false>(t, first, to_sm, sl);
   auto mul = [&](int p) -> V {
-    const R s = ok ? load_spec<V>(srow + (long long)min(p, M - p) * (n2 + 1)) : R(0);
+    R s = R(0);
+    if constexpr (MODE != kMulDdiGrid) s = ok ? load_spec<V>(srow + (long long)min(p, M - p) * (n2 + 1)) : R(0);
+    if constexpr (MODE != kMulSpectrum) s = ok ? ddi.template value<MODE>(s, p, M) : R(0);
     return cscale(sl.get(p), s);
   };
   auto last = [&](int p, V v) {
     if (p < n && ok) col[(long long)p * M2] = canon(v);
   };
-  fft_line<P, false, T, V, false, true>(t, mul, last, sl);
+  fft_line<P, false, T, V, false, PAD>(t, mul, last, sl);
   }
 }
 
@@ -214,9 +225,9 @@ __global__ void __launch_bounds__(W * T, MinB<V>::value) k_row_mid(const Jobs jo
 }
 
 // ---------------------------------------------------------------- pass 4 --
-template <typename V, class P, int W, int T>
+template <typename V, class P, int W, int T, bool PAD = true>
 __global__ void __launch_bounds__(W * T, MinB<V>::value) k_row_inv(const Jobs jobs, long long rows) {
-  constexpr int M = P::M, n = M / 2, PITCH = M + 1, NT = W * T;
+  constexpr int M = P::M, n = PAD ? M / 2 : M, PITCH = M + 1, NT = W * T;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const long long tpj = (rows + W - 1) / W;
@@ -235,7 +246,7 @@ __global__ void __launch_bounds__(W * T, MinB<V>::value) k_row_inv(const Jobs jo
   SLine<V, 1> sl{sm + l * PITCH};
   auto first = [&](int p) -> V { return sl.get(p); };
   auto last = [&](int p, V v) { sl.put(p, v); };
-  fft_line<P, false, T, V, false, true>(t, first, last, sl);
+  fft_line<P, false, T, V, false, PAD>(t, first, last, sl);
   for (int i = threadIdx.x; i < W * n; i += NT) {
     const int l2 = i / n, p = i - l2 * n;
     const long long row = row0 + l2;
@@ -246,10 +257,12 @@ __global__ void __launch_bounds__(W * T, MinB<V>::value) k_row_inv(const Jobs jo
 }
 
 // ---------------------------------------------------------------- pass 5 --
-template <typename V, class P, int W, int T>
+// EPI: the output is phi + beta * rho with rho = jb.aux, beta = jb.par[kDdiBeta]
+// (the DDI grid reading's local term).
+template <typename V, class P, int W, int T, bool PAD = true, bool EPI = false>
 __global__ void __launch_bounds__(W * T, MinB<V>::value) k_c2r_ax0(const Jobs jobs, long long C) {
   using R = typename RealOf<V>::T;
-  constexpr int M = P::M, n = M / 2;
+  constexpr int M = P::M, n = M / 2, NV = PAD ? M / 2 : M;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int l = threadIdx.x % W, t = threadIdx.x / W;
@@ -270,9 +283,16 @@ __global__ void __launch_bounds__(W * T, MinB<V>::value) k_c2r_ax0(const Jobs jo
     return lo ? mk(a.x - b.y, a.y + b.x) : mk(a.x + b.y, b.x - a.y);
   };
   auto last = [&](int p, V v) {
-    if (p < n && ok) store_pair<V>(phi + (long long)p * C + c, v);
+    if (p < NV && ok) {
+      if constexpr (EPI) {
+        store_pair_axpy<V>(phi + (long long)p * C + c, v, jb.par[kDdiBeta],
+                           static_cast<const typename Io<V>::T*>(jb.aux) + (long long)p * C + c);
+      } else {
+        store_pair<V>(phi + (long long)p * C + c, v);
+      }
+    }
   };
-  fft_line<P, false, T, V, false, true>(t, first, last, sl);
+  fft_line<P, false, T, V, false, PAD>(t, first, last, sl);
   }
 }
 

@@ -12,6 +12,7 @@
 // are contiguous per half-warp; the shared tile is sm[l * R1 (R2+1) + q (R2+1) + t]
 // (padded rows: conflict-free for both steps).
 #pragma once
+#include "ddi.cuh"
 #include "fft_reg.cuh"
 
 namespace fsa {
@@ -154,29 +155,51 @@ __device__ __forceinline__ void mid_load(MidSpec<P>& sp, const float* __restrict
   }
 }
 
-template <class P> __device__ __forceinline__ void mid_apply(float2* b, const MidSpec<P>& sp, int u) {
+// f(s, S) turns the spectrum value of element s (k1 = u + R1 s) into the
+// value that multiplies it (the identity for the plain spectrum multiply).
+struct SpecOnly {
+  __device__ __forceinline__ float operator()(int, float v) const { return v; }
+};
+
+template <class P, class F = SpecOnly>
+__device__ __forceinline__ void mid_apply(float2* b, const MidSpec<P>& sp, int u, F f = F()) {
   constexpr int R1 = P::R1, R2 = P::R2, H = R2 / 2;
   if constexpr (MidSpec<P>::PAIRED) {
 #pragma unroll
-    for (int s = 0; s < H; ++s) b[s] = cscale(b[s], sp.v[s]);
+    for (int s = 0; s < H; ++s) b[s] = cscale(b[s], f(s, sp.v[s]));
     // s >= R2/2: S(M - k1) with M - k1 = (R1 - u) + R1 (R2 - 1 - s) for u > 0
     if ((threadIdx.x >> 5) == 0) {  // u = 0 (M - k1 = R1 (R2 - s); Nyquist at s = R2/2) or u = R1/2
       sfor<H, R2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
         const float a = sp.v[s == H ? H : R2 - s];
-        b[s] = cscale(b[s], u == 0 ? a : sp.v[R2 - 1 - s]);
+        b[s] = cscale(b[s], f(s, u == 0 ? a : sp.v[R2 - 1 - s]));
       });
     } else {  // the mirror u' = R1 - u is the other half of this warp
 #pragma unroll
-      for (int s = H; s < R2; ++s) b[s] = cscale(b[s], __shfl_xor_sync(0xffffffffu, sp.v[R2 - 1 - s], 16));
+      for (int s = H; s < R2; ++s) b[s] = cscale(b[s], f(s, __shfl_xor_sync(0xffffffffu, sp.v[R2 - 1 - s], 16)));
     }
   } else {
 #pragma unroll
-    for (int s = 0; s < R2; ++s) b[s] = cscale(b[s], sp.v[s]);
+    for (int s = 0; s < R2; ++s) b[s] = cscale(b[s], f(s, sp.v[s]));
   }
 }
 
-template <class P>
+// The middle pass's multiply: the spectrum alone, or (kMulDdiKernel) the 3-D
+// DDI kernel reading's cmul * S * D + cadd at k1 = u + R1 s.
+template <class P, int MODE>
+__device__ __forceinline__ void mid_multiply(float2* b, const MidSpec<P>& sp, int u, const Job& jb, int k0, int k2,
+                                             int M2, bool ok) {
+  if constexpr (MODE == kMulSpectrum) {
+    mid_apply<P>(b, sp, u);
+  } else {
+    static_assert(MODE == kMulDdiKernel, "the second-generation middle pass runs on the padded grid");
+    DdiLine<float> ddi;
+    ddi.init(jb.par, k0, ok ? k2 : 0, M2);
+    mid_apply<P>(b, sp, u, [&](int s, float v) { return ddi.template value<MODE>(v, u + P::R1 * s, P::M); });
+  }
+}
+
+template <class P, int MODE = kMulSpectrum>
 __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2_col_mid(const Jobs jobs, int M2, int planes) {
   using V = float2;
   constexpr int M = P::M, n = M / 2, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2;
@@ -210,7 +233,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2_col_mid(con
     for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
     rfft<R2, true>(b);
     // b[s] = transform at k1 = u + R1 s: multiply by the spectrum (real, even)
-    mid_apply<P>(b, sp, u);
+    mid_multiply<P, MODE>(b, sp, u, jb, k0, k2, M2, ok);
     // the locations this thread read are the ones it writes: no barrier needed
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
@@ -244,7 +267,7 @@ template <class P> struct Stage2 {
   static constexpr int BYTES = SLOTS * P::T * Geo2<P>::W * 8;
 };
 
-template <class P>
+template <class P, int MODE = kMulSpectrum>
 __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2p_col_mid(const Jobs jobs, int M2, int planes) {
   using V = float2;
   constexpr int M = P::M, n = M / 2, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2, T = P::T;
@@ -303,7 +326,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2p_col_mid(co
 #pragma unroll
     for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
     rfft<R2, true>(b);
-    mid_apply<P>(b, sp, u);
+    mid_multiply<P, MODE>(b, sp, u, jb, k0, k2, M2, ok);
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
     stepA_inv<P, V, true>(
@@ -467,7 +490,9 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2_row_inv(const Jobs jobs, long 
 }
 
 // ---------------------------------------------------------------- pass 5 --
-template <class P>
+// EPI: phi + beta * rho (rho = jb.aux, beta = jb.par[kDdiBeta]), the DDI grid
+// reading's local term.
+template <class P, bool EPI = false>
 __global__ void __launch_bounds__(Geo2<P>::NT) k2_c2r_ax0(const Jobs jobs, long long C) {
   using V = float2;
   constexpr int M = P::M, n = M / 2, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2;
@@ -502,7 +527,14 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2_c2r_ax0(const Jobs jobs, long 
         u, [&](int q, int t) { return sm[(q * R2 + t) * W + l]; },
         [&](int t, int r, V v) {
           const int p = t + R2 * r;
-          if (p < n && ok) *reinterpret_cast<V*>(phi + (long long)p * C + c) = v;
+          if (p < n && ok) {
+            if constexpr (EPI) {
+              store_pair_axpy<V>(phi + (long long)p * C + c, v, jb.par[kDdiBeta],
+                                 static_cast<const float*>(jb.aux) + (long long)p * C + c);
+            } else {
+              *reinterpret_cast<V*>(phi + (long long)p * C + c) = v;
+            }
+          }
         });
     __syncthreads();
   }

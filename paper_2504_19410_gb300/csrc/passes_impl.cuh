@@ -16,6 +16,10 @@ namespace detail {
 
 template <typename V, int M> struct Inst {
   using P = typename PlanFor<M>::type;
+  // the DDI grid reading's unpadded passes: FP32 and native FP64 only (an
+  // FP64 plan runs them natively whatever its arithmetic: their output, the
+  // real array d_n d_m rho, is what the double-word passes read too)
+  static constexpr bool kUnpadded = !std::is_same<V, cdw>::value;
   static constexpr int W = TileW<V>::W;
   static constexpr int T = threads_per_line<P, W>();
   static constexpr int NT = W * T;
@@ -39,6 +43,15 @@ template <typename V, int M> struct Inst {
     set((const void*)k_r2c_ax0<V, P, WM, TM>, SM_STRM);
     set((const void*)k_c2r_ax0<V, P, WM, TM>, SM_STRM);
     set((const void*)k_c2r_ax0<V, P, W, T>, SM_STRIDED);
+    set((const void*)k_col_mid<V, P, WC, TC, kMulDdiKernel>, SM_MID);
+    set((const void*)k_c2r_ax0<V, P, W, T, true, true>, SM_STRIDED);
+    if constexpr (kUnpadded) {
+      set((const void*)k_r2c_ax0<V, P, W, T, false>, SM_STRIDED);
+      set((const void*)k_row_fwd<V, P, W, T, false>, SM_ROWS);
+      set((const void*)k_col_mid<V, P, WC, TC, kMulDdiGrid>, SM_MID);
+      set((const void*)k_row_inv<V, P, W, T, false>, SM_ROWS);
+      set((const void*)k_c2r_ax0<V, P, W, T, false>, SM_STRIDED);
+    }
     return e;
   }
   static Geometry geometry(PassKind k) {
@@ -105,6 +118,54 @@ template <typename V, int M> struct Inst {
     f<<<persistent_grid((const void*)f, NT, SM_STRIDED, tiles), NT, SM_STRIDED, s>>>(jobs, C);
     return cudaGetLastError();
   }
+
+  // 3-D DDI (Sec. 5, Example 4).  Kernel reading: the middle pass with the
+  // multiplier cmul * S * D + cadd.  Grid reading: the C2R pass adding
+  // beta * rho, and the five passes of the unpadded transform of length M
+  // (this instance's length is the grid's n there) whose middle multiplies by
+  // cmul * D.
+  static cudaError_t colm_ddi(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
+    const long long tiles = (long long)((M2 + WC - 1) / WC) * planes * jobs.count;
+    auto f = k_col_mid<V, P, WC, TC, kMulDdiKernel>;
+    f<<<persistent_grid((const void*)f, NTC, SM_MID, tiles), NTC, SM_MID, s>>>(jobs, M2, planes);
+    return cudaGetLastError();
+  }
+  static cudaError_t c2r_epi(const Jobs& jobs, long long C, cudaStream_t s) {
+    const long long tiles = (C + 2 * W - 1) / (2 * W) * jobs.count;
+    auto f = k_c2r_ax0<V, P, W, T, true, true>;
+    f<<<persistent_grid((const void*)f, NT, SM_STRIDED, tiles), NT, SM_STRIDED, s>>>(jobs, C);
+    return cudaGetLastError();
+  }
+  static cudaError_t r2c_per(const Jobs& jobs, long long C, cudaStream_t s) {
+    const long long tiles = (C + 2 * W - 1) / (2 * W) * jobs.count;
+    auto f = k_r2c_ax0<V, P, W, T, false>;
+    f<<<persistent_grid((const void*)f, NT, SM_STRIDED, tiles), NT, SM_STRIDED, s>>>(jobs, C);
+    return cudaGetLastError();
+  }
+  static cudaError_t rowf_per(const Jobs& jobs, long long rows, cudaStream_t s) {
+    const long long tiles = (rows + W - 1) / W * jobs.count;
+    auto f = k_row_fwd<V, P, W, T, false>;
+    f<<<persistent_grid((const void*)f, NT, SM_ROWS, tiles), NT, SM_ROWS, s>>>(jobs, rows);
+    return cudaGetLastError();
+  }
+  static cudaError_t colm_per(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
+    const long long tiles = (long long)((M2 + WC - 1) / WC) * planes * jobs.count;
+    auto f = k_col_mid<V, P, WC, TC, kMulDdiGrid>;
+    f<<<persistent_grid((const void*)f, NTC, SM_MID, tiles), NTC, SM_MID, s>>>(jobs, M2, planes);
+    return cudaGetLastError();
+  }
+  static cudaError_t rowi_per(const Jobs& jobs, long long rows, cudaStream_t s) {
+    const long long tiles = (rows + W - 1) / W * jobs.count;
+    auto f = k_row_inv<V, P, W, T, false>;
+    f<<<persistent_grid((const void*)f, NT, SM_ROWS, tiles), NT, SM_ROWS, s>>>(jobs, rows);
+    return cudaGetLastError();
+  }
+  static cudaError_t c2r_per(const Jobs& jobs, long long C, cudaStream_t s) {
+    const long long tiles = (C + 2 * W - 1) / (2 * W) * jobs.count;
+    auto f = k_c2r_ax0<V, P, W, T, false>;
+    f<<<persistent_grid((const void*)f, NT, SM_STRIDED, tiles), NT, SM_STRIDED, s>>>(jobs, C);
+    return cudaGetLastError();
+  }
 };
 
 // Second-generation (two-step register) kernels, FP32.
@@ -127,6 +188,9 @@ template <int M> struct Inst2 {
     set((const void*)k2p_row_inv<P, 8>, RowGeo<P, 8>::SM_INV);
     set((const void*)k4_row_fwd<P, WRF>, GF::SMEM);
     set((const void*)k4_row_inv<P, WRI>, GI::SMEM);
+    set((const void*)k2_col_mid<P, kMulDdiKernel>, G::SM_STRIDED);
+    set((const void*)k2p_col_mid<P, kMulDdiKernel>, G::SM_STRIDED + Stage2<P>::BYTES);
+    set((const void*)k2_c2r_ax0<P, true>, G::SM_STRIDED);
     return e;
   }
   // bulk-copy row passes: rows per tile, fewer for the longest lines
@@ -217,6 +281,27 @@ template <int M> struct Inst2 {
     f<<<persistent_grid((const void*)f, G::NT, G::SM_STRIDED, tiles), G::NT, G::SM_STRIDED, s>>>(jobs, C);
     return cudaGetLastError();
   }
+  // 3-D DDI: the kernel reading's middle pass and the grid reading's C2R
+  static cudaError_t colm_ddi(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
+    const long long tiles = (long long)((M2 + W - 1) / W) * planes * jobs.count;
+    auto f = k2_col_mid<P, kMulDdiKernel>;
+    f<<<persistent_grid((const void*)f, G::NT, G::SM_STRIDED, tiles), G::NT, G::SM_STRIDED, s>>>(jobs, M2,
+                                                                                                  planes);
+    return cudaGetLastError();
+  }
+  static cudaError_t colm_p_ddi(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
+    const long long tiles = (long long)((M2 + W - 1) / W) * planes * jobs.count;
+    constexpr int smem = G::SM_STRIDED + Stage2<P>::BYTES;
+    auto f = k2p_col_mid<P, kMulDdiKernel>;
+    f<<<persistent_grid((const void*)f, G::NT, smem, tiles), G::NT, smem, s>>>(jobs, M2, planes);
+    return cudaGetLastError();
+  }
+  static cudaError_t c2r_epi(const Jobs& jobs, long long C, cudaStream_t s) {
+    const long long tiles = (C + 2 * W - 1) / (2 * W) * jobs.count;
+    auto f = k2_c2r_ax0<P, true>;
+    f<<<persistent_grid((const void*)f, G::NT, G::SM_STRIDED, tiles), G::NT, G::SM_STRIDED, s>>>(jobs, C);
+    return cudaGetLastError();
+  }
 };
 
 
@@ -225,6 +310,8 @@ template <int M> struct Inst2 {
 // Launchers of one instance as a function table (see fsa_internal.h).
 template <class I, class = void> struct HasRowm : std::false_type {};
 template <class I> struct HasRowm<I, std::void_t<decltype(&I::rowm)>> : std::true_type {};
+template <class I, class = void> struct HasUnpadded : std::false_type {};
+template <class I> struct HasUnpadded<I, std::void_t<decltype(I::kUnpadded)>> : std::bool_constant<I::kUnpadded> {};
 
 template <class I> PassFns fns_of() {
   PassFns f;
@@ -233,6 +320,15 @@ template <class I> PassFns fns_of() {
     f.r2c_plane = &I::r2c_plane;
     f.c2r_plane = &I::c2r_plane;
   }
+  if constexpr (HasUnpadded<I>::value) {
+    f.r2c_per = &I::r2c_per;
+    f.rowf_per = &I::rowf_per;
+    f.colm_per = &I::colm_per;
+    f.rowi_per = &I::rowi_per;
+    f.c2r_per = &I::c2r_per;
+  }
+  f.colm_ddi = &I::colm_ddi;
+  f.c2r_epi = &I::c2r_epi;
   f.prepare = &I::prepare;
   f.geometry = &I::geometry;
   f.r2c = &I::r2c;
@@ -281,6 +377,7 @@ static cudaError_t init_tu_twiddles() {
   {                                                                                   \
     fsa::PassFns f3 = fsa::fns_of<fsa::detail::Inst2<M>>();                           \
     f3.colm = &fsa::detail::Inst2<M>::colm_p;                                         \
+    f3.colm_ddi = &fsa::detail::Inst2<M>::colm_p_ddi;                                 \
     f3.rowf = &fsa::detail::Inst2<M>::rowf_p;                                         \
     f3.rowi = &fsa::detail::Inst2<M>::rowi_p;                                         \
     fsa::register_pass_fns(fsa::kArithF32G3, M, f3);                                  \

@@ -314,8 +314,99 @@ cudaError_t group_passes_2d(const int* n, int count, const void* const* rho, voi
   return e;
 }
 
+// The 3-D DDI (Sec. 5, Example 4) for `count` solves of one plan shape,
+// Phi = -(m.n) rho - 3 (1/(4 pi |x|)) * (d_n d_m rho).
+// Kernel reading: the five Coulomb passes, the middle one multiplying by
+// -3 S D - (m.n)/(8 n0 n1 n2) (par).  Grid reading: -3 d_n d_m rho by five
+// passes of the unpadded transform (length n_j per axis; R2C along axis 0
+// into Y, row forward Y -> X, middle in place on X with -3 D / (n0 n1 n2),
+// row inverse X -> Y, C2R into the back half of Y), first generation with
+// native arithmetic; then the five Coulomb passes on it, the last adding
+// -(m.n) rho.  No pass split (the DDI middle pass takes absolute plane
+// indices).
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+template <typename V>
+cudaError_t group_passes_ddi(const fsa_plan* shape, int count, const void* const* rho, void* const* phi,
+                             void* const* X, void* const* Y, const void* const* S, const double* const* par,
+                             cudaStream_t s, PassTrace* tr) {
+  using Vu = typename std::conditional<std::is_same<V, cdw>::value, double2, V>::type;
+  const int n0 = shape->n[0], n1 = shape->n[1], n2 = shape->n[2];
+  const long long C = (long long)n1 * n2;
+  const long long rows = (long long)(n0 + 1) * n1;
+  const bool grid = shape->ddi == FSA_DDI_GRID;
+  if (!par) return cudaErrorInvalidValue;
+  const PassFns& f1 = pass_fns(arith_for<V>(kR2C, 2 * n0), 2 * n0);
+  const PassFns& f2 = pass_fns(arith_for<V>(kRowFwd, 2 * n2), 2 * n2);
+  const PassFns& f3 = pass_fns(arith_for<V>(kColMid, 2 * n1), 2 * n1);
+  const PassFns& f4 = pass_fns(arith_for<V>(kRowInv, 2 * n2), 2 * n2);
+  const PassFns& f5 = pass_fns(arith_for<V>(kC2R, 2 * n0), 2 * n0);
+  if (!f1.r2c || !f2.rowf || !f3.colm || !f3.colm_ddi || !f4.rowi || !f5.c2r || !f5.c2r_epi)
+    return cudaErrorInvalidValue;
+  const int ua = first_gen_arith<Vu>();
+  const PassFns& u0 = pass_fns(ua, n0);
+  const PassFns& u1 = pass_fns(ua, n1);
+  const PassFns& u2 = pass_fns(ua, n2);
+  if (grid && (!u0.r2c_per || !u0.c2r_per || !u1.colm_per || !u2.rowf_per || !u2.rowi_per))
+    return cudaErrorInvalidValue;
+  const long long Kn = n0 / 2 + 1;  // unpadded half spectrum along axis 0
+  const size_t xn_bytes = align256((size_t)Kn * n1 * n2 * sizeof(Vu));
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < count && e == cudaSuccess; b += kMaxJobs) {
+    const int m = count - b < kMaxJobs ? count - b : kMaxJobs;
+    Jobs g1{}, g2{}, g3{}, g4{}, g5{}, j1{}, j2{}, j3{}, j4{}, j5{};
+    g1.count = g2.count = g3.count = g4.count = g5.count = m;
+    j1.count = j2.count = j3.count = j4.count = j5.count = m;
+    for (int i = 0; i < m; ++i) {
+      const int k = b + i;
+      char* Yk = static_cast<char*>(Y[k]);
+      void* drho = Yk + xn_bytes;
+      g1.j[i] = Job{rho[k], Yk, nullptr};
+      g2.j[i] = Job{Yk, X[k], nullptr};
+      g3.j[i] = Job{X[k], X[k], nullptr, nullptr, par[k]};
+      g4.j[i] = Job{X[k], Yk, nullptr};
+      g5.j[i] = Job{Yk, drho, nullptr};
+      j1.j[i] = Job{grid ? drho : rho[k], X[k], nullptr};
+      j2.j[i] = Job{X[k], Y[k], nullptr};
+      j3.j[i] = Job{Y[k], Y[k], S[k], nullptr, par[k]};
+      j4.j[i] = Job{Y[k], X[k], nullptr};
+      j5.j[i] = Job{X[k], phi[k], nullptr, rho[k], par[k]};
+    }
+    e = trace_mark(tr, -1, s);
+    if (grid) {
+      if (e == cudaSuccess) e = u0.r2c_per(g1, C, s);
+      if (e == cudaSuccess) e = trace_mark(tr, kR2C, s);
+      if (e == cudaSuccess) e = u2.rowf_per(g2, Kn * n1, s);
+      if (e == cudaSuccess) e = trace_mark(tr, kRowFwd, s);
+      if (e == cudaSuccess) e = u1.colm_per(g3, n2, (int)Kn, s);
+      if (e == cudaSuccess) e = trace_mark(tr, kColMid, s);
+      if (e == cudaSuccess) e = u2.rowi_per(g4, Kn * n1, s);
+      if (e == cudaSuccess) e = trace_mark(tr, kRowInv, s);
+      if (e == cudaSuccess) e = u0.c2r_per(g5, C, s);
+      if (e == cudaSuccess) e = trace_mark(tr, kC2R, s);
+    }
+    if (e == cudaSuccess) e = f1.r2c(j1, C, s);
+    if (e == cudaSuccess) e = trace_mark(tr, kR2C, s);
+    if (e == cudaSuccess) e = f2.rowf(j2, rows, s);
+    if (e == cudaSuccess) e = trace_mark(tr, kRowFwd, s);
+    if (e == cudaSuccess) e = grid ? f3.colm(j3, 2 * n2, n0 + 1, s) : f3.colm_ddi(j3, 2 * n2, n0 + 1, s);
+    if (e == cudaSuccess) e = trace_mark(tr, kColMid, s);
+    if (e == cudaSuccess) e = f4.rowi(j4, rows, s);
+    if (e == cudaSuccess) e = trace_mark(tr, kRowInv, s);
+    if (e == cudaSuccess) e = grid ? f5.c2r_epi(j5, C, s) : f5.c2r(j5, C, s);
+    if (e == cudaSuccess) e = trace_mark(tr, kC2R, s);
+  }
+  return e;
+}
+
 cudaError_t run_group(const fsa_plan* shape, int count, const void* const* rho, void* const* phi, void* const* X,
-                      void* const* Y, const void* const* S, cudaStream_t s, PassTrace* tr) {
+                      void* const* Y, const void* const* S, cudaStream_t s, PassTrace* tr,
+                      const double* const* par) {
+  if (shape->ddi >= 0) {
+    if (shape->dtype == FSA_F32) return group_passes_ddi<float2>(shape, count, rho, phi, X, Y, S, par, s, tr);
+    if (shape->f64_dw) return group_passes_ddi<cdw>(shape, count, rho, phi, X, Y, S, par, s, tr);
+    return group_passes_ddi<double2>(shape, count, rho, phi, X, Y, S, par, s, tr);
+  }
   if (shape->d == 2) {
     if (shape->dtype == FSA_F32) return group_passes_2d<float2>(shape->n, count, rho, phi, X, S, s, tr);
     if (shape->f64_dw) return group_passes_2d<cdw>(shape->n, count, rho, phi, X, S, s, tr);
@@ -413,7 +504,9 @@ struct DeviceGuard {
   }
 };
 
-fsa_status prepare_device(int dev, fsa_dtype dt, const int* n, int d) {
+// unpadded: also the transform lengths n_j themselves (the DDI grid
+// reading's unpadded passes)
+fsa_status prepare_device(int dev, fsa_dtype dt, const int* n, int d, bool unpadded = false) {
   std::lock_guard<std::mutex> lk(g_init_mu);
   if (!g_tw_ready.count(dev)) {
     cudaError_t e = init_all_twiddles();
@@ -423,8 +516,9 @@ fsa_status prepare_device(int dev, fsa_dtype dt, const int* n, int d) {
     if (e != cudaSuccess) return cuda_error(e, "fault word");
     g_tw_ready.insert(dev);
   }
-  for (int j = 0; j < d; ++j) {  // a plane's unit third axis has no kernels
-    const int M = 2 * n[j];
+  for (int jj = 0; jj < (unpadded ? 2 * d : d); ++jj) {  // a plane's unit third axis has no kernels
+    const int j = jj % d;
+    const int M = jj < d ? 2 * n[j] : n[j];
     const int key = M * 4 + (int)dt;
     if (g_prepared.count({dev, key})) continue;
     cudaError_t e = cudaSuccess;
@@ -448,7 +542,8 @@ cudaError_t apply_passes(const fsa_plan* p, const void* rho, void* phi, void* X,
   void* xs[1] = {X};
   void* ys[1] = {Y};
   const void* ss[1] = {plan_apply_spectrum(p)};
-  return run_group(p, 1, rhos, phis, xs, ys, ss, s, nullptr);
+  const double* pars[1] = {p->ddi_par};
+  return run_group(p, 1, rhos, phis, xs, ys, ss, s, nullptr, pars);
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -471,7 +566,8 @@ cudaError_t plan_apply_passes_trace(const fsa_plan* p, const void* rho, void* ph
   void* xs[1] = {p->ws};
   void* ys[1] = {(char*)p->ws + p->x_bytes};
   const void* ss[1] = {plan_apply_spectrum(p)};
-  return run_group(p, 1, rhos, phis, xs, ys, ss, s, tr);
+  const double* pars[1] = {p->ddi_par};
+  return run_group(p, 1, rhos, phis, xs, ys, ss, s, tr, pars);
 }
 }  // namespace fsa
 
@@ -581,8 +677,10 @@ fsa_status plan_validate(fsa_kernel kernel, const double* L, const int* n, fsa_d
   return FSA_OK;
 }
 
-fsa_status plan_create_internal(fsa_plan** out, fsa_kernel kernel, const double* L, const int* n, fsa_dtype dtype,
-                                double eps_in, double eps_tol, bool with_workspace) {
+// extra_ws: device bytes appended to the workspace; unpadded: prepare the
+// kernels of the transform lengths n_j too (the DDI grid reading).
+fsa_status plan_create_core(fsa_plan** out, fsa_kernel kernel, const double* L, const int* n, fsa_dtype dtype,
+                            double eps_in, double eps_tol, bool with_workspace, size_t extra_ws, bool unpadded) {
   *out = nullptr;
   double eps = 0, bound = 0;
   fsa_status vs = plan_validate(kernel, L, n, dtype, eps_in, eps_tol, &eps, &bound);
@@ -592,7 +690,7 @@ fsa_status plan_create_internal(fsa_plan** out, fsa_kernel kernel, const double*
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "fsa_plan_create: cudaGetDevice");
-  fsa_status st = prepare_device(dev, dtype, n, d);
+  fsa_status st = prepare_device(dev, dtype, n, d, unpadded);
   if (st != FSA_OK) return st;
 
   fsa_plan* p = new fsa_plan{};
@@ -606,13 +704,14 @@ fsa_status plan_create_internal(fsa_plan** out, fsa_kernel kernel, const double*
   p->eps_bound = bound;
   p->kernel = kernel;
   p->d = d;
+  p->ddi = -1;
   p->chunk_bytes = 0;  // one slab: measured fastest at 256^3 (see fsa_plan_opts.l2_chunk_mb)
   p->dtype = dtype;
   p->device = dev;
   const size_t s = dtype == FSA_F32 ? 4 : 8;
   p->spectrum_bytes = (size_t)(n[0] + 1) * (n[1] + 1) * (d == 2 ? 1 : n[2] + 1) * s;
   p->x_bytes = (size_t)(n[0] + 1) * n[1] * n[2] * 2 * s;
-  p->ws_bytes = with_workspace ? plan_workspace_bytes(n, dtype) : 0;
+  p->ws_bytes = with_workspace ? plan_workspace_bytes(n, dtype) + extra_ws : 0;
   // The workspace always holds the FP64 generation scratch of an FP32 plan.
   e = cudaMalloc(&p->spectrum, p->spectrum_bytes);
   if (e == cudaSuccess && dtype == FSA_F64) e = cudaMalloc(&p->spectrum_dw, p->spectrum_bytes);
@@ -635,6 +734,33 @@ fsa_status plan_create_internal(fsa_plan** out, fsa_kernel kernel, const double*
   }
   *out = p;
   return FSA_OK;
+}
+
+fsa_status plan_create_internal(fsa_plan** out, fsa_kernel kernel, const double* L, const int* n, fsa_dtype dtype,
+                                double eps_in, double eps_tol, bool with_workspace) {
+  return plan_create_core(out, kernel, L, n, dtype, eps_in, eps_tol, with_workspace, 0, false);
+}
+
+// The DDI parameter block (fsa_consts.h) of a plan: transform lengths
+// M_j = 2 n_j for the kernel reading (the doubled grid, period 4 L_j) and
+// n_j for the grid reading (period 2 L_j).
+void ddi_params(const fsa_plan* p, int derivative, double* par) {
+  const double pi = 3.141592653589793238462643383279502884;
+  const bool grid = derivative == FSA_DDI_GRID;
+  double nm = 0;
+  for (int j = 0; j < 3; ++j) {
+    const double M = grid ? p->n[j] : 2.0 * p->n[j];
+    par[kDdiN + j] = p->dipole_n[j];
+    par[kDdiM + j] = p->dipole_m[j];
+    par[kDdiW + j] = 2.0 * pi / (M * p->h[j]);
+    par[kDdiNu + j] = -pi / p->h[j];
+    nm += p->dipole_n[j] * p->dipole_m[j];
+  }
+  const double vol = (double)p->n[0] * p->n[1] * p->n[2];
+  par[kDdiCmul] = grid ? -3.0 / vol : -3.0;
+  par[kDdiCadd] = grid ? 0.0 : -nm / (8.0 * vol);
+  par[kDdiNyq0] = grid ? p->n[0] / 2 : p->n[0];
+  par[kDdiBeta] = -nm;
 }
 
 // Autotuner: for an FP32 plan, time both kernel generations of each pass on the
@@ -758,7 +884,9 @@ cudaError_t tune_f64(fsa_plan* p) {
 
 cudaError_t plan_generate_into(fsa_plan* p, void* scratch, cudaStream_t s) {
   double* oct = p->dtype == FSA_F64 ? (double*)p->spectrum : (double*)scratch;
-  cudaError_t e = tensorgen_run(p->kernel, p->n, p->L, p->eps, oct, p->spectrum, p->dtype, s);
+  // a DDI plan's tensor is the Coulomb kernel's (Sec. 5, Example 4)
+  const fsa_kernel k = p->kernel == FSA_KERNEL_DDI3D ? FSA_KERNEL_COULOMB3D : p->kernel;
+  cudaError_t e = tensorgen_run(k, p->n, p->L, p->eps, oct, p->spectrum, p->dtype, s);
   if (e == cudaSuccess && p->spectrum_dw)
     e = spectrum_to_dw((const double*)p->spectrum, p->spectrum_dw, p->spectrum_bytes / 8, s);
   if (e == cudaSuccess) p->generated = 1;
@@ -773,6 +901,8 @@ fsa_status fsa_plan_create(fsa_plan** out, fsa_kernel kernel, int d, const doubl
                            fsa_dtype dtype, const fsa_plan_opts* opts) {
   if (!out) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: out is NULL");
   *out = nullptr;
+  if (kernel == FSA_KERNEL_DDI3D)
+    return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: DDI plans need their dipoles: use fsa_plan_create_ddi3d");
   if (kernel < FSA_KERNEL_COULOMB3D || kernel > FSA_KERNEL_BIHARMONIC2D)
     return set_error(FSA_ERR_UNSUPPORTED, "fsa_plan_create: unknown kernel");
   if (d != kernel_dim(kernel))
@@ -798,11 +928,60 @@ fsa_status fsa_plan_create(fsa_plan** out, fsa_kernel kernel, int d, const doubl
   return st;
 }
 
+fsa_status fsa_plan_create_ddi3d(fsa_plan** out, const double* L, const int* n, fsa_dtype dtype,
+                                 const double* dipole_n, const double* dipole_m, fsa_ddi_derivative derivative,
+                                 const fsa_plan_opts* opts) {
+  if (!out) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create_ddi3d: out is NULL");
+  *out = nullptr;
+  if (!L || !n || !dipole_n || !dipole_m)
+    return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create_ddi3d: NULL argument");
+  if (derivative != FSA_DDI_GRID && derivative != FSA_DDI_KERNEL)
+    return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create_ddi3d: unknown derivative");
+  for (int j = 0; j < 3; ++j)
+    if (!std::isfinite(dipole_n[j]) || !std::isfinite(dipole_m[j]))
+      return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create_ddi3d: dipoles must be finite");
+  fsa_plan_opts o{};
+  o.device = -1;
+  if (opts) o = *opts;
+  double eps = 0, bound = 0;
+  fsa_status vs = plan_validate(FSA_KERNEL_COULOMB3D, L, n, dtype, o.eps, o.eps_tol, &eps, &bound);
+  if (vs != FSA_OK) return vs;  // no device touched
+  const bool grid = derivative == FSA_DDI_GRID;
+  for (int j = 0; j < 3 && grid; ++j)
+    if (n[j] < 8)
+      return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create_ddi3d: the grid reading needs n_j >= 8");
+  DeviceGuard dg;
+  cudaError_t e = dg.set(o.device);
+  if (e != cudaSuccess) return cuda_error(e, "fsa_plan_create_ddi3d: cudaSetDevice");
+  const size_t stage = (size_t)n[0] * n[1] * n[2] * (dtype == FSA_F32 ? 4 : 8);
+  fsa_plan* p = nullptr;
+  fsa_status st = plan_create_core(&p, FSA_KERNEL_COULOMB3D, L, n, dtype, o.eps, o.eps_tol, true, stage + 256, grid);
+  if (st != FSA_OK) return st;
+  p->kernel = FSA_KERNEL_DDI3D;
+  p->ddi = derivative;
+  for (int j = 0; j < 3; ++j) {
+    p->dipole_n[j] = dipole_n[j];
+    p->dipole_m[j] = dipole_m[j];
+  }
+  double par[kDdiParCount];
+  ddi_params(p, derivative, par);
+  e = cudaMalloc(&p->ddi_par, sizeof par);
+  if (e == cudaSuccess) e = cudaMemcpy(p->ddi_par, par, sizeof par, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    fsa_plan_destroy(p);
+    cudaGetLastError();
+    return cuda_error(e, "fsa_plan_create_ddi3d: parameter block");
+  }
+  *out = p;
+  return FSA_OK;
+}
+
 fsa_status fsa_plan_destroy(fsa_plan* p) {
   if (!p) return FSA_OK;
   batched_forget_plan(p);
   DeviceGuard dg;
   dg.set(p->device);
+  if (p->ddi_par) cudaFree(p->ddi_par);
   cudaFree(p->spectrum);
   if (p->spectrum_dw) cudaFree(p->spectrum_dw);
   if (p->ws) cudaFree(p->ws);
@@ -841,12 +1020,18 @@ fsa_status fsa_plan_info_get(const fsa_plan* p, fsa_plan_info* info) {
     const int K0 = p->n[0] + 1;
     const int pc = p->chunk_bytes > 0 ? (int)std::max<long long>(1, p->chunk_bytes / plane) : K0;
     info->launches_per_apply = p->d == 2 ? 3 : 2 + 3 * ((K0 + std::min(pc, K0) - 1) / std::min(pc, K0));
+    if (p->ddi >= 0) info->launches_per_apply = p->ddi == FSA_DDI_GRID ? 10 : 5;
   }
   info->workspace_bytes = p->ws_bytes;
   info->spectrum_bytes = p->spectrum_bytes;
   info->spectrum = p->spectrum;
   info->kernel = p->kernel;
   info->d = p->d;
+  info->ddi_derivative = p->ddi;
+  for (int j = 0; j < 3; ++j) {
+    info->dipole_n[j] = p->ddi >= 0 ? p->dipole_n[j] : 0.0;
+    info->dipole_m[j] = p->ddi >= 0 ? p->dipole_m[j] : 0.0;
+  }
   return FSA_OK;
 }
 
@@ -884,13 +1069,16 @@ fsa_status fsa_apply_host(const fsa_plan* p, const void* rho_host, void* phi_hos
   const size_t vbytes = (size_t)p->n[0] * p->n[1] * p->n[2] * (p->dtype == FSA_F32 ? 4 : 8);
   // rho is staged in the Y region (free until the second pass writes it);
   // phi is produced there too (Y is dead once the fourth pass has read it).
+  // DDI plans read rho again in their last pass: they stage it (and produce
+  // phi, element by element in place) behind X and Y.
   void* X = p->ws;
   void* Y = (char*)p->ws + p->x_bytes;
+  void* R = p->ddi >= 0 ? (void*)((char*)p->ws + align256(plan_workspace_bytes(p->n, p->dtype))) : Y;
   cudaStream_t s = (cudaStream_t)stream;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(Y, rho_host, vbytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(R, rho_host, vbytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = apply_passes(p, Y, Y, X, Y, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(phi_host, Y, vbytes, cudaMemcpyDeviceToHost, s);
+    e = apply_passes(p, R, R, X, Y, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(phi_host, R, vbytes, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_error(e, "fsa_apply_host");
   return FSA_OK;
 }

@@ -133,3 +133,26 @@ def test_plan_create_checks_dimension_against_kernel(capi):
     with pytest.raises(capi.FsaError) as ei:
         capi.fsa_plan_create(capi.FSA_KERNEL_COULOMB2D, 2, (8, 8), (8, 8), capi.FSA_F32, eps=5.0)
     assert ei.value.status == capi.FSA_ERR_EPS
+
+
+def test_ddi_plan_create_rejects_before_touching_the_device(capi):
+    """fsa_plan_create_ddi3d's argument checks (no device needed)."""
+    good = dict(eps=0.5)
+    cases = [
+        ((1, 1, 1), (8, 4, 8), (0, 0, 1), (0, 0, 1), capi.FSA_DDI_GRID),       # grid reading needs n_j >= 8
+        ((1, 1, 1), (8, 8, 8), (0, 0, float("nan")), (0, 0, 1), capi.FSA_DDI_KERNEL),
+        ((1, 1, 1), (8, 8, 8), (0, 0, 1), (0, float("inf"), 1), capi.FSA_DDI_GRID),
+        ((1, 1, 1), (8, 8, 8), (0, 0, 1), (0, 0, 1), 7),                         # unknown derivative
+        ((1, 1, 1), (8, 8, 10), (0, 0, 1), (0, 0, 1), capi.FSA_DDI_KERNEL),    # unsupported n
+    ]
+    for L, n, dn, dm, der in cases:
+        with pytest.raises(capi.FsaError) as ei:
+            capi.fsa_plan_create_ddi3d(L, n, capi.FSA_F32, dn, dm, der, **good)
+        assert ei.value.status == capi.FSA_ERR_INVALID_ARG, (n, dn, dm, der)
+    with pytest.raises(capi.FsaError) as ei:  # Coulomb's App. B check applies
+        capi.fsa_plan_create_ddi3d((8, 8, 8), (8, 8, 8), capi.FSA_F32, (0, 0, 1), (0, 0, 1), capi.FSA_DDI_GRID,
+                                   eps=5.0)
+    assert ei.value.status == capi.FSA_ERR_EPS
+    with pytest.raises(capi.FsaError) as ei:  # DDI plans need their dipoles
+        capi.fsa_plan_create(capi.FSA_KERNEL_DDI3D, 3, (1, 1, 1), (8, 8, 8), capi.FSA_F32)
+    assert ei.value.status == capi.FSA_ERR_INVALID_ARG

@@ -71,3 +71,30 @@ def test_noalloc_rejects_grids_beyond_the_static_scratch(capi):
     finally:
         torch.cuda.synchronize()
         capi.fsa_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("dt,derivative", [("f32", 0), ("f64", 0), ("f32", 1), ("f64", 1)])
+def test_noalloc_matches_apply_for_ddi_plans(capi, dt, derivative):
+    """3-D DDI plans (both readings) take the same static scratch: the grid
+    reading's unpadded passes live inside the same X and Y regions."""
+    import torch
+    tdt = torch.float32 if dt == "f32" else torch.float64
+    n = (32, 24, 48)
+    plan = capi.fsa_plan_create_ddi3d((4.0, 3.0, 5.0), n, capi.FSA_F32 if dt == "f32" else capi.FSA_F64,
+                                      (0.6, 0.0, 0.8), (0.0, 1.0, 0.0), derivative, eps=0.8)
+    stream = torch.cuda.current_stream()
+    capi.fsa_tensor_generate(plan, stream)
+    rng = np.random.default_rng(13)
+    try:
+        for call in range(2):
+            rho = torch.from_numpy(rng.standard_normal(n)).to(tdt).cuda()
+            ref = torch.empty_like(rho)
+            out = torch.full_like(rho, float("nan"))
+            capi.fsa_apply(plan, rho, ref, stream)
+            capi.fsa_apply_noalloc(plan, rho, out, stream)
+            torch.cuda.synchronize()
+            a, b = out.double().cpu().numpy(), ref.double().cpu().numpy()
+            assert np.isfinite(a).all()
+            assert rel_error(a, b) <= TOL[dt], (call, rel_error(a, b))
+    finally:
+        capi.fsa_plan_destroy(plan)
