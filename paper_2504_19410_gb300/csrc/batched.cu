@@ -64,7 +64,7 @@ cudaError_t launch_group(const std::vector<int>& idx, const fsa_plan* const* pla
   const fsa_plan* p0 = plans[idx[0]];
   std::vector<const void*> r, S;
   std::vector<void*> f, X, Y;
-  std::vector<const double*> par;
+  std::vector<const DdiPar*> par;
   for (int k : idx) {
     const fsa_plan* p = plans[k];
     r.push_back(rho[k]);

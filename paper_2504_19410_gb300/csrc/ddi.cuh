@@ -17,71 +17,68 @@ namespace fsa {
 // unpadded grid (cmul * D, no spectrum).
 enum : int { kMulSpectrum = 0, kMulDdiKernel = 1, kMulDdiGrid = 2 };
 
-// The multiplier is evaluated in FP32 for FP32 plans and in FP64 for FP64
-// plans (native or double-word).
-template <typename V> struct DdiReal { using T = double; };
-template <> struct DdiReal<float2> { using T = float; };
+// A line's coefficients (see DdiPar): (c0, c1, cN) from the plan's table,
+// c2 and cadd global.  An element costs two multiply-adds in the path's own
+// arithmetic (FP32; FP64; double-word for double-word plans) and the line
+// three loads, issued at the tile's start.
+template <typename V> struct DdiCoef { using T = typename RealOf<V>::T; };
+template <typename C> struct DdiTriple { C c0, c1, cN; };
 
-template <typename Q> struct DdiLine {
-  Q an, am, bn, bm;   // axes 0 and 2: n.mu0, m.mu0, n.nu, m.nu
-  Q n1, m1, w1, nu1;  // axis 1, along the line
-  Q cmul, cadd;
+// Parameter i of the block in the arithmetic C.
+template <typename C> __device__ __forceinline__ C ddi_par(const DdiPar* __restrict__ p, int i);
+template <> __device__ __forceinline__ float ddi_par<float>(const DdiPar* __restrict__ p, int i) { return p->f[i]; }
+template <> __device__ __forceinline__ double ddi_par<double>(const DdiPar* __restrict__ p, int i) { return p->d[i]; }
+template <> __device__ __forceinline__ dw ddi_par<dw>(const DdiPar* __restrict__ p, int i) { return dw(p->f[i], p->lo[i]); }
 
-  // k0: the axis-0 index (half spectrum; Nyquist at par[kDdiNyq0]); k2: the
-  // axis-2 index of a transform of length M2.
-  __device__ __forceinline__ void init(const double* __restrict__ par, int k0, int k2, int M2) {
-    const bool y0 = k0 == (int)par[kDdiNyq0];
-    const int h2 = M2 / 2;
-    const bool y2 = k2 == h2;
-    const double mu0 = y0 ? 0.0 : (double)k0 * par[kDdiW + 0];
-    const double mu2 = y2 ? 0.0 : (double)(k2 < h2 ? k2 : k2 - M2) * par[kDdiW + 2];
-    const double nu0 = y0 ? par[kDdiNu + 0] : 0.0;
-    const double nu2 = y2 ? par[kDdiNu + 2] : 0.0;
-    an = (Q)(par[kDdiN + 0] * mu0 + par[kDdiN + 2] * mu2);
-    am = (Q)(par[kDdiM + 0] * mu0 + par[kDdiM + 2] * mu2);
-    bn = (Q)(par[kDdiN + 0] * nu0 + par[kDdiN + 2] * nu2);
-    bm = (Q)(par[kDdiM + 0] * nu0 + par[kDdiM + 2] * nu2);
-    n1 = (Q)par[kDdiN + 1];
-    m1 = (Q)par[kDdiM + 1];
-    w1 = (Q)par[kDdiW + 1];
-    nu1 = (Q)par[kDdiNu + 1];
-    cmul = (Q)par[kDdiCmul];
-    cadd = (Q)par[kDdiCadd];
+template <typename V> struct DdiLine {
+  using C = typename DdiCoef<V>::T;
+  C c0, c1, c2, cN, cadd;
+
+  // k0: the axis-0 index (half spectrum); k2: the axis-2 index of a
+  // transform of length M2.
+  __device__ __forceinline__ void init(const DdiPar* __restrict__ par, int k0, int k2, int M2) {
+    const DdiTriple<C>* row = static_cast<const DdiTriple<C>*>(par->tab) + (long long)k0 * M2 + k2;
+    c0 = row->c0;
+    c1 = row->c1;
+    cN = row->cN;
+    c2 = ddi_par<C>(par, kDdiC2);
+    cadd = ddi_par<C>(par, kDdiCadd);
   }
 
-  // D at the axis-1 index k1 of a transform of length M1.
-  __device__ __forceinline__ Q D(int k1, int M1) const {
+  // The value that multiplies the element at the axis-1 index k1 of a
+  // transform of length M1: s * cmul D + cadd (kMulDdiKernel, s the stored
+  // spectrum value) or cmul D (kMulDdiGrid).
+  template <int MODE> __device__ __forceinline__ C value(C s, int k1, int M1) const {
     const int h1 = M1 / 2;
-    const bool y1 = k1 == h1;
-    const Q x = y1 ? Q(0) : (Q)(k1 < h1 ? k1 : k1 - M1) * w1;
-    const Q y = y1 ? nu1 : Q(0);
-    return -(an + n1 * x) * (am + m1 * x) - (bn + n1 * y) * (bm + m1 * y);
-  }
-
-  // The value that multiplies the element: s is the stored spectrum value
-  // (kMulDdiKernel) or unused (kMulDdiGrid).
-  template <int MODE, typename R> __device__ __forceinline__ R value(R s, int k1, int M1) const {
-    const Q d = D(k1, M1);
-    if constexpr (std::is_same<R, dw>::value) {
-      const double v = MODE == kMulDdiKernel ? cmul * dw_to_double(s) * d + cadd : cmul * d;
-      return dw_from_double(v);
-    } else {
-      return MODE == kMulDdiKernel ? (R)(cmul * (Q)s * d + cadd) : (R)(cmul * d);
-    }
+    const C q = C(k1 < h1 ? k1 : k1 - M1);
+    const C d = k1 == h1 ? cN : c0 + q * (c1 + c2 * q);
+    if constexpr (MODE == kMulDdiKernel) return s * d + cadd;
+    else return d;
   }
 };
 
+// beta of the grid reading's local term in the output array's precision
+template <typename T> __device__ __forceinline__ T ddi_beta(const DdiPar* __restrict__ p) { return ddi_par<T>(p, kDdiBeta); }
+
 // phi[0..1] = v + beta * rho[0..1] (the grid reading's -(m.n) rho term),
 // added in the precision of the output array.
+// The pair of rho values the epilogue adds, as loaded (FP64 arrays for both
+// FP64 arithmetics).
+template <typename V> struct PairOf { using T = V; };
+template <> struct PairOf<cdw> { using T = double2; };
+
 template <typename V>
-__device__ __forceinline__ void store_pair_axpy(typename Io<V>::T* p, V v, double beta, const typename Io<V>::T* r) {
-  using T = typename Io<V>::T;
+__device__ __forceinline__ typename PairOf<V>::T load_rho_pair(const typename Io<V>::T* r) {
+  return *reinterpret_cast<const typename PairOf<V>::T*>(r);
+}
+
+template <typename V>
+__device__ __forceinline__ void store_pair_axpy(typename Io<V>::T* p, V v, typename Io<V>::T beta,
+                                                typename PairOf<V>::T a) {
   if constexpr (std::is_same<V, cdw>::value) {
-    const double2 a = *reinterpret_cast<const double2*>(r);
     *reinterpret_cast<double2*>(p) = make_double2(dw_to_double(v.x) + beta * a.x, dw_to_double(v.y) + beta * a.y);
   } else {
-    const V a = *reinterpret_cast<const V*>(r);
-    *reinterpret_cast<V*>(p) = mk(v.x + (T)beta * a.x, v.y + (T)beta * a.y);
+    *reinterpret_cast<V*>(p) = mk(v.x + beta * a.x, v.y + beta * a.y);
   }
 }
 

@@ -6,8 +6,10 @@ namespace fsa {
 // of every supported transform length 2n (n = 2^a or 3 * 2^a, n <= 512).
 constexpr int kTwN = 3072;
 
+struct DdiPar;
+
 // One solve inside a launch: its pass input, pass output and spectrum.
-// `par` (3-D DDI plans only): the plan's block of kDdiParCount doubles below;
+// `par` (3-D DDI plans only): the plan's DDI parameters (DdiPar below);
 // `aux`: a second input of the pass (the DDI grid reading's final pass adds
 // beta * rho from it).
 struct Job {
@@ -15,10 +17,10 @@ struct Job {
   void* out;
   const void* S;
   const void* aux;
-  const double* par;
+  const DdiPar* par;
 };
 
-// The 3-D DDI multiplier (Sec. 5, Example 4) of one plan, as doubles:
+// The 3-D DDI multiplier (Sec. 5, Example 4) of one plan:
 //   D(q) = -(n.mu0)(m.mu0) - (n.nu)(m.nu),  mu_j = w_j q_j,
 // q_j the signed DFT frequency of axis j (transform length M_j: q_j in
 // [-M_j/2, M_j/2)), mu0 = mu with its Nyquist components (q_j = -M_j/2)
@@ -26,6 +28,13 @@ struct Job {
 // the real, Hermitian part of the multiplier -(k.n)(k.m), so the real
 // inverse transform is exact.  Applied value: cmul * S * D + cadd (kernel
 // reading, S the stored spectrum) or cmul * D (grid reading).
+// Along one middle-pass line (axis 1, fixed axis-0 and axis-2 frequencies)
+// cmul D is a quadratic in q1 off its Nyquist index,
+//   cmul D = c0 + q1 (c1 + c2 q1),   with a = n.mu0, b = m.mu0 and
+//   an = n.nu, bn = m.nu over axes 0 and 2:
+//   c0 = -cmul (a b + an bn),  c1 = -cmul (a m1 + b n1) w1,  c2 = -cmul n1 m1 w1^2,
+// and at q1 = -M1/2 the constant cN = -cmul (a b + (an + n1 nu1)(bn + m1 nu1)).
+// c2 is global (kDdiC2); (c0, c1, cN) per line are tabulated on the host.
 enum : int {
   kDdiN = 0,     // n[3]
   kDdiM = 3,     // m[3]
@@ -35,7 +44,23 @@ enum : int {
   kDdiCadd = 13,
   kDdiNyq0 = 14,  // axis-0 Nyquist index M_0 / 2 of the pass (the half spectrum's last plane)
   kDdiBeta = 15,  // grid reading: the C2R pass adds beta * rho, beta = -(m.n)
-  kDdiParCount = 16
+  kDdiC2 = 16,
+  kDdiParCount = 17
+};
+
+// The parameters in each arithmetic the kernels use, so that no kernel
+// converts from FP64 (conversions run on the FP64 pipe, a small fraction of
+// the FP32 rate on GB300): d for native FP64, f for FP32, (f, lo) the
+// double-word split d = f + lo (to 48 bits).
+// `tab`: the per-line coefficients (c0, c1, cN) of the middle pass's lines,
+// [k0][k2] for k0 <= nyq0 and k2 < M2, each a triple in the plan's
+// arithmetic (float; double; double-word as float pairs).
+struct DdiPar {
+  double d[kDdiParCount];
+  float f[kDdiParCount];
+  float lo[kDdiParCount];
+  int nyq0;  // = d[kDdiNyq0]
+  const void* tab;
 };
 constexpr int kMaxJobs = 64;
 // The jobs of one launch, passed by value as a kernel parameter (about 2.6 KB):

@@ -106,7 +106,7 @@ cudaError_t plan_apply_passes(const fsa_plan* p, const void* rho, void* phi, cud
 // par[k]: solve k's DDI parameter block (3-D DDI plans; may be null otherwise).
 cudaError_t run_group(const fsa_plan* shape, int count, const void* const* rho, void* const* phi,
                       void* const* X, void* const* Y, const void* const* S, cudaStream_t s,
-                      PassTrace* tr = nullptr, const double* const* par = nullptr);
+                      PassTrace* tr = nullptr, const DdiPar* const* par = nullptr);
 // The spectrum the apply kernels read (the double-word copy for f64_dw plans).
 const void* plan_apply_spectrum(const fsa_plan* p);
 // Converts an FP64 octant to double-word pairs (tensor_gen.cu).
@@ -152,6 +152,6 @@ struct fsa_plan {
   size_t x_bytes;
   // 3-D DDI (Sec. 5, Example 4): -1 = not a DDI plan, else the fsa_ddi_derivative
   int ddi;
-  double* ddi_par;  // device: kDdiParCount doubles (fsa_consts.h)
+  fsa::DdiPar* ddi_par;  // device: the DDI parameters (fsa_consts.h)
   double dipole_n[3], dipole_m[3];
 };

@@ -1,4 +1,4 @@
-// Double-word (FP64-accuracy on FP32 pipes) apply passes, lengths 8-48.
+// Double-word apply passes, lengths 8-24.
 // Compiled as its own translation unit so that the library's kernel
 // instances build in parallel; registers its launchers at library load.
 #include "passes_impl.cuh"
@@ -8,6 +8,4 @@ FSA_REGISTER(
     FSA_REG_V1(fsa::kArithDW, fsa::cdw, 12)
     FSA_REG_V1(fsa::kArithDW, fsa::cdw, 16)
     FSA_REG_V1(fsa::kArithDW, fsa::cdw, 24)
-    FSA_REG_V1(fsa::kArithDW, fsa::cdw, 32)
-    FSA_REG_V1(fsa::kArithDW, fsa::cdw, 48)
 )

@@ -1,10 +1,10 @@
-// Double-word apply passes, lengths 64-128.
+// Double-word apply passes, lengths 32-64.
 // Compiled as its own translation unit so that the library's kernel
 // instances build in parallel; registers its launchers at library load.
 #include "passes_impl.cuh"
 
 FSA_REGISTER(
+    FSA_REG_V1(fsa::kArithDW, fsa::cdw, 32)
+    FSA_REG_V1(fsa::kArithDW, fsa::cdw, 48)
     FSA_REG_V1(fsa::kArithDW, fsa::cdw, 64)
-    FSA_REG_V1(fsa::kArithDW, fsa::cdw, 96)
-    FSA_REG_V1(fsa::kArithDW, fsa::cdw, 128)
 )

@@ -1,9 +1,8 @@
-// Double-word apply passes, lengths 384-512.
+// Double-word apply passes, length 192.
 // Compiled as its own translation unit so that the library's kernel
 // instances build in parallel; registers its launchers at library load.
 #include "passes_impl.cuh"
 
 FSA_REGISTER(
-    FSA_REG_V1(fsa::kArithDW, fsa::cdw, 384)
-    FSA_REG_V1(fsa::kArithDW, fsa::cdw, 512)
+    FSA_REG_V1(fsa::kArithDW, fsa::cdw, 192)
 )

@@ -1,4 +1,4 @@
-// FP32 two-step register apply passes, lengths 8-128.
+// FP32 two-step register apply passes, lengths 8-48.
 // Compiled as its own translation unit so that the library's kernel
 // instances build in parallel; registers its launchers at library load.
 #include "passes_impl.cuh"
@@ -10,7 +10,4 @@ FSA_REGISTER(
     FSA_REG_V2(24)
     FSA_REG_V2(32)
     FSA_REG_V2(48)
-    FSA_REG_V2(64)
-    FSA_REG_V2(96)
-    FSA_REG_V2(128)
 )

@@ -1,10 +1,10 @@
-// FP32 two-step register apply passes, lengths 192-384.
+// FP32 two-step register apply passes, lengths 64-128.
 // Compiled as its own translation unit so that the library's kernel
 // instances build in parallel; registers its launchers at library load.
 #include "passes_impl.cuh"
 
 FSA_REGISTER(
-    FSA_REG_V2(192)
-    FSA_REG_V2(256)
-    FSA_REG_V2(384)
+    FSA_REG_V2(64)
+    FSA_REG_V2(96)
+    FSA_REG_V2(128)
 )

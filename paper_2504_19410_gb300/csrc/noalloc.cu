@@ -78,7 +78,7 @@ extern "C" fsa_status fsa_apply_noalloc(const fsa_plan* p, const void* rho, void
     void* X[1] = {base};
     void* Y[1] = {static_cast<char*>(base) + x_bytes};
     const void* S[1] = {plan_apply_spectrum(p)};
-    const double* par[1] = {p->ddi_par};
+    const DdiPar* par[1] = {p->ddi_par};
     e = run_group(p, 1, r, f, X, Y, S, (cudaStream_t)stream, nullptr, par);
   }
   if (prev != p->device) cudaSetDevice(prev);

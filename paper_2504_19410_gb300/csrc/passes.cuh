@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(W * T, minb_mid<V, W * T>()) k_col_mid(const J
   const int p2 = ok ? min(k2, M2 - k2) : 0;
   V* col = Y + (long long)k0 * n * M2 + k2;
   const typename Io<V>::S* srow = PAD ? S + (long long)k0 * (n + 1) * (n2 + 1) + p2 : S;
-  DdiLine<typename DdiReal<V>::T> ddi;
+  DdiLine<V> ddi;
   if constexpr (MODE != kMulSpectrum) ddi.init(jb.par, k0, ok ? k2 : 0, M2);
   SLine<V, W> sl{sm + l};
   auto first = [&](int p) -> V { return (p < n && ok) ? col[(long long)p * M2] : czero<V>(); };
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(W * T, MinB<V>::value) k_row_inv(const Jobs jo
 }
 
 // ---------------------------------------------------------------- pass 5 --
-// EPI: the output is phi + beta * rho with rho = jb.aux, beta = jb.par[kDdiBeta]
+// EPI: the output is phi + beta * rho with rho = jb.aux, beta = the DDI block's kDdiBeta
 // (the DDI grid reading's local term).
 template <typename V, class P, int W, int T, bool PAD = true, bool EPI = false>
 __global__ void __launch_bounds__(W * T, MinB<V>::value) k_c2r_ax0(const Jobs jobs, long long C) {
@@ -282,17 +282,38 @@ __global__ void __launch_bounds__(W * T, MinB<V>::value) k_c2r_ax0(const Jobs jo
     const V a = X[kk * C + c], b = X[kk * C + c + 1];
     return lo ? mk(a.x - b.y, a.y + b.x) : mk(a.x + b.y, b.x - a.y);
   };
-  auto last = [&](int p, V v) {
-    if (p < NV && ok) {
-      if constexpr (EPI) {
-        store_pair_axpy<V>(phi + (long long)p * C + c, v, jb.par[kDdiBeta],
-                           static_cast<const typename Io<V>::T*>(jb.aux) + (long long)p * C + c);
-      } else {
-        store_pair<V>(phi + (long long)p * C + c, v);
-      }
+  if constexpr (!EPI) {
+    auto last = [&](int p, V v) {
+      if (p < NV && ok) store_pair<V>(phi + (long long)p * C + c, v);
+    };
+    fft_line<P, false, T, V, false, PAD>(t, first, last, sl);
+  } else {
+    // The outputs stay in shared memory; the tile's rho values are all
+    // loaded before any of its stores (phi may be rho: each element is read
+    // and written by the same thread), then added.
+    auto to_sm = [&](int p, V v) { sl.put(p, v); };
+    fft_line<P, false, T, V, false, PAD>(t, first, to_sm, sl);
+    using A = typename PairOf<V>::T;
+    using IoT = typename Io<V>::T;
+    constexpr int NT = W * T, PER = (W * NV + NT - 1) / NT;
+    const IoT* rho = static_cast<const IoT*>(jb.aux);
+    const IoT beta = ddi_beta<IoT>(jb.par);
+    const long long cb = (tile % tpj) * (2 * W);
+    A a[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * NT, l2 = i % W, p = i / W;
+      const long long cc = cb + 2 * l2;
+      a[k] = (p < NV && cc < C) ? load_rho_pair<V>(rho + (long long)p * C + cc) : A{};
     }
-  };
-  fft_line<P, false, T, V, false, PAD>(t, first, last, sl);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * NT, l2 = i % W, p = i / W;
+      const long long cc = cb + 2 * l2;
+      if (p < NV && cc < C) store_pair_axpy<V>(phi + (long long)p * C + cc, sm[p * W + l2], beta, a[k]);
+    }
+    __syncthreads();
+  }
   }
 }
 

@@ -32,10 +32,12 @@ template <class P> struct Geo2 {
 };
 
 // ---------------------------------------------------------------- pass 1 --
-template <class P>
+// PAD = false: the unpadded transform over all M inputs (the DDI grid
+// reading), same K = M/2 + 1 outputs.
+template <class P, bool PAD = true>
 __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB) k2_r2c_ax0(const Jobs jobs, long long C) {
   using V = float2;
-  constexpr int M = P::M, n = M / 2, K = n + 1, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2;
+  constexpr int M = P::M, n = PAD ? M / 2 : M, K = M / 2 + 1, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int l = threadIdx.x % W, u = threadIdx.x / W;
@@ -46,7 +48,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB) k2_r2c_ax0(const J
     V* __restrict__ X = static_cast<V*>(jb.out);
     const long long c = (tile % tpj) * (2 * W) + 2 * l;
     const bool ok = c < C;
-    stepA_fwd<P, V, true>(
+    stepA_fwd<P, V, PAD>(
         u,
         [&](int t, int r) {
           const int p = t + R2 * r;
@@ -191,18 +193,23 @@ __device__ __forceinline__ void mid_multiply(float2* b, const MidSpec<P>& sp, in
                                              int M2, bool ok) {
   if constexpr (MODE == kMulSpectrum) {
     mid_apply<P>(b, sp, u);
-  } else {
-    static_assert(MODE == kMulDdiKernel, "the second-generation middle pass runs on the padded grid");
-    DdiLine<float> ddi;
+  } else if constexpr (MODE == kMulDdiKernel) {
+    DdiLine<float2> ddi;
     ddi.init(jb.par, k0, ok ? k2 : 0, M2);
     mid_apply<P>(b, sp, u, [&](int s, float v) { return ddi.template value<MODE>(v, u + P::R1 * s, P::M); });
+  } else {  // kMulDdiGrid: no spectrum
+    DdiLine<float2> ddi;
+    ddi.init(jb.par, k0, ok ? k2 : 0, M2);
+#pragma unroll
+    for (int s = 0; s < P::R2; ++s) b[s] = cscale(b[s], ddi.template value<MODE>(0.f, u + P::R1 * s, P::M));
   }
 }
 
 template <class P, int MODE = kMulSpectrum>
 __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2_col_mid(const Jobs jobs, int M2, int planes) {
   using V = float2;
-  constexpr int M = P::M, n = M / 2, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2;
+  constexpr bool PAD = MODE != kMulDdiGrid;
+  constexpr int M = P::M, n = PAD ? M / 2 : M, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int l = threadIdx.x % W, u = mid_u<P>(threadIdx.x);
@@ -217,8 +224,9 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2_col_mid(con
     const bool ok = k2 < M2;
     V* __restrict__ col = static_cast<V*>(jb.out) + (long long)k0 * n * M2 + k2;
     const float* __restrict__ srow =
-        static_cast<const float*>(jb.S) + (long long)k0 * (n + 1) * (n2 + 1) + (ok ? min(k2, M2 - k2) : 0);
-    stepA_fwd<P, V, true>(
+        PAD ? static_cast<const float*>(jb.S) + (long long)k0 * (n + 1) * (n2 + 1) + (ok ? min(k2, M2 - k2) : 0)
+            : nullptr;
+    stepA_fwd<P, V, PAD>(
         u,
         [&](int t, int r) {
           const int p = t + R2 * r;
@@ -227,7 +235,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2_col_mid(con
         [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
     MidSpec<P> sp;
-    mid_load<P>(sp, srow, u, ok, n2 + 1);
+    if constexpr (PAD) mid_load<P>(sp, srow, u, ok, n2 + 1);
     V b[R2];
 #pragma unroll
     for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
@@ -237,7 +245,7 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2_col_mid(con
     // the locations this thread read are the ones it writes: no barrier needed
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
-    stepA_inv<P, V, true>(
+    stepA_inv<P, V, PAD>(
         u, [&](int q, int t) { return sm[(q * R2 + t) * W + l]; },
         [&](int t, int r, V v) {
           const int p = t + R2 * r;
@@ -490,12 +498,13 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2_row_inv(const Jobs jobs, long 
 }
 
 // ---------------------------------------------------------------- pass 5 --
-// EPI: phi + beta * rho (rho = jb.aux, beta = jb.par[kDdiBeta]), the DDI grid
-// reading's local term.
-template <class P, bool EPI = false>
+// EPI: phi + beta * rho (rho = jb.aux, beta = the DDI block's kDdiBeta), the
+// DDI grid reading's local term.  The rho values this thread will add are
+// loaded at the start of the tile, before any store (phi may be rho).
+template <class P, bool EPI = false, bool PAD = true>
 __global__ void __launch_bounds__(Geo2<P>::NT) k2_c2r_ax0(const Jobs jobs, long long C) {
   using V = float2;
-  constexpr int M = P::M, n = M / 2, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2;
+  constexpr int M = P::M, n = M / 2, NV = PAD ? M / 2 : M, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int l = threadIdx.x % W, u = threadIdx.x / W;
@@ -506,6 +515,19 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2_c2r_ax0(const Jobs jobs, long 
     float* __restrict__ phi = static_cast<float*>(jb.out);
     const long long c = (tile % tpj) * (2 * W) + 2 * l;
     const bool ok = c < C;
+    constexpr int RH = PAD && R1 % 2 == 0 ? R1 / 2 : R1;  // outputs per sub-transform (step A keeps p < NV)
+    V rr[EPI ? P::PA : 1][EPI ? RH : 1];
+    if constexpr (EPI) {
+      const float* rho = static_cast<const float*>(jb.aux);
+#pragma unroll
+      for (int i = 0; i < P::PA; ++i) {
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+          const int t = u + P::T * i, p = t + R2 * r;
+          rr[i][r] = (ok && t < R2 && p < NV) ? *reinterpret_cast<const V*>(rho + (long long)p * C + c) : czero<V>();
+        }
+      }
+    }
     // Z[k] = A[k] + i B[k] with A, B Hermitian: rebuild k > n from M - k.
     V b[R2];
 #pragma unroll
@@ -523,14 +545,13 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2_c2r_ax0(const Jobs jobs, long 
     }
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
-    stepA_inv<P, V, true>(
+    stepA_inv<P, V, PAD>(
         u, [&](int q, int t) { return sm[(q * R2 + t) * W + l]; },
         [&](int t, int r, V v) {
           const int p = t + R2 * r;
-          if (p < n && ok) {
+          if (p < NV && ok) {
             if constexpr (EPI) {
-              store_pair_axpy<V>(phi + (long long)p * C + c, v, jb.par[kDdiBeta],
-                                 static_cast<const float*>(jb.aux) + (long long)p * C + c);
+              store_pair_axpy<V>(phi + (long long)p * C + c, v, ddi_beta<float>(jb.par), rr[(t - u) / P::T][r]);
             } else {
               *reinterpret_cast<V*>(phi + (long long)p * C + c) = v;
             }

@@ -67,10 +67,11 @@ __device__ __forceinline__ void bulk_prologue(const Jobs& jobs, long long tpj, l
 }
 
 // ------------------------------------------------------------ row forward --
-template <class P, int WR>
+// PAD = false: rows of M inputs (the DDI grid reading's unpadded transform).
+template <class P, int WR, bool PAD = true>
 __global__ void __launch_bounds__(BulkGeo<P, WR, P::M / 2>::NT) k4_row_fwd(const Jobs jobs, long long rows) {
   using V = float2;
-  constexpr int M = P::M, n = M / 2, R1 = P::R1, R2 = P::R2, T = P::T;
+  constexpr int M = P::M, n = PAD ? M / 2 : M, R1 = P::R1, R2 = P::R2, T = P::T;
   using G = BulkGeo<P, WR, n>;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* stg = reinterpret_cast<V*>(smraw);
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(BulkGeo<P, WR, P::M / 2>::NT) k4_row_fwd(const
     const bool ok = row < rows;
     V* __restrict__ y = static_cast<V*>(jb.out) + row * M;
     const V* src = stg + l * n;
-    stepA_fwd<P, V, true>(
+    stepA_fwd<P, V, PAD>(
         u,
         [&](int t, int r) {
           const int p = t + R2 * r;
@@ -115,10 +116,11 @@ __global__ void __launch_bounds__(BulkGeo<P, WR, P::M / 2>::NT) k4_row_fwd(const
 }
 
 // ------------------------------------------------------------ row inverse --
-template <class P, int WR>
+// PAD = false: all M outputs of a row kept.
+template <class P, int WR, bool PAD = true>
 __global__ void __launch_bounds__(BulkGeo<P, WR, P::M>::NT) k4_row_inv(const Jobs jobs, long long rows) {
   using V = float2;
-  constexpr int M = P::M, n = M / 2, R1 = P::R1, R2 = P::R2, T = P::T;
+  constexpr int M = P::M, n = PAD ? M / 2 : M, R1 = P::R1, R2 = P::R2, T = P::T;
   using G = BulkGeo<P, WR, M>;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* stg = reinterpret_cast<V*>(smraw);
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(BulkGeo<P, WR, P::M>::NT) k4_row_inv(const Job
       return;
     }
     if (threadIdx.x == 0 && tile + gridDim.x < total) issue_rows<WR, M>(jobs, tpj, rows, tile + gridDim.x, stg, bar);
-    stepA_inv<P, V, true>(
+    stepA_inv<P, V, PAD>(
         u, [&](int q, int t) { return line[q * (R2 + 1) + t]; },
         [&](int t, int r, V v) {
           const int p = t + R2 * r;

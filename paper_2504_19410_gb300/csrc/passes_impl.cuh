@@ -16,10 +16,8 @@ namespace detail {
 
 template <typename V, int M> struct Inst {
   using P = typename PlanFor<M>::type;
-  // the DDI grid reading's unpadded passes: FP32 and native FP64 only (an
-  // FP64 plan runs them natively whatever its arithmetic: their output, the
-  // real array d_n d_m rho, is what the double-word passes read too)
-  static constexpr bool kUnpadded = !std::is_same<V, cdw>::value;
+  // the DDI grid reading's unpadded passes (every arithmetic)
+  static constexpr bool kUnpadded = true;
   static constexpr int W = TileW<V>::W;
   static constexpr int T = threads_per_line<P, W>();
   static constexpr int NT = W * T;
@@ -191,6 +189,11 @@ template <int M> struct Inst2 {
     set((const void*)k2_col_mid<P, kMulDdiKernel>, G::SM_STRIDED);
     set((const void*)k2p_col_mid<P, kMulDdiKernel>, G::SM_STRIDED + Stage2<P>::BYTES);
     set((const void*)k2_c2r_ax0<P, true>, G::SM_STRIDED);
+    set((const void*)k2_r2c_ax0<P, false>, G::SM_STRIDED);
+    set((const void*)k4_row_fwd<P, WRF, false>, GFU::SMEM);
+    set((const void*)k2_col_mid<P, kMulDdiGrid>, G::SM_STRIDED);
+    set((const void*)k4_row_inv<P, WRI, false>, GI::SMEM);
+    set((const void*)k2_c2r_ax0<P, false, false>, G::SM_STRIDED);
     return e;
   }
   // bulk-copy row passes: rows per tile, fewer for the longest lines
@@ -198,6 +201,8 @@ template <int M> struct Inst2 {
   static constexpr int WRI = M >= 1024 ? 4 : 8;
   using GF = BulkGeo<P, WRF, M / 2>;
   using GI = BulkGeo<P, WRI, M>;
+  using GFU = BulkGeo<P, WRF, M>;  // unpadded forward rows: M inputs
+  static constexpr bool kUnpadded = true;
   // bulk copies need 16-byte aligned sources (row offsets are: n is even)
   static bool inputs_aligned(const Jobs& jobs) {
     for (int i = 0; i < jobs.count; ++i)
@@ -299,6 +304,46 @@ template <int M> struct Inst2 {
   static cudaError_t c2r_epi(const Jobs& jobs, long long C, cudaStream_t s) {
     const long long tiles = (C + 2 * W - 1) / (2 * W) * jobs.count;
     auto f = k2_c2r_ax0<P, true>;
+    f<<<persistent_grid((const void*)f, G::NT, G::SM_STRIDED, tiles), G::NT, G::SM_STRIDED, s>>>(jobs, C);
+    return cudaGetLastError();
+  }
+  // the DDI grid reading's unpadded passes of length M (this instance's M is
+  // the grid's n there).  Their buffers are the plan's workspace regions,
+  // 16-byte aligned by construction, as the bulk row copies need.
+  static cudaError_t r2c_per(const Jobs& jobs, long long C, cudaStream_t s) {
+    const long long tiles = (C + 2 * W - 1) / (2 * W) * jobs.count;
+    auto f = k2_r2c_ax0<P, false>;
+    f<<<persistent_grid((const void*)f, G::NT, G::SM_STRIDED, tiles), G::NT, G::SM_STRIDED, s>>>(jobs, C);
+    return cudaGetLastError();
+  }
+  static cudaError_t rowf_per(const Jobs& jobs, long long rows, cudaStream_t s) {
+    if (!inputs_aligned(jobs)) return cudaErrorInvalidValue;
+    Jobs jj = jobs;
+    jj.fault = device_fault_word();
+    const long long tiles = (rows + WRF - 1) / WRF * jobs.count;
+    auto f = k4_row_fwd<P, WRF, false>;
+    f<<<persistent_grid((const void*)f, GFU::NT, GFU::SMEM, tiles), GFU::NT, GFU::SMEM, s>>>(jj, rows);
+    return cudaGetLastError();
+  }
+  static cudaError_t colm_per(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
+    const long long tiles = (long long)((M2 + W - 1) / W) * planes * jobs.count;
+    auto f = k2_col_mid<P, kMulDdiGrid>;
+    f<<<persistent_grid((const void*)f, G::NT, G::SM_STRIDED, tiles), G::NT, G::SM_STRIDED, s>>>(jobs, M2,
+                                                                                                  planes);
+    return cudaGetLastError();
+  }
+  static cudaError_t rowi_per(const Jobs& jobs, long long rows, cudaStream_t s) {
+    if (!inputs_aligned(jobs)) return cudaErrorInvalidValue;
+    Jobs jj = jobs;
+    jj.fault = device_fault_word();
+    const long long tiles = (rows + WRI - 1) / WRI * jobs.count;
+    auto f = k4_row_inv<P, WRI, false>;
+    f<<<persistent_grid((const void*)f, GI::NT, GI::SMEM, tiles), GI::NT, GI::SMEM, s>>>(jj, rows);
+    return cudaGetLastError();
+  }
+  static cudaError_t c2r_per(const Jobs& jobs, long long C, cudaStream_t s) {
+    const long long tiles = (C + 2 * W - 1) / (2 * W) * jobs.count;
+    auto f = k2_c2r_ax0<P, false, false>;
     f<<<persistent_grid((const void*)f, G::NT, G::SM_STRIDED, tiles), G::NT, G::SM_STRIDED, s>>>(jobs, C);
     return cudaGetLastError();
   }

@@ -7,6 +7,7 @@
 #include <tuple>
 #include <type_traits>
 #include <mutex>
+#include <vector>
 #include <set>
 #include <string>
 
@@ -320,17 +321,18 @@ cudaError_t group_passes_2d(const int* n, int count, const void* const* rho, voi
 // -3 S D - (m.n)/(8 n0 n1 n2) (par).  Grid reading: -3 d_n d_m rho by five
 // passes of the unpadded transform (length n_j per axis; R2C along axis 0
 // into Y, row forward Y -> X, middle in place on X with -3 D / (n0 n1 n2),
-// row inverse X -> Y, C2R into the back half of Y), first generation with
-// native arithmetic; then the five Coulomb passes on it, the last adding
+// row inverse X -> Y, C2R into the back half of Y): the bulk-copy kernels for
+// FP32 plans, the first generation in the plan's arithmetic for FP64; then
+// the five Coulomb passes on it, the last adding
 // -(m.n) rho.  No pass split (the DDI middle pass takes absolute plane
 // indices).
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 template <typename V>
 cudaError_t group_passes_ddi(const fsa_plan* shape, int count, const void* const* rho, void* const* phi,
-                             void* const* X, void* const* Y, const void* const* S, const double* const* par,
+                             void* const* X, void* const* Y, const void* const* S, const DdiPar* const* par,
                              cudaStream_t s, PassTrace* tr) {
-  using Vu = typename std::conditional<std::is_same<V, cdw>::value, double2, V>::type;
+  using Vu = V;
   const int n0 = shape->n[0], n1 = shape->n[1], n2 = shape->n[2];
   const long long C = (long long)n1 * n2;
   const long long rows = (long long)(n0 + 1) * n1;
@@ -343,7 +345,9 @@ cudaError_t group_passes_ddi(const fsa_plan* shape, int count, const void* const
   const PassFns& f5 = pass_fns(arith_for<V>(kC2R, 2 * n0), 2 * n0);
   if (!f1.r2c || !f2.rowf || !f3.colm || !f3.colm_ddi || !f4.rowi || !f5.c2r || !f5.c2r_epi)
     return cudaErrorInvalidValue;
-  const int ua = first_gen_arith<Vu>();
+  // unpadded passes: the bulk-copy generation for FP32, first generation in
+  // the plan's arithmetic for FP64
+  const int ua = std::is_same<V, float2>::value ? (int)kArithF32G4 : first_gen_arith<Vu>();
   const PassFns& u0 = pass_fns(ua, n0);
   const PassFns& u1 = pass_fns(ua, n1);
   const PassFns& u2 = pass_fns(ua, n2);
@@ -401,7 +405,7 @@ cudaError_t group_passes_ddi(const fsa_plan* shape, int count, const void* const
 
 cudaError_t run_group(const fsa_plan* shape, int count, const void* const* rho, void* const* phi, void* const* X,
                       void* const* Y, const void* const* S, cudaStream_t s, PassTrace* tr,
-                      const double* const* par) {
+                      const DdiPar* const* par) {
   if (shape->ddi >= 0) {
     if (shape->dtype == FSA_F32) return group_passes_ddi<float2>(shape, count, rho, phi, X, Y, S, par, s, tr);
     if (shape->f64_dw) return group_passes_ddi<cdw>(shape, count, rho, phi, X, Y, S, par, s, tr);
@@ -542,7 +546,7 @@ cudaError_t apply_passes(const fsa_plan* p, const void* rho, void* phi, void* X,
   void* xs[1] = {X};
   void* ys[1] = {Y};
   const void* ss[1] = {plan_apply_spectrum(p)};
-  const double* pars[1] = {p->ddi_par};
+  const DdiPar* pars[1] = {p->ddi_par};
   return run_group(p, 1, rhos, phis, xs, ys, ss, s, nullptr, pars);
 }
 
@@ -566,7 +570,7 @@ cudaError_t plan_apply_passes_trace(const fsa_plan* p, const void* rho, void* ph
   void* xs[1] = {p->ws};
   void* ys[1] = {(char*)p->ws + p->x_bytes};
   const void* ss[1] = {plan_apply_spectrum(p)};
-  const double* pars[1] = {p->ddi_par};
+  const DdiPar* pars[1] = {p->ddi_par};
   return run_group(p, 1, rhos, phis, xs, ys, ss, s, tr, pars);
 }
 }  // namespace fsa
@@ -744,7 +748,8 @@ fsa_status plan_create_internal(fsa_plan** out, fsa_kernel kernel, const double*
 // The DDI parameter block (fsa_consts.h) of a plan: transform lengths
 // M_j = 2 n_j for the kernel reading (the doubled grid, period 4 L_j) and
 // n_j for the grid reading (period 2 L_j).
-void ddi_params(const fsa_plan* p, int derivative, double* par) {
+void ddi_params(const fsa_plan* p, int derivative, DdiPar* block) {
+  double* par = block->d;
   const double pi = 3.141592653589793238462643383279502884;
   const bool grid = derivative == FSA_DDI_GRID;
   double nm = 0;
@@ -761,6 +766,54 @@ void ddi_params(const fsa_plan* p, int derivative, double* par) {
   par[kDdiCadd] = grid ? 0.0 : -nm / (8.0 * vol);
   par[kDdiNyq0] = grid ? p->n[0] / 2 : p->n[0];
   par[kDdiBeta] = -nm;
+  par[kDdiC2] = -par[kDdiCmul] * par[kDdiN + 1] * par[kDdiM + 1] * par[kDdiW + 1] * par[kDdiW + 1];
+  for (int i = 0; i < kDdiParCount; ++i) {
+    block->f[i] = (float)par[i];
+    block->lo[i] = (float)(par[i] - (double)block->f[i]);
+  }
+  block->nyq0 = grid ? p->n[0] / 2 : p->n[0];
+}
+
+// The per-line coefficients (c0, c1, cN) of the DDI middle pass (fsa_consts.h)
+// for k0 in [0, nyq0], k2 in [0, M2), computed in FP64 and stored in the
+// plan's arithmetic: 3 floats (FP32), 3 doubles (native FP64) or 3
+// double-word float pairs.  Returns the bytes written to out (null: size only).
+size_t ddi_table(const fsa_plan* p, const DdiPar& b, void* out) {
+  const double* par = b.d;
+  const bool grid = p->ddi == FSA_DDI_GRID;
+  const int K0 = b.nyq0 + 1, M2 = grid ? p->n[2] : 2 * p->n[2];
+  const int kind = p->dtype == FSA_F32 ? 0 : (p->f64_dw ? 2 : 1);
+  const size_t each = kind == 0 ? 12 : 24;
+  const size_t bytes = (size_t)K0 * M2 * each;
+  if (!out) return bytes;
+  const double cm = par[kDdiCmul], n1 = par[kDdiN + 1], m1 = par[kDdiM + 1];
+  const double w1 = par[kDdiW + 1], nu1 = par[kDdiNu + 1];
+  for (int k0 = 0; k0 < K0; ++k0) {
+    const bool y0 = k0 == b.nyq0;
+    const double mu0 = y0 ? 0.0 : k0 * par[kDdiW + 0], nu0 = y0 ? par[kDdiNu + 0] : 0.0;
+    for (int k2 = 0; k2 < M2; ++k2) {
+      const bool y2 = k2 == M2 / 2;
+      const double mu2 = y2 ? 0.0 : (k2 < M2 / 2 ? k2 : k2 - M2) * par[kDdiW + 2];
+      const double nu2 = y2 ? par[kDdiNu + 2] : 0.0;
+      const double a = par[kDdiN] * mu0 + par[kDdiN + 2] * mu2, bb = par[kDdiM] * mu0 + par[kDdiM + 2] * mu2;
+      const double an = par[kDdiN] * nu0 + par[kDdiN + 2] * nu2, bn = par[kDdiM] * nu0 + par[kDdiM + 2] * nu2;
+      const double c[3] = {-cm * (a * bb + an * bn), -cm * (a * m1 + bb * n1) * w1,
+                           -cm * (a * bb + (an + n1 * nu1) * (bn + m1 * nu1))};
+      const size_t i = (size_t)k0 * M2 + k2;
+      for (int j = 0; j < 3; ++j) {
+        if (kind == 0) {
+          static_cast<float*>(out)[3 * i + j] = (float)c[j];
+        } else if (kind == 1) {
+          static_cast<double*>(out)[3 * i + j] = c[j];
+        } else {
+          const float hi = (float)c[j];
+          static_cast<float*>(out)[6 * i + 2 * j] = hi;
+          static_cast<float*>(out)[6 * i + 2 * j + 1] = (float)(c[j] - (double)hi);
+        }
+      }
+    }
+  }
+  return bytes;
 }
 
 // Autotuner: for an FP32 plan, time both kernel generations of each pass on the
@@ -963,10 +1016,19 @@ fsa_status fsa_plan_create_ddi3d(fsa_plan** out, const double* L, const int* n, 
     p->dipole_n[j] = dipole_n[j];
     p->dipole_m[j] = dipole_m[j];
   }
-  double par[kDdiParCount];
-  ddi_params(p, derivative, par);
-  e = cudaMalloc(&p->ddi_par, sizeof par);
-  if (e == cudaSuccess) e = cudaMemcpy(p->ddi_par, par, sizeof par, cudaMemcpyHostToDevice);
+  DdiPar par{};
+  ddi_params(p, derivative, &par);
+  // one allocation: the block, then the per-line coefficient table
+  const size_t off = align256(sizeof(DdiPar));
+  std::vector<unsigned char> tab(ddi_table(p, par, nullptr));
+  ddi_table(p, par, tab.data());
+  e = cudaMalloc(&p->ddi_par, off + tab.size());
+  if (e == cudaSuccess) {
+    par.tab = reinterpret_cast<const unsigned char*>(p->ddi_par) + off;
+    e = cudaMemcpy(p->ddi_par, &par, sizeof par, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy(reinterpret_cast<unsigned char*>(p->ddi_par) + off, tab.data(), tab.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     fsa_plan_destroy(p);
     cudaGetLastError();
