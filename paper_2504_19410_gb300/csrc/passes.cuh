@@ -159,12 +159,14 @@ __global__ void __launch_bounds__(W * T, minb_mid<V, W * T>()) k_col_mid(const J
   const int p2 = ok ? min(k2, M2 - k2) : 0;
   V* col = Y + (long long)k0 * n * M2 + k2;
   const typename Io<V>::S* srow = PAD ? S + (long long)k0 * (n + 1) * (n2 + 1) + p2 : S;
-  DdiLine<V> ddi;
-  if constexpr (MODE != kMulSpectrum) ddi.init(jb.par, k0, ok ? k2 : 0, M2);
   SLine<V, W> sl{sm + l};
   auto first = [&](int p) -> V { return (p < n && ok) ? col[(long long)p * M2] : czero<V>(); };
   auto to_sm = [&](int p, V v) { sl.put(p, v); };
   fft_line<P, true, T, V, PAD, false>(t, first, to_sm, sl);
+  // the line's DDI coefficients, loaded here rather than held across the
+  // forward transform (registers)
+  DdiLine<V> ddi;
+  if constexpr (MODE != kMulSpectrum) ddi.init(jb.par, k0, ok ? k2 : 0, M2);
   auto mul = [&](int p) -> V {
     R s = R(0);
     if constexpr (MODE != kMulDdiGrid) s = ok ? load_spec<V>(srow + (long long)min(p, M - p) * (n2 + 1)) : R(0);
