@@ -386,6 +386,7 @@ def run_ours(args):
     main = tiers.get("f32") or tiers["f64"]
 
     batched = None if args.no_batched else bench_batched(args, fsa, W, torch, stream)
+    many = None if args.no_many else bench_many(args, fsa, W, torch, stream)
     serving = None if args.no_serve else bench_serving(args, fsa, W, torch, rank)
 
     cpu = None
@@ -422,6 +423,8 @@ def run_ours(args):
         }
         if batched is not None:
             line["batched"] = batched
+        if many is not None:
+            line["many"] = many
         if serving is not None:
             line["serving"] = serving
         if "f64" in tiers and main is not tiers["f64"]:
@@ -481,6 +484,47 @@ def bench_batched(args, fsa, W, torch, stream):
         p.close()
     del rhos, phis
     torch.cuda.empty_cache()
+    return out
+
+
+# ------------------------------------------- many densities, one plan ----
+
+def bench_many(args, fsa, W, torch, stream):
+    """Many densities through one plan (fsa_apply_many: one launch sequence,
+    the middle pass reading each spectrum tile once for all densities) against
+    the same solves issued one fsa_apply at a time: 8 densities at 256^3 and
+    64 at 64^3, FP32, 8-Gaussian sums (seeds 2504 + k) on [-16,16]^3."""
+    out = {}
+    for n, K in ((256, 8), (64, 64)):
+        dens = [W.gaussian_sum(seed=2504 + k, n=n) for k in range(K)]
+        plan = fsa.Plan(dens[0].L, dens[0].n, "f32", eps=dens[0].eps)
+        plan.reserve(K)
+        rhos = [d.rho_torch(torch.float32) for d in dens]
+        phis = [torch.empty_like(r) for r in rhos]
+        for _ in range(2):
+            plan.apply_many(rhos, phis)
+        torch.cuda.synchronize()
+        reps = max(3, args.steps // 5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            plan.apply_many(rhos, phis)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tm = e0.elapsed_time(e1) / reps
+        e0.record(stream)
+        for _ in range(reps):
+            for r, f in zip(rhos, phis):
+                plan.apply(r, f)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts = e0.elapsed_time(e1) / reps
+        out[f"{n}^3 x{K}"] = {"value": K / (tm * 1e-3), "unit": UNIT, "ms_per_call": tm,
+                             "sequential_solves_per_s": K / (ts * 1e-3), "ms_sequential": ts,
+                             "gpu_launches_per_call": 5}
+        plan.close()
+        del rhos, phis
+        torch.cuda.empty_cache()
     return out
 
 
@@ -656,6 +700,7 @@ def main():
     ap.add_argument("--l2-chunk-mb", type=int, default=0,
                     help="plane-slab size of the middle passes in MB (0 = library default, -1 = one slab)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-many", action="store_true", help="skip the many-densities-one-plan leg")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-n", type=int, default=10000, help="requests in the serving run")

@@ -124,6 +124,8 @@ typedef struct {
   fsa_kernel kernel;        /* the plan's kernel                                      */
   int d;                    /* 3, or 2 for the plane kernels (then n[2] = 1, the      */
                             /* spectrum octant is (n0+1) x (n1+1), 3 launches/apply)  */
+  int many_capacity;        /* densities one fsa_apply_many call may take (1 + the    */
+                            /* workspaces added by fsa_plan_reserve)                  */
   int ddi_derivative;       /* FSA_KERNEL_DDI3D plans: their fsa_ddi_derivative; -1   */
   double dipole_n[3];       /* FSA_KERNEL_DDI3D plans: n and m; zero otherwise        */
   double dipole_m[3];
@@ -215,6 +217,26 @@ fsa_status fsa_apply_host(const fsa_plan* plan, const void* rho_host, void* phi_
  * a plan may appear at most once per call (FSA_ERR_INVALID_ARG otherwise). */
 fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void* const* rho,
                              void* const* phi, int count, fsa_stream_t stream);
+
+/* Many densities through one plan (the paper's Execution phase repeated with one
+ * cached tensor, e.g. the steps of a time-dependent solver).  fsa_plan_reserve
+ * allocates device workspace so that fsa_apply_many can take up to `count`
+ * densities at once (count - 1 more copies of the plan's X and Y regions;
+ * fsa_plan_info.workspace_bytes does not include them); it never shrinks and
+ * may be called again to grow.  fsa_apply_many(plan, rho, phi, count) computes
+ * phi[k] = T * rho[k] (the plan's kernel, DDI plans included) for k < count in
+ * one launch sequence: every pass is one persistent launch over the tiles of
+ * all densities, and the middle pass takes a column tile for every density in
+ * turn, reading the tile's spectrum values once (FP32, generations 3 and 4).
+ * Results equal fsa_apply's bit for bit.  rho[k], phi[k]: device arrays as for
+ * fsa_apply, 16-byte aligned; phi[k] == rho[k] is allowed, other overlaps are
+ * not.  Asynchronous on stream; calls on one plan must not overlap on the GPU.
+ * Errors: FSA_ERR_INVALID_ARG (count < 1 or above the capacity, NULL or
+ * misaligned pointers), FSA_ERR_NOT_GENERATED, FSA_ERR_OOM (reserve),
+ * FSA_ERR_CUDA. */
+fsa_status fsa_plan_reserve(fsa_plan* plan, int count);
+fsa_status fsa_apply_many(const fsa_plan* plan, const void* const* rho, void* const* phi, int count,
+                          fsa_stream_t stream);
 
 fsa_status fsa_plan_info_get(const fsa_plan* plan, fsa_plan_info* info);
 fsa_status fsa_plan_destroy(fsa_plan* plan); /* NULL is a no-op */

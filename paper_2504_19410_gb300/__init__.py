@@ -80,6 +80,23 @@ class Plan:
         capi.fsa_apply(self.handle, rho, phi, _cur_stream(stream))
         return phi
 
+    def reserve(self, count):
+        """Workspace for apply_many on up to count densities."""
+        capi.fsa_plan_reserve(self.handle, count)
+
+    def apply_many(self, rhos, phis=None, stream=None):
+        """phi_k = T * rho_k for a list of densities in one launch sequence
+        (reserve(len(rhos)) first); returns the list of outputs."""
+        import torch
+        for r in rhos:
+            self._check(r, "rho")
+        if phis is None:
+            phis = [torch.empty_like(r) for r in rhos]
+        for f in phis:
+            self._check(f, "phi")
+        capi.fsa_apply_many(self.handle, rhos, phis, _cur_stream(stream))
+        return phis
+
     def apply_host(self, rho_host, phi_host, stream=None):
         """Host-buffer variant (copies inside); caller synchronises the stream."""
         capi.fsa_apply_host(self.handle, rho_host, phi_host, _cur_stream(stream))

@@ -49,7 +49,8 @@ class PlanInfo(C.Structure):
                 ("generated", C.c_int), ("arithmetic", C.c_int), ("launches_per_apply", C.c_int),
                 ("workspace_bytes", C.c_size_t),
                 ("spectrum_bytes", C.c_size_t),
-                ("spectrum", C.c_void_p), ("kernel", C.c_int), ("d", C.c_int), ("ddi_derivative", C.c_int),
+                ("spectrum", C.c_void_p), ("kernel", C.c_int), ("d", C.c_int), ("many_capacity", C.c_int),
+                ("ddi_derivative", C.c_int),
                 ("dipole_n", C.c_double * 3), ("dipole_m", C.c_double * 3)]
 
 
@@ -86,6 +87,8 @@ _PROTOS = {
     "fsa_apply_host": (C.c_int, [_VP, _VP, _VP, _VP]),
     "fsa_apply_noalloc": (C.c_int, [_VP, _VP, _VP, _VP]),
     "fsa_apply_batched": (C.c_int, [C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), C.c_int, _VP]),
+    "fsa_plan_reserve": (C.c_int, [_VP, C.c_int]),
+    "fsa_apply_many": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP), C.c_int, _VP]),
     "fsa_plan_info_get": (C.c_int, [_VP, C.POINTER(PlanInfo)]),
     "fsa_plan_destroy": (C.c_int, [_VP]),
     "fsa_plan_spectrum_copy": (C.c_int, [_VP, _VP, C.c_size_t, _VP]),
@@ -197,6 +200,17 @@ def fsa_apply_batched(plans, rhos, phis, stream=None):
     R = (_VP * k)(*[_ptr(r) for r in rhos])
     F = (_VP * k)(*[_ptr(f) for f in phis])
     return check(lib().fsa_apply_batched(P, R, F, k, _stream(stream)))
+
+
+def fsa_plan_reserve(plan, count):
+    return check(lib().fsa_plan_reserve(plan, int(count)))
+
+
+def fsa_apply_many(plan, rhos, phis, stream=None):
+    k = len(rhos)
+    R = (_VP * k)(*[_ptr(r) for r in rhos])
+    F = (_VP * k)(*[_ptr(f) for f in phis])
+    return check(lib().fsa_apply_many(plan, R, F, k, _stream(stream)))
 
 
 def fsa_plan_info_get(plan):

@@ -54,6 +54,9 @@ struct PassFns {
   // grid reading's C2R with the local term (every generation), and the grid
   // reading's unpadded passes of length M (first generation only)
   cudaError_t (*colm_ddi)(const Jobs&, int M2, int planes, cudaStream_t) = nullptr;
+  // the middle pass for jobs that all share one spectrum (densities of one
+  // plan): one spectrum read per column tile where the generation has it
+  cudaError_t (*colm_shared)(const Jobs&, int M2, int planes, cudaStream_t) = nullptr;
   cudaError_t (*c2r_epi)(const Jobs&, long long C, cudaStream_t) = nullptr;
   cudaError_t (*r2c_per)(const Jobs&, long long C, cudaStream_t) = nullptr;
   cudaError_t (*rowf_per)(const Jobs&, long long rows, cudaStream_t) = nullptr;
@@ -150,6 +153,11 @@ struct fsa_plan {
   void* ws;  // X then Y (then, for DDI plans, the host path's staging of rho)
   size_t ws_bytes;
   size_t x_bytes;
+  // fsa_apply_many: workspaces for densities 1 .. many_cap - 1 (X then Y each,
+  // many_stride bytes apart); density 0 uses ws
+  void* ws_many;
+  int many_cap;
+  size_t many_stride;
   // 3-D DDI (Sec. 5, Example 4): -1 = not a DDI plan, else the fsa_ddi_derivative
   int ddi;
   fsa::DdiPar* ddi_par;  // device: the DDI parameters (fsa_consts.h)

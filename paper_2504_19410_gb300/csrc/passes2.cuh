@@ -275,7 +275,10 @@ template <class P> struct Stage2 {
   static constexpr int BYTES = SLOTS * P::T * Geo2<P>::W * 8;
 };
 
-template <class P, int MODE = kMulSpectrum>
+// SHARED: every job of the launch has the same spectrum (densities of one
+// plan).  A CTA then takes a column tile for all jobs in turn and loads the
+// tile's spectrum values once (one spectrum read per tile, not per job).
+template <class P, int MODE = kMulSpectrum, bool SHARED = false>
 __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2p_col_mid(const Jobs jobs, int M2, int planes) {
   using V = float2;
   constexpr int M = P::M, n = M / 2, W = Geo2<P>::W, R1 = P::R1, R2 = P::R2, T = P::T;
@@ -286,11 +289,20 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2p_col_mid(co
   const int l = threadIdx.x % W, u = mid_u<P>(threadIdx.x);
   const int tiles_per_plane = (M2 + W - 1) / W;
   const long long tpj = (long long)tiles_per_plane * planes;
-  const long long total = tpj * jobs.count;
+  const long long K = jobs.count;
+  const long long total = tpj * K;
   const int n2 = M2 / 2;
+  // work item -> (job, tile of the job); SHARED orders the jobs innermost
+  auto job_of = [&](long long tile) -> int { return (int)(SHARED ? tile % K : tile / tpj); };
+  auto lt_of = [&](long long tile) -> int { return (int)(SHARED ? tile / K : tile % tpj); };
+  auto next_of = [&](long long tile) -> long long {
+    if constexpr (SHARED) return tile % K + 1 < K ? tile + 1 : (tile / K + gridDim.x) * K;
+    else return tile + gridDim.x;
+  };
+  const long long first = SHARED ? (long long)blockIdx.x * K : (long long)blockIdx.x;
   auto issue = [&](long long tile) {
-    const Job& jb = jobs.j[tile / tpj];
-    const int lt = (int)(tile % tpj);
+    const Job& jb = jobs.j[job_of(tile)];
+    const int lt = lt_of(tile);
     const int k0 = lt / tiles_per_plane;
     const int k2 = (lt % tiles_per_plane) * W + l;
     const bool ok = k2 < M2;
@@ -307,10 +319,12 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2p_col_mid(co
     }
     cp_async_commit();
   };
-  if (blockIdx.x < total) issue(blockIdx.x);
-  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
-    const Job& jb = jobs.j[tile / tpj];
-    const int lt = (int)(tile % tpj);
+  if (first < total) issue(first);
+  MidSpec<P> sp;
+  for (long long tile = first; tile < total; tile = next_of(tile)) {
+    const int job = job_of(tile);
+    const Job& jb = jobs.j[job];
+    const int lt = lt_of(tile);
     const int k0 = lt / tiles_per_plane;
     const int k2 = (lt % tiles_per_plane) * W + l;
     const bool ok = k2 < M2;
@@ -326,10 +340,9 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2p_col_mid(co
         },
         [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     // this thread's staged elements are consumed: fetch the next tile's
-    if (tile + gridDim.x < total) issue(tile + gridDim.x);
+    if (next_of(tile) < total) issue(next_of(tile));
     __syncthreads();
-    MidSpec<P> sp;
-    mid_load<P>(sp, srow, u, ok, n2 + 1);
+    if (!SHARED || job == 0) mid_load<P>(sp, srow, u, ok, n2 + 1);
     V b[R2];
 #pragma unroll
     for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];

@@ -188,6 +188,7 @@ template <int M> struct Inst2 {
     set((const void*)k4_row_inv<P, WRI>, GI::SMEM);
     set((const void*)k2_col_mid<P, kMulDdiKernel>, G::SM_STRIDED);
     set((const void*)k2p_col_mid<P, kMulDdiKernel>, G::SM_STRIDED + Stage2<P>::BYTES);
+    set((const void*)k2p_col_mid<P, kMulSpectrum, true>, G::SM_STRIDED + Stage2<P>::BYTES);
     set((const void*)k2_c2r_ax0<P, true>, G::SM_STRIDED);
     set((const void*)k2_r2c_ax0<P, false>, G::SM_STRIDED);
     set((const void*)k4_row_fwd<P, WRF, false>, GFU::SMEM);
@@ -294,6 +295,14 @@ template <int M> struct Inst2 {
                                                                                                   planes);
     return cudaGetLastError();
   }
+  // densities of one plan: one spectrum read per column tile for all of them
+  static cudaError_t colm_p_shared(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
+    const long long tiles = (long long)((M2 + W - 1) / W) * planes;
+    constexpr int smem = G::SM_STRIDED + Stage2<P>::BYTES;
+    auto f = k2p_col_mid<P, kMulSpectrum, true>;
+    f<<<persistent_grid((const void*)f, G::NT, smem, tiles), G::NT, smem, s>>>(jobs, M2, planes);
+    return cudaGetLastError();
+  }
   static cudaError_t colm_p_ddi(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
     const long long tiles = (long long)((M2 + W - 1) / W) * planes * jobs.count;
     constexpr int smem = G::SM_STRIDED + Stage2<P>::BYTES;
@@ -374,6 +383,7 @@ template <class I> PassFns fns_of() {
   }
   f.colm_ddi = &I::colm_ddi;
   f.c2r_epi = &I::c2r_epi;
+  f.colm_shared = &I::colm;
   f.prepare = &I::prepare;
   f.geometry = &I::geometry;
   f.r2c = &I::r2c;
@@ -423,6 +433,7 @@ static cudaError_t init_tu_twiddles() {
     fsa::PassFns f3 = fsa::fns_of<fsa::detail::Inst2<M>>();                           \
     f3.colm = &fsa::detail::Inst2<M>::colm_p;                                         \
     f3.colm_ddi = &fsa::detail::Inst2<M>::colm_p_ddi;                                 \
+    f3.colm_shared = &fsa::detail::Inst2<M>::colm_p_shared;                           \
     f3.rowf = &fsa::detail::Inst2<M>::rowf_p;                                         \
     f3.rowi = &fsa::detail::Inst2<M>::rowi_p;                                         \
     fsa::register_pass_fns(fsa::kArithF32G3, M, f3);                                  \

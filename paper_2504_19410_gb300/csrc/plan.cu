@@ -249,10 +249,14 @@ cudaError_t group_passes(const int* n, int count, const void* const* rho, void* 
     const long long plane = (long long)m * n1 * (n2 + 2 * n2) * (long long)sizeof(V);
     const int K0 = n0 + 1;
     int pc = chunk_bytes > 0 ? (int)std::max<long long>(1, chunk_bytes / plane) : K0;
+    // jobs that share one spectrum (densities of one plan) take the middle
+    // pass that reads each spectrum tile once for all of them
+    bool shared = m > 1 && f3.colm_shared;
+    for (int i = 1; i < m && shared; ++i) shared = j3.j[i].S == j3.j[0].S;
     if (pc >= K0) {
       if (e == cudaSuccess) e = f2.rowf(j2, rows, s);
       if (e == cudaSuccess) e = trace_mark(tr, kRowFwd, s);
-      if (e == cudaSuccess) e = f3.colm(j3, 2 * n2, n0 + 1, s);
+      if (e == cudaSuccess) e = shared ? f3.colm_shared(j3, 2 * n2, n0 + 1, s) : f3.colm(j3, 2 * n2, n0 + 1, s);
       if (e == cudaSuccess) e = trace_mark(tr, kColMid, s);
       if (e == cudaSuccess) e = f4.rowi(j4, rows, s);
       if (e == cudaSuccess) e = trace_mark(tr, kRowInv, s);
@@ -709,6 +713,7 @@ fsa_status plan_create_core(fsa_plan** out, fsa_kernel kernel, const double* L, 
   p->kernel = kernel;
   p->d = d;
   p->ddi = -1;
+  p->many_cap = 1;
   p->chunk_bytes = 0;  // one slab: measured fastest at 256^3 (see fsa_plan_opts.l2_chunk_mb)
   p->dtype = dtype;
   p->device = dev;
@@ -1044,6 +1049,7 @@ fsa_status fsa_plan_destroy(fsa_plan* p) {
   DeviceGuard dg;
   dg.set(p->device);
   if (p->ddi_par) cudaFree(p->ddi_par);
+  if (p->ws_many) cudaFree(p->ws_many);
   cudaFree(p->spectrum);
   if (p->spectrum_dw) cudaFree(p->spectrum_dw);
   if (p->ws) cudaFree(p->ws);
@@ -1089,6 +1095,7 @@ fsa_status fsa_plan_info_get(const fsa_plan* p, fsa_plan_info* info) {
   info->spectrum = p->spectrum;
   info->kernel = p->kernel;
   info->d = p->d;
+  info->many_capacity = p->many_cap;
   info->ddi_derivative = p->ddi;
   for (int j = 0; j < 3; ++j) {
     info->dipole_n[j] = p->ddi >= 0 ? p->dipole_n[j] : 0.0;
@@ -1119,6 +1126,58 @@ fsa_status fsa_apply(const fsa_plan* p, const void* rho, void* phi, fsa_stream_t
   cudaError_t e = dg.set(p->device);
   if (e == cudaSuccess) e = plan_apply_passes(p, rho, phi, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_error(e, "fsa_apply: launch");
+  return FSA_OK;
+}
+
+fsa_status fsa_plan_reserve(fsa_plan* p, int count) {
+  if (!p || count < 1) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_reserve: NULL plan or count < 1");
+  if (count <= p->many_cap) return FSA_OK;
+  DeviceGuard dg;
+  cudaError_t e = dg.set(p->device);
+  if (e != cudaSuccess) return cuda_error(e, "fsa_plan_reserve: cudaSetDevice");
+  const size_t stride = align256(plan_workspace_bytes(p->n, p->dtype));
+  void* mem = nullptr;
+  e = cudaMalloc(&mem, stride * (size_t)(count - 1));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(FSA_ERR_OOM, "fsa_plan_reserve: cudaMalloc of " + std::to_string(stride * (count - 1)) + " bytes");
+  }
+  // the old workspaces may still be in use by queued work: free them in order
+  if (p->ws_many) {
+    cudaDeviceSynchronize();
+    cudaFree(p->ws_many);
+  }
+  p->ws_many = mem;
+  p->many_stride = stride;
+  p->many_cap = count;
+  return FSA_OK;
+}
+
+fsa_status fsa_apply_many(const fsa_plan* p, const void* const* rho, void* const* phi, int count,
+                          fsa_stream_t stream) {
+  if (!p || !rho || !phi) return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_many: NULL argument");
+  if (count < 1 || count > p->many_cap)
+    return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_many: count " + std::to_string(count) + " outside [1, " +
+                                              std::to_string(p->many_cap) + "] (fsa_plan_reserve grows it)");
+  if (!p->ws) return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_many: plan has no workspace");
+  if (!p->generated) return set_error(FSA_ERR_NOT_GENERATED, "fsa_apply_many: call fsa_tensor_generate first");
+  std::vector<const void*> r(count), S(count, plan_apply_spectrum(p));
+  std::vector<void*> f(count), X(count), Y(count);
+  std::vector<const DdiPar*> par(count, p->ddi_par);
+  for (int k = 0; k < count; ++k) {
+    if (!rho[k] || !phi[k] || !aligned16(rho[k]) || !aligned16(phi[k]))
+      return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_many: rho and phi must be non-NULL and 16-byte aligned");
+    r[k] = rho[k];
+    f[k] = phi[k];
+    X[k] = k == 0 ? p->ws : static_cast<char*>(p->ws_many) + (size_t)(k - 1) * p->many_stride;
+    Y[k] = static_cast<char*>(X[k]) + p->x_bytes;
+  }
+  DeviceGuard dg;
+  cudaError_t e = dg.set(p->device);
+  if (e == cudaSuccess)
+    e = run_group(p, count, r.data(), f.data(), X.data(), Y.data(), S.data(), (cudaStream_t)stream, nullptr,
+                  par.data());
+  if (e != cudaSuccess) return cuda_error(e, "fsa_apply_many: launch");
   return FSA_OK;
 }
 
