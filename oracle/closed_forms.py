@@ -277,3 +277,48 @@ def ddi3d_gaussian_grid(s2, L, n, nvec, mvec):
     x = grid_axes(L, n)
     X = np.stack(np.meshgrid(*x, indexing="ij"), axis=-1)
     return ddi3d_gaussian_points(s2, X, nvec, mvec)
+
+
+# ---- Yukawa (Example 4), rho = exp(-|x|^2/s2) ----------------------------------
+
+def yukawa3d_smoothed_r(r, w, lam):
+    """The 3-D Yukawa kernel exp(-lam r)/(4 pi r) convolved with the Gaussian
+    whose Fourier transform is exp(-k^2 w^2/4), in closed form (inverting
+    exp(-(k^2 + lam^2) w^2/4) / (k^2 + lam^2) times exp(lam^2 w^2/4) by the
+    radial sine transform):
+      (1/(8 pi r)) [exp(-lam r) erfc(b - r/w) - exp(lam r) erfc(b + r/w)],
+    b = lam w / 2, the second product taken as erfcx(b + r/w) exp(lam r - (b + r/w)^2);
+    at r = 0: (1/(4 pi)) (2 exp(-b^2)/(sqrt(pi) w) - lam erfc(b))."""
+    r = np.asarray(r, dtype=np.float64)
+    b = lam * w / 2.0
+    out = np.empty_like(r)
+    nz = r > 0
+    rr = r[nz]
+    x = b + rr / w
+    out[nz] = (np.exp(-lam * rr) * sp.erfc(b - rr / w) - sp.erfcx(x) * np.exp(lam * rr - x * x)) / (8.0 * math.pi * rr)
+    out[~nz] = (2.0 * math.exp(-b * b) / (math.sqrt(math.pi) * w) - lam * sp.erfc(b)) / (4.0 * math.pi)
+    return out
+
+
+def yukawa3d_gaussian_r(s2, lam, r):
+    """Exact 3-D Yukawa potential of exp(-|x|^2/s2): its transform is
+    q exp(-k^2 s2/4), q = (pi s2)^{3/2}, so Phi = q exp(lam^2 s2/4) times the
+    smoothed kernel with w = sqrt(s2)."""
+    return (math.pi * s2) ** 1.5 * math.exp(lam * lam * s2 / 4.0) * yukawa3d_smoothed_r(r, math.sqrt(s2), lam)
+
+
+def yukawa2d_gaussian_r(s2, lam, r):
+    """Exact 2-D Yukawa (K0(lam r)/(2 pi)) potential of exp(-|x|^2/s2) by the
+    Hankel transform: Phi(r) = (1/(2 pi)) int_0^inf pi s2 exp(-k^2 s2/4)
+    J0(k r) k / (k^2 + lam^2) dk, adaptive quadrature."""
+    import scipy.integrate as si
+    r = np.asarray(r, dtype=np.float64)
+    out = np.empty(r.shape)
+    uniq, inv = np.unique(r.ravel(), return_inverse=True)
+    res = np.empty(uniq.shape)
+    kmax = 2.0 * math.sqrt(40.0 / s2)
+    for i, rv in enumerate(uniq):
+        f = lambda k: math.pi * s2 * math.exp(-k * k * s2 / 4.0) * sp.j0(k * rv) * k / (k * k + lam * lam)
+        res[i], _ = si.quad(f, 0.0, kmax, epsabs=0.0, epsrel=2e-14, limit=800)
+    out[...] = (res[inv] / (2.0 * math.pi)).reshape(r.shape)
+    return out

@@ -193,6 +193,77 @@ def biharmonic2d_What(k, eps):
     return eps ** 4 / 16.0 * h
 
 
+# ---- Yukawa kernels (Example 4) -----------------------------------------------
+# The paper gives U = exp(-lam r)/(4 pi r) (d = 3) and K0(lam r)/(2 pi) (d = 2)
+# but neither lam nor the far-field approximation it used (U erf(r/eps) has a
+# cusp at r = 0 here; Sec. 4 then prescribes an unspecified window).  Reading
+# taken: the Gaussian-smoothed kernel, U^eps = U * g with g the Gaussian whose
+# Fourier transform is exp(-k^2 eps^2/4) -- for lam = 0 exactly Table 1's
+# Coulomb (d = 3) and, up to a constant, Poisson (d = 2) approximations.  From
+# U(r) = int_0^inf exp(-lam^2 t) (4 pi t)^{-d/2} exp(-r^2/(4t)) dt (the heat
+# kernel), U^eps is the same integral from t = eps^2/4 and U - U^eps the part
+# below it, whose transform is (1 - exp(-(k^2 + lam^2) eps^2/4)) / (k^2 + lam^2).
+# A kernel spec is the pair (name, lam).
+
+
+def _yukawa_heat(r, eps, lam, d, lower):
+    """int exp(-lam^2 t - r^2/(4t)) (4 pi t)^{-d/2} dt over t >= eps^2/4
+    (lower = False: U^eps) or 0 < t < eps^2/4 (lower = True: U - U^eps), by
+    adaptive quadrature in x = ln(4t/eps^2)."""
+    r = np.asarray(r, dtype=np.float64)
+    a = eps * eps / 4.0
+    out = np.empty(r.shape)
+    flat = r.ravel()
+    vals = np.empty(flat.shape)
+    uniq, inv = np.unique(flat, return_inverse=True)
+    res = np.empty(uniq.shape)
+    for i, rv in enumerate(uniq):
+        def f(x, rv=rv):
+            t = a * math.exp(x)
+            return math.exp(-lam * lam * t - rv * rv / (4.0 * t)) * (4.0 * math.pi * t) ** (-d / 2.0) * t
+        if lower:
+            if rv == 0.0:  # only reachable for d = 2 at r = 0, where U is infinite
+                res[i] = math.inf
+                continue
+            # the integrand is negligible below t = r^2 / (4 * 800)
+            lo = max(-80.0, math.log(rv * rv / (4.0 * a * 800.0))) if rv > 0 else -80.0
+            pts = [p for p in (math.log(rv * rv / (4.0 * a)) if rv > 0 else None,) if p is not None and lo < p < 0.0]
+            res[i], _ = si.quad(f, lo, 0.0, epsabs=0.0, epsrel=2e-14, limit=400, points=pts or None)
+        else:
+            hi = max(60.0, math.log(800.0 / max(lam * lam * a, 1e-300)))
+            hi = min(hi, 200.0)
+            pts = [p for p in (math.log(rv * rv / (4.0 * a)) if rv > 0 else None,) if p is not None and 0.0 < p < hi]
+            res[i], _ = si.quad(f, 0.0, hi, epsabs=0.0, epsrel=2e-14, limit=400, points=pts or None)
+    vals[:] = res[inv]
+    out[...] = vals.reshape(r.shape)
+    return out
+
+
+def yukawa3d_U(r, lam):
+    """3-D Yukawa kernel exp(-lam r)/(4 pi r) (Example 4)."""
+    r = np.asarray(r, dtype=np.float64)
+    return np.exp(-lam * r) / (4.0 * math.pi * r)
+
+
+def yukawa2d_U(r, lam):
+    """2-D Yukawa kernel K0(lam r)/(2 pi) (Example 4)."""
+    return sp.k0(lam * np.asarray(r, dtype=np.float64)) / (2.0 * math.pi)
+
+
+def yukawa3d_Ueps(r, eps, lam=1.0):
+    return _yukawa_heat(r, eps, lam, 3, lower=False)
+
+
+def yukawa2d_Ueps(r, eps, lam=1.0):
+    return _yukawa_heat(r, eps, lam, 2, lower=False)
+
+
+def yukawa_What(k, eps, lam=1.0):
+    """(1 - exp(-(k^2 + lam^2) eps^2/4)) / (k^2 + lam^2), d = 2 and 3."""
+    k2 = np.asarray(k, dtype=np.float64) ** 2 + lam * lam
+    return -np.expm1(-k2 * eps * eps / 4.0) / k2
+
+
 # kernel name -> names of its (U^eps, What) of Table 1, looked up at call time
 KERNELS = {
     "coulomb3d": ("coulomb3d_Ueps", "coulomb3d_What"),
@@ -200,12 +271,26 @@ KERNELS = {
     "poisson2d": ("poisson2d_Ueps", "poisson2d_What"),
     "coulomb2d": ("coulomb2d_Ueps", "coulomb2d_What"),
     "biharmonic2d": ("biharmonic2d_Ueps", "biharmonic2d_What"),
+    "yukawa3d": ("yukawa3d_Ueps", "yukawa_What"),
+    "yukawa2d": ("yukawa2d_Ueps", "yukawa_What"),
 }
-KERNEL_DIM = {"coulomb3d": 3, "biharmonic3d": 3, "poisson2d": 2, "coulomb2d": 2, "biharmonic2d": 2}
+KERNEL_DIM = {"coulomb3d": 3, "biharmonic3d": 3, "poisson2d": 2, "coulomb2d": 2, "biharmonic2d": 2,
+              "yukawa3d": 3, "yukawa2d": 2}
+
+
+def kernel_name(kernel):
+    """The name of a kernel spec (a name, or (name, parameter))."""
+    return kernel[0] if isinstance(kernel, tuple) else kernel
 
 
 def kernel_fns(kernel):
-    """(U^eps, What) of a kernel of Table 1."""
+    """(U^eps, What) of a kernel spec: a name of Table 1, or (name, lam) for
+    the Yukawa kernels."""
+    if isinstance(kernel, tuple):
+        name, lam = kernel
+        u, w = KERNELS[name]
+        fu, fw = globals()[u], globals()[w]
+        return (lambda r, eps: fu(r, eps, lam)), (lambda k, eps: fw(k, eps, lam))
     u, w = KERNELS[kernel]
     return globals()[u], globals()[w]
 
@@ -244,6 +329,16 @@ def appendix_b_bound(R0, eps, kernel="coulomb3d"):
     int_{R0}^inf |U - U^eps| r dr of App. B's general bound with d = 2 (the
     paper gives its thresholds R0/5.64 for Coulomb and R0/5.75 for Poisson)."""
     c = R0 / eps
+    if kernel_name(kernel) in ("yukawa3d", "yukawa2d"):
+        # swapping the order: int_{R0}^inf r^{d-1} int_0^{eps^2/4} ... dt dr
+        name, lam = kernel
+        d = KERNEL_DIM[name]
+        inner = (lambda t: math.exp(-lam * lam * t - R0 * R0 / (4 * t)) / (2 * math.pi)) if d == 2 else \
+            (lambda t: math.exp(-lam * lam * t) * (4 * math.pi * t) ** -1.5 *
+             (2 * t * R0 * math.exp(-R0 * R0 / (4 * t)) + math.sqrt(math.pi) * (4 * t) ** 1.5 / 4 *
+              sp.erfc(R0 / (2 * math.sqrt(t)))))
+        val, _ = si.quad(inner, 0.0, eps * eps / 4.0, epsabs=0.0, epsrel=1e-12, limit=200)
+        return val
     if KERNEL_DIM.get(kernel) == 2:
         # d = 2: int_{R0}^inf |U - U^eps| r dr
         diff = {"poisson2d": lambda r: sp.exp1((r / eps) ** 2) / (4.0 * math.pi),

@@ -305,3 +305,65 @@ def test_ddi_pins_catch_mutation(name, monkeypatch):
     attr, fn = MUTATIONS_DDI[name]
     monkeypatch.setattr(fsa, attr, fn)
     assert not pins_pass_ddi(), f"pins missed the planted mistake: {name}"
+
+
+# ---- Yukawa (Gaussian-smoothed split) ----------------------------------------
+
+def pins_pass_yukawa():
+    """Spectral accuracy to round-off at h = 1/4 (3-D and 2-D, lam = 1), and the
+    3-D U^eps against its erfc closed form."""
+    from workloads import grid_axes
+    r = np.array([0.5, 1.0, 2.0, 4.0])
+    if np.max(np.abs(fsa.yukawa3d_Ueps(r, 1.0, 1.0) / cf.yukawa3d_smoothed_r(r, 1.0, 1.0) - 1)) > 1e-13:
+        return False
+    L, s2, h = 8.0, 1.2, 0.25
+    n = int(round(2 * L / h))
+    d = W.paper_case1(L=L, sigma2=s2, h_over_gamma=h)
+    x = grid_axes(d.L, d.n)
+    R = np.sqrt(x[0][:, None, None] ** 2 + x[1][None, :, None] ** 2 + x[2][None, None, :] ** 2)
+    if fsa.rel_error(fsa.solve(d.L, d.n, 1.0, d.rho(), kernel=("yukawa3d", 1.0)), cf.yukawa3d_gaussian_r(s2, 1.0, R)) > 3e-15:
+        return False
+    x2 = grid_axes((L, L), (n, n))
+    R2 = np.sqrt(x2[0][:, None] ** 2 + x2[1][None, :] ** 2)
+    e2 = fsa.rel_error(fsa.solve((L, L), (n, n), 1.0, np.exp(-R2 ** 2 / s2), kernel=("yukawa2d", 1.0)),
+                       cf.yukawa2d_gaussian_r(s2, 1.0, R2))
+    return e2 < 3e-15
+
+
+def test_unmutated_yukawa_pins_pass():
+    assert pins_pass_yukawa()
+
+
+_yuk_orig = {k: getattr(fsa, k) for k in ("yukawa_What", "_yukawa_heat")}
+
+
+def _yuk_what_no_lambda(k, eps, lam=1.0):
+    return fsa_orig["coulomb3d_What"](k, eps)
+
+
+def _yuk_what_lambda_only_in_denominator(k, eps, lam=1.0):
+    k2 = np.asarray(k, dtype=np.float64) ** 2
+    return -np.expm1(-k2 * eps * eps / 4.0) / (k2 + lam * lam)
+
+
+def _yuk_heat_lower_eps2(r, eps, lam, d, lower):
+    return _yuk_orig["_yukawa_heat"](r, 2.0 * eps, lam, d, lower)
+
+
+def _yuk_heat_wrong_dimension(r, eps, lam, d, lower):
+    return _yuk_orig["_yukawa_heat"](r, eps, lam, 5 - d, lower) * (4 * math.pi * eps * eps / 4) ** ((5 - 2 * d) / 2)
+
+
+MUTATIONS_YUK = {
+    "Yukawa W without lam": ("yukawa_What", _yuk_what_no_lambda),
+    "Yukawa W with lam only in the denominator": ("yukawa_What", _yuk_what_lambda_only_in_denominator),
+    "Yukawa U^eps smoothed from t = eps^2 instead of eps^2/4": ("_yukawa_heat", _yuk_heat_lower_eps2),
+    "Yukawa heat kernel of the other dimension": ("_yukawa_heat", _yuk_heat_wrong_dimension),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS_YUK))
+def test_yukawa_pins_catch_mutation(name, monkeypatch):
+    attr, fn = MUTATIONS_YUK[name]
+    monkeypatch.setattr(fsa, attr, fn)
+    assert not pins_pass_yukawa(), f"pins missed the planted mistake: {name}"

@@ -9,6 +9,7 @@ import math
 
 import numpy as np
 import pytest
+import scipy.special as sp
 
 import workloads as W
 from oracle import closed_forms as cf
@@ -598,3 +599,116 @@ def test_ddi3d_readings_equal_brute_force():
     want_kernel = -nm * rho - 3 * fsa.apply_direct(fsa.spectral_dnm(T, [4 * l for l in L], nv, mv), rho)
     assert fsa.rel_error(fsa.ddi3d_solve(L, n, 0.6, rho, nv, mv, "grid"), want_grid) < 1e-13
     assert fsa.rel_error(fsa.ddi3d_solve(L, n, 0.6, rho, nv, mv, "kernel"), want_kernel) < 1e-13
+
+
+# ---- Yukawa (Example 4), Gaussian-smoothed far-field split --------------------
+
+YUK = 1.0  # lam of the tests (the paper does not print its lam)
+
+
+def test_yukawa3d_Ueps_definition_equals_closed_form():
+    """The oracle's U^eps (the heat-kernel integral from t = eps^2/4) against
+    the erfc closed form of the Gaussian-smoothed kernel, and its far field."""
+    r = np.array([0.0, 1e-3, 0.05, 0.3, 1.0, 2.5, 6.0, 15.0, 40.0])
+    for eps, lam in ((1.0, 1.0), (0.6, 0.3), (1.5, 3.0)):
+        a = fsa.yukawa3d_Ueps(r, eps, lam)
+        b = cf.yukawa3d_smoothed_r(r, eps, lam)
+        # the closed form is a difference of two positive terms: its rounding is
+        # about 1e-16 times their sum over their difference (the condition kappa)
+        bb = lam * eps / 2
+        rp = np.where(r > 0, r, 1.0)
+        t1 = np.where(r > 0, np.exp(-lam * rp) * sp.erfc(bb - rp / eps), 2 * math.exp(-bb * bb) / (math.sqrt(math.pi) * eps))
+        t2 = np.where(r > 0, np.exp(lam * rp) * sp.erfc(bb + rp / eps), lam * sp.erfc(bb))
+        kappa = (t1 + t2) / np.abs(t1 - t2)
+        assert np.all(np.abs(a - b) <= 1e-15 * (5 + kappa) * np.abs(b)), (np.abs(a - b) / np.abs(b), kappa)
+    far = np.array([12.0, 20.0])
+    np.testing.assert_allclose(fsa.yukawa3d_Ueps(far, 1.0, 1.0), fsa.yukawa3d_U(far, 1.0), rtol=1e-14)
+
+
+def test_yukawa_lambda_to_zero_gives_table1():
+    """lam -> 0: the 3-D kernel's U^eps and W become Table 1's Coulomb row;
+    the 2-D U - U^eps becomes the Poisson row's E1(r^2/eps^2)/(4 pi)."""
+    r = np.array([0.2, 1.0, 3.0])
+    np.testing.assert_allclose(fsa.yukawa3d_Ueps(r, 1.0, 1e-9), fsa.coulomb3d_Ueps(r, 1.0), rtol=1e-8)
+    k = np.array([0.0, 0.4, 2.0, 9.0])
+    np.testing.assert_allclose(fsa.yukawa_What(k, 1.0, 0.0)[1:], fsa.coulomb3d_What(k, 1.0)[1:], rtol=1e-15)
+    d2 = fsa._yukawa_heat(r, 1.0, 1e-9, 2, lower=True)
+    np.testing.assert_allclose(d2, sp.exp1(r * r) / (4 * math.pi), rtol=1e-8)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("k", [0.0, 0.3, 1.0, 4.0, 12.0])
+def test_yukawa_What_equals_radial_fourier_integral(d, k):
+    """W(k) against Eq. (Fourier-Symmetric) of U - U^eps by quadrature (d = 3:
+    the closed form of U - U^eps; d = 2: its heat-kernel integral)."""
+    import scipy.integrate as si
+    eps, lam = 1.0, YUK
+    if d == 3:
+        diff = lambda r: fsa.yukawa3d_U(np.array([r]), lam)[0] - cf.yukawa3d_smoothed_r(np.array([r]), eps, lam)[0]
+        f = lambda r: 4 * math.pi * diff(r) * (math.sin(k * r) / (k * r) if k * r > 1e-12 else 1.0) * r * r
+        val, _ = si.quad(f, 1e-12, 14 * eps, epsabs=0, epsrel=1e-13, limit=400)
+    else:
+        diff = lambda r: fsa._yukawa_heat(np.array([r]), eps, lam, 2, lower=True)[0]
+        f = lambda r: 2 * math.pi * diff(r) * sp.j0(k * r) * r
+        val, _ = si.quad(f, 1e-12, 14 * eps, epsabs=0, epsrel=1e-12, limit=400, points=[1e-6, 1e-3, 0.5])
+    assert fsa.yukawa_What(np.array([k]), eps, lam)[0] == pytest.approx(val, rel=1e-11, abs=1e-16)
+
+
+def test_yukawa2d_exact_potential_by_two_routes():
+    """The 2-D exact potential (Hankel quadrature) equals q exp(lam^2 s2/4)
+    times the smoothed kernel at w^2 = s2 (heat-kernel integral): two
+    different integrals of the same function."""
+    r = np.array([0.0, 0.4, 1.3, 4.0, 9.0])
+    s2, lam = 1.2, YUK
+    a = cf.yukawa2d_gaussian_r(s2, lam, r)
+    b = math.pi * s2 * math.exp(lam * lam * s2 / 4) * fsa.yukawa2d_Ueps(r, math.sqrt(s2), lam)
+    np.testing.assert_allclose(a, b, rtol=1e-12)
+
+
+@pytest.mark.parametrize("h", [1.0, 0.5, 0.25])
+def test_yukawa3d_spectral_accuracy(h):
+    """rho = exp(-|x|^2/1.2) on [-8,8]^3, eps = 1, lam = 1: the FSA solve
+    against the exact potential converges spectrally, to round-off at h = 1/4
+    (Table 5's Yukawa rows show the same behaviour for the paper's unstated
+    lam and window)."""
+    L, s2 = 8.0, 1.2
+    d = W.paper_case1(L=L, sigma2=s2, h_over_gamma=h)
+    x = W.grid_axes(d.L, d.n)
+    R = np.sqrt(x[0][:, None, None] ** 2 + x[1][None, :, None] ** 2 + x[2][None, None, :] ** 2)
+    err = fsa.rel_error(fsa.solve(d.L, d.n, 1.0, d.rho(), kernel=("yukawa3d", YUK)), cf.yukawa3d_gaussian_r(s2, YUK, R))
+    bound = {1.0: 2e-2, 0.5: 2e-7, 0.25: 3e-15}[h]
+    assert err < bound, err
+
+
+@pytest.mark.parametrize("h", [1.0, 0.5, 0.25])
+def test_yukawa2d_spectral_accuracy(h):
+    L, s2 = 8.0, 1.2
+    n = int(round(2 * L / h))
+    x = W.grid_axes((L, L), (n, n))
+    R = np.sqrt(x[0][:, None] ** 2 + x[1][None, :] ** 2)
+    rho = np.exp(-R ** 2 / s2)
+    err = fsa.rel_error(fsa.solve((L, L), (n, n), 1.0, rho, kernel=("yukawa2d", YUK)),
+                        cf.yukawa2d_gaussian_r(s2, YUK, R))
+    bound = {1.0: 2e-2, 0.5: 2e-7, 0.25: 3e-15}[h]
+    assert err < bound, err
+
+
+def test_yukawa_fft_route_equals_brute_force():
+    rng = np.random.default_rng(17)
+    for kernel, n, L in ((("yukawa3d", 0.7), (4, 6, 8), (3.0, 4.0, 2.5)), (("yukawa2d", 1.3), (6, 8), (3.0, 2.5))):
+        T = fsa.tensor_T(L, n, 0.6, kernel=kernel)
+        rho = rng.standard_normal(n)
+        assert fsa.rel_error(fsa.apply_fft(T, rho), fsa.apply_direct(T, rho)) < 1e-13
+
+
+def test_yukawa_appendix_b_bound_by_direct_integral():
+    """The swapped-order bound against the direct integral of the closed-form
+    3-D U - U^eps (and the 2-D heat-kernel difference)."""
+    import scipy.integrate as si
+    for R0, eps, lam in ((8.0, 1.0, 1.0), (6.0, 1.2, 0.5), (4.0, 1.0, 2.0)):
+        f3 = lambda r: (fsa.yukawa3d_U(np.array([r]), lam)[0] - cf.yukawa3d_smoothed_r(np.array([r]), eps, lam)[0]) * r * r
+        v3, _ = si.quad(f3, R0, R0 + 12 * eps, epsabs=0, epsrel=1e-10, limit=200)
+        assert fsa.appendix_b_bound(R0, eps, kernel=("yukawa3d", lam)) == pytest.approx(v3, rel=1e-8)
+        f2 = lambda r: fsa._yukawa_heat(np.array([r]), eps, lam, 2, lower=True)[0] * r
+        v2, _ = si.quad(f2, R0, R0 + 12 * eps, epsabs=0, epsrel=1e-10, limit=200)
+        assert fsa.appendix_b_bound(R0, eps, kernel=("yukawa2d", lam)) == pytest.approx(v2, rel=1e-8)
