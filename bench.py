@@ -37,8 +37,9 @@ METRIC = "solves/s and HBM-roofline % at 256^3 FP64/FP32; p50/p99 latency under 
 UNIT = "solves/s"
 PASSES = ["r2c_ax0", "row_fwd", "col_mid", "row_inv", "c2r_ax0"]
 KERNEL_TEXT = {"coulomb3d": "3-D Coulomb", "biharmonic3d": "3-D biharmonic", "poisson2d": "2-D Poisson",
-               "coulomb2d": "2-D Coulomb", "biharmonic2d": "2-D biharmonic", "ddi3d": "3-D DDI (Example 4)"}
-PLANE_KERNELS = ("poisson2d", "coulomb2d", "biharmonic2d")
+               "coulomb2d": "2-D Coulomb", "biharmonic2d": "2-D biharmonic", "ddi3d": "3-D DDI (Example 4)",
+               "yukawa3d": "3-D Yukawa (Example 4, lam = 1)", "yukawa2d": "2-D Yukawa (Example 4, lam = 1)"}
+PLANE_KERNELS = ("poisson2d", "coulomb2d", "biharmonic2d", "yukawa2d")
 
 
 def plane_pass_bytes(n, s):

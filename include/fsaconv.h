@@ -67,8 +67,15 @@ typedef enum {
   FSA_KERNEL_COULOMB2D = 3,    /* d = 2: U = 1/(2 pi r), U^eps = U erf(r/eps) (Table 1)       */
   FSA_KERNEL_BIHARMONIC2D = 4, /* d = 2: U = -r^2 (ln r - 1)/(8 pi),                          */
                                /* U^eps = -r^2 (ln r + E1(r^2/eps^2)/2 - 1)/(8 pi) (Table 1)  */
-  FSA_KERNEL_DDI3D = 5         /* d = 3: the dipole-dipole kernel of Sec. 5, Example 4,       */
+  FSA_KERNEL_DDI3D = 5,        /* d = 3: the dipole-dipole kernel of Sec. 5, Example 4,       */
                                /* through the Coulomb kernel; see fsa_plan_create_ddi3d      */
+  FSA_KERNEL_YUKAWA3D = 6,     /* d = 3: U = exp(-lam r)/(4 pi r) (Example 4)                 */
+  FSA_KERNEL_YUKAWA2D = 7      /* d = 2: U = K0(lam r)/(2 pi) (Example 4).  For both:         */
+                               /* U^eps = U convolved with the Gaussian of transform          */
+                               /* exp(-k^2 eps^2/4) (the heat-kernel integral of U from       */
+                               /* t = eps^2/4), W = (1 - exp(-(k^2+lam^2) eps^2/4))/(k^2+lam^2); */
+                               /* lam = fsa_plan_opts.kernel_param.  The paper states neither   */
+                               /* lam nor its window for these kernels (Sec. 4, Eq. GeneralApprox1) */
 } fsa_kernel;
 
 /* How a 3-D DDI plan discretises d_n d_m rho (Sec. 5, Example 4, which
@@ -97,6 +104,8 @@ typedef struct {
   double eps_tol; /* App. B bound R0^2 f(R0/eps) must not exceed this;         */
                   /* 0 selects 1e-8, a negative value disables the check       */
   int device;     /* CUDA device ordinal; -1 = the calling thread's current one */
+  double kernel_param; /* the Yukawa kernels' lam (> 0; 0 selects 1); ignored by  */
+                       /* the other kernels                                         */
   int l2_chunk_mb; /* pass split: run the three middle passes per slab of planes   */
                    /* whose intermediates take about this many MB, so they stay  */
                    /* in L2; 0 or negative = one slab (the default: slabs of     */
@@ -124,6 +133,7 @@ typedef struct {
   fsa_kernel kernel;        /* the plan's kernel                                      */
   int d;                    /* 3, or 2 for the plane kernels (then n[2] = 1, the      */
                             /* spectrum octant is (n0+1) x (n1+1), 3 launches/apply)  */
+  double kernel_param;      /* the Yukawa lam in use; 0 for the other kernels         */
   int many_capacity;        /* densities one fsa_apply_many call may take (1 + the    */
                             /* workspaces added by fsa_plan_reserve)                  */
   int ddi_derivative;       /* FSA_KERNEL_DDI3D plans: their fsa_ddi_derivative; -1   */
@@ -260,6 +270,16 @@ double fsa_appendix_b_bound(double R0, double eps);
  * erfc(c) (3/16 - c^4/4) + exp(-c^2) (c^3/2 + 3c/4) / (2 sqrt(pi)).
  * Host-only; NaN for non-positive arguments or an unknown kernel. */
 double fsa_appendix_b_bound_kernel(fsa_kernel kernel, double R0, double eps);
+
+/* The same for a kernel with a parameter (the Yukawa kernels: param = lam):
+ * int_{R0}^inf (U - U^eps) r^{d-1} dr with U - U^eps the heat-kernel integral
+ * below t = eps^2/4, by Gauss-Legendre quadrature after swapping the order:
+ * d = 3: int_0^{eps^2/4} exp(-lam^2 t) (4 pi t)^{-3/2} (2 t R0 exp(-R0^2/(4t))
+ *        + 2 sqrt(pi) t^{3/2} erfc(R0/(2 sqrt t))) dt;
+ * d = 2: (1/(2 pi)) int_0^{eps^2/4} exp(-lam^2 t - R0^2/(4t)) dt.
+ * Other kernels: as fsa_appendix_b_bound_kernel.  NaN for non-positive
+ * arguments. */
+double fsa_appendix_b_bound_kernel_param(fsa_kernel kernel, double param, double R0, double eps);
 
 const char* fsa_status_string(fsa_status s);
 const char* fsa_last_error(void); /* calling thread's last error message ("" if none) */

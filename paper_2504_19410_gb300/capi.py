@@ -22,11 +22,15 @@ FSA_KERNEL_POISSON2D = 2
 FSA_KERNEL_COULOMB2D = 3
 FSA_KERNEL_BIHARMONIC2D = 4
 FSA_KERNEL_DDI3D = 5
+FSA_KERNEL_YUKAWA3D = 6
+FSA_KERNEL_YUKAWA2D = 7
 KERNELS = {"coulomb3d": FSA_KERNEL_COULOMB3D, "biharmonic3d": FSA_KERNEL_BIHARMONIC3D,
            "poisson2d": FSA_KERNEL_POISSON2D, "coulomb2d": FSA_KERNEL_COULOMB2D,
-           "biharmonic2d": FSA_KERNEL_BIHARMONIC2D, "ddi3d": FSA_KERNEL_DDI3D}
+           "biharmonic2d": FSA_KERNEL_BIHARMONIC2D, "ddi3d": FSA_KERNEL_DDI3D,
+           "yukawa3d": FSA_KERNEL_YUKAWA3D, "yukawa2d": FSA_KERNEL_YUKAWA2D}
 KERNEL_DIM = {FSA_KERNEL_COULOMB3D: 3, FSA_KERNEL_BIHARMONIC3D: 3, FSA_KERNEL_POISSON2D: 2,
-              FSA_KERNEL_COULOMB2D: 2, FSA_KERNEL_BIHARMONIC2D: 2, FSA_KERNEL_DDI3D: 3}
+              FSA_KERNEL_COULOMB2D: 2, FSA_KERNEL_BIHARMONIC2D: 2, FSA_KERNEL_DDI3D: 3,
+              FSA_KERNEL_YUKAWA3D: 3, FSA_KERNEL_YUKAWA2D: 2}
 FSA_DDI_GRID, FSA_DDI_KERNEL = 0, 1
 DDI_DERIVATIVES = {"grid": FSA_DDI_GRID, "kernel": FSA_DDI_KERNEL}
 FSA_F32, FSA_F64 = 0, 1
@@ -40,7 +44,8 @@ class FsaError(RuntimeError):
 
 
 class PlanOpts(C.Structure):
-    _fields_ = [("eps", C.c_double), ("eps_tol", C.c_double), ("device", C.c_int), ("l2_chunk_mb", C.c_int)]
+    _fields_ = [("eps", C.c_double), ("eps_tol", C.c_double), ("device", C.c_int), ("kernel_param", C.c_double),
+                ("l2_chunk_mb", C.c_int)]
 
 
 class PlanInfo(C.Structure):
@@ -49,7 +54,8 @@ class PlanInfo(C.Structure):
                 ("generated", C.c_int), ("arithmetic", C.c_int), ("launches_per_apply", C.c_int),
                 ("workspace_bytes", C.c_size_t),
                 ("spectrum_bytes", C.c_size_t),
-                ("spectrum", C.c_void_p), ("kernel", C.c_int), ("d", C.c_int), ("many_capacity", C.c_int),
+                ("spectrum", C.c_void_p), ("kernel", C.c_int), ("d", C.c_int), ("kernel_param", C.c_double),
+                ("many_capacity", C.c_int),
                 ("ddi_derivative", C.c_int),
                 ("dipole_n", C.c_double * 3), ("dipole_m", C.c_double * 3)]
 
@@ -94,6 +100,7 @@ _PROTOS = {
     "fsa_plan_spectrum_copy": (C.c_int, [_VP, _VP, C.c_size_t, _VP]),
     "fsa_appendix_b_bound": (C.c_double, [C.c_double, C.c_double]),
     "fsa_appendix_b_bound_kernel": (C.c_double, [C.c_int, C.c_double, C.c_double]),
+    "fsa_appendix_b_bound_kernel_param": (C.c_double, [C.c_int, C.c_double, C.c_double, C.c_double]),
     "fsa_status_string": (C.c_char_p, [C.c_int]),
     "fsa_last_error": (C.c_char_p, []),
     "fsa_autotune_set": (C.c_int, [C.c_int]),
@@ -161,9 +168,10 @@ def _stream(s):
 
 # ---- the C-ABI calls, same names ------------------------------------------------
 
-def fsa_plan_create(kernel, d, L, n, dtype, eps=0.0, eps_tol=0.0, device=-1, l2_chunk_mb=0):
+def fsa_plan_create(kernel, d, L, n, dtype, eps=0.0, eps_tol=0.0, device=-1, l2_chunk_mb=0, kernel_param=0.0):
     h = _VP()
-    o = PlanOpts(float(eps), float(eps_tol), int(device), int(l2_chunk_mb))
+    o = PlanOpts(eps=float(eps), eps_tol=float(eps_tol), device=int(device), kernel_param=float(kernel_param),
+                 l2_chunk_mb=int(l2_chunk_mb))
     check(lib().fsa_plan_create(C.byref(h), int(kernel), int(d), (C.c_double * 3)(*[float(x) for x in L]),
                                 (C.c_int * 3)(*[int(x) for x in n]), int(dtype), C.byref(o)))
     return h.value
@@ -171,7 +179,7 @@ def fsa_plan_create(kernel, d, L, n, dtype, eps=0.0, eps_tol=0.0, device=-1, l2_
 
 def fsa_plan_create_ddi3d(L, n, dtype, dipole_n, dipole_m, derivative, eps=0.0, eps_tol=0.0, device=-1):
     h = _VP()
-    o = PlanOpts(float(eps), float(eps_tol), int(device), 0)
+    o = PlanOpts(eps=float(eps), eps_tol=float(eps_tol), device=int(device), kernel_param=0.0, l2_chunk_mb=0)
     d3 = lambda v: (C.c_double * 3)(*[float(x) for x in v])
     check(lib().fsa_plan_create_ddi3d(C.byref(h), d3(L), (C.c_int * 3)(*[int(x) for x in n]), int(dtype),
                                       d3(dipole_n), d3(dipole_m), int(derivative), C.byref(o)))
@@ -233,6 +241,10 @@ def fsa_appendix_b_bound(R0, eps):
 
 def fsa_appendix_b_bound_kernel(kernel, R0, eps):
     return lib().fsa_appendix_b_bound_kernel(int(kernel), float(R0), float(eps))
+
+
+def fsa_appendix_b_bound_kernel_param(kernel, param, R0, eps):
+    return lib().fsa_appendix_b_bound_kernel_param(int(kernel), float(param), float(R0), float(eps))
 
 
 def fsa_status_string(s):

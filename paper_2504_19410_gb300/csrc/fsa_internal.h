@@ -13,8 +13,12 @@ namespace fsa {
 
 // Dimension of a kernel of Table 1 (2 for the plane kernels, else 3).
 inline int kernel_dim(fsa_kernel k) {
-  return (k == FSA_KERNEL_POISSON2D || k == FSA_KERNEL_COULOMB2D || k == FSA_KERNEL_BIHARMONIC2D) ? 2 : 3;
+  return (k == FSA_KERNEL_POISSON2D || k == FSA_KERNEL_COULOMB2D || k == FSA_KERNEL_BIHARMONIC2D ||
+          k == FSA_KERNEL_YUKAWA2D)
+             ? 2
+             : 3;
 }
+inline bool kernel_has_param(fsa_kernel k) { return k == FSA_KERNEL_YUKAWA3D || k == FSA_KERNEL_YUKAWA2D; }
 
 enum PassKind { kR2C = 0, kRowFwd = 1, kColMid = 2, kRowInv = 3, kC2R = 4, kNumPass = 5 };
 
@@ -121,8 +125,9 @@ void batched_forget_plan(const fsa_plan* p);
 // Tensor generation (tensor_gen.cu), all FP64.
 cudaError_t tensorgen_prepare(int M);
 cudaError_t tensorgen_init_twiddles();
-cudaError_t tensorgen_run(fsa_kernel kernel, const int n[3], const double L[3], double eps, double* oct64, void* out,
-                          fsa_dtype dtype, cudaStream_t s);
+// param: the kernel's parameter (the Yukawa lam), ignored by the others
+cudaError_t tensorgen_run(fsa_kernel kernel, const int n[3], const double L[3], double eps, double param,
+                          double* oct64, void* out, fsa_dtype dtype, cudaStream_t s);
 
 // Twiddle table exp(-2 pi i k / 3072), k < 3072, computed on the host.
 void host_twiddles(double* re, double* im);
@@ -141,6 +146,7 @@ struct fsa_plan {
   double R0;
   double eps_bound;
   fsa_kernel kernel;
+  double param;  // the kernel's parameter (the Yukawa lam), 0 if it has none
   int d;  // 3, or 2 for the plane kernels (then n[2] = 1 and the octant is (n0+1)(n1+1))
   fsa_dtype dtype;
   int device;

@@ -13,6 +13,7 @@
 
 #include "dw.cuh"
 #include "fsa_internal.h"
+#include "quad.h"
 
 namespace fsa {
 
@@ -460,7 +461,37 @@ long double expint_e1(long double x) {
   return h * expl(-x);
 }
 
-double appendix_b_bound_kernel_impl(fsa_kernel kernel, double R0, double eps) {
+// The Yukawa kernels' far-field integral (fsa_appendix_b_bound_kernel_param):
+// int_0^{eps^2/4} f(t) dt with t = (eps^2/4) exp(-y), y in [0, Y], where the
+// factor exp(-R0^2/(4t)) = exp(-Q e^y), Q = R0^2/eps^2, has fallen by e^-60;
+// 32 panels of the 16-point Gauss-Legendre rule, in long double.
+double yukawa_bound(int d, double lam, double R0, double eps) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  const long double a = 0.25L * eps * eps, Q = (long double)R0 * R0 / ((long double)eps * eps), L2 = (long double)lam * lam;
+  long double gx[16], gw[16];
+  gauss_legendre(16, gx, gw);
+  const long double Y = logl(1.0L + 60.0L / Q), hw = Y / 64.0L;
+  long double sum = 0;
+  for (int k = 0; k < 32; ++k) {
+    const long double mid = (2 * k + 1) * hw;
+    for (int i = 0; i < 16; ++i) {
+      const long double y = mid + hw * gx[i], t = a * expl(-y);
+      long double f;
+      if (d == 2) {
+        f = expl(-L2 * t - (long double)R0 * R0 / (4 * t)) / (2 * pi);
+      } else {
+        f = expl(-L2 * t) * powl(4 * pi * t, -1.5L) *
+            (2 * t * R0 * expl(-(long double)R0 * R0 / (4 * t)) + 2 * sqrtl(pi) * powl(t, 1.5L) * erfcl(R0 / (2 * sqrtl(t))));
+      }
+      sum += gw[i] * hw * f * t;  // dt = t dy
+    }
+  }
+  return (double)sum;
+}
+
+double appendix_b_bound_kernel_impl(fsa_kernel kernel, double R0, double eps, double param = 0.0) {
+  if (kernel == FSA_KERNEL_YUKAWA3D || kernel == FSA_KERNEL_YUKAWA2D)
+    return param > 0 ? yukawa_bound(kernel_dim(kernel), param, R0, eps) : NAN;
   if (kernel == FSA_KERNEL_COULOMB3D) return appendix_b_bound_impl(R0, eps);
   const long double c = (long double)R0 / (long double)eps, e = eps;
   const long double pi = 3.141592653589793238462643383279502884L;
@@ -636,6 +667,11 @@ double fsa_appendix_b_bound_kernel(fsa_kernel kernel, double R0, double eps) {
   return appendix_b_bound_kernel_impl(kernel, R0, eps);
 }
 
+double fsa_appendix_b_bound_kernel_param(fsa_kernel kernel, double param, double R0, double eps) {
+  if (!(R0 > 0) || !(eps > 0)) return NAN;
+  return appendix_b_bound_kernel_impl(kernel, R0, eps, param);
+}
+
 }  // extern "C"
 
 namespace fsa {
@@ -656,8 +692,8 @@ cudaError_t tune_plan(fsa_plan* p);
 // Argument checks that need no device.  On success *eps_out / *bound_out
 // hold the eps in use and its App. B bound.
 fsa_status plan_validate(fsa_kernel kernel, const double* L, const int* n, fsa_dtype dtype, double eps_in,
-                         double eps_tol, double* eps_out, double* bound_out) {
-  if (kernel < FSA_KERNEL_COULOMB3D || kernel > FSA_KERNEL_BIHARMONIC2D)
+                         double eps_tol, double* eps_out, double* bound_out, double param = 0.0) {
+  if (kernel < FSA_KERNEL_COULOMB3D || kernel > FSA_KERNEL_YUKAWA2D || kernel == FSA_KERNEL_DDI3D)
     return set_error(FSA_ERR_UNSUPPORTED, "fsa_plan_create: unknown kernel");
   if (dtype != FSA_F32 && dtype != FSA_F64) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: bad dtype");
   const int d = kernel_dim(kernel);
@@ -672,7 +708,7 @@ fsa_status plan_validate(fsa_kernel kernel, const double* L, const int* n, fsa_d
   if (eps_in < 0 || !std::isfinite(eps_in)) return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: eps < 0");
   const double R0 = 2.0 * (d == 2 ? std::min(L[0], L[1]) : std::min(L[0], std::min(L[1], L[2])));
   const double eps = eps_in > 0 ? eps_in : std::min(1.0, R0 / 6.0);
-  const double bound = appendix_b_bound_kernel_impl(kernel, R0, eps);
+  const double bound = appendix_b_bound_kernel_impl(kernel, R0, eps, param);
   const double tol = eps_tol == 0 ? 1e-8 : eps_tol;
   if (tol > 0 && !(bound <= tol)) {
     char buf[256];
@@ -688,10 +724,11 @@ fsa_status plan_validate(fsa_kernel kernel, const double* L, const int* n, fsa_d
 // extra_ws: device bytes appended to the workspace; unpadded: prepare the
 // kernels of the transform lengths n_j too (the DDI grid reading).
 fsa_status plan_create_core(fsa_plan** out, fsa_kernel kernel, const double* L, const int* n, fsa_dtype dtype,
-                            double eps_in, double eps_tol, bool with_workspace, size_t extra_ws, bool unpadded) {
+                            double eps_in, double eps_tol, bool with_workspace, size_t extra_ws, bool unpadded,
+                            double param = 0.0) {
   *out = nullptr;
   double eps = 0, bound = 0;
-  fsa_status vs = plan_validate(kernel, L, n, dtype, eps_in, eps_tol, &eps, &bound);
+  fsa_status vs = plan_validate(kernel, L, n, dtype, eps_in, eps_tol, &eps, &bound, param);
   if (vs != FSA_OK) return vs;
   const int d = kernel_dim(kernel);
   const double R0 = 2.0 * (d == 2 ? std::min(L[0], L[1]) : std::min(L[0], std::min(L[1], L[2])));
@@ -711,6 +748,7 @@ fsa_status plan_create_core(fsa_plan** out, fsa_kernel kernel, const double* L, 
   p->R0 = R0;
   p->eps_bound = bound;
   p->kernel = kernel;
+  p->param = param;
   p->d = d;
   p->ddi = -1;
   p->many_cap = 1;
@@ -944,7 +982,7 @@ cudaError_t plan_generate_into(fsa_plan* p, void* scratch, cudaStream_t s) {
   double* oct = p->dtype == FSA_F64 ? (double*)p->spectrum : (double*)scratch;
   // a DDI plan's tensor is the Coulomb kernel's (Sec. 5, Example 4)
   const fsa_kernel k = p->kernel == FSA_KERNEL_DDI3D ? FSA_KERNEL_COULOMB3D : p->kernel;
-  cudaError_t e = tensorgen_run(k, p->n, p->L, p->eps, oct, p->spectrum, p->dtype, s);
+  cudaError_t e = tensorgen_run(k, p->n, p->L, p->eps, p->param, oct, p->spectrum, p->dtype, s);
   if (e == cudaSuccess && p->spectrum_dw)
     e = spectrum_to_dw((const double*)p->spectrum, p->spectrum_dw, p->spectrum_bytes / 8, s);
   if (e == cudaSuccess) p->generated = 1;
@@ -961,7 +999,7 @@ fsa_status fsa_plan_create(fsa_plan** out, fsa_kernel kernel, int d, const doubl
   *out = nullptr;
   if (kernel == FSA_KERNEL_DDI3D)
     return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: DDI plans need their dipoles: use fsa_plan_create_ddi3d");
-  if (kernel < FSA_KERNEL_COULOMB3D || kernel > FSA_KERNEL_BIHARMONIC2D)
+  if (kernel < FSA_KERNEL_COULOMB3D || kernel > FSA_KERNEL_YUKAWA2D)
     return set_error(FSA_ERR_UNSUPPORTED, "fsa_plan_create: unknown kernel");
   if (d != kernel_dim(kernel))
     return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: d = " + std::to_string(d) + " does not match the kernel (d = " +
@@ -975,13 +1013,17 @@ fsa_status fsa_plan_create(fsa_plan** out, fsa_kernel kernel, int d, const doubl
   fsa_plan_opts o{};
   o.device = -1;
   if (opts) o = *opts;
+  if (!(o.kernel_param >= 0) || !std::isfinite(o.kernel_param))
+    return set_error(FSA_ERR_INVALID_ARG, "fsa_plan_create: kernel_param must be finite and >= 0");
+  // the Yukawa lam (0 selects 1); no parameter for the other kernels
+  const double param = kernel_has_param(kernel) ? (o.kernel_param > 0 ? o.kernel_param : 1.0) : 0.0;
   double eps = 0, bound = 0;
-  fsa_status vs = plan_validate(kernel, L, n, dtype, o.eps, o.eps_tol, &eps, &bound);
+  fsa_status vs = plan_validate(kernel, L, n, dtype, o.eps, o.eps_tol, &eps, &bound, param);
   if (vs != FSA_OK) return vs;  // no device touched
   DeviceGuard dg;
   cudaError_t e = dg.set(o.device);
   if (e != cudaSuccess) return cuda_error(e, "fsa_plan_create: cudaSetDevice");
-  fsa_status st = plan_create_internal(out, kernel, L, n, dtype, o.eps, o.eps_tol, true);
+  fsa_status st = plan_create_core(out, kernel, L, n, dtype, o.eps, o.eps_tol, true, 0, false, param);
   if (st == FSA_OK && o.l2_chunk_mb != 0) (*out)->chunk_bytes = o.l2_chunk_mb > 0 ? (long long)o.l2_chunk_mb << 20 : 0;
   return st;
 }
@@ -1095,6 +1137,7 @@ fsa_status fsa_plan_info_get(const fsa_plan* p, fsa_plan_info* info) {
   info->spectrum = p->spectrum;
   info->kernel = p->kernel;
   info->d = p->d;
+  info->kernel_param = p->param;
   info->many_capacity = p->many_cap;
   info->ddi_derivative = p->ddi;
   for (int j = 0; j < 3; ++j) {

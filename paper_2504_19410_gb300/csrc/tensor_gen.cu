@@ -29,14 +29,28 @@
 //     Lentz) for u >= 1.  W: Poisson (1 - exp(-k^2 eps^2/4))/k^2, Coulomb
 //     erf(k eps/2)/k (limit eps/sqrt(pi)), biharmonic (eps^4/16) h(x),
 //     h(x) = (exp(-x)(1 + x + x^2) - 1)/x^2 from its Taylor series below x = 1.
+//   * Yukawa (Example 4; lam = the plan's parameter): U^eps is U convolved with
+//     the Gaussian of transform exp(-k^2 eps^2/4), i.e. the heat-kernel
+//     integral int_{eps^2/4}^inf exp(-lam^2 t - r^2/(4t)) (4 pi t)^{-d/2} dt,
+//     and W = (1 - exp(-(k^2 + lam^2) eps^2/4)) / (k^2 + lam^2).  d = 3, r >= eps/2:
+//     the closed form (1/(8 pi r)) [exp(-lam r) erfc(b - r/eps)
+//     - erfcx(b + r/eps) exp(lam r - (b + r/eps)^2)], b = lam eps / 2; otherwise
+//     (d = 2 everywhere, d = 3 near r = 0 where the closed form cancels) the
+//     integral in x = ln(4t/eps^2) by composite 16-point Gauss-Legendre
+//     quadrature on panels of width 1/2 up to where exp(-lam^2 t) < e^-60.
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "fsa_internal.h"
 #include "passes.cuh"
+#include "quad.h"
 
 namespace fsa {
+
+// 16-point Gauss-Legendre rule on [-1, 1] (quad.h), set per device
+__constant__ double c_gl_x[16];
+__constant__ double c_gl_w[16];
 
 // Taylor coefficients of (exp(-x)(1 + x + a x^2) - 1)/x^2 (a = 2: 3-D
 // biharmonic g; a = 1: 2-D biharmonic h): the coefficient of x^m is c_{m+2},
@@ -111,8 +125,44 @@ __device__ __forceinline__ double series30(const BihSeries& c, double x) {
   return g;
 }
 
+// The Yukawa heat-kernel integral int_{eps^2/4}^inf exp(-lam^2 t - r^2/(4t))
+// (4 pi t)^{-d/2} dt in x = ln(4t/eps^2) (see the file comment).
+__device__ double yukawa_heat(double r, double eps, double lam, int d) {
+  const double pi = 3.14159265358979323846;
+  const double a = 0.25 * eps * eps, la = lam * lam * a, q = (r / eps) * (r / eps);
+  // exp(-la e^x) < e^-60 beyond X; the r term only shrinks the integrand
+  const double X = fmax(log(60.0 / la), 0.5);
+  const int panels = (int)ceil(X / 0.5);
+  const double c = d == 3 ? 1.0 / (8.0 * pi * sqrt(pi) * sqrt(a)) : 1.0 / (4.0 * pi);
+  double sum = 0.0;
+  for (int k = 0; k < panels; ++k) {
+    const double mid = 0.5 * k + 0.25;
+    double ps = 0.0;
+#pragma unroll 4
+    for (int i = 0; i < 16; ++i) {
+      const double x = mid + 0.25 * c_gl_x[i];
+      const double ex = exp(x);
+      const double v = exp(-la * ex - q / ex);
+      ps += c_gl_w[i] * (d == 3 ? v * exp(-0.5 * x) : v);
+    }
+    sum += 0.25 * ps;
+  }
+  return c * sum;
+}
+
+__device__ double yukawa3d_U(double r, double eps, double lam) {
+  if (r < 0.5 * eps) return yukawa_heat(r, eps, lam, 3);
+  const double pi = 3.14159265358979323846;
+  const double b = 0.5 * lam * eps, x = b + r / eps;
+  return (exp(-lam * r) * erfc(b - r / eps) - erfcx(x) * exp(lam * r - x * x)) / (8.0 * pi * r);
+}
+
 // W(k) of Table 1 at k^2 (see the file comment)
-__device__ __forceinline__ double singular_W(int kernel, double k2, double e2) {
+__device__ __forceinline__ double singular_W(int kernel, double k2, double e2, double lam) {
+  if (kernel == FSA_KERNEL_YUKAWA3D || kernel == FSA_KERNEL_YUKAWA2D) {
+    const double s = k2 + lam * lam;
+    return -expm1(-0.25 * s * e2) / s;
+  }
   if (kernel == FSA_KERNEL_BIHARMONIC3D || kernel == FSA_KERNEL_BIHARMONIC2D) {
     const bool d3 = kernel == FSA_KERNEL_BIHARMONIC3D;
     const double a = d3 ? 2.0 : 1.0;
@@ -128,9 +178,11 @@ __device__ __forceinline__ double singular_W(int kernel, double k2, double e2) {
 }
 
 // U^eps of Table 1 at r
-__device__ __forceinline__ double smooth_U(int kernel, double r, double eps) {
+__device__ __forceinline__ double smooth_U(int kernel, double r, double eps, double lam) {
   const double pi = 3.14159265358979323846;
   switch (kernel) {
+    case FSA_KERNEL_YUKAWA3D: return yukawa3d_U(r, eps, lam);
+    case FSA_KERNEL_YUKAWA2D: return yukawa_heat(r, eps, lam, 2);
     case FSA_KERNEL_BIHARMONIC3D: return r * erf(r / eps) / (8.0 * pi);
     case FSA_KERNEL_POISSON2D: return -log_half_e1(r, eps) / (2.0 * pi);
     case FSA_KERNEL_COULOMB2D:
@@ -142,7 +194,7 @@ __device__ __forceinline__ double smooth_U(int kernel, double r, double eps) {
 }
 
 __global__ void k_t1_octant(double* __restrict__ O, int kernel, int n0, int n1, int n2, double h0, double h1,
-                            double h2, double eps) {
+                            double h2, double eps, double lam) {
   const long long total = (long long)(n0 + 1) * (n1 + 1) * (n2 + 1);
   const double hv = h0 * h1 * h2;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -153,14 +205,14 @@ __global__ void k_t1_octant(double* __restrict__ O, int kernel, int n0, int n1, 
     const int p0 = (int)(r01 / (n1 + 1));
     const double x = p0 * h0, y = p1 * h1, z = p2 * h2;
     const double r = sqrt(x * x + y * y + z * z);
-    O[i] = hv * smooth_U(kernel, r, eps);
+    O[i] = hv * smooth_U(kernel, r, eps, lam);
   }
 }
 
 template <typename R>
 __global__ void k_spectrum_finalize(const double* S1, R* S,  // may alias (FP64 plans)
                                     int kernel, int n0, int n1, int n2,
-                                    double c0, double c1, double c2, double eps, double inv_norm) {
+                                    double c0, double c1, double c2, double eps, double lam, double inv_norm) {
   const long long total = (long long)(n0 + 1) * (n1 + 1) * (n2 + 1);
   const double e2 = eps * eps;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -171,7 +223,7 @@ __global__ void k_spectrum_finalize(const double* S1, R* S,  // may alias (FP64 
     const int p0 = (int)(r01 / (n1 + 1));
     const double m0 = c0 * p0, m1 = c1 * p1, m2 = c2 * p2;  // mu_j = pi p_j / (2 L_j)
     const double k2 = m0 * m0 + m1 * m1 + m2 * m2;
-    const double w = singular_W(kernel, k2, e2);
+    const double w = singular_W(kernel, k2, e2, lam);
     S[i] = (R)((S1[i] + w) * inv_norm);
   }
 }
@@ -258,11 +310,15 @@ cudaError_t tensorgen_init_twiddles() {
   }
   cudaError_t e = cudaMemcpyToSymbol(g_tw64, t64.data(), sizeof(double2) * kTwN);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tw32, t32.data(), sizeof(float2) * kTwN);
+  double gx[16], gw[16];
+  gauss_legendre(16, gx, gw);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gl_x, gx, sizeof gx);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gl_w, gw, sizeof gw);
   return e;
 }
 
-cudaError_t tensorgen_run(fsa_kernel kernel, const int n[3], const double L[3], double eps, double* O, void* out,
-                          fsa_dtype dtype, cudaStream_t s) {
+cudaError_t tensorgen_run(fsa_kernel kernel, const int n[3], const double L[3], double eps, double lam, double* O,
+                          void* out, fsa_dtype dtype, cudaStream_t s) {
   // d = 2: a single plane of the octant (n2 = 0 here, unit h2), no axis-2 DCT
   const bool plane = kernel_dim(kernel) == 2;
   const int n0 = n[0], n1 = n[1], n2 = plane ? 0 : n[2];
@@ -271,7 +327,7 @@ cudaError_t tensorgen_run(fsa_kernel kernel, const int n[3], const double L[3], 
   const long long total = e0 * e1 * e2;
   const int threads = 256;
   const int blocks = (int)std::min<long long>((total + threads - 1) / threads, 152LL * 16);
-  k_t1_octant<<<blocks, threads, 0, s>>>(O, (int)kernel, n0, n1, n2, h0, h1, h2, eps);
+  k_t1_octant<<<blocks, threads, 0, s>>>(O, (int)kernel, n0, n1, n2, h0, h1, h2, eps, lam);
   cudaError_t e = cudaGetLastError();
   // axis 2: lines (p0, p1) contiguous, element stride 1
   if (e == cudaSuccess && !plane) e = dct_run(2 * n2, O, e0 * e1, e1, e1 * e2, e2, 1, s);
@@ -285,10 +341,10 @@ cudaError_t tensorgen_run(fsa_kernel kernel, const int n[3], const double L[3], 
   const double c2 = plane ? 0.0 : pi / (2 * L[2]);
   if (dtype == FSA_F64)
     k_spectrum_finalize<double><<<blocks, threads, 0, s>>>(O, (double*)out, (int)kernel, n0, n1, n2, pi / (2 * L[0]),
-                                                           pi / (2 * L[1]), c2, eps, inv_norm);
+                                                           pi / (2 * L[1]), c2, eps, lam, inv_norm);
   else
     k_spectrum_finalize<float><<<blocks, threads, 0, s>>>(O, (float*)out, (int)kernel, n0, n1, n2, pi / (2 * L[0]),
-                                                          pi / (2 * L[1]), c2, eps, inv_norm);
+                                                          pi / (2 * L[1]), c2, eps, lam, inv_norm);
   return cudaGetLastError();
 }
 

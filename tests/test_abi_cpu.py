@@ -103,7 +103,7 @@ def test_plan_create_rejects_dimension_and_kernel(capi):
         capi.fsa_plan_create(capi.FSA_KERNEL_COULOMB3D, 2, (1, 1, 1), (8, 8, 8), capi.FSA_F32)
     assert ei.value.status == capi.FSA_ERR_INVALID_ARG
     with pytest.raises(capi.FsaError) as ei:
-        capi.fsa_plan_create(7, 3, (1, 1, 1), (8, 8, 8), capi.FSA_F32)
+        capi.fsa_plan_create(9, 3, (1, 1, 1), (8, 8, 8), capi.FSA_F32)
     assert ei.value.status == capi.FSA_ERR_UNSUPPORTED
 
 
@@ -156,3 +156,27 @@ def test_ddi_plan_create_rejects_before_touching_the_device(capi):
     with pytest.raises(capi.FsaError) as ei:  # DDI plans need their dipoles
         capi.fsa_plan_create(capi.FSA_KERNEL_DDI3D, 3, (1, 1, 1), (8, 8, 8), capi.FSA_F32)
     assert ei.value.status == capi.FSA_ERR_INVALID_ARG
+
+
+def test_yukawa_bound_matches_oracle(capi):
+    """The library's swapped-order quadrature of the Yukawa far-field integral
+    against the oracle's adaptive quadrature of the same integral."""
+    from oracle import fsa
+    for name, k in (("yukawa3d", capi.FSA_KERNEL_YUKAWA3D), ("yukawa2d", capi.FSA_KERNEL_YUKAWA2D)):
+        for R0, eps, lam in [(24.0, 4.0, 1.0), (16.0, 2.7, 0.5), (8.0, 1.0, 1.0), (4.0, 0.9, 3.0), (2.0, 0.5, 0.1)]:
+            a = capi.fsa_appendix_b_bound_kernel_param(k, lam, R0, eps)
+            b = fsa.appendix_b_bound(R0, eps, kernel=(name, lam))
+            assert a == pytest.approx(b, rel=1e-9, abs=1e-300), (name, R0, eps, lam)
+        assert math.isnan(capi.fsa_appendix_b_bound_kernel_param(k, 0.0, 8.0, 1.0))
+
+
+def test_yukawa_plan_create_checks(capi):
+    with pytest.raises(capi.FsaError) as ei:  # d mismatch
+        capi.fsa_plan_create(capi.FSA_KERNEL_YUKAWA2D, 3, (1, 1, 1), (8, 8, 8), capi.FSA_F32)
+    assert ei.value.status == capi.FSA_ERR_INVALID_ARG
+    with pytest.raises(capi.FsaError) as ei:  # negative lam
+        capi.fsa_plan_create(capi.FSA_KERNEL_YUKAWA3D, 3, (8, 8, 8), (8, 8, 8), capi.FSA_F32, eps=1.0, kernel_param=-1.0)
+    assert ei.value.status == capi.FSA_ERR_INVALID_ARG
+    with pytest.raises(capi.FsaError) as ei:  # App. B rejects a large eps (R0 = 4, eps = 2)
+        capi.fsa_plan_create(capi.FSA_KERNEL_YUKAWA3D, 3, (2, 2, 2), (8, 8, 8), capi.FSA_F32, eps=2.0, kernel_param=0.5)
+    assert ei.value.status == capi.FSA_ERR_EPS
