@@ -587,6 +587,14 @@ def bench_serving(args, fsa, W, torch, rank):
     capacity = len(reqs) / wall
     arrivals = W.poisson_arrivals(2504, len(reqs), args.serve_load * capacity)
     wall2, lat2 = run(arrivals)
+    # the other offered loads (same stream, same seed for the arrival process)
+    per_load = {f"{args.serve_load:g}": {"solves_per_s": len(reqs) / wall2,
+                                         "p50_ms": float(np.percentile(lat2, 50)),
+                                         "p99_ms": float(np.percentile(lat2, 99))}}
+    for f in [float(x) for x in args.serve_other_loads.split(",") if x]:
+        w_f, lat_f = run(W.poisson_arrivals(2504, len(reqs), f * capacity))
+        per_load[f"{f:g}"] = {"solves_per_s": len(reqs) / w_f, "p50_ms": float(np.percentile(lat_f, 50)),
+                              "p99_ms": float(np.percentile(lat_f, 99))}
     st = srv.stats()
     srv.close()
     torch.cuda.empty_cache()
@@ -621,6 +629,7 @@ def bench_serving(args, fsa, W, torch, rank):
             "value": len(reqs) / wall2, "unit": UNIT,
             "p50_ms": float(np.percentile(lat2, 50)), "p99_ms": float(np.percentile(lat2, 99)),
             "closed_loop_p50_ms": float(np.percentile(lat, 50)),
+            "per_load": dict(sorted(per_load.items())),
             "plan_hit_rate": st.plan_hits / max(1, st.plan_hits + st.plan_misses),
             "fp64_single_solve_solves_per_s": fp64_single,
             "fp64_single_solve_sample": f"first {len(sample)} requests, each solved alone in FP64 "
@@ -702,6 +711,8 @@ def main():
                     help="plane-slab size of the middle passes in MB (0 = library default, -1 = one slab)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-many", action="store_true", help="skip the many-densities-one-plan leg")
+    ap.add_argument("--serve-other-loads", default="0.5,0.95",
+                    help="further offered loads (fractions of the measured capacity) for the serving leg's p50/p99")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-n", type=int, default=10000, help="requests in the serving run")
