@@ -428,7 +428,13 @@ static cudaError_t init_tu_twiddles() {
   }
 #define FSA_REG_V1(ARITH, V, M) fsa::register_pass_fns(ARITH, M, fsa::fns_of<fsa::detail::Inst<V, M>>());
 #define FSA_REG_V2(M)                                                                 \
-  fsa::register_pass_fns(fsa::kArithF32G2, M, fsa::fns_of<fsa::detail::Inst2<M>>()); \
+  {                                                                                   \
+    /* densities of one plan: the prefetching middle pass, whichever the     */      \
+    /* tuner picks for single solves (it overlaps loads across the densities) */     \
+    fsa::PassFns f2 = fsa::fns_of<fsa::detail::Inst2<M>>();                           \
+    f2.colm_shared = &fsa::detail::Inst2<M>::colm_p_shared;                           \
+    fsa::register_pass_fns(fsa::kArithF32G2, M, f2);                                  \
+  }                                                                                   \
   {                                                                                   \
     fsa::PassFns f3 = fsa::fns_of<fsa::detail::Inst2<M>>();                           \
     f3.colm = &fsa::detail::Inst2<M>::colm_p;                                         \
