@@ -34,12 +34,15 @@ namespace fsa {
 
 template <typename V> struct TileW { static constexpr int W = 16; };
 template <> struct TileW<double2> { static constexpr int W = 8; };
-template <> struct TileW<cdw> { static constexpr int W = 8; };
+template <> struct TileW<cdw> { static constexpr int W = 4; };
 
 // Resident CTAs per SM the compiler should allow for: double-word passes are
-// bound by the FP32 pipes, so they ask for two (at most 64 registers).
+// bound by the FP32 pipes; they run 4-line tiles (256 threads for length
+// 512) four to an SM (at most 64 registers), so a barrier holds fewer warps
+// (R2C 0.218 against 0.255 ms, C2R 0.204 against 0.230 ms at 256^3 with
+// 8-line tiles two to an SM; the row passes the same).
 template <typename V> struct MinB { static constexpr int value = 1; };
-template <> struct MinB<cdw> { static constexpr int value = 2; };
+template <> struct MinB<cdw> { static constexpr int value = 4; };
 
 // The middle pass keeps a whole line's forward transform, multiply and
 // inverse in one CTA; for double-word values it takes half-width tiles so
