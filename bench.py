@@ -82,6 +82,15 @@ def ddi_grid_pass_bytes(n, s):
     return {k: b[k] + extra[k] for k in b}
 
 
+def fused_text(c, M):
+    """The outer pass pair in use: separate passes or a cluster configuration."""
+    from paper_2504_19410_gb300 import capi
+    if not c:
+        return "separate passes"
+    cs, nt = capi.fsa_fused_configs(M)[c - 1]
+    return f"fused, clusters of {cs} CTAs x {nt} threads"
+
+
 def reference_model_bytes(n, s):
     """Reference 5-pass byte model: E = 2V + 24 n0 n1 (n2+1) + octant reals per solve."""
     n0, n1, n2 = n
@@ -253,6 +262,8 @@ def run_ours(args):
     # 8 Gaussians, [-16,16]^3 at 256^3 (or [-16,16]^2 at 512^2 for a plane kernel), eps = 1
     d = W.gaussian_sum_2d(seed=2504) if plane else W.gaussian_sum(seed=2504)
     n = d.n
+    if args.outer_pairs != "auto" and capi.fsa_fused_configs(2 * n[0]):
+        capi.fsa_fused_select(2 * n[0], 2, 0 if args.outer_pairs == "separate" else int(args.outer_pairs))
     rho64 = d.rho()
     hbm_peak, peak_kind = peaks()
     stream = torch.cuda.current_stream()
@@ -299,6 +310,17 @@ def run_ours(args):
         pb = (plane_pass_bytes(n, s) if plane else
               ddi_grid_pass_bytes(n, s) if args.kernel == "ddi3d" and args.ddi_derivative == "grid" else
               pass_bytes(n, s))
+        info = plan.info
+        if not plane and args.kernel != "ddi3d" and (info.fused_fwd or info.fused_inv):
+            # the fused outer pairs (clusters): rho -> Y reported as row_fwd,
+            # Y -> phi as row_inv; X never goes to HBM
+            pb = dict(pb)
+            V = n[0] * n[1] * n[2]
+            Yr = (n[0] + 1) * n[1] * 2 * n[2] * 2
+            if info.fused_fwd:
+                pb["r2c_ax0"], pb["row_fwd"] = 0, (V + Yr) * s
+            if info.fused_inv:
+                pb["row_inv"], pb["c2r_ax0"] = (Yr + V) * s, 0
         dom = max(range(5), key=lambda i: pass_ms[i])
         kname = PASSES[dom]
         achieved = pb[kname] / (pass_ms[dom] * 1e-3) / 1e9
@@ -336,6 +358,10 @@ def run_ours(args):
             "clocks": clocks,
             "gpu_launches": plan.info.launches_per_apply * args.steps,
             "launches_per_solve": plan.info.launches_per_apply,
+            "outer_pairs": {"forward": fused_text(info.fused_fwd, 2 * n[0]),
+                            "inverse": fused_text(info.fused_inv, 2 * n[0])},
+            "pass_hbm_frac": {k: round(pb[k] / (v * 1e-3) / 1e9 / hbm_peak, 4)
+                              for k, v in zip(PASSES, pass_ms) if v > 0 and pb[k] > 0},
         }
         # e2e through the C-ABI host-buffer entry point: every step copies its rho
         # from pinned host memory and its phi back (both inside the timed
@@ -418,6 +444,8 @@ def run_ours(args):
             "gpu_launches": main["gpu_launches"],
             "clocks": main["clocks"],
             "pass_ms": main["pass_ms"],
+            "pass_hbm_frac": main["pass_hbm_frac"],
+            "outer_pairs": main["outer_pairs"],
             "precomp_ms": main["precomp_ms"],
             "plan_create_ms": main["plan_create_ms"],
             "step_roofline_frac_27V_model": main["step_roofline_frac_27V_model"],
@@ -704,6 +732,9 @@ def main():
     ap.add_argument("--ddi-derivative", choices=["grid", "kernel"], default="grid",
                     help="--kernel ddi3d: d_n d_m rho on the computational grid (the paper's Table 5) or "
                          "fused into the middle multiply")
+    ap.add_argument("--outer-pairs", default="auto",
+                    help="the outer pass pairs of FP32 cubes: auto (tuned), separate, or a fused cluster "
+                         "configuration 1, 2, ... (fsa_fused_configs)")
     ap.add_argument("--kernel-gen", choices=["auto", "1", "2", "3", "4"], default="auto",
                     help="auto: autotuned per plan; 1 / 2 / 3 / 4: force one kernel generation "
                          "(FP64: native for 1, double-word otherwise)")

@@ -139,6 +139,8 @@ typedef struct {
   int ddi_derivative;       /* FSA_KERNEL_DDI3D plans: their fsa_ddi_derivative; -1   */
   double dipole_n[3];       /* FSA_KERNEL_DDI3D plans: n and m; zero otherwise        */
   double dipole_m[3];
+  int fused_fwd;            /* the outer forward pair in use (fsa_fused_select): 0    */
+  int fused_inv;            /* separate passes, c >= 1 fused configuration c - 1     */
 } fsa_plan_info;
 
 /* Create a plan (the "Precomp" object of Sec. 5, Example 2) for the grid
@@ -317,6 +319,30 @@ fsa_status fsa_profiler_destroy(fsa_profiler* prof);
  * mode 2, double-word in modes 3 to 5.  FSA_ERR_INVALID_ARG for other modes.
  * Not thread-safe against concurrent launches. */
 fsa_status fsa_autotune_set(int mode);
+
+/* Fused outer passes (FP32 plans of d = 3 with n0 = n2 and transform length
+ * M = 2 n0 in {256, 384, 512}).  The five passes of Sec. 2.3 stay the same
+ * transforms in the same order, but the pad + R2C along axis 0 and the
+ * forward axis-2 transform run as one kernel, and so do the inverse axis-2
+ * transform and the C2R along axis 0 + crop: a thread-block cluster holds one
+ * i1-slab of the half spectrum X in the distributed shared memory of its CTAs,
+ * so X never goes to HBM.
+ * fsa_fused_configs returns how many cluster configurations exist for length
+ * M (0: none) and writes, for the first min(count, cap) of them, the CTAs per
+ * cluster and the threads per CTA (either pointer may be NULL).
+ * fsa_fused_select(M, dir, c) pins the pair used for direction dir (0 forward,
+ * 1 inverse, 2 both): c = 0 the separate passes, c >= 1 configuration c - 1,
+ * c = -1 unpinned (the default).  Unpinned, autotune mode 1 times the separate
+ * passes and every configuration on the first plan of the length and keeps the
+ * fastest; mode 0 runs the separate passes; modes 2 to 5 always run the
+ * separate passes of the forced generation, pinned or not.  The pass profiler reports a
+ * fused pair under row_fwd / row_inv (r2c_ax0 / c2r_ax0 then read 0).
+ * Plans with a pass split (l2_chunk_mb), DDI, FP64 and d = 2 plans use the
+ * separate passes.  FSA_ERR_INVALID_ARG for a length without configurations,
+ * dir outside 0..2 or c outside -1..count.  Not thread-safe against
+ * concurrent launches. */
+int fsa_fused_configs(int M, int* cluster_ctas, int* threads, int cap);
+fsa_status fsa_fused_select(int M, int dir, int c);
 
 /* Device-side wait status (no counterpart in the paper: it reports on the
  * kernels, not on the method).  Kernels that wait on an mbarrier for their own

@@ -57,7 +57,8 @@ class PlanInfo(C.Structure):
                 ("spectrum", C.c_void_p), ("kernel", C.c_int), ("d", C.c_int), ("kernel_param", C.c_double),
                 ("many_capacity", C.c_int),
                 ("ddi_derivative", C.c_int),
-                ("dipole_n", C.c_double * 3), ("dipole_m", C.c_double * 3)]
+                ("dipole_n", C.c_double * 3), ("dipole_m", C.c_double * 3),
+                ("fused_fwd", C.c_int), ("fused_inv", C.c_int)]
 
 
 class ServeOpts(C.Structure):
@@ -104,6 +105,8 @@ _PROTOS = {
     "fsa_status_string": (C.c_char_p, [C.c_int]),
     "fsa_last_error": (C.c_char_p, []),
     "fsa_autotune_set": (C.c_int, [C.c_int]),
+    "fsa_fused_configs": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]),
+    "fsa_fused_select": (C.c_int, [C.c_int, C.c_int, C.c_int]),
     "fsa_device_fault": (C.c_int, [C.c_int, C.POINTER(C.c_uint), C.c_int]),
     "fsa_wait_selftest": (C.c_int, [C.c_int, C.POINTER(C.c_uint)]),
     "fsa_profiler_create": (C.c_int, [C.POINTER(_VP), C.c_int]),
@@ -257,6 +260,21 @@ def fsa_last_error():
 
 def fsa_autotune_set(mode):
     return check(lib().fsa_autotune_set(int(mode)))
+
+
+def fsa_fused_configs(M):
+    """[(CTAs per cluster, threads per CTA), ...] of the fused outer pass
+    pairs for transform length M (empty: none)."""
+    cs = (C.c_int * 4)()
+    nt = (C.c_int * 4)()
+    k = lib().fsa_fused_configs(int(M), cs, nt, 4)
+    return [(cs[i], nt[i]) for i in range(min(k, 4))]
+
+
+def fsa_fused_select(M, direction, c):
+    """Pin the outer pair for length M: direction 0 forward, 1 inverse, 2
+    both; c = 0 separate passes, c >= 1 fused configuration c - 1, -1 tuner."""
+    return check(lib().fsa_fused_select(int(M), int(direction), int(c)))
 
 
 def fsa_device_fault(device=-1, clear=False):

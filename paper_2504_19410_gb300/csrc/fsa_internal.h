@@ -30,7 +30,7 @@ struct Geometry {
 };
 
 bool supported_n(int n);
-int& autotune_mode();  // fsa_autotune_set: 0 defaults, 1 tune per plan, 2..5 force generation 1..4
+int& autotune_mode();  // fsa_autotune_set: 0 defaults, 1 tune per plan, 2..5 force generation 1..4, 6 fused
 // Kernel generation used for a pass of length M in a dtype: 1 = Stockham
 // radix-8 (passes.cuh), 2 = two-step register kernels (passes2.cuh, FP32).
 int kernel_variant(int pass, int M, fsa_dtype dt);
@@ -67,6 +67,15 @@ struct PassFns {
   cudaError_t (*colm_per)(const Jobs&, int M2, int planes, cudaStream_t) = nullptr;
   cudaError_t (*rowi_per)(const Jobs&, long long rows, cudaStream_t) = nullptr;
   cudaError_t (*c2r_per)(const Jobs&, long long C, cudaStream_t) = nullptr;
+  // fifth generation (FP32, transform length M on axes 0 and 2): the fused
+  // outer pass pairs run by thread-block clusters (passes5.cuh), rho -> Y and
+  // Y -> phi, in cluster configuration cfg < nfused (CTAs per cluster
+  // fused_cs[cfg], threads per CTA fused_nt[cfg])
+  cudaError_t (*fwd5)(int cfg, const Jobs&, int n1, cudaStream_t) = nullptr;
+  cudaError_t (*inv5)(int cfg, const Jobs&, int n1, cudaStream_t) = nullptr;
+  int nfused = 0;
+  int fused_cs[4] = {0, 0, 0, 0};
+  int fused_nt[4] = {0, 0, 0, 0};
 };
 // FP32 generations: 1 Stockham radix-8, 2 two-step register, 3 = 2 with the
 // middle pass prefetching its next tile (cp.async), 4 = 3 with the row passes
@@ -78,8 +87,15 @@ enum Arith {
   kArithDW = 3,
   kArithF32G3 = 4,
   kArithF32G4 = 5,
-  kNumArith = 6
+  kArithF32G5 = 6,  // the fused outer pass pairs only (fwd5 / inv5)
+  kNumArith = 7
 };
+// The fused outer pass pair used for FP32 grids with n0 = n2 and transform
+// length M = 2 n0 (dir 0 forward, 1 inverse): 0 = the separate passes, c >= 1
+// = fused cluster configuration c - 1.  set_fused_config(M, dir, -1) leaves
+// the choice to the tuner.
+int fused_config(int M, int dir);
+void set_fused_config(int M, int dir, int c);
 // This device's fault word (Jobs::fault), allocated by prepare_device;
 // ensure_device_fault_word allocates it if needed (current device).
 unsigned int* device_fault_word();

@@ -118,6 +118,38 @@ void set_kernel_variant(int pass, int M, fsa_dtype dt, int variant) {
   if (M >= 0 && M <= 1024) g_variant[pass][M][dt].store((signed char)variant, std::memory_order_relaxed);
 }
 
+namespace {
+// Fused outer pair per (length, direction): -1 unpinned and untuned, else as
+// fused_config.  Pins (fsa_fused_select) and tuner results share the table.
+std::atomic<signed char> g_fused[1025][2];
+std::atomic<bool> g_fused_init{false};
+void fused_table_init() {
+  if (g_fused_init.load()) return;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (g_fused_init.load()) return;
+  for (auto& m : g_fused)
+    for (auto& d : m) d.store(-1);
+  g_fused_init.store(true);
+}
+}  // namespace
+
+int fused_config(int M, int dir) {
+  const int mode = autotune_mode();
+  if (mode >= 2 || M < 0 || M > 1024 || dir < 0 || dir > 1) return 0;
+  const int nf = pass_fns(kArithF32G5, M).nfused;
+  if (nf == 0) return 0;
+  fused_table_init();
+  const int c = g_fused[M][dir].load(std::memory_order_relaxed);
+  return c >= 0 && c <= nf ? c : 0;  // unpinned and untuned: the separate passes
+}
+
+void set_fused_config(int M, int dir, int c) {
+  if (M < 0 || M > 1024 || dir < 0 || dir > 1) return;
+  fused_table_init();
+  g_fused[M][dir].store((signed char)c, std::memory_order_relaxed);
+}
+
 bool supported_n(int n) {
   if (n < 4 || n > 512 || (n & 1)) return false;
   int m = n;
@@ -216,6 +248,16 @@ cudaError_t middle_slab(const int* n, int m, int b, void* const* X, void* const*
   return e;
 }
 
+// The fused outer pair for a grid (0: the separate passes): FP32, n0 = n2.
+template <typename V> int fused_pair(const int* n, int dir) {
+  if constexpr (!std::is_same<V, float2>::value) {
+    return 0;
+  } else {
+    if (n[0] != n[2]) return 0;
+    return fused_config(2 * n[0], dir);
+  }
+}
+
 template <typename V>
 cudaError_t group_passes(const int* n, int count, const void* const* rho, void* const* phi, void* const* X,
                          void* const* Y, const void* const* S, cudaStream_t s, PassTrace* tr,
@@ -243,32 +285,54 @@ cudaError_t group_passes(const int* n, int count, const void* const* rho, void* 
     const PassFns& f4 = pass_fns(arith_for<V>(kRowInv, 2 * n2), 2 * n2);
     const PassFns& f5 = pass_fns(arith_for<V>(kC2R, 2 * n0), 2 * n0);
     if (!f1.r2c || !f2.rowf || !f3.colm || !f4.rowi || !f5.c2r) return cudaErrorInvalidValue;
-    e = e == cudaSuccess ? f1.r2c(j1, C, s) : e;
-    if (e == cudaSuccess) e = trace_mark(tr, kR2C, s);
     // pass split: slabs of planes whose X + Y fit chunk_bytes stay in L2
     // between the row-forward, middle and row-inverse passes
     const long long plane = (long long)m * n1 * (n2 + 2 * n2) * (long long)sizeof(V);
     const int K0 = n0 + 1;
     int pc = chunk_bytes > 0 ? (int)std::max<long long>(1, chunk_bytes / plane) : K0;
+    // the fused outer pairs (rho -> Y, Y -> phi by clusters; no split)
+    const int ff = pc >= K0 ? fused_pair<V>(n, 0) : 0;
+    const int fi = pc >= K0 ? fused_pair<V>(n, 1) : 0;
+    const PassFns& f55 = pass_fns(kArithF32G5, 2 * n0);
     // jobs that share one spectrum (densities of one plan) take the middle
     // pass that reads each spectrum tile once for all of them
     bool shared = m > 1 && f3.colm_shared;
     for (int i = 1; i < m && shared; ++i) shared = j3.j[i].S == j3.j[0].S;
-    if (pc >= K0) {
-      if (e == cudaSuccess) e = f2.rowf(j2, rows, s);
+    if (ff > 0) {
+      Jobs jf = j1;
+      for (int i = 0; i < m; ++i) jf.j[i].out = Y[b + i];
+      e = e == cudaSuccess ? f55.fwd5(ff - 1, jf, n1, s) : e;
       if (e == cudaSuccess) e = trace_mark(tr, kRowFwd, s);
+    } else {
+      e = e == cudaSuccess ? f1.r2c(j1, C, s) : e;
+      if (e == cudaSuccess) e = trace_mark(tr, kR2C, s);
+    }
+    if (pc >= K0) {
+      if (ff == 0) {
+        if (e == cudaSuccess) e = f2.rowf(j2, rows, s);
+        if (e == cudaSuccess) e = trace_mark(tr, kRowFwd, s);
+      }
       if (e == cudaSuccess) e = shared ? f3.colm_shared(j3, 2 * n2, n0 + 1, s) : f3.colm(j3, 2 * n2, n0 + 1, s);
       if (e == cudaSuccess) e = trace_mark(tr, kColMid, s);
-      if (e == cudaSuccess) e = f4.rowi(j4, rows, s);
-      if (e == cudaSuccess) e = trace_mark(tr, kRowInv, s);
+      if (fi == 0) {
+        if (e == cudaSuccess) e = f4.rowi(j4, rows, s);
+        if (e == cudaSuccess) e = trace_mark(tr, kRowInv, s);
+      }
     } else {
       for (int k0s = 0; k0s < K0 && e == cudaSuccess; k0s += pc) {
         const int c = std::min(pc, K0 - k0s);
         e = middle_slab<V>(n, m, b, X, Y, S, k0s, c, f2, f3, f4, s, tr);
       }
     }
-    if (e == cudaSuccess) e = f5.c2r(j5, C, s);
-    if (e == cudaSuccess) e = trace_mark(tr, kC2R, s);
+    if (fi > 0) {
+      Jobs ji = j5;
+      for (int i = 0; i < m; ++i) ji.j[i].in = Y[b + i];
+      if (e == cudaSuccess) e = f55.inv5(fi - 1, ji, n1, s);
+      if (e == cudaSuccess) e = trace_mark(tr, kRowInv, s);
+    } else {
+      if (e == cudaSuccess) e = f5.c2r(j5, C, s);
+      if (e == cudaSuccess) e = trace_mark(tr, kC2R, s);
+    }
   }
   return e;
 }
@@ -568,6 +632,8 @@ fsa_status prepare_device(int dev, fsa_dtype dt, const int* n, int d, bool unpad
       if (!f.prepare) return set_error(FSA_ERR_UNSUPPORTED, "no kernels registered for this length");
       if (e == cudaSuccess) e = f.prepare();
     }
+    const PassFns& f5g = pass_fns(kArithF32G5, M);  // fused outer pairs (some lengths)
+    if (dt == FSA_F32 && f5g.prepare && e == cudaSuccess) e = f5g.prepare();
     if (e == cudaSuccess) e = tensorgen_prepare(M);
     if (e != cudaSuccess) return cuda_error(e, "kernel shared-memory opt-in");
     g_prepared.insert({dev, key});
@@ -654,6 +720,26 @@ fsa_status fsa_device_fault(int device, unsigned int* code, int clear) {
 fsa_status fsa_autotune_set(int mode) {
   if (mode < 0 || mode > 5) return set_error(FSA_ERR_INVALID_ARG, "fsa_autotune_set: mode must be 0..5");
   autotune_mode() = mode;
+  return FSA_OK;
+}
+
+int fsa_fused_configs(int M, int* cluster_ctas, int* threads, int cap) {
+  if (M < 0 || M > 1024) return 0;
+  const PassFns& f = pass_fns(kArithF32G5, M);
+  for (int k = 0; k < f.nfused && k < cap; ++k) {
+    if (cluster_ctas) cluster_ctas[k] = f.fused_cs[k];
+    if (threads) threads[k] = f.fused_nt[k];
+  }
+  return f.nfused;
+}
+
+fsa_status fsa_fused_select(int M, int dir, int c) {
+  const int nf = (M >= 0 && M <= 1024) ? pass_fns(kArithF32G5, M).nfused : 0;
+  if (nf == 0) return set_error(FSA_ERR_INVALID_ARG, "fsa_fused_select: no fused configurations for this length");
+  if (dir < 0 || dir > 2) return set_error(FSA_ERR_INVALID_ARG, "fsa_fused_select: dir must be 0, 1 or 2");
+  if (c < -1 || c > nf) return set_error(FSA_ERR_INVALID_ARG, "fsa_fused_select: configuration out of range");
+  for (int d = 0; d < 2; ++d)
+    if (dir == 2 || dir == d) set_fused_config(M, d, c);
   return FSA_OK;
 }
 
@@ -872,6 +958,10 @@ cudaError_t tune_plan(fsa_plan* p) {
   const int Ms[kNumPass] = {2 * n0, 2 * n2, 2 * n1, 2 * n2, 2 * n0};
   bool need = false;
   for (int k = 0; k < kNumPass; ++k) need |= g_variant[k][Ms[k]][FSA_F32].load() == 0;
+  const PassFns& f5g = pass_fns(kArithF32G5, 2 * n0);
+  fused_table_init();
+  const bool fuse = n0 == n2 && f5g.nfused > 0;
+  for (int dir = 0; dir < 2 && fuse; ++dir) need |= g_fused[2 * n0][dir].load() < 0;
   if (!need) return cudaSuccess;
   cudaStream_t s;
   cudaEvent_t e0, e1;
@@ -916,6 +1006,40 @@ cudaError_t tune_plan(fsa_plan* p) {
       }
     }
     set_kernel_variant(k, Ms[k], FSA_F32, e == cudaSuccess ? pick : 0);
+  }
+  // the fused outer pairs against the separate passes just chosen (X stands
+  // in for rho and phi: the kernels' cost does not depend on the data)
+  auto run_pair = [&](int dir, int c) -> cudaError_t {
+    if (c == 0) {
+      const int a = dir == 0 ? kR2C : kRowInv, b = dir == 0 ? kRowFwd : kC2R;
+      cudaError_t r = run(a, kernel_variant(a, Ms[a], FSA_F32));
+      return r == cudaSuccess ? run(b, kernel_variant(b, Ms[b], FSA_F32)) : r;
+    }
+    j.j[0] = dir == 0 ? Job{X, Y, nullptr} : Job{Y, X, nullptr};
+    return dir == 0 ? f5g.fwd5(c - 1, j, n1, s) : f5g.inv5(c - 1, j, n1, s);
+  };
+  for (int dir = 0; dir < 2 && fuse && e == cudaSuccess; ++dir) {
+    if (g_fused[2 * n0][dir].load() >= 0) continue;
+    float best = 1e30f;
+    int pick = 0;
+    for (int c = 0; c <= f5g.nfused && e == cudaSuccess; ++c) {
+      e = run_pair(dir, c);  // warm-up
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, s);
+        e = run_pair(dir, c);
+        cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        tmin = std::min(tmin, ms);
+      }
+      if (tmin < best) {
+        best = tmin;
+        pick = c;
+      }
+    }
+    if (e == cudaSuccess) set_fused_config(2 * n0, dir, pick);
   }
   cudaStreamSynchronize(s);
   cudaEventDestroy(e0);
@@ -1130,6 +1254,10 @@ fsa_status fsa_plan_info_get(const fsa_plan* p, fsa_plan_info* info) {
     const int K0 = p->n[0] + 1;
     const int pc = p->chunk_bytes > 0 ? (int)std::max<long long>(1, p->chunk_bytes / plane) : K0;
     info->launches_per_apply = p->d == 2 ? 3 : 2 + 3 * ((K0 + std::min(pc, K0) - 1) / std::min(pc, K0));
+    const bool fusable = p->d == 3 && p->ddi < 0 && pc >= K0 && p->dtype == FSA_F32;
+    info->fused_fwd = fusable ? fused_pair<float2>(p->n, 0) : 0;
+    info->fused_inv = fusable ? fused_pair<float2>(p->n, 1) : 0;
+    info->launches_per_apply -= (info->fused_fwd > 0) + (info->fused_inv > 0);
     if (p->ddi >= 0) info->launches_per_apply = p->ddi == FSA_DDI_GRID ? 10 : 5;
   }
   info->workspace_bytes = p->ws_bytes;

@@ -180,3 +180,20 @@ def test_yukawa_plan_create_checks(capi):
     with pytest.raises(capi.FsaError) as ei:  # App. B rejects a large eps (R0 = 4, eps = 2)
         capi.fsa_plan_create(capi.FSA_KERNEL_YUKAWA3D, 3, (2, 2, 2), (8, 8, 8), capi.FSA_F32, eps=2.0, kernel_param=0.5)
     assert ei.value.status == capi.FSA_ERR_EPS
+
+
+def test_fused_configs_and_select_arguments(capi):
+    """The fused outer pass pairs' cluster configurations are host-side
+    registry data (no device needed); selection checks its arguments."""
+    assert capi.fsa_fused_configs(512) == [(8, 128)]
+    assert capi.fsa_fused_configs(384) == [(4, 128)]
+    assert capi.fsa_fused_configs(256) == [(4, 256), (8, 128)]
+    for M in (8, 64, 128, 768, 1024, 2048, -2):
+        assert capi.fsa_fused_configs(M) == []
+    for args in ((128, 2, 1), (512, 3, 1), (512, -1, 0), (512, 2, 2), (512, 0, -2)):
+        with pytest.raises(capi.FsaError) as ei:
+            capi.fsa_fused_select(*args)
+        assert ei.value.status == capi.FSA_ERR_INVALID_ARG
+    for c in (-1, 0, 1):
+        capi.fsa_fused_select(512, 2, c)
+    capi.fsa_fused_select(512, 2, -1)

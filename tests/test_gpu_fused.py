@@ -1,0 +1,205 @@
+"""The fused outer pass pairs (thread-block clusters; FP32 grids with n0 = n2)
+on the CUDA path against the oracle, and against the separate passes.
+
+Each cluster configuration of each length is pinned in turn
+(fsa_fused_select).  Tolerance as for every FP32 solve: max-norm relative
+error <= 2e-6 against the FP64 oracle on the same seeded inputs.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fsa as oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 2e-6
+LENGTHS = (256, 384, 512)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2504_19410_gb300 as fsa
+    return fsa
+
+
+@pytest.fixture
+def capi(lib):
+    """Restores the default selection (tuner decides) after each test."""
+    from paper_2504_19410_gb300 import capi as c
+    c.fsa_device_fault(clear=True)
+    yield c
+    for M in LENGTHS:
+        c.fsa_fused_select(M, 2, -1)
+    c.fsa_autotune_set(1)
+    import torch
+    torch.cuda.synchronize()
+
+
+def cases():
+    out = []
+    for M in LENGTHS:
+        from paper_2504_19410_gb300 import capi as c
+        try:
+            k = len(c.fsa_fused_configs(M))
+        except Exception:  # library not built yet at collection: the registry is fixed
+            k = {256: 2, 384: 1, 512: 1}[M]
+        for cfg in range(1, k + 1):
+            out.append((M, cfg))
+    return out
+
+
+def to_dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def solve(lib, L, n, eps, rho):
+    import torch
+    plan = lib.Plan(L, n, "f32", eps=eps)
+    out = plan.apply(to_dev(rho))
+    torch.cuda.synchronize()
+    info = plan.info
+    res = out.double().cpu().numpy()
+    plan.close()
+    return res, info
+
+
+@pytest.mark.parametrize("n1", [6, 16, 24])
+@pytest.mark.parametrize("M,cfg", cases())
+def test_fused_matches_oracle(lib, capi, M, cfg, n1):
+    n = (M // 2, n1, M // 2)
+    capi.fsa_autotune_set(0)
+    capi.fsa_fused_select(M, 2, cfg)
+    rng = np.random.default_rng(M + 7 * n1 + cfg)
+    L = (3.0, 1.0 + n1 / 16, 2.5)
+    rho = rng.standard_normal(n)
+    got, info = solve(lib, L, n, 0.4, rho)
+    assert (info.fused_fwd, info.fused_inv) == (cfg, cfg)
+    assert info.launches_per_apply == 3
+    want = oracle.solve(L, n, 0.4, rho)
+    err = oracle.rel_error(got, want)
+    print(f"fused M={M} cfg={cfg} n1={n1}: {err:.2e}")
+    assert err <= TOL32, err
+
+
+@pytest.mark.parametrize("M,cfg", cases())
+def test_fused_one_direction_each(lib, capi, M, cfg):
+    """Fused forward with separate inverse and the other way round: both
+    match the oracle (the pairs exchange Y in the separate passes' layout)."""
+    n = (M // 2, 8, M // 2)
+    rng = np.random.default_rng(3 * M + cfg)
+    L = (2.0, 1.5, 2.0)
+    rho = rng.standard_normal(n)
+    want = oracle.solve(L, n, 0.5, rho)
+    capi.fsa_autotune_set(0)
+    for fwd, inv in ((cfg, 0), (0, cfg)):
+        capi.fsa_fused_select(M, 0, fwd)
+        capi.fsa_fused_select(M, 1, inv)
+        got, info = solve(lib, L, n, 0.5, rho)
+        assert (info.fused_fwd, info.fused_inv) == (fwd, inv)
+        assert info.launches_per_apply == 4
+        assert oracle.rel_error(got, want) <= TOL32
+
+
+def test_fused_c2_256_sampled_all_configs(lib, capi):
+    """The 256^3 8-Gaussian sum (the headline workload) through each
+    configuration: sampled outputs against the oracle's direct sum, and every
+    output against the separate passes."""
+    import torch
+    d = W.gaussian_sum(seed=2504)
+    rho = d.rho()
+    capi.fsa_autotune_set(0)
+    capi.fsa_fused_select(512, 2, 0)
+    sep, _ = solve(lib, d.L, d.n, d.eps, rho)
+    T = oracle.tensor_T(d.L, d.n, d.eps)
+    pts = [tuple(int(v) for v in p) for p in np.random.default_rng(9).integers(0, 256, size=(16, 3))]
+    pts.append(np.unravel_index(np.argmax(np.abs(sep)), sep.shape))
+    want = oracle.apply_direct_at(T, rho, pts)
+    for cfg in range(1, len(capi.fsa_fused_configs(512)) + 1):
+        capi.fsa_fused_select(512, 2, cfg)
+        got, info = solve(lib, d.L, d.n, d.eps, rho)
+        assert (info.fused_fwd, info.fused_inv) == (cfg, cfg)
+        sampled = np.array([got[p] for p in pts])
+        err = np.max(np.abs(sampled - want)) / np.max(np.abs(want))
+        diff = oracle.rel_error(got, sep)
+        print(f"C2 256^3 fused cfg {cfg}: sampled vs oracle {err:.2e}, vs separate passes {diff:.2e}")
+        assert err <= TOL32
+        assert diff <= 1e-6
+    torch.cuda.synchronize()
+
+
+def test_fused_many_batched_and_host_equal_single(lib, capi):
+    """apply_many, apply_batched (with a plan of another grid in the batch)
+    and apply_host under the fused pairs: each equal to its single apply bit
+    for bit."""
+    import torch
+    capi.fsa_autotune_set(0)
+    capi.fsa_fused_select(256, 2, 1)
+    capi.fsa_fused_select(512, 2, 1)
+    L = (2.0, 2.0, 2.0)
+    p1 = lib.Plan(L, (128, 16, 128), "f32", eps=0.5)
+    p2 = lib.Plan(L, (256, 8, 256), "f32", eps=0.5)
+    p3 = lib.Plan(L, (32, 32, 32), "f32", eps=0.5)
+    assert p1.info.fused_fwd == 1 and p2.info.fused_fwd == 1 and p3.info.fused_fwd == 0
+    rng = np.random.default_rng(4)
+    r1 = [to_dev(rng.standard_normal((128, 16, 128))) for _ in range(3)]
+    single = [p1.apply(r).clone() for r in r1]
+    p1.reserve(3)
+    many = [torch.empty_like(r) for r in r1]
+    p1.apply_many(r1, many)
+    r2 = to_dev(rng.standard_normal((256, 8, 256)))
+    r3 = to_dev(rng.standard_normal((32, 32, 32)))
+    s2, s3 = p2.apply(r2).clone(), p3.apply(r3).clone()
+    outs = [torch.empty_like(r) for r in (r1[0], r2, r3)]
+    lib.apply_batched([p1, p2, p3], [r1[0], r2, r3], outs)
+    host_in = r2.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    p2.apply_host(host_in, host_out)
+    torch.cuda.synchronize()
+    for a, b in zip(single, many):
+        assert torch.equal(a, b)
+    assert torch.equal(outs[0], single[0]) and torch.equal(outs[1], s2) and torch.equal(outs[2], s3)
+    assert torch.equal(host_out, s2.cpu())
+    for p in (p1, p2, p3):
+        p.close()
+
+
+def test_fused_profiler_reports_pairs(lib, capi):
+    """With both pairs fused the profiler sees three launches: the forward
+    pair under row_fwd, the inverse pair under row_inv, r2c_ax0 = c2r_ax0 = 0."""
+    from paper_2504_19410_gb300 import capi as c
+    capi.fsa_autotune_set(0)
+    capi.fsa_fused_select(256, 2, 2)
+    plan = lib.Plan((2.0, 2.0, 2.0), (128, 32, 128), "f32", eps=0.5)
+    rho = to_dev(np.random.default_rng(1).standard_normal((128, 32, 128)))
+    import torch
+    phi = torch.empty_like(rho)
+    prof = c.fsa_profiler_create(4)
+    for _ in range(2):
+        c.fsa_apply_profiled(plan.handle, rho.data_ptr(), phi.data_ptr(), 0, prof)
+    pass_ms, step_ms, steps = c.fsa_profiler_read(prof)
+    c.fsa_profiler_destroy(prof)
+    plan.close()
+    assert steps == 2
+    assert pass_ms[0] == 0 and pass_ms[4] == 0
+    assert pass_ms[1] > 0 and pass_ms[2] > 0 and pass_ms[3] > 0
+    assert sum(pass_ms) == pytest.approx(step_ms, rel=0.05)
+
+
+def test_tuner_picks_a_pair(lib, capi):
+    """Autotune mode 1 times the separate passes and every configuration on
+    the first plan of a length and keeps one choice per direction."""
+    capi.fsa_autotune_set(1)
+    capi.fsa_fused_select(384, 2, -1)
+    plan = lib.Plan((2.0, 2.0, 2.0), (192, 8, 192), "f32", eps=0.5)
+    info = plan.info
+    plan.close()
+    k = len(capi.fsa_fused_configs(384))
+    assert 0 <= info.fused_fwd <= k and 0 <= info.fused_inv <= k
+    print(f"tuner at M = 384: forward {info.fused_fwd}, inverse {info.fused_inv}")
