@@ -321,7 +321,7 @@ fsa_status fsa_profiler_destroy(fsa_profiler* prof);
 fsa_status fsa_autotune_set(int mode);
 
 /* Fused outer passes (FP32 plans of d = 3 with n0 = n2 and transform length
- * M = 2 n0 in {256, 384, 512}).  The five passes of Sec. 2.3 stay the same
+ * M = 2 n0 in {64, 128, 256, 384, 512}).  The five passes of Sec. 2.3 stay the same
  * transforms in the same order, but the pad + R2C along axis 0 and the
  * forward axis-2 transform run as one kernel, and so do the inverse axis-2
  * transform and the C2R along axis 0 + crop: a thread-block cluster holds one

@@ -1,5 +1,5 @@
-// FP32 fused outer pass pairs (passes5.cuh), transform lengths 256, 384 and
-// 512 on axes 0 and 2, in their cluster configurations; registers the
+// FP32 fused outer pass pairs (passes5.cuh), transform lengths 64, 128, 256,
+// 384 and 512 on axes 0 and 2, in their cluster configurations; registers the
 // launchers at library load under kArithF32G5.
 #include <map>
 #include <mutex>
@@ -134,4 +134,6 @@ FSA_REGISTER(
     fsa::detail::Fused<512, fsa::detail::Inst5<512, 8, 128>>::add();
     fsa::detail::Fused<384, fsa::detail::Inst5<384, 4, 128>>::add();
     fsa::detail::Fused<256, fsa::detail::Inst5<256, 4, 256>, fsa::detail::Inst5<256, 8, 128>>::add();
+    fsa::detail::Fused<128, fsa::detail::Inst5<128, 4, 64>, fsa::detail::Inst5<128, 2, 64>>::add();
+    fsa::detail::Fused<64, fsa::detail::Inst5<64, 2, 64>>::add();
 )

@@ -188,9 +188,11 @@ def test_fused_configs_and_select_arguments(capi):
     assert capi.fsa_fused_configs(512) == [(8, 128)]
     assert capi.fsa_fused_configs(384) == [(4, 128)]
     assert capi.fsa_fused_configs(256) == [(4, 256), (8, 128)]
-    for M in (8, 64, 128, 768, 1024, 2048, -2):
+    assert capi.fsa_fused_configs(128) == [(4, 64), (2, 64)]
+    assert capi.fsa_fused_configs(64) == [(2, 64)]
+    for M in (8, 32, 96, 192, 768, 1024, 2048, -2):
         assert capi.fsa_fused_configs(M) == []
-    for args in ((128, 2, 1), (512, 3, 1), (512, -1, 0), (512, 2, 2), (512, 0, -2)):
+    for args in ((192, 2, 1), (512, 3, 1), (512, -1, 0), (512, 2, 2), (512, 0, -2)):
         with pytest.raises(capi.FsaError) as ei:
             capi.fsa_fused_select(*args)
         assert ei.value.status == capi.FSA_ERR_INVALID_ARG

@@ -14,7 +14,7 @@ from oracle import fsa as oracle
 pytestmark = pytest.mark.gpu
 
 TOL32 = 2e-6
-LENGTHS = (256, 384, 512)
+LENGTHS = (64, 128, 256, 384, 512)
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +48,7 @@ def cases():
         try:
             k = len(c.fsa_fused_configs(M))
         except Exception:  # library not built yet at collection: the registry is fixed
-            k = {256: 2, 384: 1, 512: 1}[M]
+            k = {64: 1, 128: 2, 256: 2, 384: 1, 512: 1}[M]
         for cfg in range(1, k + 1):
             out.append((M, cfg))
     return out
