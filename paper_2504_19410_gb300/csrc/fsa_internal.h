@@ -30,7 +30,7 @@ struct Geometry {
 };
 
 bool supported_n(int n);
-int& autotune_mode();  // fsa_autotune_set: 0 defaults, 1 tune per plan, 2..5 force generation 1..4, 6 fused
+int& autotune_mode();  // fsa_autotune_set: 0 defaults, 1 tune per plan, 2..5 force generation 1..4
 // Kernel generation used for a pass of length M in a dtype: 1 = Stockham
 // radix-8 (passes.cuh), 2 = two-step register kernels (passes2.cuh, FP32).
 int kernel_variant(int pass, int M, fsa_dtype dt);
