@@ -260,7 +260,7 @@ def run_ours(args):
     ddi_kw = ({"dipoles": (W.DDI_N, W.DDI_M), "ddi_derivative": args.ddi_derivative}
               if args.kernel == "ddi3d" else {})
     # 8 Gaussians, [-16,16]^3 at 256^3 (or [-16,16]^2 at 512^2 for a plane kernel), eps = 1
-    d = W.gaussian_sum_2d(seed=2504) if plane else W.gaussian_sum(seed=2504)
+    d = W.gaussian_sum_2d(seed=2504) if plane else W.gaussian_sum(seed=2504, n=args.n)
     n = d.n
     if args.outer_pairs != "auto" and capi.fsa_fused_configs(2 * n[0]):
         capi.fsa_fused_select(2 * n[0], 2, 0 if args.outer_pairs == "separate" else int(args.outer_pairs))
@@ -330,7 +330,8 @@ def run_ours(args):
         hbm_roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
                     "unit": "GB/s", "frac": achieved / hbm_peak, "peak_kind": f"of {peak_kind}",
                     "alg_bytes_per_launch": pb[kname],
-                    "traffic": None if plane or args.kernel == "ddi3d" else read_traffic(kname, "c2_256", dt)}
+                    "traffic": (None if plane or args.kernel == "ddi3d" or args.n != 256
+                                else read_traffic(kname, "c2_256", dt))}
         roof = hbm_roof
         if arith == "double-word" and kname == "col_mid" and not plane:
             # bound by the FP32 pipes: FP32 operations per launch over the
@@ -418,7 +419,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(args.cpu_n)
+        cpu = cpu_baseline(min(args.cpu_n, n[0]), n)
 
     if rank == 0:
         line = {
@@ -429,14 +430,18 @@ def run_ours(args):
             "config": {"workload": (f"plane_512: {KERNEL_TEXT[args.kernel]} FSA apply, 8-Gaussian plane density "
                                     "(seed 2504) on [-16,16]^2, 512^2 grid, eps=1, spectrum cached on device")
                                    if args.kernel in PLANE_KERNELS else
-                                   (f"c2_256: {KERNEL_TEXT[args.kernel]} FSA apply, 8-Gaussian density (seed 2504) on "
-                                    "[-16,16]^3, 256^3 grid, eps=1, spectrum cached on device"
+                                   (f"{'c2_256' if args.n == 256 else f'gaussian8_{args.n}'}: "
+                                    f"{KERNEL_TEXT[args.kernel]} FSA apply, 8-Gaussian density (seed 2504) on "
+                                    f"[-16,16]^3, {args.n}^3 grid, eps=1, spectrum cached on device"
                                     + (f"; dipoles n, m of Example 4, {args.ddi_derivative} reading of d_n d_m rho"
                                        if args.kernel == "ddi3d" else "")),
                        "grid": list(n),
                        "l2": ("plane: per-step working set ~12 MB (FP32) < 129 MB L2, L2-resident, not flushed"
                               if args.kernel in PLANE_KERNELS else
-                              "per-step working set ~0.6 GB (FP32) > 129 MB L2; 4 rotating rho/phi buffers"),
+                              f"per-step working set ~{reference_model_bytes(n, 4) / 3e9:.3g} GB (FP32) "
+                              + ("> 129 MB L2; 4 rotating rho/phi buffers"
+                                 if reference_model_bytes(n, 4) / 3 > 129e6 else
+                                 "< 129 MB L2: L2-resident, not flushed (a latency-bound small grid)")),
                        "parallelism": f"replicas x{ws}"},
             "roofline": main["roofline"],
             "cpu_baseline": cpu,
@@ -685,12 +690,12 @@ def oracle_sample(n_sample):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(n_sample):
+def cpu_baseline(n_sample, n=(256, 256, 256)):
     secs = oracle_sample(n_sample)
-    scale = fft_work((256, 256, 256)) / fft_work((n_sample,) * 3)
+    scale = fft_work(tuple(n)) / fft_work((n_sample,) * 3)
     return {"value": 1.0 / (secs * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"one oracle solve (numpy FP64 FFT route, cached spectrum) of the same 8-Gaussian "
-                      f"density on a {n_sample}^3 grid of [-16,16]^3, {secs:.2f} s, scaled to 256^3 by the "
+                      f"density on a {n_sample}^3 grid of [-16,16]^3, {secs:.2f} s, scaled to {n[0]}^3 by the "
                       f"FFT-work ratio {scale:.2f} (M log2 M); numpy's FFT is single-threaded"}
 
 
@@ -732,6 +737,9 @@ def main():
     ap.add_argument("--ddi-derivative", choices=["grid", "kernel"], default="grid",
                     help="--kernel ddi3d: d_n d_m rho on the computational grid (the paper's Table 5) or "
                          "fused into the middle multiply")
+    ap.add_argument("--n", type=int, default=256,
+                    help="3-D kernels: grid points per axis of the 8-Gaussian workload (default 256, the "
+                         "headline workload; smaller grids are L2-resident and latency-bound)")
     ap.add_argument("--outer-pairs", default="auto",
                     help="the outer pass pairs of FP32 cubes: auto (tuned), separate, or a fused cluster "
                          "configuration 1, 2, ... (fsa_fused_configs)")
