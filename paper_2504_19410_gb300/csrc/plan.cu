@@ -1024,6 +1024,12 @@ cudaError_t tune_plan(fsa_plan* p) {
     int pick = 0;
     for (int c = 0; c <= f5g.nfused && e == cudaSuccess; ++c) {
       e = run_pair(dir, c);  // warm-up
+      if (c > 0 && (e == cudaErrorInvalidConfiguration || e == cudaErrorInvalidClusterSize)) {
+        // a cluster configuration this device cannot place: not a candidate
+        cudaGetLastError();
+        e = cudaSuccess;
+        continue;
+      }
       float tmin = 1e30f;
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
         cudaEventRecord(e0, s);
