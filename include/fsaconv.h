@@ -126,7 +126,8 @@ typedef struct {
   int device;
   int generated;            /* 1 once fsa_tensor_generate has been enqueued           */
   int arithmetic;           /* 0 FP32; FP64 plans: 1 native FP64, 2 double-word       */
-  int launches_per_apply;   /* kernel launches of one fsa_apply (2 + 3 x plane slabs)  */
+  int launches_per_apply;   /* kernel launches of one fsa_apply: 2 + 3 x plane slabs, */
+                            /* one fewer per fused outer pair (fused_fwd, fused_inv)  */
   size_t workspace_bytes;   /* device scratch the plan owns                           */
   size_t spectrum_bytes;    /* device bytes of the stored spectrum octant             */
   const void* spectrum;     /* device pointer: (n0+1) x (n1+1) x (n2+1) dtype, C order */
