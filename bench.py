@@ -513,7 +513,8 @@ def bench_batched(args, fsa, W, torch, stream):
            "value": len(dens) / (tb * 1e-3), "unit": UNIT, "ms_per_batch": tb,
            "sequential_solves_per_s": len(dens) / (ts * 1e-3), "ms_sequential": ts,
            "step_roofline_frac_27V_model": bytes_model / (hbm_peak * 1e9) / (tb * 1e-3),
-           "gpu_launches_per_batch": 5 * len(hist) * 1}
+           # one launch per pass per shape group (3 or 4 where an outer pair runs fused)
+           "gpu_launches_per_batch": sum({tuple(p.n): p.info.launches_per_apply for p in plans}.values())}
     for p in plans:
         p.close()
     del rhos, phis
@@ -555,7 +556,9 @@ def bench_many(args, fsa, W, torch, stream):
         ts = e0.elapsed_time(e1) / reps
         out[f"{n}^3 x{K}"] = {"value": K / (tm * 1e-3), "unit": UNIT, "ms_per_call": tm,
                              "sequential_solves_per_s": K / (ts * 1e-3), "ms_sequential": ts,
-                             "gpu_launches_per_call": 5}
+                             "gpu_launches_per_call": plan.info.launches_per_apply,
+                             "outer_pairs": {"forward": fused_text(plan.info.fused_fwd, 2 * n),
+                                             "inverse": fused_text(plan.info.fused_inv, 2 * n)}}
         plan.close()
         del rhos, phis
         torch.cuda.empty_cache()
