@@ -13,9 +13,9 @@ replica on its own GPU (solves are independent: replicas only, weak
 scaling), the ranks are barrier-synchronised around the timed region, the
 time is the max over ranks and the value is all ranks' solves / that time.
 
---impl reference times the CPU oracle (oracle/, numpy FP64) on the host
-cores instead: each step is one oracle solve of the same density family on
-a smaller grid, scaled to 256^3 by the ratio of FFT work (M log M).
+--impl reference times the CPU oracle (oracle/, FP64 FFT route) on the host
+cores instead: each step is one oracle solve of the same 256^3 density with
+the spectrum cached, its FFTs on every host thread (scipy).
 """
 from __future__ import annotations
 
@@ -268,6 +268,13 @@ def run_ours(args):
     hbm_peak, peak_kind = peaks()
     stream = torch.cuda.current_stream()
     out = {}
+    # measured ALU peaks of this GPU: the denominators of the ALU rooflines
+    f32_rate, f32_ms = capi.fsa_measure_alu_peak(0)
+    f64_rate, f64_ms = capi.fsa_measure_alu_peak(1)
+    alu_peaks = {"fp32_fma_gops": f32_rate / 1e9, "fp64_fma_gops": f64_rate / 1e9,
+                 "fp32_tflops": 2 * f32_rate / 1e12, "fp64_tflops": 2 * f64_rate / 1e12,
+                 "how": "fsa_measure_alu_peak: every resident thread runs 8 independent FMA chains, "
+                        f"best of 3 launches by CUDA events ({f32_ms:.2f} / {f64_ms:.2f} ms); 1 FMA = 1 op = 2 flop"}
 
     def bench_tier(dt):
         tdt = torch.float32 if dt == "f32" else torch.float64
@@ -333,20 +340,18 @@ def run_ours(args):
                     "traffic": (None if plane or args.kernel == "ddi3d" or args.n != 256
                                 else read_traffic(kname, "c2_256", dt))}
         roof = hbm_roof
-        if arith == "double-word" and kname == "col_mid" and not plane:
-            # bound by the FP32 pipes: FP32 operations per launch over the
-            # FP32 issue peak (SMs x 128 lanes x maximum SM clock)
-            sms = torch.cuda.get_device_properties(local).multi_processor_count
-            max_mhz = clocks.get("sm_max_mhz") or 2070.0
-            alu_peak = sms * 128 * max_mhz * 1e6 / 1e9
+        if arith == "double-word" and kname == "col_mid" and not plane and args.kernel != "ddi3d":
+            # The double-word passes run on the FP32 pipes: besides the HBM
+            # roofline (the metric's), the pass's FP32 operations per launch
+            # over the MEASURED FP32 FMA rate (fsa_measure_alu_peak).
             ops = dw_mid_ops(n)
             alu = ops / (pass_ms[dom] * 1e-3) / 1e9
-            roof = {"bound": "alu", "kernel": kname, "achieved": alu, "peak": alu_peak,
-                    "unit": "Gop/s (FP32 lane operations)", "frac": alu / alu_peak,
-                    "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz max SM clock",
-                    "alg_ops_per_launch": ops, "traffic": hbm_roof["traffic"],
-                    "hbm": {k: hbm_roof[k] for k in ("achieved", "peak", "unit", "frac", "peak_kind",
-                                                     "alg_bytes_per_launch")}}
+            alu_peak = alu_peaks["fp32_fma_gops"]
+            roof = dict(hbm_roof)
+            roof["alu"] = {"bound": "alu", "achieved": alu, "peak": alu_peak,
+                           "unit": "Gop/s (FP32 lane operations)", "frac": alu / alu_peak,
+                           "peak_kind": "measured FP32 FMA rate (fsa_measure_alu_peak)",
+                           "alg_ops_per_launch": ops}
         res = {
             "value": ws * args.steps / (elapsed * 1e-3),
             "ms_per_step": elapsed / args.steps,
@@ -419,7 +424,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(min(args.cpu_n, n[0]), n)
+        cpu = cpu_baseline(d, args.kernel)
 
     if rank == 0:
         line = {
@@ -444,6 +449,7 @@ def run_ours(args):
                                  "< 129 MB L2: L2-resident, not flushed (a latency-bound small grid)")),
                        "parallelism": f"replicas x{ws}"},
             "roofline": main["roofline"],
+            "alu_peaks": alu_peaks,
             "cpu_baseline": cpu,
             "e2e": main["e2e"],
             "gpu_launches": main["gpu_launches"],
@@ -675,43 +681,78 @@ def bench_serving(args, fsa, W, torch, rank):
 
 # -------------------------------------------------------------- oracle ----
 
-def fft_work(n):
-    M = 8 * n[0] * n[1] * n[2]
-    return M * math.log2(M)
+def host_cores():
+    """Host threads this process may run on (the cgroup / affinity set)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
-def oracle_sample(n_sample):
-    """One oracle solve (FFT route, spectrum precomputed) of the 8-Gaussian
-    density family on an n_sample^3 grid of the same box; returns seconds."""
-    import workloads as W
+def oracle_timing(d, reps, workers_list, kernel="coulomb3d"):
+    """The oracle's Execution phase (FFT route with the spectrum cached, FP64,
+    numpy / scipy FFT) on density d at its own grid: the spectrum is computed
+    once (untimed, on all host threads), then each entry of workers_list
+    (None = numpy's single-threaded FFT, k = scipy's FFT on k threads) is
+    timed over ``reps`` solves; returns {workers: seconds per solve}."""
     from oracle import fsa as oracle
-    d = W.gaussian_sum(seed=2504, n=n_sample)
     rho = d.rho()
-    S = oracle.spectrum(oracle.tensor_T(d.L, d.n, d.eps))
-    t0 = time.perf_counter()
-    oracle.apply_spectrum(S, rho)
-    return time.perf_counter() - t0
+    allw = host_cores()
+    S = oracle.spectrum(oracle.tensor_T(d.L, d.n, d.eps, kernel=kernel, workers=allw), workers=allw)
+    out = {}
+    for w in workers_list:
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            oracle.apply_spectrum(S, rho, workers=w)
+            ts.append(time.perf_counter() - t0)
+        out[w] = min(ts)
+    del S
+    return out
 
 
-def cpu_baseline(n_sample, n=(256, 256, 256)):
-    secs = oracle_sample(n_sample)
-    scale = fft_work(tuple(n)) / fft_work((n_sample,) * 3)
-    return {"value": 1.0 / (secs * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one oracle solve (numpy FP64 FFT route, cached spectrum) of the same 8-Gaussian "
-                      f"density on a {n_sample}^3 grid of [-16,16]^3, {secs:.2f} s, scaled to {n[0]}^3 by the "
-                      f"FFT-work ratio {scale:.2f} (M log2 M); numpy's FFT is single-threaded"}
+def cpu_baseline(d, kernel="coulomb3d"):
+    """The oracle timed on this host's cores on the benchmarked density and
+    grid itself (no scaling): one solve on 1 thread, one on every thread; for
+    3-D grids also C1 (32^3) and the cigar (128 x 128 x 512)."""
+    import workloads as W
+    cores = host_cores()
+    n = d.n
+    kern = "coulomb3d" if kernel == "ddi3d" else kernel  # the DDI solve's FFT route is Coulomb's
+    t = oracle_timing(d, 1, [cores, None], kern)
+    three_d = len(n) == 3
+    c1 = oracle_timing(W.iso_gaussian(), 5, [cores, None]) if three_d else None
+    cig = oracle_timing(W.aniso_gaussian("cigar"), 1, [cores, None]) if three_d else None
+
+    def rate(x):
+        return {"all_cores_solves_per_s": 1.0 / x[cores], "one_core_solves_per_s": 1.0 / x[None]}
+    return {"value": 1.0 / t[cores], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one oracle solve (FFT route, FP64, spectrum cached) of the same 8-Gaussian density "
+                      f"on the same {'x'.join(map(str, n))} grid, measured (not scaled): {t[cores]:.2f} s on "
+                      f"{cores} threads (scipy FFT, workers={cores}), {t[None]:.2f} s on 1 thread (numpy FFT)",
+            "one_core": {"value": 1.0 / t[None], "unit": UNIT, "cores": 1},
+            "configs": ({"benchmarked_grid": rate(t), "c1_32": rate(c1), "cigar_128x128x512": rate(cig)}
+                        if three_d else {"benchmarked_grid": rate(t)})}
 
 
 def run_reference(args):
     ws, rank, local = dist_setup()
     if rank != 0:
         return
-    n_ref = args.ref_n
+    import workloads as W
+    from oracle import fsa as oracle
+    cores = host_cores()
+    d = W.gaussian_sum(seed=2504, n=256)
+    rho = d.rho()
+    S = oracle.spectrum(oracle.tensor_T(d.L, d.n, d.eps, workers=cores), workers=cores)
     for _ in range(args.warmup):
-        oracle_sample(n_ref)
-    secs = [oracle_sample(n_ref) for _ in range(args.steps)]
-    scale = fft_work((256, 256, 256)) / fft_work((n_ref,) * 3)
-    total = sum(secs) * scale
+        oracle.apply_spectrum(S, rho, workers=cores)
+    secs = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.apply_spectrum(S, rho, workers=cores)
+        secs.append(time.perf_counter() - t0)
+    total = sum(secs)
     value = args.steps / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -719,10 +760,10 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "c2_256: 3-D Coulomb FSA apply, 8-Gaussian density (seed 2504) on "
                                "[-16,16]^3, 256^3 grid, eps=1, spectrum cached",
-                   "grid": [256, 256, 256], "parallelism": "host cores (oracle)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step one oracle solve on a {n_ref}^3 grid of the same density "
-                                   f"family, scaled to 256^3 by the FFT-work ratio {scale:.2f}"},
+                   "grid": [256, 256, 256], "parallelism": f"host cores (oracle, {cores} threads)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step one oracle solve (FFT route, FP64, spectrum cached) of the "
+                                   f"8-Gaussian density on the 256^3 grid itself, scipy FFT on {cores} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -762,8 +803,6 @@ def main():
                     help="requests of the stream re-run through the plain FP64 single-solve path")
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered load as a fraction of capacity")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-n", type=int, default=128, help="cpu_baseline oracle sample grid (per axis)")
-    ap.add_argument("--ref-n", type=int, default=96, help="--impl reference: oracle grid per step")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -102,7 +102,8 @@ typedef enum {
 typedef struct {
   double eps;     /* FSA parameter; 0 selects min(1, R0/6), R0 = min_j 2 L_j     */
   double eps_tol; /* App. B bound R0^2 f(R0/eps) must not exceed this;         */
-                  /* 0 selects 1e-8, a negative value disables the check       */
+                  /* 0 selects App. B's 1e-16 for FSA_F64 plans and 1e-8 for  */
+                  /* FSA_F32 plans; a negative value disables the check        */
   int device;     /* CUDA device ordinal; -1 = the calling thread's current one */
   double kernel_param; /* the Yukawa kernels' lam (> 0; 0 selects 1); ignored by  */
                        /* the other kernels                                         */
@@ -205,9 +206,12 @@ fsa_status fsa_apply(const fsa_plan* plan, const void* rho, void* phi, fsa_strea
  * workspace, and the call allocates nothing.  Size limit: the workspace
  * 6 (n0+1) n1 n2 s bytes (s = 4 for FP32, 8 for FP64) must fit in 16 MiB,
  * e.g. grids up to 64^3 in both precisions; larger grids get
- * FSA_ERR_INVALID_ARG.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls on a device share the array and it keeps the
+ * FSA_ERR_INVALID_ARG.  The array is reserved on a device (its address
+ * looked up with cudaGetSymbolAddress, which loads its module) when the
+ * first plan is created there, so create plans before the caller's
+ * allocator takes the remaining memory; if that lookup failed, the first
+ * call here retries it, and that call should come before any stream
+ * capture.  All calls on a device share the array and it keeps the
  * last call's contents; nothing in it needs to start at zero, but calls that
  * overlap on the GPU race, so order them (one stream, or events).
  * Errors as fsa_apply. */
@@ -367,6 +371,17 @@ fsa_status fsa_device_fault(int device, unsigned int* code, int clear);
  * Errors: FSA_ERR_INVALID_ARG (code NULL), FSA_ERR_CUDA. */
 fsa_status fsa_wait_selftest(int device, unsigned int* code);
 
+/* Measured ALU peak (no counterpart in the paper: the denominator of the
+ * ALU rooflines of the FP64 tier, whose double-word passes run on the FP32
+ * pipes and whose native passes run on the FP64 pipe).  kind 0: FP32 fused
+ * multiply-add, kind 1: FP64 fused multiply-add.  On `device` (-1 = current)
+ * every resident thread runs 8 independent FMA chains for a fixed count;
+ * the best of 3 timed launches (after one warm-up) gives *lane_ops_per_s
+ * (one FMA = one lane operation = 2 flops); *ms (may be NULL) receives that
+ * launch's time.  Synchronous, a few ms per kind.  Errors:
+ * FSA_ERR_INVALID_ARG (NULL result, kind not 0 or 1), FSA_ERR_CUDA. */
+fsa_status fsa_measure_alu_peak(int device, int kind, double* lane_ops_per_s, float* ms);
+
 /* ---------------------------------------------------------------- serving -- */
 
 typedef struct fsa_server fsa_server;
@@ -374,7 +389,9 @@ typedef struct fsa_server fsa_server;
 typedef struct {
   int max_inflight;        /* requests on the GPU at once (0 = 64)                    */
   int streams;             /* device streams the requests are spread over (0 = 8)    */
-  double hbm_fraction;     /* admit while workspace fits this share of free HBM (0 = 0.9) */
+  double hbm_fraction;     /* admit while plans + workspaces fit this share of the
+                              device memory free now plus what the server holds,
+                              re-read before each admission round (0 = 0.9)      */
   size_t hbm_budget_bytes; /* hard cap on server-held device bytes (0 = none)        */
   int plan_cache_max;      /* plans kept resident (0 = 64), least recently used out  */
   int queue_max;           /* pending requests before FSA_ERR_BUSY (0 = 1 << 20)     */
@@ -382,14 +399,15 @@ typedef struct {
 } fsa_serve_opts;
 
 typedef struct {
-  fsa_kernel kernel;
-  int d;          /* 3 */
+  fsa_kernel kernel; /* any kernel but FSA_KERNEL_DDI3D (its plans need dipoles) */
+  int d;          /* the kernel's dimension: 3, or 2 for the plane kernels (n[2], L[2] ignored) */
   double L[3];
   int n[3];
   fsa_dtype dtype;
   double eps;     /* 0 = default rule */
   const void* rho; /* device, caller-owned until the ticket is DONE or FAILED */
   void* phi;       /* device, caller-owned */
+  double kernel_param; /* Yukawa kernels: lam (0 selects 1); ignored by the others */
 } fsa_request;
 
 typedef enum {
@@ -414,9 +432,10 @@ typedef struct {
   int queued;
 } fsa_serve_stats;
 
-/* A serving loop: one host thread admits queued requests while their
- * workspace fits the free-HBM budget and fewer than max_inflight are on the
- * GPU, launches each on one of the server's streams (requests that arrive
+/* A serving loop: one host thread admits queued requests while their plan
+ * (on a cache miss: the spectrum octant, for FP64 plans also its double-word
+ * copy, and the generation scratch) and workspace fit the HBM budget and
+ * fewer than max_inflight are on the GPU, launches each on one of the server's streams (requests that arrive
  * while others run are admitted as soon as a slot and memory free up, and
  * their kernels overlap on the device), keeps plans resident in an LRU
  * cache, and marks a ticket DONE when its completion event has fired.

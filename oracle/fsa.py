@@ -2,8 +2,10 @@
 
 Every function follows one passage of the paper (Liu & Zhang, "Fast
 convolution solver based on far-field smooth approximation",
-arXiv 2504.19410).  Library primitives used as steps: numpy's FFT and
-scipy's erf / erfc / quad.  There is no pruning, blocking or symmetry trick:
+arXiv 2504.19410).  Library primitives used as steps: numpy's FFT (or,
+where a caller asks for threads, scipy's FFT of the same definition run on
+several host cores) and scipy's erf / erfc / quad.  There is no pruning,
+blocking or symmetry trick:
 the convolution tensor T is built on the full doubled grid and the
 convolution is a full-size complex FFT product, as Sec. 2.3 states it.
 
@@ -389,27 +391,44 @@ def fourier_W(L, n, eps, kernel="coulomb3d"):
     return kernel_fns(kernel)[1](k, eps)
 
 
-def tensor_T2(L, n, eps, return_imag=False, kernel="coulomb3d"):
+def tensor_T2(L, n, eps, return_imag=False, kernel="coulomb3d", workers=None):
     """T^(2)_o = (2N)^{-d} sum_p W(mu_p) exp(2 pi i p.o / 2N) (Sec. 2.2,
     Eq. Tensor2; Eq. TensorAnis second term): numpy's ifftn carries exactly
     this sign and normalisation.  The imaginary part vanishes in exact
     arithmetic (W is real and even); its max is returned on request."""
-    T2 = np.fft.ifftn(fourier_W(L, n, eps, kernel))
+    T2 = _ifftn(fourier_W(L, n, eps, kernel), workers)
     if return_imag:
         return T2.real.copy(), float(np.abs(T2.imag).max())
     return T2.real.copy()
 
 
-def tensor_T(L, n, eps, kernel="coulomb3d"):
+def tensor_T(L, n, eps, kernel="coulomb3d", workers=None):
     """T = T^(1) + T^(2) (Sec. 2.3, Eq. DiscConv)."""
-    return tensor_T1(L, n, eps, kernel) + tensor_T2(L, n, eps, kernel=kernel)
+    return tensor_T1(L, n, eps, kernel) + tensor_T2(L, n, eps, kernel=kernel, workers=workers)
 
 
-def spectrum(T):
+def _fftn(a, workers):
+    """The unnormalised forward DFT over all axes: numpy's, or with
+    ``workers`` threads scipy's (the same transform, lines split over cores)."""
+    if workers is None:
+        return np.fft.fftn(a)
+    import scipy.fft
+    return scipy.fft.fftn(a, workers=workers)
+
+
+def _ifftn(a, workers):
+    """The inverse DFT with the 1/size normalisation, as _fftn."""
+    if workers is None:
+        return np.fft.ifftn(a)
+    import scipy.fft
+    return scipy.fft.ifftn(a, workers=workers)
+
+
+def spectrum(T, workers=None):
     """DFT over the doubled grid of T, divided by prod_j 2 n_j (the inverse
     transform's normalisation), real part.  T is real and even per axis
     (Sec. 2.3), so this is real up to round-off."""
-    S = np.fft.fftn(T)
+    S = _fftn(T, workers)
     return S.real / T.size
 
 
@@ -432,13 +451,14 @@ def apply_fft(T, rho):
     return out.real[box].copy()
 
 
-def apply_spectrum(S, rho):
+def apply_spectrum(S, rho, workers=None):
     """Same as apply_fft with the spectrum of T (from ``spectrum``) cached:
-    the 'Execution' phase of Example 2."""
+    the 'Execution' phase of Example 2.  ``workers``: host threads for the
+    two FFTs (None: numpy's single-threaded FFT)."""
     box = tuple(slice(0, nj) for nj in rho.shape)
     pad = np.zeros(S.shape)
     pad[box] = rho
-    out = np.fft.ifftn(S * S.size * np.fft.fftn(pad))
+    out = _ifftn(S * S.size * _fftn(pad, workers), workers)
     return out.real[box].copy()
 
 

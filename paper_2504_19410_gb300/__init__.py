@@ -132,9 +132,9 @@ class Server:
         self.handle = capi.fsa_serve_create(max_inflight, streams, hbm_fraction, hbm_budget_bytes,
                                             plan_cache_max, queue_max, device)
 
-    def submit(self, L, n, dtype, rho, phi, eps=0.0, kernel="coulomb3d"):
+    def submit(self, L, n, dtype, rho, phi, eps=0.0, kernel="coulomb3d", kernel_param=0.0):
         k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
-        return capi.fsa_serve_submit(self.handle, L, n, _DT[dtype], rho, phi, eps, k)
+        return capi.fsa_serve_submit(self.handle, L, n, _DT[dtype], rho, phi, eps, k, kernel_param)
 
     def poll(self, ticket, timeout=0.0):
         """(state, times); times has submit_s, admit_s, done_s, plan_hit, status."""

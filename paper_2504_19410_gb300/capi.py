@@ -69,7 +69,8 @@ class ServeOpts(C.Structure):
 
 class Request(C.Structure):
     _fields_ = [("kernel", C.c_int), ("d", C.c_int), ("L", C.c_double * 3), ("n", C.c_int * 3),
-                ("dtype", C.c_int), ("eps", C.c_double), ("rho", C.c_void_p), ("phi", C.c_void_p)]
+                ("dtype", C.c_int), ("eps", C.c_double), ("rho", C.c_void_p), ("phi", C.c_void_p),
+                ("kernel_param", C.c_double)]
 
 
 class ReqTimes(C.Structure):
@@ -109,6 +110,7 @@ _PROTOS = {
     "fsa_fused_select": (C.c_int, [C.c_int, C.c_int, C.c_int]),
     "fsa_device_fault": (C.c_int, [C.c_int, C.POINTER(C.c_uint), C.c_int]),
     "fsa_wait_selftest": (C.c_int, [C.c_int, C.POINTER(C.c_uint)]),
+    "fsa_measure_alu_peak": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_float)]),
     "fsa_profiler_create": (C.c_int, [C.POINTER(_VP), C.c_int]),
     "fsa_apply_profiled": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "fsa_profiler_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]),
@@ -284,6 +286,14 @@ def fsa_device_fault(device=-1, clear=False):
     return code.value
 
 
+def fsa_measure_alu_peak(kind, device=-1):
+    """(lane operations per second, ms of the timed launch); kind 0 = FP32 FMA,
+    1 = FP64 FMA (one FMA = one lane operation)."""
+    rate, ms = C.c_double(), C.c_float()
+    check(lib().fsa_measure_alu_peak(int(device), int(kind), C.byref(rate), C.byref(ms)))
+    return rate.value, ms.value
+
+
 def fsa_wait_selftest(device=-1):
     """Runs one bounded device wait that nothing completes; returns the fault
     word it left (1 = the wait gave up and was recorded)."""
@@ -323,9 +333,11 @@ def fsa_serve_create(max_inflight=0, streams=0, hbm_fraction=0.0, hbm_budget_byt
     return h.value
 
 
-def fsa_serve_submit(server, L, n, dtype, rho, phi, eps=0.0, kernel=FSA_KERNEL_COULOMB3D):
-    req = Request(kernel, len(n), (C.c_double * 3)(*map(float, L)), (C.c_int * 3)(*map(int, n)), int(dtype),
-                  float(eps), _ptr(rho), _ptr(phi))
+def fsa_serve_submit(server, L, n, dtype, rho, phi, eps=0.0, kernel=FSA_KERNEL_COULOMB3D, kernel_param=0.0):
+    L3 = list(map(float, L)) + [1.0] * (3 - len(L))
+    n3 = list(map(int, n)) + [1] * (3 - len(n))
+    req = Request(kernel, len(n), (C.c_double * 3)(*L3), (C.c_int * 3)(*n3), int(dtype),
+                  float(eps), _ptr(rho), _ptr(phi), float(kernel_param))
     t = C.c_uint64()
     check(lib().fsa_serve_submit(server, C.byref(req), C.byref(t)))
     return t.value

@@ -140,6 +140,9 @@ void batched_forget_plan(const fsa_plan* p);
 
 // Tensor generation (tensor_gen.cu), all FP64.
 cudaError_t tensorgen_prepare(int M);
+// Look up (and so reserve) fsa_apply_noalloc's static scratch on device dev,
+// which must be current; once per device (noalloc.cu).
+cudaError_t noalloc_resolve(int dev);
 cudaError_t tensorgen_init_twiddles();
 // param: the kernel's parameter (the Yukawa lam), ignored by the others
 cudaError_t tensorgen_run(fsa_kernel kernel, const int n[3], const double L[3], double eps, double param,

@@ -11,10 +11,17 @@
 // kNoallocScratchBytes that every GPU which loads the library holds until the
 // process exits.  It calls no allocating routine.
 //
-// Set-up: the first call on a device, with that device current, looks up the
-// array's device address with cudaGetSymbolAddress (in host code the array's
-// name is only a host-side stand-in, not a device address) and keeps it for
-// later calls.  That first call should come before any stream capture.
+// Set-up: the array's device address is looked up with cudaGetSymbolAddress
+// (in host code the array's name is only a host-side stand-in, not a device
+// address), once per device, with that device current, and kept.  The lookup
+// is also what makes the driver load this file's module and so reserve the
+// 16 MiB: the library's modules load lazily, and this one has no kernel that
+// could load it earlier.  So plan creation does the lookup (noalloc_resolve,
+// once per device, when the first plan is made there): by the time a caller
+// applies, the array is held and the apply allocates nothing.  Should that
+// lookup fail at plan creation, the first fsa_apply_noalloc call retries it
+// and reports the error; that first call should then come before any stream
+// capture.
 //
 // Sharing: every call on a device uses the same array, and it keeps the last
 // call's contents.  Nothing in it needs to start at zero (each pass writes
@@ -35,9 +42,32 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kMaxDevices] = {};  // device address of the array, per device
 
+// The array's device address on the current device (dev), looked up once.
+cudaError_t resolve_locked(int dev, void** out) {
+  if (!g_noalloc_addr[dev]) {
+    void* addr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = addr;
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
 }  // namespace
 
 using namespace fsa;
+
+namespace fsa {
+
+cudaError_t noalloc_resolve(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  void* addr = nullptr;
+  return resolve_locked(dev, &addr);
+}
+
+}  // namespace fsa
 
 extern "C" fsa_status fsa_apply_noalloc(const fsa_plan* p, const void* rho, void* phi, fsa_stream_t stream) {
   if (!p || !rho || !phi) return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_noalloc: NULL argument");
@@ -65,12 +95,7 @@ extern "C" fsa_status fsa_apply_noalloc(const fsa_plan* p, const void* rho, void
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[p->device]) {
-      void* addr = nullptr;
-      e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
-      if (e == cudaSuccess) g_noalloc_addr[p->device] = addr;
-    }
-    base = g_noalloc_addr[p->device];
+    e = resolve_locked(p->device, &base);
   }
   if (e == cudaSuccess) {
     const void* r[1] = {rho};

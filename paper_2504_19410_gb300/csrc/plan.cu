@@ -617,6 +617,10 @@ fsa_status prepare_device(int dev, fsa_dtype dt, const int* n, int d, bool unpad
     if (e != cudaSuccess) return cuda_error(e, "twiddle table upload");
     e = ensure_fault_word_locked(dev);
     if (e != cudaSuccess) return cuda_error(e, "fault word");
+    // fsa_apply_noalloc's static scratch: reserved now, while plans are being
+    // made, so that the allocation-free apply finds it held.  Not fatal here:
+    // that entry point retries the lookup and reports its own error.
+    if (noalloc_resolve(dev) != cudaSuccess) cudaGetLastError();
     g_tw_ready.insert(dev);
   }
   for (int jj = 0; jj < (unpadded ? 2 * d : d); ++jj) {  // a plane's unit third axis has no kernels
@@ -768,9 +772,22 @@ size_t plan_workspace_bytes(const int* n, fsa_dtype dt) {
   return K0 * n[1] * n[2] * 2 * s + K0 * n[1] * (2 * (size_t)n[2]) * 2 * s;
 }
 
+// Reals in the spectrum octant: (n0+1)(n1+1)(n2+1), or (n0+1)(n1+1) for a
+// plane (held with n[2] = 1).
+static size_t octant_count(const int* n, int d) {
+  return (size_t)(n[0] + 1) * (n[1] + 1) * (d == 2 ? 1 : n[2] + 1);
+}
+
 // FP32 plans generate in FP64 in a scratch octant; FP64 plans in place.
-size_t plan_gen_scratch_bytes(const int* n, fsa_dtype dt) {
-  return dt == FSA_F64 ? 0 : (size_t)(n[0] + 1) * (n[1] + 1) * (n[2] + 1) * 8;
+size_t plan_gen_scratch_bytes(const int* n, fsa_dtype dt, int d) {
+  return dt == FSA_F64 ? 0 : octant_count(n, d) * 8;
+}
+
+// Device bytes a plan without workspace holds: the spectrum octant in its
+// dtype, and for FP64 plans the double-word copy of it (same size).
+size_t plan_resident_bytes(const int* n, fsa_dtype dt, int d) {
+  const size_t s = dt == FSA_F32 ? 4 : 8;
+  return octant_count(n, d) * s * (dt == FSA_F64 ? 2 : 1);
 }
 
 cudaError_t tune_plan(fsa_plan* p);
@@ -795,7 +812,10 @@ fsa_status plan_validate(fsa_kernel kernel, const double* L, const int* n, fsa_d
   const double R0 = 2.0 * (d == 2 ? std::min(L[0], L[1]) : std::min(L[0], std::min(L[1], L[2])));
   const double eps = eps_in > 0 ? eps_in : std::min(1.0, R0 / 6.0);
   const double bound = appendix_b_bound_kernel_impl(kernel, R0, eps, param);
-  const double tol = eps_tol == 0 ? 1e-8 : eps_tol;
+  // Default tolerance: App. B's eps_tol = 1e-16 (16 digits) for FP64 plans,
+  // so that an FP64 solve cannot carry a far-field truncation far above its
+  // round-off; 1e-8 for FP32 plans (round-off near 1e-7).
+  const double tol = eps_tol == 0 ? (dtype == FSA_F64 ? 1e-16 : 1e-8) : eps_tol;
   if (tol > 0 && !(bound <= tol)) {
     char buf[256];
     snprintf(buf, sizeof buf, "fsa_plan_create: eps = %g fails App. B: int_R0^inf |U - U^eps| r^2 dr = %.3g > %.3g (R0 = %g)",
@@ -842,7 +862,7 @@ fsa_status plan_create_core(fsa_plan** out, fsa_kernel kernel, const double* L, 
   p->dtype = dtype;
   p->device = dev;
   const size_t s = dtype == FSA_F32 ? 4 : 8;
-  p->spectrum_bytes = (size_t)(n[0] + 1) * (n[1] + 1) * (d == 2 ? 1 : n[2] + 1) * s;
+  p->spectrum_bytes = octant_count(n, d) * s;
   p->x_bytes = (size_t)(n[0] + 1) * n[1] * n[2] * 2 * s;
   p->ws_bytes = with_workspace ? plan_workspace_bytes(n, dtype) + extra_ws : 0;
   // The workspace always holds the FP64 generation scratch of an FP32 plan.
@@ -870,8 +890,8 @@ fsa_status plan_create_core(fsa_plan** out, fsa_kernel kernel, const double* L, 
 }
 
 fsa_status plan_create_internal(fsa_plan** out, fsa_kernel kernel, const double* L, const int* n, fsa_dtype dtype,
-                                double eps_in, double eps_tol, bool with_workspace) {
-  return plan_create_core(out, kernel, L, n, dtype, eps_in, eps_tol, with_workspace, 0, false);
+                                double eps_in, double eps_tol, bool with_workspace, double param) {
+  return plan_create_core(out, kernel, L, n, dtype, eps_in, eps_tol, with_workspace, 0, false, param);
 }
 
 // The DDI parameter block (fsa_consts.h) of a plan: transform lengths

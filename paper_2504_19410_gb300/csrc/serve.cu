@@ -5,9 +5,12 @@
 //      workspace goes back to the stream-ordered pool, their ticket -> DONE);
 //   2. admits queued requests in arrival order while fewer than max_inflight
 //      are on the GPU and the bytes the server holds (resident plans plus
-//      in-flight workspaces) plus the request's need fit the HBM budget
-//      (hbm_fraction x free device memory when the server started, capped by
-//      hbm_budget_bytes); idle plans are evicted LRU-first to make room;
+//      in-flight workspaces) plus the request's need fit the HBM budget:
+//      hbm_fraction x (device memory free now + what the server holds),
+//      re-read from the driver before each admission round so that memory
+//      taken or returned by other users of the device counts, capped by
+//      hbm_budget_bytes; idle plans are evicted LRU-first, and workspace the
+//      pool keeps but no request uses is trimmed, to make room;
 //   3. enqueues each admitted request's five passes on one of its streams
 //      (round robin) with a workspace from cudaMallocAsync, so requests that
 //      arrive while others run start as soon as a slot and memory free up
@@ -16,6 +19,7 @@
 // its own workspace with its plan's spectrum; nothing is reduced across
 // requests.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -31,10 +35,11 @@
 
 namespace fsa {
 fsa_status plan_create_internal(fsa_plan** out, fsa_kernel kernel, const double* L, const int* n, fsa_dtype dtype,
-                                double eps, double eps_tol, bool with_workspace);
+                                double eps, double eps_tol, bool with_workspace, double param);
 cudaError_t plan_generate_into(fsa_plan* p, void* scratch, cudaStream_t s);
 size_t plan_workspace_bytes(const int* n, fsa_dtype dt);
-size_t plan_gen_scratch_bytes(const int* n, fsa_dtype dt);
+size_t plan_gen_scratch_bytes(const int* n, fsa_dtype dt, int d);
+size_t plan_resident_bytes(const int* n, fsa_dtype dt, int d);
 }  // namespace fsa
 
 using namespace fsa;
@@ -52,6 +57,7 @@ struct PlanKey {
   double L[3];
   int dt;
   double eps;
+  double param;
   bool operator<(const PlanKey& o) const {
     return std::memcmp(this, &o, sizeof(PlanKey)) < 0;
   }
@@ -97,6 +103,8 @@ struct fsa_server {
   std::map<PlanKey, CachedPlan> plans;
   std::list<PlanKey> plan_lru;  // front = most recent
   size_t held = 0;              // plan bytes + in-flight workspace bytes
+  size_t ws_inflight = 0;       // the in-flight workspace part of held
+  size_t budget_cap = 0;        // hbm_budget_bytes (0 = none)
   fsa_serve_stats st{};
 };
 
@@ -135,6 +143,31 @@ void evict_one(fsa_server* s, const PlanKey& keep) {
   }
 }
 
+// Bytes the workspace pool keeps reserved on the device (in use or idle).
+size_t pool_reserved(fsa_server* s) {
+  uint64_t r = 0;
+  if (cudaMemPoolGetAttribute(s->pool, cudaMemPoolAttrReservedMemCurrent, &r) != cudaSuccess) {
+    cudaGetLastError();
+    return s->ws_inflight;
+  }
+  return (size_t)r;
+}
+
+// Re-read the device's free memory: the budget is hbm_fraction x (free now +
+// what this server holds on the device), so that memory other users take or
+// return since the server started counts.  Capped by hbm_budget_bytes.
+void refresh_budget(fsa_server* s) {
+  size_t freeb = 0, total = 0;
+  if (cudaMemGetInfo(&freeb, &total) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const size_t mine = (s->held - s->ws_inflight) + std::max(pool_reserved(s), s->ws_inflight);
+  size_t b = (size_t)(s->o.hbm_fraction * (double)(freeb + mine));
+  if (s->budget_cap && s->budget_cap < b) b = s->budget_cap;
+  s->budget = b;
+}
+
 // Try to start request `id`; returns false if it must wait for room.
 bool try_admit(fsa_server* s, uint64_t id) {
   Req& q = s->reqs[id];
@@ -142,15 +175,21 @@ bool try_admit(fsa_server* s, uint64_t id) {
   const bool hit = s->plans.count(q.key) != 0;
   size_t plan_bytes = 0, gen_scratch = 0;
   if (!hit) {
-    const size_t so = q.r.dtype == FSA_F32 ? 4 : 8;
-    plan_bytes = (size_t)(q.r.n[0] + 1) * (q.r.n[1] + 1) * (q.r.n[2] + 1) * so;
-    gen_scratch = plan_gen_scratch_bytes(q.r.n, q.r.dtype);
+    plan_bytes = plan_resident_bytes(q.r.n, q.r.dtype, q.r.d);
+    gen_scratch = plan_gen_scratch_bytes(q.r.n, q.r.dtype, q.r.d);
   }
   const size_t need = ws + plan_bytes + gen_scratch;
   // make_room never evicts this request's own plan, so `hit` stays valid
   if (s->held + need > s->budget) make_room(s, need, q.key);
   if ((int)s->plans.size() >= s->o.plan_cache_max && !hit) evict_one(s, q.key);
   if (s->held + need > s->budget && !(s->inflight.empty() && s->held == 0)) return false;
+  // Workspace the pool keeps from finished requests is reused first; when the
+  // pool holds more idle memory than the new request can reuse and the total
+  // would pass the budget, give the idle part back before allocating.
+  if (s->held - s->ws_inflight + pool_reserved(s) + plan_bytes + gen_scratch + ws > s->budget) {
+    cudaMemPoolTrimTo(s->pool, s->ws_inflight);
+    cudaGetLastError();
+  }
   auto pit = s->plans.find(q.key);
 
   cudaStream_t stream = s->streams[s->rr++ % s->streams.size()];
@@ -158,7 +197,9 @@ bool try_admit(fsa_server* s, uint64_t id) {
   cudaError_t e = cudaSuccess;
   if (!hit) {
     fsa_plan* p = nullptr;
-    status = plan_create_internal(&p, q.r.kernel, q.r.L, q.r.n, q.r.dtype, q.r.eps, 0.0, false);
+    status = plan_create_internal(&p, q.r.kernel, q.r.L, q.r.n, q.r.dtype, q.r.eps, 0.0, false, q.r.kernel_param);
+    if (status == FSA_OK)  // charge what the plan really holds
+      plan_bytes = p->spectrum_bytes + (p->spectrum_dw ? p->spectrum_bytes : 0);
     // server plans have no workspace of their own; FP64 arithmetic follows the
     // per-shape choice made by earlier plans (double-word by default)
     if (status == FSA_OK) {
@@ -235,6 +276,7 @@ bool try_admit(fsa_server* s, uint64_t id) {
   q.ws_bytes = ws;
   q.stream = stream;
   s->held += ws;
+  s->ws_inflight += ws;
   q.state = FSA_REQ_RUNNING;
   s->inflight.push_back(id);
   return true;
@@ -261,6 +303,7 @@ void retire(fsa_server* s) {
     s->free_events.push_back(q.done);
     q.done = nullptr;
     s->held -= q.ws_bytes;
+    s->ws_inflight -= q.ws_bytes;
     auto pit = s->plans.find(q.key);
     if (pit != s->plans.end()) pit->second.refs--;
     s->inflight[i] = s->inflight.back();
@@ -275,6 +318,7 @@ void loop(fsa_server* s) {
     const size_t before = s->inflight.size();
     retire(s);
     bool changed = s->inflight.size() != before;
+    if (!s->queue.empty() && (int)s->inflight.size() < s->o.max_inflight) refresh_budget(s);
     while (!s->queue.empty() && (int)s->inflight.size() < s->o.max_inflight) {
       const uint64_t id = s->queue.front();
       if (!try_admit(s, id)) break;
@@ -291,7 +335,9 @@ void loop(fsa_server* s) {
 }
 
 bool valid_request(const fsa_request* r) {
-  if (!r || r->kernel < FSA_KERNEL_COULOMB3D || r->kernel > FSA_KERNEL_BIHARMONIC2D) return false;
+  if (!r || r->kernel < FSA_KERNEL_COULOMB3D || r->kernel > FSA_KERNEL_YUKAWA2D) return false;
+  if (r->kernel == FSA_KERNEL_DDI3D) return false;  // DDI plans need dipoles: fsa_plan_create_ddi3d
+  if (!(r->kernel_param >= 0) || !std::isfinite(r->kernel_param)) return false;
   if (r->d != kernel_dim(r->kernel)) return false;
   if (r->dtype != FSA_F32 && r->dtype != FSA_F64) return false;
   if (!r->rho || !r->phi || (((uintptr_t)r->rho | (uintptr_t)r->phi) & 15u)) return false;
@@ -327,6 +373,7 @@ fsa_status fsa_serve_create(fsa_server** out, const fsa_serve_opts* opts) {
   size_t freeb = 0, total = 0;
   if (e == cudaSuccess) e = cudaMemGetInfo(&freeb, &total);
   s->budget = (size_t)(o.hbm_fraction * (double)freeb);
+  s->budget_cap = o.hbm_budget_bytes;
   if (o.hbm_budget_bytes && o.hbm_budget_bytes < s->budget) s->budget = o.hbm_budget_bytes;
   for (int i = 0; e == cudaSuccess && i < o.streams; ++i) {
     cudaStream_t st;
@@ -379,6 +426,11 @@ fsa_status fsa_serve_submit(fsa_server* s, const fsa_request* req, uint64_t* tic
   q.key.kernel = req->kernel;
   q.key.dt = req->dtype;
   q.key.eps = req->eps;
+  // Yukawa: 0 selects lam = 1, so both spellings share a plan; other kernels
+  // ignore the parameter
+  const bool yuk = req->kernel == FSA_KERNEL_YUKAWA3D || req->kernel == FSA_KERNEL_YUKAWA2D;
+  q.r.kernel_param = yuk ? (req->kernel_param > 0 ? req->kernel_param : 1.0) : 0.0;
+  q.key.param = q.r.kernel_param;
   s->queue.push_back(id);
   s->st.submitted++;
   *ticket = id;

@@ -98,6 +98,23 @@ def test_plan_create_rejects_before_touching_the_device(capi, n, L, kw, status):
     assert capi.fsa_status_string(ei.value.status) == status
 
 
+def test_fp64_plans_default_to_the_16_digit_tolerance(capi):
+    """App. B: eps_tol = 1e-16 for 16 digits.  eps = 3 on [-8,8]^3 (R0 = 16,
+    c = 5.33) has a bound between 1e-16 and 1e-8: an FP32 plan takes it by
+    default, an FP64 plan rejects it unless the caller loosens eps_tol."""
+    b = capi.fsa_appendix_b_bound(16.0, 3.0)
+    assert 1e-16 < b < 1e-8
+    with pytest.raises(capi.FsaError) as ei:
+        capi.fsa_plan_create(capi.FSA_KERNEL_COULOMB3D, 3, (8, 8, 8), (8, 8, 8), capi.FSA_F64, eps=3.0)
+    assert ei.value.status == capi.FSA_ERR_EPS
+    for dt, kw in ((capi.FSA_F32, {}), (capi.FSA_F64, {"eps_tol": 1e-8})):
+        try:
+            capi.fsa_plan_destroy(capi.fsa_plan_create(capi.FSA_KERNEL_COULOMB3D, 3, (8, 8, 8), (8, 8, 8), dt,
+                                                       eps=3.0, **kw))
+        except capi.FsaError as e:  # without a device, creation stops after validation
+            assert e.status != capi.FSA_ERR_EPS
+
+
 def test_plan_create_rejects_dimension_and_kernel(capi):
     with pytest.raises(capi.FsaError) as ei:
         capi.fsa_plan_create(capi.FSA_KERNEL_COULOMB3D, 2, (1, 1, 1), (8, 8, 8), capi.FSA_F32)

@@ -1,0 +1,169 @@
+"""Every output of the full-size workloads against the oracle.
+
+Eq. DiscConv (Sec. 2.3) has one discrete answer; the oracle reaches it by the
+paper's literal route (T = T^(1) + iDFT(W) on the doubled grid, zero-padded
+FFT, product, inverse FFT, crop) in numpy FP64.  These tests compare the CUDA
+path with it at EVERY grid point of:
+
+* the headline workload: 8 seeded Gaussians on [-16,16]^3, 256^3, eps = 1;
+* the cigar 128 x 128 x 512 and the pancake 512 x 512 x 128 (Sec. 2.4's
+  anisotropic boxes, gamma = 8, eps = 0.4);
+
+each in FP32 (<= 2e-6) and in the FP64 tier (<= 1e-12), under the autotuned
+launch configuration that ``bench.py`` times and under every forced kernel
+generation (gen1: Stockham radix-8 FP32 and native FP64; gen2: two-step
+register FP32 and double-word FP64; gen3: + prefetching middle pass; gen4: +
+bulk-copy row passes).  The transform-length-512 middle passes and their tile
+edges are exercised only at these sizes.  Each result's max-norm error against
+the oracle and against the exact potential is printed.
+
+A C4-style batch (sizes 64..256, gamma in {1, 4, 8}) through one
+``fsa_apply_batched`` call is compared with the oracle too, on two calls in a
+row (the second replays the captured graph).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import closed_forms as cf
+from oracle import fsa as oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 2e-6}
+# autotune modes of fsa_autotune_set: 1 = tuned (the bench's configuration),
+# 2..5 = forced generations 1..4
+MODES = [("tuned", 1), ("gen1", 2), ("gen2", 3), ("gen3", 4), ("gen4", 5)]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2504_19410_gb300 as fsa
+    return fsa
+
+
+def _oracle_solution(d, rho):
+    S = oracle.spectrum(oracle.tensor_T(d.L, d.n, d.eps))
+    want = oracle.apply_spectrum(S, rho)
+    del S
+    return want
+
+
+def _gpu(lib, d, rho, dt, mode):
+    import torch
+    from paper_2504_19410_gb300 import capi
+    capi.fsa_device_fault(clear=True)
+    capi.fsa_autotune_set(mode)
+    try:
+        plan = lib.Plan(d.L, d.n, dt, eps=d.eps)
+        x = torch.from_numpy(np.ascontiguousarray(rho, dtype=np.float64 if dt == "f64" else np.float32)).cuda()
+        out = plan.apply(x)
+        torch.cuda.synchronize()
+        arith = plan.info.arithmetic
+        got = out.double().cpu().numpy()
+        plan.close()
+        del x, out
+    finally:
+        capi.fsa_autotune_set(1)
+    assert capi.fsa_device_fault(clear=True) == 0
+    return got, arith
+
+
+def _check_all_modes(lib, d, exact_fn, label):
+    rho = d.rho()
+    want = _oracle_solution(d, rho)
+    failures, lines = [], []
+    for dt in ("f64", "f32"):
+        for name, mode in MODES:
+            got, arith = _gpu(lib, d, rho, dt, mode)
+            err = oracle.rel_error(got, want)
+            e_exact = exact_fn(got)
+            lines.append(f"{label} {dt} {name} (arithmetic {arith}): every output vs oracle {err:.3e}, "
+                         f"vs exact potential {e_exact:.3e}")
+            if not err <= TOL[dt]:
+                failures.append((dt, name, err))
+            del got
+    print("\n" + "\n".join(lines))
+    assert not failures, failures
+
+
+def test_c2_256_every_output(lib):
+    """Headline workload, 16.8 M outputs per solve, 10 solves."""
+    d = W.gaussian_sum(seed=2504)
+    exact = cf.density_potential(d)
+    _check_all_modes(lib, d, lambda got: oracle.rel_error(got, exact), "C2 256^3")
+
+
+def _sampled_exact(d):
+    pts = [tuple(int(v) for v in p) for p in np.random.default_rng(11).integers(0, d.n, size=(24, 3))]
+    pts += [tuple(x // 2 for x in d.n), (0, 0, 0), tuple(x - 1 for x in d.n)]
+    exact = cf.density_potential_points(d, np.array(pts))
+
+    def fn(got):
+        s = np.array([got[p] for p in pts])
+        return float(np.max(np.abs(s - exact)) / np.max(np.abs(exact)))
+    return fn
+
+
+@pytest.mark.parametrize("kind", ["cigar", "pancake"])
+def test_c3_aniso_every_output(lib, kind):
+    """Cigar 128 x 128 x 512 and pancake 512 x 512 x 128: every output against
+    the oracle; the exact potential (a 1-D integral per point) at samples."""
+    d = W.aniso_gaussian(kind)
+    _check_all_modes(lib, d, _sampled_exact(d), kind)
+
+
+def _c4_subset():
+    """From the C4 mix (seed 2504, 64 requests): the first request of every
+    (n, shape) pair, shape = isotropic / cigar / pancake (15 requests; both
+    gamma = 4 and gamma = 8 occur among them)."""
+    seen, out = set(), []
+    for d in W.batch_requests(seed=2504, count=64):
+        g = tuple(round(16.0 / l, 6) for l in d.L)
+        shape = "iso" if g[0] == g[2] else ("cigar" if g[0] > g[2] else "pancake")
+        key = (d.n[0], shape)
+        if key in seen:
+            continue
+        seen.add(key)
+        out.append(d)
+    return out
+
+
+def test_batched_c4_mix_matches_oracle(lib):
+    """One fsa_apply_batched call over a C4-style mix (every size 64..256 and
+    gamma in {1, 4, 8} that the seeded mix draws), FP32 as in C4, plus two FP64
+    plans; each result against the oracle, on two calls in a row."""
+    import torch
+    ds = _c4_subset()
+    assert {d.n[0] for d in ds} == set(W.BATCH_N)
+    specs = [(d, "f32") for d in ds] + [(ds[0], "f64"), (ds[1], "f64")]
+    cache, wants = {}, []
+    for d, _ in specs:
+        key = (d.L, d.n, d.eps)
+        if key not in cache:
+            cache[key] = oracle.spectrum(oracle.tensor_T(d.L, d.n, d.eps))
+        wants.append(oracle.apply_spectrum(cache[key], d.rho()))
+    cache.clear()
+    plans, rhos = [], []
+    for d, dt in specs:
+        plans.append(lib.Plan(d.L, d.n, dt, eps=d.eps))
+        rhos.append(torch.from_numpy(d.rho().astype(np.float64 if dt == "f64" else np.float32)).cuda())
+    outs = [torch.empty_like(r) for r in rhos]
+    lines = []
+    for call in range(2):
+        for o in outs:
+            o.fill_(float("nan"))
+        lib.apply_batched(plans, rhos, outs)
+        torch.cuda.synchronize()
+        for (d, dt), o, want in zip(specs, outs, wants):
+            err = oracle.rel_error(o.double().cpu().numpy(), want)
+            lines.append(f"batched call {call} n={d.n} L={tuple(round(x, 3) for x in d.L)} {dt}: vs oracle {err:.3e}")
+            assert err <= TOL[dt], lines[-1]
+    print("\n" + "\n".join(lines))
+    for p in plans:
+        p.close()

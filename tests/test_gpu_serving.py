@@ -189,3 +189,70 @@ def test_served_plane_requests_equal_solved_alone(lib):
         e_alone = oracle.rel_error(w.double().cpu().numpy(), ref)
         assert torch.equal(o, w), (reqs[i], e_srv, e_alone)
         assert e_srv <= (1e-12 if dt == "f64" else 2e-6), (reqs[i], e_srv)
+
+
+@pytest.mark.parametrize("kernel,L,n,lam", [("yukawa3d", (3.0, 2.5, 3.5), (16, 24, 32), 0.5),
+                                            ("yukawa2d", (3.0, 4.0), (48, 32), 2.0)])
+def test_served_yukawa_request_with_lambda(lib, kernel, L, n, lam):
+    """A Yukawa request carries its lam (kernel_param): the served result
+    equals the plan solved alone with that lam and the oracle's solve for it
+    (Example 4's screened kernels), in both tiers."""
+    import torch
+    from oracle import fsa as oracle
+    rng = np.random.default_rng(21)
+    srv = lib.Server(max_inflight=4, streams=2)
+    try:
+        for dt in ("f64", "f32"):
+            tdt = torch.float64 if dt == "f64" else torch.float32
+            rho = torch.from_numpy(rng.standard_normal(n)).to(tdt).cuda()
+            p = lib.Plan(L, n, dt, eps=0.0, kernel=kernel, kernel_param=lam)
+            eps = p.eps
+            want = p.apply(rho)
+            torch.cuda.synchronize()
+            p.close()
+            out = torch.full_like(rho, float("nan"))
+            srv.wait(srv.submit(L, n, dt, rho, out, kernel=kernel, kernel_param=lam))
+            torch.cuda.synchronize()
+            assert torch.equal(out, want)
+            ref = oracle.solve(L, n, eps, rho.double().cpu().numpy(), kernel=(kernel, lam))
+            err = oracle.rel_error(out.double().cpu().numpy(), ref)
+            assert err <= (1e-12 if dt == "f64" else 2e-6), (dt, err)
+            # lam = 1 is a different plan: its result differs
+            other = torch.full_like(rho, float("nan"))
+            srv.wait(srv.submit(L, n, dt, rho, other, kernel=kernel, kernel_param=1.0))
+            torch.cuda.synchronize()
+            assert not torch.equal(other, out)
+    finally:
+        srv.close()
+
+
+def test_server_charges_each_plan_its_real_bytes(lib):
+    """Admission counts what a resident plan really holds: the spectrum octant
+    in its dtype, a second (double-word) copy for FP64 plans, and no third
+    axis for a plane.  After the requests finish the server holds exactly
+    the plans, and the device's free memory fell by at least that."""
+    import torch
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    srv = lib.Server(max_inflight=2, streams=2)
+    reqs = [("coulomb3d", (3.0, 3.0, 3.0), (32, 48, 64), "f64"), ("poisson2d", (4.0, 4.0), (64, 96), "f32"),
+            ("coulomb2d", (4.0, 3.0), (32, 48), "f64")]
+    want = 0
+    rng = np.random.default_rng(22)
+    try:
+        keep = []
+        for kernel, L, n, dt in reqs:
+            tdt = torch.float64 if dt == "f64" else torch.float32
+            rho = torch.from_numpy(rng.standard_normal(n)).to(tdt).cuda()
+            out = torch.empty_like(rho)
+            keep += [rho, out]
+            srv.wait(srv.submit(L, n, dt, rho, out, kernel=kernel))
+            octant = int(np.prod([x + 1 for x in n]))
+            want += octant * (16 if dt == "f64" else 4)
+        torch.cuda.synchronize()
+        st = srv.stats()
+        assert st.completed == len(reqs) and st.inflight == 0
+        assert st.device_bytes_held == want, (st.device_bytes_held, want)
+        assert free0 - torch.cuda.mem_get_info()[0] >= want
+    finally:
+        srv.close()

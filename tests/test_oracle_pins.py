@@ -205,6 +205,23 @@ def test_fft_route_equals_brute_force(n):
     assert np.allclose(fsa.apply_direct_at(T, rho, pts), [b[p] for p in pts], rtol=1e-13, atol=0)
 
 
+def test_threaded_fft_route_equals_brute_force():
+    """The threaded FFT route (scipy's FFT on several host cores, used to time
+    the oracle on all cores) reproduces Eq. (DiscConv) summed directly and the
+    single-threaded route, for the spectrum, T^(2) and the apply."""
+    rng = np.random.default_rng(9)
+    n, L, eps = (6, 8, 10), (3.0, 4.0, 2.5), 0.6
+    T1 = fsa.tensor_T(L, n, eps)
+    T4 = fsa.tensor_T(L, n, eps, workers=4)
+    assert np.max(np.abs(T4 - T1)) <= 1e-15 * np.max(np.abs(T1))
+    rho = rng.standard_normal(n)
+    S1, S4 = fsa.spectrum(T1), fsa.spectrum(T1, workers=4)
+    assert np.max(np.abs(S4 - S1)) <= 1e-15 * np.max(np.abs(S1))
+    a = fsa.apply_spectrum(S1, rho, workers=4)
+    assert fsa.rel_error(a, fsa.apply_direct(T1, rho)) < 1e-13
+    assert fsa.rel_error(a, fsa.apply_spectrum(S1, rho)) < 1e-14
+
+
 def test_brute_force_on_a_hand_example():
     """A 2-point case worked by hand: rho nonzero at two cells, so each output
     is T at the offsets to those two cells."""

@@ -98,3 +98,25 @@ def test_noalloc_matches_apply_for_ddi_plans(capi, dt, derivative):
             assert rel_error(a, b) <= TOL[dt], (call, rel_error(a, b))
     finally:
         capi.fsa_plan_destroy(plan)
+
+
+def test_noalloc_call_changes_no_free_memory(capi):
+    """The static scratch is reserved when plans are made, so an apply through
+    this entry point moves nothing in the device's free memory: not the first
+    call after plan creation, and not later ones."""
+    import torch
+    n = (32, 32, 32)
+    plan = capi.fsa_plan_create(capi.FSA_KERNEL_COULOMB3D, 3, (4.0, 4.0, 4.0), n, capi.FSA_F32, eps=0.8)
+    stream = torch.cuda.current_stream()
+    try:
+        capi.fsa_tensor_generate(plan, stream)
+        rho = torch.from_numpy(np.random.default_rng(3).standard_normal(n)).float().cuda()
+        out = torch.empty_like(rho)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(3):
+            capi.fsa_apply_noalloc(plan, rho, out, stream)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+    finally:
+        capi.fsa_plan_destroy(plan)
