@@ -271,7 +271,9 @@ def run_ours(args):
     # measured ALU peaks of this GPU: the denominators of the ALU rooflines
     f32_rate, f32_ms = capi.fsa_measure_alu_peak(0)
     f64_rate, f64_ms = capi.fsa_measure_alu_peak(1)
+    x2_rate, _ = capi.fsa_measure_alu_peak(2)
     alu_peaks = {"fp32_fma_gops": f32_rate / 1e9, "fp64_fma_gops": f64_rate / 1e9,
+                 "fp32x2_fma_gops": x2_rate / 1e9,
                  "fp32_tflops": 2 * f32_rate / 1e12, "fp64_tflops": 2 * f64_rate / 1e12,
                  "how": "fsa_measure_alu_peak: every resident thread runs 8 independent FMA chains, "
                         f"best of 3 launches by CUDA events ({f32_ms:.2f} / {f64_ms:.2f} ms); 1 FMA = 1 op = 2 flop"}

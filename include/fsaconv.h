@@ -374,12 +374,13 @@ fsa_status fsa_wait_selftest(int device, unsigned int* code);
 /* Measured ALU peak (no counterpart in the paper: the denominator of the
  * ALU rooflines of the FP64 tier, whose double-word passes run on the FP32
  * pipes and whose native passes run on the FP64 pipe).  kind 0: FP32 fused
- * multiply-add, kind 1: FP64 fused multiply-add.  On `device` (-1 = current)
+ * multiply-add, kind 1: FP64 fused multiply-add, kind 2: the paired FP32
+ * fused multiply-add (fma.rn.f32x2, two FMAs per instruction; counted as 2).  On `device` (-1 = current)
  * every resident thread runs 8 independent FMA chains for a fixed count;
  * the best of 3 timed launches (after one warm-up) gives *lane_ops_per_s
  * (one FMA = one lane operation = 2 flops); *ms (may be NULL) receives that
  * launch's time.  Synchronous, a few ms per kind.  Errors:
- * FSA_ERR_INVALID_ARG (NULL result, kind not 0 or 1), FSA_ERR_CUDA. */
+ * FSA_ERR_INVALID_ARG (NULL result, kind not 0, 1 or 2), FSA_ERR_CUDA. */
 fsa_status fsa_measure_alu_peak(int device, int kind, double* lane_ops_per_s, float* ms);
 
 /* ---------------------------------------------------------------- serving -- */

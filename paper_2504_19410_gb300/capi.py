@@ -288,7 +288,7 @@ def fsa_device_fault(device=-1, clear=False):
 
 def fsa_measure_alu_peak(kind, device=-1):
     """(lane operations per second, ms of the timed launch); kind 0 = FP32 FMA,
-    1 = FP64 FMA (one FMA = one lane operation)."""
+    1 = FP64 FMA, 2 = paired FP32 FMA (fma.rn.f32x2; one FMA = one lane operation)."""
     rate, ms = C.c_double(), C.c_float()
     check(lib().fsa_measure_alu_peak(int(device), int(kind), C.byref(rate), C.byref(ms)))
     return rate.value, ms.value

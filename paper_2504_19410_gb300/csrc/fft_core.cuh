@@ -96,6 +96,36 @@ __device__ __forceinline__ cdw cmulc(cdw a, cdw b) {
   return mk(dw_dot2(a.x, b.x, a.y, b.y), dw_dot2(a.y, b.x, -a.x, b.y));
 }
 template <typename V> __device__ __forceinline__ V cscale(V a, typename RealOf<V>::T s) { return mk(a.x * s, a.y * s); }
+
+#if defined(FSA_F32X2) && defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+// Paired FP32 arithmetic of sm_100 and later: one instruction adds, subtracts
+// or scales both parts of a float2 (add/sub/mul.rn.f32x2 on a register pair).
+__device__ __forceinline__ unsigned long long f2_pack(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(r);
+}
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(r);
+}
+template <> __device__ __forceinline__ float2 cscale<float2>(float2 a, float s) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(make_float2(s, s))));
+  return f2_unpack(r);
+}
+#endif
 // -i * a for the forward direction, +i * a for the inverse one
 template <bool FWD, typename V> __device__ __forceinline__ V rot_mi(V a) {
   return FWD ? mk(a.y, -a.x) : mk(-a.y, a.x);
