@@ -88,8 +88,15 @@ enum Arith {
   kArithF32G3 = 4,
   kArithF32G4 = 5,
   kArithF32G5 = 6,  // the fused outer pass pairs only (fwd5 / inv5)
-  kNumArith = 7
+  kArithF32G6 = 7,  // generation 4 with the sixth-generation middle pass
+  kNumArith = 8
 };
+// The sixth-generation middle pass (passes6.cuh, inst_f32g6.cu) for
+// transform length M, or null where it has no instance; k6_prepare sets its
+// shared-memory opt-in on the current device.
+using ColmFn = cudaError_t (*)(const Jobs&, int, int, cudaStream_t);
+ColmFn k6_colm(int M);
+cudaError_t k6_prepare(int M);
 // The fused outer pass pair used for FP32 grids with n0 = n2 and transform
 // length M = 2 n0 (dir 0 forward, 1 inverse): 0 = the separate passes, c >= 1
 // = fused cluster configuration c - 1.  set_fused_config(M, dir, -1) leaves

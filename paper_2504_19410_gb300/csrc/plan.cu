@@ -110,6 +110,7 @@ int kernel_variant(int pass, int M, fsa_dtype dt) {
   if (mode == 3) return 2;
   if (mode == 4) return 3;
   if (mode == 5) return 4;
+  if (mode == 6) return pass == kColMid ? 5 : 4;
   const int v = (M >= 0 && M <= 1024) ? g_variant[pass][M][dt].load(std::memory_order_relaxed) : 0;
   return v ? v : 2;
 }
@@ -201,10 +202,14 @@ cudaError_t init_all_twiddles() {
   return e;
 }
 
+// FP32 kernel variant (1..5, as kernel_variant) -> registered arithmetic.
+int arith_of_variant(int v) {
+  return v == 5 ? kArithF32G6 : v == 4 ? kArithF32G4 : (v == 3 ? kArithF32G3 : (v == 2 ? kArithF32G2 : kArithF32G1));
+}
+
 template <typename V> int arith_for(int pass, int M) {
   if constexpr (std::is_same<V, float2>::value) {
-    const int v = kernel_variant(pass, M, FSA_F32);
-    return v == 4 ? kArithF32G4 : (v == 3 ? kArithF32G3 : (v == 2 ? kArithF32G2 : kArithF32G1));
+    return arith_of_variant(kernel_variant(pass, M, FSA_F32));
   }
   else if constexpr (std::is_same<V, double2>::value)
     return kArithF64;
@@ -629,8 +634,8 @@ fsa_status prepare_device(int dev, fsa_dtype dt, const int* n, int d, bool unpad
     const int key = M * 4 + (int)dt;
     if (g_prepared.count({dev, key})) continue;
     cudaError_t e = cudaSuccess;
-    const int f32a[4] = {kArithF32G1, kArithF32G2, kArithF32G3, kArithF32G4};
-    const int f64a[4] = {kArithF64, kArithDW, kArithDW, kArithDW};
+    const int f32a[5] = {kArithF32G1, kArithF32G2, kArithF32G3, kArithF32G4, kArithF32G6};
+    const int f64a[5] = {kArithF64, kArithDW, kArithDW, kArithDW, kArithDW};
     for (int a : (dt == FSA_F32 ? f32a : f64a)) {
       const PassFns& f = pass_fns(a, M);
       if (!f.prepare) return set_error(FSA_ERR_UNSUPPORTED, "no kernels registered for this length");
@@ -638,6 +643,7 @@ fsa_status prepare_device(int dev, fsa_dtype dt, const int* n, int d, bool unpad
     }
     const PassFns& f5g = pass_fns(kArithF32G5, M);  // fused outer pairs (some lengths)
     if (dt == FSA_F32 && f5g.prepare && e == cudaSuccess) e = f5g.prepare();
+    if (dt == FSA_F32 && e == cudaSuccess) e = k6_prepare(M);  // the sixth-generation middle pass
     if (e == cudaSuccess) e = tensorgen_prepare(M);
     if (e != cudaSuccess) return cuda_error(e, "kernel shared-memory opt-in");
     g_prepared.insert({dev, key});
@@ -722,7 +728,7 @@ fsa_status fsa_device_fault(int device, unsigned int* code, int clear) {
 }
 
 fsa_status fsa_autotune_set(int mode) {
-  if (mode < 0 || mode > 5) return set_error(FSA_ERR_INVALID_ARG, "fsa_autotune_set: mode must be 0..5");
+  if (mode < 0 || mode > 6) return set_error(FSA_ERR_INVALID_ARG, "fsa_autotune_set: mode must be 0..6");
   autotune_mode() = mode;
   return FSA_OK;
 }
@@ -995,7 +1001,7 @@ cudaError_t tune_plan(fsa_plan* p) {
   Jobs j{};
   j.count = 1;
   auto run = [&](int k, int v) -> cudaError_t {
-    const PassFns& f = pass_fns(v == 4 ? kArithF32G4 : (v == 3 ? kArithF32G3 : (v == 2 ? kArithF32G2 : kArithF32G1)), Ms[k]);
+    const PassFns& f = pass_fns(arith_of_variant(v), Ms[k]);
     switch (k) {
       case kR2C: j.j[0] = Job{Y, X, nullptr}; return f.r2c(j, C, s);
       case kRowFwd: j.j[0] = Job{X, Y, nullptr}; return f.rowf(j, rows, s);
@@ -1008,7 +1014,9 @@ cudaError_t tune_plan(fsa_plan* p) {
     if (g_variant[k][Ms[k]][FSA_F32].load() != 0) continue;
     float best = 1e30f;
     int pick = 2;
-    for (int v = 1; v <= 4 && e == cudaSuccess; ++v) {
+    // variant 5 (the sixth-generation middle pass) only where it exists
+    const int vmax = (k == kColMid && k6_colm(Ms[k])) ? 5 : 4;
+    for (int v = 1; v <= vmax && e == cudaSuccess; ++v) {
       e = run(k, v);  // warm-up
       float tmin = 1e30f;
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {

@@ -13,7 +13,7 @@ each in FP32 (<= 2e-6) and in the FP64 tier (<= 1e-12), under the autotuned
 launch configuration that ``bench.py`` times and under every forced kernel
 generation (gen1: Stockham radix-8 FP32 and native FP64; gen2: two-step
 register FP32 and double-word FP64; gen3: + prefetching middle pass; gen4: +
-bulk-copy row passes).  The transform-length-512 middle passes and their tile
+bulk-copy row passes; gen6: gen4 with the half-task middle pass).  The transform-length-512 middle passes and their tile
 edges are exercised only at these sizes.  Each result's max-norm error against
 the oracle and against the exact potential is printed.
 
@@ -32,8 +32,8 @@ pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "f32": 2e-6}
 # autotune modes of fsa_autotune_set: 1 = tuned (the bench's configuration),
-# 2..5 = forced generations 1..4
-MODES = [("tuned", 1), ("gen1", 2), ("gen2", 3), ("gen3", 4), ("gen4", 5)]
+# 2..6 = forced generations 1..4 and 6
+MODES = [("tuned", 1), ("gen1", 2), ("gen2", 3), ("gen3", 4), ("gen4", 5), ("gen6", 6)]
 
 
 @pytest.fixture(scope="module")

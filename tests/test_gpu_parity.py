@@ -30,17 +30,18 @@ def lib():
     return fsa
 
 
-@pytest.fixture(params=["gen1", "gen2", "gen3", "gen4"])
+@pytest.fixture(params=["gen1", "gen2", "gen3", "gen4", "gen6"])
 def gen(request, lib):
     """Force one kernel generation for a test: gen1 = Stockham radix-8 (FP32) and
     native FP64; gen2 = two-step register kernels (FP32) and double-word FP64;
     gen3 = gen2 with the prefetching middle pass (FP32) and double-word FP64;
-    gen4 = gen3 with bulk-copy row passes (FP32) and double-word FP64.  No
+    gen4 = gen3 with bulk-copy row passes (FP32) and double-word FP64; gen6 =
+    gen4 with the half-task middle pass (FP32) and double-word FP64.  No
     bounded device wait may have given up during the test."""
     import torch
     from paper_2504_19410_gb300 import capi
     capi.fsa_device_fault(clear=True)
-    capi.fsa_autotune_set({"gen1": 2, "gen2": 3, "gen3": 4, "gen4": 5}[request.param])
+    capi.fsa_autotune_set({"gen1": 2, "gen2": 3, "gen3": 4, "gen4": 5, "gen6": 6}[request.param])
     yield request.param
     capi.fsa_autotune_set(1)
     torch.cuda.synchronize()
@@ -63,7 +64,10 @@ def gpu_solve(lib, L, n, eps, rho, dt):
 
 
 SMALL = [(4, 4, 4), (4, 6, 8), (8, 8, 8), (12, 16, 24), (6, 48, 32), (16, 16, 16), (24, 12, 48),
-         (8, 8, 512), (512, 4, 4), (4, 384, 6), (96, 8, 12), (32, 32, 32)]
+         (8, 8, 512), (512, 4, 4), (4, 384, 6), (96, 8, 12), (32, 32, 32),
+         # middle-axis lengths of the sixth-generation middle pass (2 n1 = 128 ... 512),
+         # with column tiles narrower than the 16-column CTA tile
+         (4, 64, 6), (6, 96, 4), (4, 128, 8), (4, 192, 4), (6, 256, 4), (8, 256, 24)]
 
 
 @pytest.mark.parametrize("dt", ["f64", "f32"])
