@@ -1,8 +1,8 @@
 // FP32 sixth-generation middle pass (passes6.cuh), lengths 128 to 512.
 // Compiled as its own translation unit; the launchers are looked up by length
 // (k6_colm) when the other FP32 instances register their function tables.
-#include "fsa_internal.h"
 #include "passes6.cuh"
+#include "passes_impl.cuh"
 
 namespace fsa {
 namespace {
@@ -45,3 +45,7 @@ cudaError_t k6_prepare(int M) {
 }
 
 }  // namespace fsa
+
+// This unit's copy of the twiddle tables (fft_core.cuh) is filled at plan
+// creation like every instance unit's: registered here, no pass tables.
+FSA_REGISTER()

@@ -179,7 +179,7 @@ namespace fsa {
 // The five passes for `count` solves that share the grid n and the dtype V.
 namespace {
 PassFns g_fns[kNumArith][1025];
-cudaError_t (*g_tw_inits[32])() = {};
+cudaError_t (*g_tw_inits[64])() = {};
 int g_ntw = 0;
 }  // namespace
 
@@ -193,7 +193,7 @@ const PassFns& pass_fns(int arith, int M) {
 }
 
 void register_twiddle_init(cudaError_t (*init)()) {
-  if (g_ntw < 32) g_tw_inits[g_ntw++] = init;
+  if (g_ntw < 64) g_tw_inits[g_ntw++] = init;
 }
 
 cudaError_t init_all_twiddles() {
