@@ -484,8 +484,8 @@ def run_ours(args):
 def bench_batched(args, fsa, W, torch, stream):
     """64 seeded Gaussian-sum densities, cubic n from {64,96,128,192,256},
     gamma in {1,4,8} (cigar or pancake), FP32, in one batched call (one
-    persistent launch per pass per shape group, captured in a CUDA graph),
-    against the same 64 solves issued one fsa_apply at a time."""
+    persistent launch per pass over all 64 solves' tiles, captured in a CUDA
+    graph), against the same 64 solves issued one fsa_apply at a time."""
     dens = W.batch_requests(seed=2504, count=64)
     plans = [fsa.Plan(d.L, d.n, "f32", eps=d.eps) for d in dens]
     rhos = [d.rho_torch(torch.float32) for d in dens]
@@ -521,8 +521,10 @@ def bench_batched(args, fsa, W, torch, stream):
            "value": len(dens) / (tb * 1e-3), "unit": UNIT, "ms_per_batch": tb,
            "sequential_solves_per_s": len(dens) / (ts * 1e-3), "ms_sequential": ts,
            "step_roofline_frac_27V_model": bytes_model / (hbm_peak * 1e9) / (tb * 1e-3),
-           # one launch per pass per shape group (3 or 4 where an outer pair runs fused)
-           "gpu_launches_per_batch": sum({tuple(p.n): p.info.launches_per_apply for p in plans}.values())}
+           # the library's own count: 5 for the mixed-length path (one launch
+           # per pass for all 64 solves), more where solves fall into groups
+           "gpu_launches_per_batch": fsa.capi.fsa_apply_batched_launches([p.handle for p in plans]),
+           "path": "mixed-length kernels: one persistent launch per pass over the concatenated tile lists"}
     for p in plans:
         p.close()
     del rhos, phis

@@ -225,15 +225,29 @@ fsa_status fsa_apply_host(const fsa_plan* plan, const void* rho_host, void* phi_
                           fsa_stream_t stream);
 
 /* Apply count plans to count densities in one launch sequence.  Plans may
- * differ in n, L, eps and dtype but must share a device; request k's result
- * equals fsa_apply(plans[k], rho[k], phi[k]) bit for bit.  Requests with the
- * same grid and dtype are grouped; each group's passes run as grid-strided
- * persistent kernels over the tiles of all its requests, the groups on
- * concurrent streams, and the whole sequence is captured once per batch
- * signature into a CUDA graph and replayed.  Uses each plan's workspace, so
- * a plan may appear at most once per call (FSA_ERR_INVALID_ARG otherwise). */
+ * differ in n, L, eps and dtype but must share a device.  The requests whose
+ * plan is an FP32 plan of d = 3 (not DDI, no pass split) with every transform
+ * length 2 n_j in {128, 192, 256, 384, 512} run as five launches in all: each
+ * pass is one persistent launch over the concatenated tile lists of all of
+ * them, whatever their sizes; such a request's result matches
+ * fsa_apply(plans[k], rho[k], phi[k]) within FP32 round-off (the same
+ * transforms, factored as 16 x (M / 16)), not bit for bit.  The other
+ * requests are grouped by grid and dtype, each group's passes run as
+ * grid-strided persistent kernels over the tiles of all its requests, on
+ * concurrent streams, and each of their results equals fsa_apply's bit for
+ * bit.  Either sequence is captured once per batch signature (plans and
+ * buffers) into a CUDA graph and replayed; a captured graph keeps the kernels
+ * chosen when it was captured (later fsa_autotune_set / fsa_fused_select
+ * calls apply to new batches).  Uses each plan's workspace, so a plan may
+ * appear at most once per call (FSA_ERR_INVALID_ARG otherwise). */
 fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void* const* rho,
                              void* const* phi, int count, fsa_stream_t stream);
+
+/* How many kernel launches fsa_apply_batched makes for these plans (no
+ * counterpart in the paper: launch accounting for the batched path): five per
+ * 64 requests of the mixed path, plus each group's launches per apply per 64
+ * requests.  Host only.  Errors: FSA_ERR_INVALID_ARG (NULL). */
+fsa_status fsa_apply_batched_launches(const fsa_plan* const* plans, int count, int* launches);
 
 /* Many densities through one plan (the paper's Execution phase repeated with one
  * cached tensor, e.g. the steps of a time-dependent solver).  fsa_plan_reserve

@@ -95,6 +95,7 @@ _PROTOS = {
     "fsa_apply_host": (C.c_int, [_VP, _VP, _VP, _VP]),
     "fsa_apply_noalloc": (C.c_int, [_VP, _VP, _VP, _VP]),
     "fsa_apply_batched": (C.c_int, [C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), C.c_int, _VP]),
+    "fsa_apply_batched_launches": (C.c_int, [C.POINTER(_VP), C.c_int, C.POINTER(C.c_int)]),
     "fsa_plan_reserve": (C.c_int, [_VP, C.c_int]),
     "fsa_apply_many": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP), C.c_int, _VP]),
     "fsa_plan_info_get": (C.c_int, [_VP, C.POINTER(PlanInfo)]),
@@ -213,6 +214,15 @@ def fsa_apply_batched(plans, rhos, phis, stream=None):
     R = (_VP * k)(*[_ptr(r) for r in rhos])
     F = (_VP * k)(*[_ptr(f) for f in phis])
     return check(lib().fsa_apply_batched(P, R, F, k, _stream(stream)))
+
+
+def fsa_apply_batched_launches(plans):
+    """Kernel launches one fsa_apply_batched call over these plans makes."""
+    k = len(plans)
+    P = (_VP * k)(*plans)
+    n = C.c_int()
+    check(lib().fsa_apply_batched_launches(P, k, C.byref(n)))
+    return n.value
 
 
 def fsa_plan_reserve(plan, count):

@@ -1,11 +1,18 @@
 // fsa_apply_batched: many solves of uneven size in one launch sequence.
 //
-// Solves with the same grid and dtype form a group.  Each pass of a group is
-// ONE persistent launch that walks the tiles of all the group's solves (the
-// kernels take a by-value job table); the groups run on forked streams so
-// their passes overlap on the device.  The whole sequence is captured once per
+// The FP32 3-D solves whose transform lengths the mixed-length kernels carry
+// (2n in {128, 192, 256, 384, 512}: the 64^3 ... 256^3 grids of the batched
+// workload) run as five launches in all: each pass is ONE persistent launch
+// over the concatenated tile lists of all of them, whatever their sizes
+// (mixed.cu, passes_mix.cuh).  The other solves (FP64, planes, DDI, other
+// lengths) form groups of one grid and dtype; each pass of a group is
+// one persistent launch that walks the tiles of all the group's solves (the
+// kernels take a by-value job table), and the groups run on forked streams so
+// their passes overlap on the device.  Either sequence is captured once per
 // batch signature (plans, buffers) into a CUDA graph and replayed, so a
-// repeated batch costs one graph launch on the caller's stream.
+// repeated batch costs one graph launch on the caller's stream.  A graph
+// keeps the kernels chosen when it was captured (fsa_autotune_set and
+// fsa_fused_select apply to batches captured afterwards).
 #include <algorithm>
 #include <tuple>
 #include <list>
@@ -98,8 +105,23 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
     if (((uintptr_t)rho[k] | (uintptr_t)phi[k]) & 15u)
       return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched: rho and phi must be 16-byte aligned");
     seen.push_back(p);
-    groups[GroupKey{p->n[0], p->n[1], p->n[2], (int)p->dtype, p->f64_dw, p->ddi}].push_back(k);
   }
+  // the solves that fit the mixed-length kernels (FP32, d = 3, transform
+  // lengths 128 ... 512) share one launch per pass; the others are grouped
+  std::vector<const fsa_plan*> mplans;
+  std::vector<const void*> mrho;
+  std::vector<void*> mphi;
+  for (int k = 0; k < count; ++k) {
+    const fsa_plan* p = plans[k];
+    if (mixed_eligible(p)) {
+      mplans.push_back(p);
+      mrho.push_back(rho[k]);
+      mphi.push_back(phi[k]);
+    } else {
+      groups[GroupKey{p->n[0], p->n[1], p->n[2], (int)p->dtype, p->f64_dw, p->ddi}].push_back(k);
+    }
+  }
+  const bool mixed = !mplans.empty();
   std::sort(seen.begin(), seen.end());
   if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
     return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched: a plan appears twice (its workspace is shared)");
@@ -116,7 +138,7 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
   if (prev != dev) cudaSetDevice(dev);
   std::lock_guard<std::mutex> lk(g_mu);
   DeviceCtx& c = g_ctx[dev];
-  cudaError_t e = ensure_ctx(c, groups.size());
+  cudaError_t e = ensure_ctx(c, groups.size() + (mixed ? 1 : 0));
   cudaGraphExec_t exec = nullptr;
   auto it = c.graphs.find(sig);
   if (e == cudaSuccess && it != c.graphs.end()) {
@@ -126,8 +148,11 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
   } else if (e == cudaSuccess) {
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(c.capture, cudaStreamCaptureModeThreadLocal);
-    size_t g = 0;
+    // the mixed launches on the capture stream; every group on a side stream
+    size_t g = mixed ? 1 : 0;
     cudaError_t le = e;
+    if (mixed && le == cudaSuccess)
+      le = mixed_passes((int)mplans.size(), mplans.data(), mrho.data(), mphi.data(), c.capture);
     for (auto& kv : groups) {
       if (le != cudaSuccess) break;
       if (g == 0) {
@@ -162,6 +187,30 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
     cudaGetLastError();
     return cuda_error(e, "fsa_apply_batched");
   }
+  return FSA_OK;
+}
+
+extern "C" fsa_status fsa_apply_batched_launches(const fsa_plan* const* plans, int count, int* launches) {
+  if (!launches || count < 0 || (count > 0 && !plans))
+    return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched_launches: bad arguments");
+  int mixed = 0;
+  std::map<GroupKey, std::pair<int, int>> groups;  // members, launches per apply
+  for (int k = 0; k < count; ++k) {
+    const fsa_plan* p = plans[k];
+    if (!p) return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched_launches: NULL plan");
+    if (mixed_eligible(p)) {
+      ++mixed;
+    } else {
+      auto& g = groups[GroupKey{p->n[0], p->n[1], p->n[2], (int)p->dtype, p->f64_dw, p->ddi}];
+      ++g.first;
+      fsa_plan_info info{};
+      fsa_plan_info_get(p, &info);
+      g.second = info.launches_per_apply;
+    }
+  }
+  int n = 5 * ((mixed + kMaxJobs - 1) / kMaxJobs);
+  for (auto& kv : groups) n += kv.second.second * ((kv.second.first + kMaxJobs - 1) / kMaxJobs);
+  *launches = n;
   return FSA_OK;
 }
 

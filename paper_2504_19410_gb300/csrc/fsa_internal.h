@@ -97,6 +97,11 @@ enum Arith {
 using ColmFn = cudaError_t (*)(const Jobs&, int, int, cudaStream_t);
 ColmFn k6_colm(int M);
 cudaError_t k6_prepare(int M);
+// The batched launcher's mixed-length path (mixed.cu, passes_mix.cuh): whether
+// a plan can join it, and the five launches for `count` such solves.
+bool mixed_eligible(const fsa_plan* p);
+cudaError_t mixed_passes(int count, const fsa_plan* const* plans, const void* const* rho, void* const* phi,
+                         cudaStream_t s);
 // The fused outer pass pair used for FP32 grids with n0 = n2 and transform
 // length M = 2 n0 (dir 0 forward, 1 inverse): 0 = the separate passes, c >= 1
 // = fused cluster configuration c - 1.  set_fused_config(M, dir, -1) leaves

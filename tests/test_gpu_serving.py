@@ -110,9 +110,14 @@ def test_serving_rejects_bad_requests_and_unknown_tickets(lib):
 
 def test_batched_c4_mix_equals_single(lib):
     """The C4-style mix (cubic n from {64,...,256}, gamma in {1,4,8}) in one
-    batched call equals each solve alone."""
+    batched call: these FP32 solves take the mixed-length path (one launch per
+    pass for all of them), whose transforms are factored differently from the
+    tuned single-solve kernels, so each result matches its solve alone within
+    FP32 round-off, and the oracle within the FP32 tolerance; a repeated call
+    (graph replay) gives the same bits."""
     import torch
     import workloads as W
+    from oracle import fsa as oracle
     dens = W.batch_requests(seed=2504, count=10, sizes=(64, 96, 128))
     plans, rhos, singles = [], [], []
     for d in dens:
@@ -121,11 +126,19 @@ def test_batched_c4_mix_equals_single(lib):
         singles.append(p.apply(r).clone())
         plans.append(p)
         rhos.append(r)
-    outs = [torch.empty_like(r) for r in rhos]
+    outs = [torch.full_like(r, float("nan")) for r in rhos]
     lib.apply_batched(plans, rhos, outs)
     torch.cuda.synchronize()
-    for s, o in zip(singles, outs):
-        assert torch.equal(s, o)
+    first = [o.clone() for o in outs]
+    for o in outs:
+        o.fill_(float("nan"))
+    lib.apply_batched(plans, rhos, outs)
+    torch.cuda.synchronize()
+    for d, s, o, f in zip(dens, singles, outs, first):
+        assert torch.equal(o, f)
+        a, b = o.double().cpu().numpy(), s.double().cpu().numpy()
+        assert oracle.rel_error(a, b) <= 1e-6
+        assert oracle.rel_error(a, oracle.solve(d.L, d.n, d.eps, d.rho())) <= 2e-6
     for p in plans:
         p.close()
 
