@@ -592,7 +592,7 @@ def bench_serving(args, fsa, W, torch, rank):
         tdt = torch.float32 if dt == "f32" else torch.float64
         inputs[(n, dt)] = W.gaussian_sum(seed=2504 + n, n=n).rho_torch(tdt)
         pools[(n, dt)] = [torch.empty_like(inputs[(n, dt)]) for _ in range(4 if n >= 384 else 8)]
-    srv = fsa.Server(max_inflight=32, streams=8)
+    srv = fsa.Server(max_inflight=32, streams=8, policy=args.serve_policy)
 
     def run(arrivals):
         free = {k: list(v) for k, v in pools.items()}
@@ -643,6 +643,16 @@ def bench_serving(args, fsa, W, torch, rank):
                               "p99_ms": float(np.percentile(lat_f, 99))}
     st = srv.stats()
     srv.close()
+    # the other scheduling policy on the same arrival stream (same offered rate)
+    other_policy = 1 - args.serve_policy
+    srv = fsa.Server(max_inflight=32, streams=8, policy=other_policy)
+    for key in keys:
+        srv.wait(srv.submit((16.0, 16.0, 16.0), (key[0],) * 3, key[1], inputs[key], pools[key][0], eps=1.0),
+                 timeout=600.0)
+    w_o, lat_o = run(arrivals)
+    srv.close()
+    other = {"policy": other_policy, "offered_load": args.serve_load, "solves_per_s": len(reqs) / w_o,
+             "p50_ms": float(np.percentile(lat_o, 50)), "p99_ms": float(np.percentile(lat_o, 99))}
     torch.cuda.empty_cache()
     lat2 = np.array(lat2)
 
@@ -676,6 +686,11 @@ def bench_serving(args, fsa, W, torch, rank):
             "p50_ms": float(np.percentile(lat2, 50)), "p99_ms": float(np.percentile(lat2, 99)),
             "closed_loop_p50_ms": float(np.percentile(lat, 50)),
             "per_load": dict(sorted(per_load.items())),
+            "policy": args.serve_policy,
+            "policy_text": {0: "size-aware lanes: large requests on low-priority bulk streams, one CTA per tile; "
+                               "others on high-priority streams, least-loaded stream per lane",
+                            1: "round robin over equal-priority streams, persistent grids"}[args.serve_policy],
+            "other_policy_same_arrivals": other,
             "plan_hit_rate": st.plan_hits / max(1, st.plan_hits + st.plan_misses),
             "fp64_single_solve_solves_per_s": fp64_single,
             "fp64_single_solve_sample": f"first {len(sample)} requests, each solved alone in FP64 "
@@ -806,6 +821,8 @@ def main():
     ap.add_argument("--serve-fp64-sample", type=int, default=1000,
                     help="requests of the stream re-run through the plain FP64 single-solve path")
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered load as a fraction of capacity")
+    ap.add_argument("--serve-policy", type=int, choices=[0, 1], default=0,
+                    help="serving policy (fsa_serve_opts.policy): 0 size-aware lanes, 1 round robin")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -415,6 +415,8 @@ typedef struct {
   int plan_cache_max;      /* plans kept resident (0 = 64), least recently used out  */
   int queue_max;           /* pending requests before FSA_ERR_BUSY (0 = 1 << 20)     */
   int device;              /* -1 = current                                           */
+  int policy;              /* 0 = size-aware lanes (default), 1 = round robin: see    */
+                           /* fsa_serve_create                                        */
 } fsa_serve_opts;
 
 typedef struct {
@@ -459,7 +461,14 @@ typedef struct {
  * their kernels overlap on the device), keeps plans resident in an LRU
  * cache, and marks a ticket DONE when its completion event has fired.
  * Results do not depend on the mix: every request runs the same kernels on
- * its own workspace, with no cross-request reduction. */
+ * its own workspace, with no cross-request reduction.  Policy 0 (default):
+ * requests of estimated work grid points x (5 for FP64) >= 4e7 (a 384^3 FP32
+ * or 256^3 FP64 solve and larger) go to a bulk lane of low-priority streams
+ * (a quarter of them, at least one) and launch one CTA per tile, the others
+ * to high-priority streams; within its lane a request takes the stream with
+ * the least estimated work in flight, so small requests neither queue behind
+ * a long solve on a stream nor wait for its persistent grids to drain.
+ * Policy 1: every stream at default priority, round robin, persistent grids. */
 fsa_status fsa_serve_create(fsa_server** out, const fsa_serve_opts* opts);
 fsa_status fsa_serve_submit(fsa_server* s, const fsa_request* req, uint64_t* ticket);
 /* Non-blocking unless timeout_s > 0: waits up to timeout_s for DONE/FAILED

@@ -128,9 +128,9 @@ class Server:
     tensors owned by the caller until their ticket is DONE or FAILED."""
 
     def __init__(self, max_inflight=0, streams=0, hbm_fraction=0.0, hbm_budget_bytes=0, plan_cache_max=0,
-                 queue_max=0, device=-1):
+                 queue_max=0, device=-1, policy=0):
         self.handle = capi.fsa_serve_create(max_inflight, streams, hbm_fraction, hbm_budget_bytes,
-                                            plan_cache_max, queue_max, device)
+                                            plan_cache_max, queue_max, device, policy)
 
     def submit(self, L, n, dtype, rho, phi, eps=0.0, kernel="coulomb3d", kernel_param=0.0):
         k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)

@@ -64,7 +64,7 @@ class PlanInfo(C.Structure):
 class ServeOpts(C.Structure):
     _fields_ = [("max_inflight", C.c_int), ("streams", C.c_int), ("hbm_fraction", C.c_double),
                 ("hbm_budget_bytes", C.c_size_t), ("plan_cache_max", C.c_int), ("queue_max", C.c_int),
-                ("device", C.c_int)]
+                ("device", C.c_int), ("policy", C.c_int)]
 
 
 class Request(C.Structure):
@@ -336,9 +336,10 @@ def fsa_profiler_destroy(prof):
 
 
 def fsa_serve_create(max_inflight=0, streams=0, hbm_fraction=0.0, hbm_budget_bytes=0, plan_cache_max=0,
-                     queue_max=0, device=-1):
+                     queue_max=0, device=-1, policy=0):
     h = _VP()
-    o = ServeOpts(max_inflight, streams, hbm_fraction, hbm_budget_bytes, plan_cache_max, queue_max, device)
+    o = ServeOpts(max_inflight, streams, hbm_fraction, hbm_budget_bytes, plan_cache_max, queue_max, device,
+                  int(policy))
     check(lib().fsa_serve_create(C.byref(h), C.byref(o)))
     return h.value
 

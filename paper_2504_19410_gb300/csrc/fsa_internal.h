@@ -119,6 +119,11 @@ cudaError_t init_all_twiddles();  // every instance unit's tables, current devic
 
 // Resident CTAs per SM for a kernel (cached per function), times the SM count.
 int persistent_grid(const void* func, int threads, int smem, long long tiles);
+// Grid policy of the calling host thread's launches: 0 = persistent grids
+// (resident CTAs x SMs, the default), 1 = one CTA per tile, so that the
+// blocks of a long solve retire one tile at a time and kernels of
+// higher-priority streams get SMs between them (the serving loop's bulk lane).
+int& launch_grid_mode();
 
 // Per-launch trace for the profiler: an event before the first launch and
 // after every launch, and the pass kind of each launch (intervals i -> i+1).

@@ -80,7 +80,19 @@ struct Req {
   size_t ws_bytes = 0;
   cudaEvent_t done = nullptr;
   cudaStream_t stream = nullptr;
+  int lane = -1;        // index into the server's streams
+  double work = 0;      // estimated work (size_aware_work)
 };
+
+// Estimated work of a request in relative units: grid points, times 5 for the
+// FP64 tier (its double-word passes run about 5x longer than FP32 ones).
+double size_aware_work(const fsa_request& r) {
+  const double V = (double)r.n[0] * r.n[1] * (r.d == 2 ? 1 : r.n[2]);
+  return V * (r.dtype == FSA_F64 ? 5.0 : 1.0);
+}
+// Requests at least this large (about a 384^3 FP32 or a 256^3 FP64 solve,
+// 2 ms and more on GB300) go to the bulk lane.
+constexpr double kBulkWork = 4.0e7;
 
 }  // namespace
 
@@ -99,6 +111,8 @@ struct fsa_server {
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> free_events;
   size_t rr = 0;
+  int nbulk = 0;                 // size-aware policy: the last nbulk streams are the bulk lane
+  std::vector<double> lane_work;  // estimated work in flight per stream
   cudaMemPool_t pool = nullptr;
   std::map<PlanKey, CachedPlan> plans;
   std::list<PlanKey> plan_lru;  // front = most recent
@@ -192,7 +206,23 @@ bool try_admit(fsa_server* s, uint64_t id) {
   }
   auto pit = s->plans.find(q.key);
 
-  cudaStream_t stream = s->streams[s->rr++ % s->streams.size()];
+  // stream: round robin (policy 1), or (policy 0) the least loaded stream of
+  // the request's lane -- large requests on low-priority bulk streams, the
+  // rest on high-priority streams -- so no request queues behind a long
+  // solve on its own stream
+  int lane = 0;
+  const double work = size_aware_work(q.r);
+  const bool bulk = s->nbulk > 0 && work >= kBulkWork;
+  if (s->nbulk == 0) {
+    lane = (int)(s->rr++ % s->streams.size());
+  } else {
+    const int nfast = (int)s->streams.size() - s->nbulk;
+    const int lo = bulk ? nfast : 0, hi = bulk ? (int)s->streams.size() : nfast;
+    lane = lo;
+    for (int i = lo + 1; i < hi; ++i)
+      if (s->lane_work[i] < s->lane_work[lane]) lane = i;
+  }
+  cudaStream_t stream = s->streams[lane];
   fsa_status status = FSA_OK;
   cudaError_t e = cudaSuccess;
   if (!hit) {
@@ -252,7 +282,11 @@ bool try_admit(fsa_server* s, uint64_t id) {
     const size_t xb = (size_t)(q.r.n[0] + 1) * q.r.n[1] * q.r.n[2] * 2 * (q.r.dtype == FSA_F32 ? 4 : 8);
     void* Y[1] = {(char*)q.ws + xb};
     const void* S[1] = {plan_apply_spectrum(p)};
+    // bulk requests launch one CTA per tile: their blocks retire as they go,
+    // so kernels of the high-priority streams get SMs in between
+    launch_grid_mode() = bulk ? 1 : 0;
     e = run_group(p, 1, rho, phi, X, Y, S, stream);
+    launch_grid_mode() = 0;
     cudaFreeAsync(q.ws, stream);
   }
   if (e == cudaSuccess) {
@@ -275,6 +309,9 @@ bool try_admit(fsa_server* s, uint64_t id) {
   pit->second.refs++;
   q.ws_bytes = ws;
   q.stream = stream;
+  q.lane = lane;
+  q.work = work;
+  s->lane_work[lane] += work;
   s->held += ws;
   s->ws_inflight += ws;
   q.state = FSA_REQ_RUNNING;
@@ -304,6 +341,7 @@ void retire(fsa_server* s) {
     q.done = nullptr;
     s->held -= q.ws_bytes;
     s->ws_inflight -= q.ws_bytes;
+    if (q.lane >= 0) s->lane_work[q.lane] -= q.work;
     auto pit = s->plans.find(q.key);
     if (pit != s->plans.end()) pit->second.refs--;
     s->inflight[i] = s->inflight.back();
@@ -362,6 +400,7 @@ fsa_status fsa_serve_create(fsa_server** out, const fsa_serve_opts* opts) {
   if (!(o.hbm_fraction > 0 && o.hbm_fraction <= 1)) o.hbm_fraction = 0.9;
   if (o.plan_cache_max <= 0) o.plan_cache_max = 64;
   if (o.queue_max <= 0) o.queue_max = 1 << 20;
+  if (o.policy != 1) o.policy = 0;
   int dev = o.device;
   if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return set_error(FSA_ERR_CUDA, "fsa_serve_create: no device");
   int prev = 0;
@@ -375,11 +414,18 @@ fsa_status fsa_serve_create(fsa_server** out, const fsa_serve_opts* opts) {
   s->budget = (size_t)(o.hbm_fraction * (double)freeb);
   s->budget_cap = o.hbm_budget_bytes;
   if (o.hbm_budget_bytes && o.hbm_budget_bytes < s->budget) s->budget = o.hbm_budget_bytes;
+  // policy 0 (size-aware): a quarter of the streams (at least one) form the
+  // bulk lane at the lowest priority, the others run at the highest
+  int prio_lo = 0, prio_hi = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  s->nbulk = (o.policy == 0 && o.streams >= 2) ? std::max(1, o.streams / 4) : 0;
   for (int i = 0; e == cudaSuccess && i < o.streams; ++i) {
     cudaStream_t st;
-    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    const bool bulk_lane = s->nbulk > 0 && i >= o.streams - s->nbulk;
+    e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, s->nbulk == 0 ? 0 : (bulk_lane ? prio_lo : prio_hi));
     if (e == cudaSuccess) s->streams.push_back(st);
   }
+  s->lane_work.assign(s->streams.size(), 0.0);
   if (e == cudaSuccess) {
     cudaMemPoolProps pp{};
     pp.allocType = cudaMemAllocationTypePinned;

@@ -269,3 +269,37 @@ def test_server_charges_each_plan_its_real_bytes(lib):
         assert free0 - torch.cuda.mem_get_info()[0] >= want
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("policy", [0, 1])
+def test_bulk_lane_results_equal_solved_alone(lib, policy):
+    """A request large enough for the bulk lane (256^3 FP64: its grids launch
+    one CTA per tile on a low-priority stream under policy 0) served among
+    small ones: every result equals its plan solved alone, bit for bit, under
+    both scheduling policies."""
+    import torch
+    rng = np.random.default_rng(30 + policy)
+    big = ((16.0, 16.0, 16.0), (256, 256, 256), "f64")
+    smalls = [((4.0, 4.0, 3.0), (32, 32, 16), "f32"), ((4.0, 3.0, 4.0), (48, 24, 32), "f64"),
+              ((3.0, 3.0, 3.0), (64, 64, 64), "f32")]
+    reqs = [big] + smalls * 3
+    srv = lib.Server(max_inflight=8, streams=4, policy=policy)
+    try:
+        rhos, outs, tickets = [], [], []
+        for L, n, dt in reqs:
+            tdt = torch.float64 if dt == "f64" else torch.float32
+            rho = torch.from_numpy(rng.standard_normal(n)).to(tdt).cuda()
+            rhos.append(rho)
+            outs.append(torch.full_like(rho, float("nan")))
+            tickets.append(srv.submit(L, n, dt, rho, outs[-1]))
+        for t in tickets:
+            srv.wait(t)
+        torch.cuda.synchronize()
+        for (L, n, dt), rho, out in zip(reqs, rhos, outs):
+            p = lib.Plan(L, n, dt, eps=0.0)
+            want = p.apply(rho)
+            torch.cuda.synchronize()
+            p.close()
+            assert torch.equal(out, want), (n, dt)
+    finally:
+        srv.close()
