@@ -1110,6 +1110,10 @@ cudaError_t tune_f64(fsa_plan* p) {
   }
   if (mode != 1 || !p->ws) {
     p->f64_dw = 1;
+    // a plan without workspace (a serving plan) cannot be timed: it takes
+    // double-word, and in mode 1 that becomes the shape's choice, so that every
+    // later plan of the shape computes alike (served = solved alone)
+    if (mode == 1) choice[key] = 1;
     return cudaSuccess;
   }
   cudaStream_t s;

@@ -283,23 +283,22 @@ def test_bulk_lane_results_equal_solved_alone(lib, policy):
     smalls = [((4.0, 4.0, 3.0), (32, 32, 16), "f32"), ((4.0, 3.0, 4.0), (48, 24, 32), "f64"),
               ((3.0, 3.0, 3.0), (64, 64, 64), "f32")]
     reqs = [big] + smalls * 3
+    rhos, wants = [], []
+    for L, n, dt in reqs:  # solved alone first (the plans tune the kernels of their sizes)
+        tdt = torch.float64 if dt == "f64" else torch.float32
+        rhos.append(torch.from_numpy(rng.standard_normal(n)).to(tdt).cuda())
+        p = lib.Plan(L, n, dt, eps=0.0)
+        wants.append(p.apply(rhos[-1]))
+        torch.cuda.synchronize()
+        p.close()
     srv = lib.Server(max_inflight=8, streams=4, policy=policy)
     try:
-        rhos, outs, tickets = [], [], []
-        for L, n, dt in reqs:
-            tdt = torch.float64 if dt == "f64" else torch.float32
-            rho = torch.from_numpy(rng.standard_normal(n)).to(tdt).cuda()
-            rhos.append(rho)
-            outs.append(torch.full_like(rho, float("nan")))
-            tickets.append(srv.submit(L, n, dt, rho, outs[-1]))
+        outs = [torch.full_like(r, float("nan")) for r in rhos]
+        tickets = [srv.submit(L, n, dt, rho, out) for (L, n, dt), rho, out in zip(reqs, rhos, outs)]
         for t in tickets:
             srv.wait(t)
         torch.cuda.synchronize()
-        for (L, n, dt), rho, out in zip(reqs, rhos, outs):
-            p = lib.Plan(L, n, dt, eps=0.0)
-            want = p.apply(rho)
-            torch.cuda.synchronize()
-            p.close()
+        for (L, n, dt), out, want in zip(reqs, outs, wants):
             assert torch.equal(out, want), (n, dt)
     finally:
         srv.close()
