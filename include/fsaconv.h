@@ -112,6 +112,12 @@ typedef struct {
                    /* in L2; 0 or negative = one slab (the default: slabs of     */
                    /* 8-64 MB measured 1.3-3.6x slower at 256^3 on GB300, the    */
                    /* small slab launches cannot fill the GPU)                   */
+  int w_quadrature; /* 0 (default): W from its closed form (Table 1; Ex. 4);     */
+                    /* 1: W by the radial integral of Eq. Fourier-Symmetric with  */
+                    /* adaptive Gauss-Kronrod quadrature on the host, tabulated   */
+                    /* as piecewise Chebyshev series of k and evaluated on the    */
+                    /* device (the paper's route for kernels without a closed     */
+                    /* form; see fsa_radial_w)                                    */
 } fsa_plan_opts;
 
 typedef struct fsa_plan fsa_plan;
@@ -143,6 +149,8 @@ typedef struct {
   double dipole_m[3];
   int fused_fwd;            /* the outer forward pair in use (fsa_fused_select): 0    */
   int fused_inv;            /* separate passes, c >= 1 fused configuration c - 1     */
+  int w_quadrature;         /* 1 if W comes from the quadrature table, else 0         */
+  int w_panels;             /* that table's Chebyshev panels (0 without it)           */
 } fsa_plan_info;
 
 /* Create a plan (the "Precomp" object of Sec. 5, Example 2) for the grid
@@ -388,6 +396,25 @@ fsa_status fsa_device_fault(int device, unsigned int* code, int clear);
  * cleared again before return.  Synchronous; nothing faults or hangs.
  * Errors: FSA_ERR_INVALID_ARG (code NULL), FSA_ERR_CUDA. */
 fsa_status fsa_wait_selftest(int device, unsigned int* code);
+
+/* W(k) of `kernel` (Table 1's kernels, the Yukawa kernels with lam =
+ * kernel_param, 0 selecting 1; a DDI kernel as Coulomb) by the radial Fourier
+ * integral of U - U^eps (Sec. 2.2, Eq. Fourier-Symmetric: 4 pi int (U - U^eps)
+ * sin(kr)/(kr) r^2 dr in 3-D, 2 pi int (U - U^eps) J0(kr) r dr in 2-D), on
+ * the host in long double, by adaptive 15-point Gauss-Kronrod quadrature
+ * (see fsa_gauss_kronrod15) over [0, 7 eps].  *err_estimate (may be NULL):
+ * the summed |Kronrod - Gauss| of the final panels at this k.  This is the
+ * routine behind fsa_plan_opts.w_quadrature.  Errors: FSA_ERR_INVALID_ARG. */
+fsa_status fsa_radial_w(fsa_kernel kernel, double kernel_param, double eps, double k, double* w,
+                        double* err_estimate);
+
+/* The 15-point Gauss-Kronrod rule on [-1, 1] the radial quadrature uses,
+ * computed (not tabulated): the Kronrod extension of the 7-point Gauss-Legendre
+ * rule, new nodes from the Stieltjes polynomial, weights from exactness on the
+ * Legendre polynomials of degree < 15.  nodes ascending; gauss_weights is 0 at
+ * the 8 Kronrod-only nodes.  Each array holds 15 doubles.  Errors:
+ * FSA_ERR_INVALID_ARG (NULL). */
+fsa_status fsa_gauss_kronrod15(double* nodes, double* kronrod_weights, double* gauss_weights);
 
 /* Measured ALU peak (no counterpart in the paper: the denominator of the
  * ALU rooflines of the FP64 tier, whose double-word passes run on the FP32

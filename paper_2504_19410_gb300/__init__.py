@@ -32,11 +32,14 @@ class Plan:
     'biharmonic3d', 'poisson2d', 'coulomb2d' or 'biharmonic2d' (Table 1), or
     'ddi3d' (Sec. 5, Example 4: dipoles = (n, m), two 3-vectors, and
     ddi_derivative 'grid' or 'kernel'), or 'yukawa3d' / 'yukawa2d' (Example 4,
-    kernel_param = lam, 0 selects 1).  eps = 0 picks min(1, R0/6).  The
-    spectrum is generated on construction unless generate=False."""
+    kernel_param = lam, 0 selects 1).  eps = 0 picks min(1, R0/6).
+    w_quadrature=1 takes W from the radial Gauss-Kronrod quadrature of
+    Eq. Fourier-Symmetric instead of its closed form.  The spectrum is
+    generated on construction unless generate=False."""
 
     def __init__(self, L, n, dtype="f32", eps=0.0, eps_tol=0.0, device=-1, generate=True, stream=None,
-                 l2_chunk_mb=0, kernel="coulomb3d", dipoles=None, ddi_derivative="grid", kernel_param=0.0):
+                 l2_chunk_mb=0, kernel="coulomb3d", dipoles=None, ddi_derivative="grid", kernel_param=0.0,
+                 w_quadrature=0):
         self.dtype = _DT[dtype]
         self.n = tuple(int(x) for x in n)
         self.L = tuple(float(x) for x in L)
@@ -49,7 +52,7 @@ class Plan:
                                                      eps_tol, device)
         else:
             self.handle = capi.fsa_plan_create(self.kernel, len(self.n), self.L, self.n, self.dtype, eps, eps_tol,
-                                               device, l2_chunk_mb, kernel_param)
+                                               device, l2_chunk_mb, kernel_param, w_quadrature)
         if generate:
             self.generate(stream)
 

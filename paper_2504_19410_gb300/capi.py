@@ -45,7 +45,7 @@ class FsaError(RuntimeError):
 
 class PlanOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("eps_tol", C.c_double), ("device", C.c_int), ("kernel_param", C.c_double),
-                ("l2_chunk_mb", C.c_int)]
+                ("l2_chunk_mb", C.c_int), ("w_quadrature", C.c_int)]
 
 
 class PlanInfo(C.Structure):
@@ -58,7 +58,7 @@ class PlanInfo(C.Structure):
                 ("many_capacity", C.c_int),
                 ("ddi_derivative", C.c_int),
                 ("dipole_n", C.c_double * 3), ("dipole_m", C.c_double * 3),
-                ("fused_fwd", C.c_int), ("fused_inv", C.c_int)]
+                ("fused_fwd", C.c_int), ("fused_inv", C.c_int), ("w_quadrature", C.c_int), ("w_panels", C.c_int)]
 
 
 class ServeOpts(C.Structure):
@@ -112,6 +112,9 @@ _PROTOS = {
     "fsa_device_fault": (C.c_int, [C.c_int, C.POINTER(C.c_uint), C.c_int]),
     "fsa_wait_selftest": (C.c_int, [C.c_int, C.POINTER(C.c_uint)]),
     "fsa_measure_alu_peak": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_float)]),
+    "fsa_radial_w": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
+                               C.POINTER(C.c_double)]),
+    "fsa_gauss_kronrod15": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "fsa_profiler_create": (C.c_int, [C.POINTER(_VP), C.c_int]),
     "fsa_apply_profiled": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "fsa_profiler_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]),
@@ -174,10 +177,11 @@ def _stream(s):
 
 # ---- the C-ABI calls, same names ------------------------------------------------
 
-def fsa_plan_create(kernel, d, L, n, dtype, eps=0.0, eps_tol=0.0, device=-1, l2_chunk_mb=0, kernel_param=0.0):
+def fsa_plan_create(kernel, d, L, n, dtype, eps=0.0, eps_tol=0.0, device=-1, l2_chunk_mb=0, kernel_param=0.0,
+                    w_quadrature=0):
     h = _VP()
     o = PlanOpts(eps=float(eps), eps_tol=float(eps_tol), device=int(device), kernel_param=float(kernel_param),
-                 l2_chunk_mb=int(l2_chunk_mb))
+                 l2_chunk_mb=int(l2_chunk_mb), w_quadrature=int(w_quadrature))
     check(lib().fsa_plan_create(C.byref(h), int(kernel), int(d), (C.c_double * 3)(*[float(x) for x in L]),
                                 (C.c_int * 3)(*[int(x) for x in n]), int(dtype), C.byref(o)))
     return h.value
@@ -294,6 +298,20 @@ def fsa_device_fault(device=-1, clear=False):
     code = C.c_uint(0)
     check(lib().fsa_device_fault(int(device), C.byref(code), 1 if clear else 0))
     return code.value
+
+
+def fsa_radial_w(kernel, eps, k, kernel_param=0.0):
+    """(W(k), error estimate) by the radial Gauss-Kronrod quadrature (host)."""
+    w, e = C.c_double(), C.c_double()
+    check(lib().fsa_radial_w(int(kernel), float(kernel_param), float(eps), float(k), C.byref(w), C.byref(e)))
+    return w.value, e.value
+
+
+def fsa_gauss_kronrod15():
+    """(nodes, Kronrod weights, Gauss weights) of the 15-point rule on [-1, 1]."""
+    x, wk, wg = (C.c_double * 15)(), (C.c_double * 15)(), (C.c_double * 15)()
+    check(lib().fsa_gauss_kronrod15(x, wk, wg))
+    return list(x), list(wk), list(wg)
 
 
 def fsa_measure_alu_peak(kind, device=-1):

@@ -1,5 +1,6 @@
 // Internal declarations shared by the host-side translation units of libfsaconv.
 #pragma once
+#include <vector>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -97,6 +98,15 @@ enum Arith {
 using ColmFn = cudaError_t (*)(const Jobs&, int, int, cudaStream_t);
 ColmFn k6_colm(int M);
 cudaError_t k6_prepare(int M);
+// W(k) by the radial integrals of Eq. Fourier-Symmetric with adaptive
+// Gauss-Kronrod quadrature (radial_w.cpp).  radial_w_table: piecewise Chebyshev
+// series of degree kWTableDegree on [0, kmax]; layout: the P + 1 panel edges,
+// then P x (kWTableDegree + 1) coefficients (the first halved), P in *panels.
+constexpr int kWTableDegree = 24;
+long double u_minus_ueps(fsa_kernel kernel, long double lam, long double eps, long double r);
+bool radial_w_value(fsa_kernel kernel, double lam, double eps, double k, double* w, double* err);
+bool radial_w_table(fsa_kernel kernel, double lam, double eps, double kmax, std::vector<double>* table,
+                    int* panels);
 // The batched launcher's mixed-length path (mixed.cu, passes_mix.cuh): whether
 // a plan can join it, and the five launches for `count` such solves.
 bool mixed_eligible(const fsa_plan* p);
@@ -163,7 +173,8 @@ cudaError_t noalloc_resolve(int dev);
 cudaError_t tensorgen_init_twiddles();
 // param: the kernel's parameter (the Yukawa lam), ignored by the others
 cudaError_t tensorgen_run(fsa_kernel kernel, const int n[3], const double L[3], double eps, double param,
-                          double* oct64, void* out, fsa_dtype dtype, cudaStream_t s);
+                          double* oct64, void* out, fsa_dtype dtype, cudaStream_t s,
+                          const double* wtab = nullptr, int wtab_panels = 0);
 
 // Twiddle table exp(-2 pi i k / 3072), k < 3072, computed on the host.
 void host_twiddles(double* re, double* im);
@@ -204,4 +215,7 @@ struct fsa_plan {
   int ddi;
   fsa::DdiPar* ddi_par;  // device: the DDI parameters (fsa_consts.h)
   double dipole_n[3], dipole_m[3];
+  // fsa_plan_opts.w_quadrature: device copy of the W(k) table (radial_w.cpp)
+  double* wtab;
+  int wtab_panels;
 };

@@ -511,30 +511,6 @@ namespace {
 double appendix_b_bound_impl(double R0, double eps);
 
 // The far-field integral for a kernel of Table 1 (see fsa_appendix_b_bound_kernel).
-// E1(x), x > 0, in long double: series (Abramowitz & Stegun 5.1.11) below 1,
-// continued fraction (Press et al., Numerical Recipes, expint; modified
-// Lentz) above.
-long double expint_e1(long double x) {
-  if (x < 1.0L) {
-    long double sum = 0.0L, term = 1.0L;
-    for (int k = 1; k < 60; ++k) {
-      term *= -x / k;
-      sum += term / k;  // (-x)^k / (k k!)
-    }
-    return -0.577215664901532860606512090082402431L - logl(x) - sum;
-  }
-  long double b = x + 1.0L, c = 1.0e300L, d = 1.0L / b, h = d;
-  for (int i = 1; i < 400; ++i) {
-    const long double an = -(long double)i * i;
-    b += 2.0L;
-    d = 1.0L / (an * d + b);
-    c = b + an / c;
-    const long double del = c * d;
-    h *= del;
-    if (fabsl(del - 1.0L) < 1e-19L) break;
-  }
-  return h * expl(-x);
-}
 
 // The Yukawa kernels' far-field integral (fsa_appendix_b_bound_kernel_param):
 // int_0^{eps^2/4} f(t) dt with t = (eps^2/4) exp(-y), y in [0, Y], where the
@@ -577,11 +553,11 @@ double appendix_b_bound_kernel_impl(fsa_kernel kernel, double R0, double eps, do
   if (kernel == FSA_KERNEL_COULOMB2D) return (double)(e / (2 * pi) * (expl(-c * c) / sqrtl(pi) - c * erfcl(c)));
   if (kernel == FSA_KERNEL_POISSON2D) {
     const long double a = c * c;
-    return (double)(e * e / (8 * pi) * (expl(-a) - a * expint_e1(a)));
+    return (double)(e * e / (8 * pi) * (expl(-a) - a * fsa::expint_e1(a)));
   }
   if (kernel == FSA_KERNEL_BIHARMONIC2D) {
     const long double a = c * c;
-    return (double)(e * e * e * e / (64 * pi) * ((1 + a) * expl(-a) - a * a * expint_e1(a)));
+    return (double)(e * e * e * e / (64 * pi) * ((1 + a) * expl(-a) - a * a * fsa::expint_e1(a)));
   }
   if (kernel != FSA_KERNEL_BIHARMONIC3D) return NAN;
   // (eps^4/(8 pi)) int_c^inf s^3 erfc(s) ds; by parts,
@@ -1146,11 +1122,38 @@ cudaError_t tune_f64(fsa_plan* p) {
   return e;
 }
 
+// fsa_plan_opts.w_quadrature: tabulate W(k) on [0, |mu|_max] by the radial
+// Gauss-Kronrod quadrature (radial_w.cpp) and copy the table to the device.
+fsa_status attach_w_table(fsa_plan* p) {
+  const double pi = 3.141592653589793238462643383279502884;
+  double k2 = 0;
+  for (int j = 0; j < p->d; ++j) {
+    const double m = pi * p->n[j] / (2.0 * p->L[j]);
+    k2 += m * m;
+  }
+  const fsa_kernel k = p->kernel == FSA_KERNEL_DDI3D ? FSA_KERNEL_COULOMB3D : p->kernel;
+  std::vector<double> tab;
+  int panels = 0;
+  if (!radial_w_table(k, p->param, p->eps, std::sqrt(k2), &tab, &panels))
+    return set_error(FSA_ERR_CUDA, "fsa_plan_create: W quadrature table failed");
+  cudaError_t e = cudaMalloc(&p->wtab, tab.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(p->wtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (p->wtab) cudaFree(p->wtab);
+    p->wtab = nullptr;
+    cudaGetLastError();
+    return cuda_error(e, "fsa_plan_create: W table upload");
+  }
+  p->wtab_panels = panels;
+  return FSA_OK;
+}
+
 cudaError_t plan_generate_into(fsa_plan* p, void* scratch, cudaStream_t s) {
   double* oct = p->dtype == FSA_F64 ? (double*)p->spectrum : (double*)scratch;
   // a DDI plan's tensor is the Coulomb kernel's (Sec. 5, Example 4)
   const fsa_kernel k = p->kernel == FSA_KERNEL_DDI3D ? FSA_KERNEL_COULOMB3D : p->kernel;
-  cudaError_t e = tensorgen_run(k, p->n, p->L, p->eps, p->param, oct, p->spectrum, p->dtype, s);
+  cudaError_t e = tensorgen_run(k, p->n, p->L, p->eps, p->param, oct, p->spectrum, p->dtype, s, p->wtab,
+                                p->wtab_panels);
   if (e == cudaSuccess && p->spectrum_dw)
     e = spectrum_to_dw((const double*)p->spectrum, p->spectrum_dw, p->spectrum_bytes / 8, s);
   if (e == cudaSuccess) p->generated = 1;
@@ -1193,6 +1196,13 @@ fsa_status fsa_plan_create(fsa_plan** out, fsa_kernel kernel, int d, const doubl
   if (e != cudaSuccess) return cuda_error(e, "fsa_plan_create: cudaSetDevice");
   fsa_status st = plan_create_core(out, kernel, L, n, dtype, o.eps, o.eps_tol, true, 0, false, param);
   if (st == FSA_OK && o.l2_chunk_mb != 0) (*out)->chunk_bytes = o.l2_chunk_mb > 0 ? (long long)o.l2_chunk_mb << 20 : 0;
+  if (st == FSA_OK && o.w_quadrature == 1) {
+    st = attach_w_table(*out);
+    if (st != FSA_OK) {
+      fsa_plan_destroy(*out);
+      *out = nullptr;
+    }
+  }
   return st;
 }
 
@@ -1231,6 +1241,13 @@ fsa_status fsa_plan_create_ddi3d(fsa_plan** out, const double* L, const int* n, 
     p->dipole_n[j] = dipole_n[j];
     p->dipole_m[j] = dipole_m[j];
   }
+  if (o.w_quadrature == 1) {
+    st = attach_w_table(p);
+    if (st != FSA_OK) {
+      fsa_plan_destroy(p);
+      return st;
+    }
+  }
   DdiPar par{};
   ddi_params(p, derivative, &par);
   // one allocation: the block, then the per-line coefficient table
@@ -1259,6 +1276,7 @@ fsa_status fsa_plan_destroy(fsa_plan* p) {
   DeviceGuard dg;
   dg.set(p->device);
   if (p->ddi_par) cudaFree(p->ddi_par);
+  if (p->wtab) cudaFree(p->wtab);
   if (p->ws_many) cudaFree(p->ws_many);
   cudaFree(p->spectrum);
   if (p->spectrum_dw) cudaFree(p->spectrum_dw);
@@ -1304,6 +1322,8 @@ fsa_status fsa_plan_info_get(const fsa_plan* p, fsa_plan_info* info) {
     info->launches_per_apply -= (info->fused_fwd > 0) + (info->fused_inv > 0);
     if (p->ddi >= 0) info->launches_per_apply = p->ddi == FSA_DDI_GRID ? 10 : 5;
   }
+  info->w_quadrature = p->wtab ? 1 : 0;
+  info->w_panels = p->wtab_panels;
   info->workspace_bytes = p->ws_bytes;
   info->spectrum_bytes = p->spectrum_bytes;
   info->spectrum = p->spectrum;

@@ -209,10 +209,33 @@ __global__ void k_t1_octant(double* __restrict__ O, int kernel, int n0, int n1, 
   }
 }
 
+// W(k) from the quadrature table of radial_w.cpp: the panel holding k (binary
+// search over the edges), then its Chebyshev series by Clenshaw's recurrence.
+__device__ double w_from_table(const double* __restrict__ tab, int P, double k) {
+  constexpr int N = kWTableDegree + 1;
+  int lo = 0, hi = P - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid] <= k) lo = mid;
+    else hi = mid - 1;
+  }
+  const double a = tab[lo], b = tab[lo + 1];
+  const double t = fmin(1.0, fmax(-1.0, (2.0 * k - a - b) / (b - a)));
+  const double* c = tab + P + 1 + (size_t)lo * N;
+  double b1 = 0, b2 = 0;
+  for (int m = N - 1; m >= 1; --m) {
+    const double b0 = fma(2.0 * t, b1, c[m] - b2);
+    b2 = b1;
+    b1 = b0;
+  }
+  return fma(t, b1, c[0] - b2);
+}
+
 template <typename R>
 __global__ void k_spectrum_finalize(const double* S1, R* S,  // may alias (FP64 plans)
                                     int kernel, int n0, int n1, int n2,
-                                    double c0, double c1, double c2, double eps, double lam, double inv_norm) {
+                                    double c0, double c1, double c2, double eps, double lam, double inv_norm,
+                                    const double* __restrict__ wtab, int wpanels) {
   const long long total = (long long)(n0 + 1) * (n1 + 1) * (n2 + 1);
   const double e2 = eps * eps;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -223,7 +246,7 @@ __global__ void k_spectrum_finalize(const double* S1, R* S,  // may alias (FP64 
     const int p0 = (int)(r01 / (n1 + 1));
     const double m0 = c0 * p0, m1 = c1 * p1, m2 = c2 * p2;  // mu_j = pi p_j / (2 L_j)
     const double k2 = m0 * m0 + m1 * m1 + m2 * m2;
-    const double w = singular_W(kernel, k2, e2, lam);
+    const double w = wtab ? w_from_table(wtab, wpanels, sqrt(k2)) : singular_W(kernel, k2, e2, lam);
     S[i] = (R)((S1[i] + w) * inv_norm);
   }
 }
@@ -318,7 +341,7 @@ cudaError_t tensorgen_init_twiddles() {
 }
 
 cudaError_t tensorgen_run(fsa_kernel kernel, const int n[3], const double L[3], double eps, double lam, double* O,
-                          void* out, fsa_dtype dtype, cudaStream_t s) {
+                          void* out, fsa_dtype dtype, cudaStream_t s, const double* wtab, int wtab_panels) {
   // d = 2: a single plane of the octant (n2 = 0 here, unit h2), no axis-2 DCT
   const bool plane = kernel_dim(kernel) == 2;
   const int n0 = n[0], n1 = n[1], n2 = plane ? 0 : n[2];
@@ -341,10 +364,12 @@ cudaError_t tensorgen_run(fsa_kernel kernel, const int n[3], const double L[3], 
   const double c2 = plane ? 0.0 : pi / (2 * L[2]);
   if (dtype == FSA_F64)
     k_spectrum_finalize<double><<<blocks, threads, 0, s>>>(O, (double*)out, (int)kernel, n0, n1, n2, pi / (2 * L[0]),
-                                                           pi / (2 * L[1]), c2, eps, lam, inv_norm);
+                                                           pi / (2 * L[1]), c2, eps, lam, inv_norm, wtab,
+                                                           wtab_panels);
   else
     k_spectrum_finalize<float><<<blocks, threads, 0, s>>>(O, (float*)out, (int)kernel, n0, n1, n2, pi / (2 * L[0]),
-                                                          pi / (2 * L[1]), c2, eps, lam, inv_norm);
+                                                          pi / (2 * L[1]), c2, eps, lam, inv_norm, wtab,
+                                                          wtab_panels);
   return cudaGetLastError();
 }
 
