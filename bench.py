@@ -483,24 +483,33 @@ def run_ours(args):
 
 def bench_batched(args, fsa, W, torch, stream):
     """64 seeded Gaussian-sum densities, cubic n from {64,96,128,192,256},
-    gamma in {1,4,8} (cigar or pancake), FP32, in one batched call (one
-    persistent launch per pass over all 64 solves' tiles, captured in a CUDA
-    graph), against the same 64 solves issued one fsa_apply at a time."""
+    gamma in {1,4,8} (cigar or pancake), FP32, in one batched call (persistent
+    launches over all 64 solves' concatenated tile lists, captured in a CUDA
+    graph; every scheduling mode of fsa_batched_mode_set timed), against the
+    same 64 solves issued one fsa_apply at a time."""
     dens = W.batch_requests(seed=2504, count=64)
     plans = [fsa.Plan(d.L, d.n, "f32", eps=d.eps) for d in dens]
     rhos = [d.rho_torch(torch.float32) for d in dens]
     phis = [torch.empty_like(r) for r in rhos]
-    for _ in range(2):
-        fsa.apply_batched(plans, rhos, phis)
-    torch.cuda.synchronize()
     k = max(3, args.steps // 5)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(k):
-        fsa.apply_batched(plans, rhos, phis)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    tb = e0.elapsed_time(e1) / k
+    modes = {}
+    # fsa_batched_mode_set: 0 pipelined mixed path (the default), 1 one mixed
+    # launch per pass, 2 per-shape groups on concurrent streams
+    for mode in (1, 2, 0):
+        fsa.capi.fsa_batched_mode_set(mode)
+        for _ in range(2):
+            fsa.apply_batched(plans, rhos, phis)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fsa.apply_batched(plans, rhos, phis)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_m = e0.elapsed_time(e1) / k
+        modes[mode] = {"ms_per_batch": t_m, "solves_per_s": len(dens) / (t_m * 1e-3),
+                       "gpu_launches_per_batch": fsa.capi.fsa_apply_batched_launches([p.handle for p in plans])}
+    tb = modes[0]["ms_per_batch"]
     for p, r, f in zip(plans, rhos, phis):
         p.apply(r, f)
     torch.cuda.synchronize()
@@ -521,10 +530,12 @@ def bench_batched(args, fsa, W, torch, stream):
            "value": len(dens) / (tb * 1e-3), "unit": UNIT, "ms_per_batch": tb,
            "sequential_solves_per_s": len(dens) / (ts * 1e-3), "ms_sequential": ts,
            "step_roofline_frac_27V_model": bytes_model / (hbm_peak * 1e9) / (tb * 1e-3),
-           # the library's own count: 5 for the mixed-length path (one launch
-           # per pass for all 64 solves), more where solves fall into groups
-           "gpu_launches_per_batch": fsa.capi.fsa_apply_batched_launches([p.handle for p in plans]),
-           "path": "mixed-length kernels: one persistent launch per pass over the concatenated tile lists"}
+           # the library's own count of the default mode's launches
+           "gpu_launches_per_batch": modes[0]["gpu_launches_per_batch"],
+           "path": "mixed-length kernels, software-pipelined over two halves: six launches, the middle four "
+                   "each a pass of one half beside the previous pass of the other, tiles interleaved",
+           "modes": {"0 pipelined mixed (default)": modes[0], "1 one mixed launch per pass": modes[1],
+                     "2 per-shape groups, concurrent streams": modes[2]}}
     for p in plans:
         p.close()
     del rhos, phis

@@ -235,9 +235,10 @@ fsa_status fsa_apply_host(const fsa_plan* plan, const void* rho_host, void* phi_
 /* Apply count plans to count densities in one launch sequence.  Plans may
  * differ in n, L, eps and dtype but must share a device.  The requests whose
  * plan is an FP32 plan of d = 3 (not DDI, no pass split) with every transform
- * length 2 n_j in {128, 192, 256, 384, 512} run as five launches in all: each
- * pass is one persistent launch over the concatenated tile lists of all of
- * them, whatever their sizes; such a request's result matches
+ * length 2 n_j in {128, 192, 256, 384, 512} share one persistent launch per
+ * pass over the concatenated tile lists of all of them, whatever their sizes
+ * (six launches in all by default, pipelined in two halves; five with
+ * fsa_batched_mode_set(1)); such a request's result matches
  * fsa_apply(plans[k], rho[k], phi[k]) within FP32 round-off (the same
  * transforms, factored as 16 x (M / 16)), not bit for bit.  The other
  * requests are grouped by grid and dtype, each group's passes run as
@@ -251,10 +252,23 @@ fsa_status fsa_apply_host(const fsa_plan* plan, const void* rho_host, void* phi_
 fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void* const* rho,
                              void* const* phi, int count, fsa_stream_t stream);
 
+/* How fsa_apply_batched schedules the requests that fit the mixed-length
+ * kernels (no counterpart in the paper: a tuning switch of the batched path;
+ * process-wide, applies to batches captured afterwards).  mode 0 (default):
+ * software-pipelined, the requests split into two halves of balanced work and
+ * six launches in all, the middle four each running half A's pass p beside half
+ * B's pass p - 1 with their tiles interleaved (the arithmetic-bound middle pass
+ * beside an HBM-bound row pass).  mode 1: one launch per pass, five in all.
+ * mode 2: no mixed path; every request in its shape group (one persistent
+ * launch per pass per group, groups on concurrent streams).  Results of modes
+ * 0 and 1 are the same bits.  Errors: FSA_ERR_INVALID_ARG (other modes). */
+fsa_status fsa_batched_mode_set(int mode);
+
 /* How many kernel launches fsa_apply_batched makes for these plans (no
  * counterpart in the paper: launch accounting for the batched path): five per
  * 64 requests of the mixed path, plus each group's launches per apply per 64
- * requests.  Host only.  Errors: FSA_ERR_INVALID_ARG (NULL). */
+ * requests (six for a pipelined batch, see fsa_batched_mode_set).  Host
+ * only.  Errors: FSA_ERR_INVALID_ARG (NULL). */
 fsa_status fsa_apply_batched_launches(const fsa_plan* const* plans, int count, int* launches);
 
 /* Many densities through one plan (the paper's Execution phase repeated with one

@@ -96,6 +96,7 @@ _PROTOS = {
     "fsa_apply_noalloc": (C.c_int, [_VP, _VP, _VP, _VP]),
     "fsa_apply_batched": (C.c_int, [C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), C.c_int, _VP]),
     "fsa_apply_batched_launches": (C.c_int, [C.POINTER(_VP), C.c_int, C.POINTER(C.c_int)]),
+    "fsa_batched_mode_set": (C.c_int, [C.c_int]),
     "fsa_plan_reserve": (C.c_int, [_VP, C.c_int]),
     "fsa_apply_many": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP), C.c_int, _VP]),
     "fsa_plan_info_get": (C.c_int, [_VP, C.POINTER(PlanInfo)]),
@@ -218,6 +219,11 @@ def fsa_apply_batched(plans, rhos, phis, stream=None):
     R = (_VP * k)(*[_ptr(r) for r in rhos])
     F = (_VP * k)(*[_ptr(f) for f in phis])
     return check(lib().fsa_apply_batched(P, R, F, k, _stream(stream)))
+
+
+def fsa_batched_mode_set(mode):
+    """0 pipelined mixed path (default), 1 one launch per pass, 2 shape groups only."""
+    return check(lib().fsa_batched_mode_set(int(mode)))
 
 
 def fsa_apply_batched_launches(plans):

@@ -113,7 +113,7 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
   std::vector<void*> mphi;
   for (int k = 0; k < count; ++k) {
     const fsa_plan* p = plans[k];
-    if (mixed_eligible(p)) {
+    if (batched_mode() != 2 && mixed_eligible(p)) {
       mplans.push_back(p);
       mrho.push_back(rho[k]);
       mphi.push_back(phi[k]);
@@ -127,6 +127,7 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
     return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched: a plan appears twice (its workspace is shared)");
 
   Sig sig;
+  sig.v.push_back(reinterpret_cast<const void*>((uintptr_t)batched_mode()));  // the mode shapes the graph
   for (int k = 0; k < count; ++k) {
     sig.v.push_back(plans[k]);
     sig.v.push_back(rho[k]);
@@ -190,6 +191,12 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
   return FSA_OK;
 }
 
+extern "C" fsa_status fsa_batched_mode_set(int mode) {
+  if (mode < 0 || mode > 2) return set_error(FSA_ERR_INVALID_ARG, "fsa_batched_mode_set: mode must be 0, 1 or 2");
+  batched_mode() = mode;
+  return FSA_OK;
+}
+
 extern "C" fsa_status fsa_apply_batched_launches(const fsa_plan* const* plans, int count, int* launches) {
   if (!launches || count < 0 || (count > 0 && !plans))
     return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched_launches: bad arguments");
@@ -198,7 +205,7 @@ extern "C" fsa_status fsa_apply_batched_launches(const fsa_plan* const* plans, i
   for (int k = 0; k < count; ++k) {
     const fsa_plan* p = plans[k];
     if (!p) return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched_launches: NULL plan");
-    if (mixed_eligible(p)) {
+    if (batched_mode() != 2 && mixed_eligible(p)) {
       ++mixed;
     } else {
       auto& g = groups[GroupKey{p->n[0], p->n[1], p->n[2], (int)p->dtype, p->f64_dw, p->ddi}];
@@ -208,7 +215,7 @@ extern "C" fsa_status fsa_apply_batched_launches(const fsa_plan* const* plans, i
       g.second = info.launches_per_apply;
     }
   }
-  int n = 5 * ((mixed + kMaxJobs - 1) / kMaxJobs);
+  int n = mixed_launches(mixed);
   for (auto& kv : groups) n += kv.second.second * ((kv.second.first + kMaxJobs - 1) / kMaxJobs);
   *launches = n;
   return FSA_OK;
@@ -223,7 +230,7 @@ void batched_forget_plan(const fsa_plan* p) {
     DeviceCtx& c = dc.second;
     for (auto it = c.lru.begin(); it != c.lru.end();) {
       bool uses = false;
-      for (size_t i = 0; i < it->v.size(); i += 3) uses |= (it->v[i] == p);
+      for (size_t i = 1; i < it->v.size(); i += 3) uses |= (it->v[i] == p);  // v = mode, then (plan, rho, phi)...
       if (uses) {
         cudaGraphExecDestroy(c.graphs[*it]);
         c.graphs.erase(*it);

@@ -112,6 +112,9 @@ bool radial_w_table(fsa_kernel kernel, double lam, double eps, double kmax, std:
 bool mixed_eligible(const fsa_plan* p);
 cudaError_t mixed_passes(int count, const fsa_plan* const* plans, const void* const* rho, void* const* phi,
                          cudaStream_t s);
+int mixed_launches(int count);  // launches mixed_passes makes for `count` solves
+// fsa_batched_mode_set: 0 pipelined mixed path, 1 one launch per pass, 2 shape groups only
+int& batched_mode();
 // The fused outer pass pair used for FP32 grids with n0 = n2 and transform
 // length M = 2 n0 (dir 0 forward, 1 inverse): 0 = the separate passes, c >= 1
 // = fused cluster configuration c - 1.  set_fused_config(M, dir, -1) leaves

@@ -235,6 +235,49 @@ __host__ __device__ constexpr bool mix_supported(int M) {
   return M == 128 || M == 192 || M == 256 || M == 384 || M == 512;
 }
 
+template <int PASS> __device__ __forceinline__ void mix_dispatch(const MixJob& jb, long long lt, float2* sm) {
+  switch (mix_length(PASS, jb.n0, jb.n1, jb.n2)) {
+    case 128: mix_tile<PASS, 128>(jb, lt, sm); break;
+    case 192: mix_tile<PASS, 192>(jb, lt, sm); break;
+    case 256: mix_tile<PASS, 256>(jb, lt, sm); break;
+    case 384: mix_tile<PASS, 384>(jb, lt, sm); break;
+    default: mix_tile<PASS, 512>(jb, lt, sm); break;
+  }
+}
+
+// Two passes of two halves of a batch in one launch (software pipelining:
+// half A's pass PA beside half B's pass PB, whose inputs are ready): the two
+// tile lists are interleaved tile by tile, so the CTAs on an SM run tiles of
+// both passes at once -- the middle pass, bound by its arithmetic, beside a
+// row pass, bound by HBM.
+template <int PA, int PB>
+__global__ void __launch_bounds__(kMixNT, 2) k_mix2(const MixJobs a, const MixJobs b) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const long long ta = a.begin[a.count], tb = b.begin[b.count], both = ta < tb ? ta : tb;
+  const long long total = ta + tb;
+  int ka = 0, kb = 0;
+  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    // tile -> (list, index): alternate while both lists last, then the longer one
+    bool in_a;
+    long long i;
+    if (tile < 2 * both) {
+      in_a = (tile & 1) == 0;
+      i = tile >> 1;
+    } else {
+      in_a = ta > tb;
+      i = tile - both;
+    }
+    if (in_a) {
+      while (i >= a.begin[ka + 1]) ++ka;
+      mix_dispatch<PA>(a.j[ka], i - a.begin[ka], sm);
+    } else {
+      while (i >= b.begin[kb + 1]) ++kb;
+      mix_dispatch<PB>(b.j[kb], i - b.begin[kb], sm);
+    }
+  }
+}
+
 template <int PASS>
 __global__ void __launch_bounds__(kMixNT, 2) k_mix(const MixJobs js) {
   extern __shared__ __align__(16) unsigned char smraw[];

@@ -139,6 +139,23 @@ def test_batched_c4_mix_equals_single(lib):
         a, b = o.double().cpu().numpy(), s.double().cpu().numpy()
         assert oracle.rel_error(a, b) <= 1e-6
         assert oracle.rel_error(a, oracle.solve(d.L, d.n, d.eps, d.rho())) <= 2e-6
+    # the other schedules: one mixed launch per pass gives the same bits as the
+    # pipelined default; the per-shape groups give fsa_apply's bits
+    from paper_2504_19410_gb300 import capi
+    try:
+        for mode, want in ((1, first), (2, singles)):
+            capi.fsa_batched_mode_set(mode)
+            assert capi.fsa_apply_batched_launches([p.handle for p in plans]) == (5 if mode == 1 else
+                                                                                    capi.fsa_apply_batched_launches([p.handle for p in plans]))
+            for o in outs:
+                o.fill_(float("nan"))
+            lib.apply_batched(plans, rhos, outs)
+            torch.cuda.synchronize()
+            for o, w in zip(outs, want):
+                assert torch.equal(o, w), mode
+    finally:
+        capi.fsa_batched_mode_set(0)
+    assert capi.fsa_apply_batched_launches([p.handle for p in plans]) == 6
     for p in plans:
         p.close()
 
