@@ -494,9 +494,10 @@ def bench_batched(args, fsa, W, torch, stream):
     k = max(3, args.steps // 5)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     modes = {}
-    # fsa_batched_mode_set: 0 pipelined mixed path (the default), 1 one mixed
-    # launch per pass, 2 per-shape groups on concurrent streams
-    for mode in (1, 2, 0):
+    # fsa_batched_mode_set: 0 auto (the default: times 1 and 2 on the first
+    # call, keeps the faster), 1 one mixed launch per pass, 2 per-shape groups
+    # on concurrent streams, 3 mixed pipelined in two halves
+    for mode in (1, 2, 3, 0):
         fsa.capi.fsa_batched_mode_set(mode)
         for _ in range(2):
             fsa.apply_batched(plans, rhos, phis)
@@ -532,10 +533,11 @@ def bench_batched(args, fsa, W, torch, stream):
            "step_roofline_frac_27V_model": bytes_model / (hbm_peak * 1e9) / (tb * 1e-3),
            # the library's own count of the default mode's launches
            "gpu_launches_per_batch": modes[0]["gpu_launches_per_batch"],
-           "path": "mixed-length kernels, software-pipelined over two halves: six launches, the middle four "
-                   "each a pass of one half beside the previous pass of the other, tiles interleaved",
-           "modes": {"0 pipelined mixed (default)": modes[0], "1 one mixed launch per pass": modes[1],
-                     "2 per-shape groups, concurrent streams": modes[2]}}
+           "path": "auto: the faster of the mixed path (one persistent launch per pass over the 64 solves' "
+                   "concatenated tile lists) and per-shape groups, timed on the first call",
+           "modes": {"0 auto (default)": modes[0], "1 mixed, one launch per pass": modes[1],
+                     "2 per-shape groups, concurrent streams": modes[2],
+                     "3 mixed, pipelined halves": modes[3]}}
     for p in plans:
         p.close()
     del rhos, phis

@@ -235,10 +235,11 @@ fsa_status fsa_apply_host(const fsa_plan* plan, const void* rho_host, void* phi_
 /* Apply count plans to count densities in one launch sequence.  Plans may
  * differ in n, L, eps and dtype but must share a device.  The requests whose
  * plan is an FP32 plan of d = 3 (not DDI, no pass split) with every transform
- * length 2 n_j in {128, 192, 256, 384, 512} share one persistent launch per
- * pass over the concatenated tile lists of all of them, whatever their sizes
- * (six launches in all by default, pipelined in two halves; five with
- * fsa_batched_mode_set(1)); such a request's result matches
+ * length 2 n_j in {128, 192, 256, 384, 512} can share one persistent launch
+ * per pass over the concatenated tile lists of all of them, whatever their
+ * sizes (the mixed path; whether a batch takes it is fsa_batched_mode_set's
+ * choice, by default timed on the batch's first call); such a request's
+ * result matches
  * fsa_apply(plans[k], rho[k], phi[k]) within FP32 round-off (the same
  * transforms, factored as 16 x (M / 16)), not bit for bit.  The other
  * requests are grouped by grid and dtype, each group's passes run as
@@ -253,22 +254,28 @@ fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void* const* rh
                              void* const* phi, int count, fsa_stream_t stream);
 
 /* How fsa_apply_batched schedules the requests that fit the mixed-length
- * kernels (no counterpart in the paper: a tuning switch of the batched path;
- * process-wide, applies to batches captured afterwards).  mode 0 (default):
- * software-pipelined, the requests split into two halves of balanced work and
- * six launches in all, the middle four each running half A's pass p beside half
- * B's pass p - 1 with their tiles interleaved (the arithmetic-bound middle pass
- * beside an HBM-bound row pass).  mode 1: one launch per pass, five in all.
+ * kernels (no counterpart in the paper: the batched path's schedule choice;
+ * process-wide, applies to batch signatures captured afterwards).
+ * mode 0 (default, auto): the first call of a batch signature captures the
+ * candidates of modes 1 and 2, launches each twice (the second timed) and
+ * keeps the faster; that call's results are from the kept schedule.
+ * mode 1: the mixed-length requests in one launch per pass, five in all.
  * mode 2: no mixed path; every request in its shape group (one persistent
- * launch per pass per group, groups on concurrent streams).  Results of modes
- * 0 and 1 are the same bits.  Errors: FSA_ERR_INVALID_ARG (other modes). */
+ * launch per pass per group, groups on concurrent streams).
+ * mode 3: the mixed-length requests software-pipelined in two halves of
+ * balanced work, six launches, the middle four each running one half's pass
+ * beside the other's previous pass with their tiles interleaved.
+ * Results of modes 1 and 3 are the same bits; mode 2 gives fsa_apply's bits.
+ * Errors: FSA_ERR_INVALID_ARG (other modes). */
 fsa_status fsa_batched_mode_set(int mode);
 
 /* How many kernel launches fsa_apply_batched makes for these plans (no
  * counterpart in the paper: launch accounting for the batched path): five per
  * 64 requests of the mixed path, plus each group's launches per apply per 64
- * requests (six for a pipelined batch, see fsa_batched_mode_set).  Host
- * only.  Errors: FSA_ERR_INVALID_ARG (NULL). */
+ * requests (six for a pipelined batch), under the schedule
+ * fsa_batched_mode_set selects (mode 0: the one kept for these plans once a
+ * batch of them has run, the mixed path before).  Host only.  Errors:
+ * FSA_ERR_INVALID_ARG (NULL). */
 fsa_status fsa_apply_batched_launches(const fsa_plan* const* plans, int count, int* launches);
 
 /* Many densities through one plan (the paper's Execution phase repeated with one

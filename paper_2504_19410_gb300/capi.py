@@ -222,7 +222,8 @@ def fsa_apply_batched(plans, rhos, phis, stream=None):
 
 
 def fsa_batched_mode_set(mode):
-    """0 pipelined mixed path (default), 1 one launch per pass, 2 shape groups only."""
+    """0 auto (time 1 and 2 on a batch's first call), 1 mixed one launch per pass,
+    2 shape groups only, 3 mixed pipelined in two halves."""
     return check(lib().fsa_batched_mode_set(int(mode)))
 
 

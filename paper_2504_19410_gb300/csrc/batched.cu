@@ -18,6 +18,7 @@
 #include <list>
 #include <map>
 #include <mutex>
+#include <set>
 #include <vector>
 
 #include "fsa_internal.h"
@@ -84,6 +85,60 @@ cudaError_t launch_group(const std::vector<int>& idx, const fsa_plan* const* pla
   return run_group(p0, (int)idx.size(), r.data(), f.data(), X.data(), Y.data(), S.data(), s, nullptr, par.data());
 }
 
+// Schedule chosen for a list of plans (auto mode's pick, or the forced one),
+// for fsa_apply_batched_launches.
+std::map<std::vector<const void*>, int> g_choice;
+
+// Capture one batch into an executable graph.  sched 1: the mixed-length
+// requests in one launch per pass (mixed.cu), the rest in shape groups on side
+// streams; 3: the same with the mixed requests pipelined in two halves; 2: every
+// request in its shape group (one persistent launch per pass per group, the
+// groups on concurrent streams).
+cudaError_t capture_batch(DeviceCtx& c, int count, const fsa_plan* const* plans, const void* const* rho,
+                          void* const* phi, int sched, cudaGraphExec_t* exec) {
+  std::map<GroupKey, std::vector<int>> groups;
+  std::vector<const fsa_plan*> mplans;
+  std::vector<const void*> mrho;
+  std::vector<void*> mphi;
+  for (int k = 0; k < count; ++k) {
+    const fsa_plan* p = plans[k];
+    if (sched != 2 && mixed_eligible(p)) {
+      mplans.push_back(p);
+      mrho.push_back(rho[k]);
+      mphi.push_back(phi[k]);
+    } else {
+      groups[GroupKey{p->n[0], p->n[1], p->n[2], (int)p->dtype, p->f64_dw, p->ddi}].push_back(k);
+    }
+  }
+  const bool mixed = !mplans.empty();
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c.capture, cudaStreamCaptureModeThreadLocal);
+  // the mixed launches on the capture stream; every group on a side stream
+  size_t g = mixed ? 1 : 0;
+  cudaError_t le = e;
+  if (mixed && le == cudaSuccess)
+    le = mixed_passes((int)mplans.size(), mplans.data(), mrho.data(), mphi.data(), c.capture, sched == 3);
+  for (auto& kv : groups) {
+    if (le != cudaSuccess) break;
+    if (g == 0) {
+      le = launch_group(kv.second, plans, rho, phi, c.capture);
+    } else {
+      cudaStream_t s = c.side[g - 1];
+      le = cudaEventRecord(c.ev[2 * g], c.capture);
+      if (le == cudaSuccess) le = cudaStreamWaitEvent(s, c.ev[2 * g], 0);
+      if (le == cudaSuccess) le = launch_group(kv.second, plans, rho, phi, s);
+      if (le == cudaSuccess) le = cudaEventRecord(c.ev[2 * g + 1], s);
+      if (le == cudaSuccess) le = cudaStreamWaitEvent(c.capture, c.ev[2 * g + 1], 0);
+    }
+    ++g;
+  }
+  if (e == cudaSuccess) e = cudaStreamEndCapture(c.capture, &graph);
+  if (e == cudaSuccess) e = le;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  return e;
+}
+
 }  // namespace
 }  // namespace fsa
 
@@ -95,7 +150,6 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
     return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched: bad arguments");
   if (count == 0) return FSA_OK;
   const int dev = plans[0] ? plans[0]->device : -1;
-  std::map<GroupKey, std::vector<int>> groups;
   std::vector<const fsa_plan*> seen;
   for (int k = 0; k < count; ++k) {
     const fsa_plan* p = plans[k];
@@ -106,32 +160,25 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
       return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched: rho and phi must be 16-byte aligned");
     seen.push_back(p);
   }
-  // the solves that fit the mixed-length kernels (FP32, d = 3, transform
-  // lengths 128 ... 512) share one launch per pass; the others are grouped
-  std::vector<const fsa_plan*> mplans;
-  std::vector<const void*> mrho;
-  std::vector<void*> mphi;
-  for (int k = 0; k < count; ++k) {
-    const fsa_plan* p = plans[k];
-    if (batched_mode() != 2 && mixed_eligible(p)) {
-      mplans.push_back(p);
-      mrho.push_back(rho[k]);
-      mphi.push_back(phi[k]);
-    } else {
-      groups[GroupKey{p->n[0], p->n[1], p->n[2], (int)p->dtype, p->f64_dw, p->ddi}].push_back(k);
-    }
-  }
-  const bool mixed = !mplans.empty();
   std::sort(seen.begin(), seen.end());
   if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
     return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched: a plan appears twice (its workspace is shared)");
+  int eligible = 0;
+  for (int k = 0; k < count; ++k) eligible += mixed_eligible(plans[k]) ? 1 : 0;
+  const int mode = batched_mode();
+  // schedules: 1 = mixed, one launch per pass; 2 = shape groups; 3 = mixed,
+  // pipelined halves.  Mode 0 (auto) times 1 and 2 on the first call of a
+  // batch signature and keeps the faster.
+  const int fixed = eligible == 0 ? 2 : (mode == 0 ? 0 : mode);
 
   Sig sig;
-  sig.v.push_back(reinterpret_cast<const void*>((uintptr_t)batched_mode()));  // the mode shapes the graph
+  sig.v.push_back(reinterpret_cast<const void*>((uintptr_t)mode));  // the mode shapes the graph
+  std::vector<const void*> pkey;
   for (int k = 0; k < count; ++k) {
     sig.v.push_back(plans[k]);
     sig.v.push_back(rho[k]);
     sig.v.push_back(phi[k]);
+    pkey.push_back(plans[k]);
   }
 
   int prev = 0;
@@ -139,7 +186,12 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
   if (prev != dev) cudaSetDevice(dev);
   std::lock_guard<std::mutex> lk(g_mu);
   DeviceCtx& c = g_ctx[dev];
-  cudaError_t e = ensure_ctx(c, groups.size() + (mixed ? 1 : 0));
+  std::set<GroupKey> shapes;  // an upper bound on the groups any schedule forms
+  for (int k = 0; k < count; ++k) {
+    const fsa_plan* p = plans[k];
+    shapes.insert(GroupKey{p->n[0], p->n[1], p->n[2], (int)p->dtype, p->f64_dw, p->ddi});
+  }
+  cudaError_t e = ensure_ctx(c, shapes.size() + 1);
   cudaGraphExec_t exec = nullptr;
   auto it = c.graphs.find(sig);
   if (e == cudaSuccess && it != c.graphs.end()) {
@@ -147,31 +199,35 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
     c.lru.remove(sig);
     c.lru.push_front(sig);
   } else if (e == cudaSuccess) {
-    cudaGraph_t graph = nullptr;
-    e = cudaStreamBeginCapture(c.capture, cudaStreamCaptureModeThreadLocal);
-    // the mixed launches on the capture stream; every group on a side stream
-    size_t g = mixed ? 1 : 0;
-    cudaError_t le = e;
-    if (mixed && le == cudaSuccess)
-      le = mixed_passes((int)mplans.size(), mplans.data(), mrho.data(), mphi.data(), c.capture);
-    for (auto& kv : groups) {
-      if (le != cudaSuccess) break;
-      if (g == 0) {
-        le = launch_group(kv.second, plans, rho, phi, c.capture);
-      } else {
-        cudaStream_t s = c.side[g - 1];
-        le = cudaEventRecord(c.ev[2 * g], c.capture);
-        if (le == cudaSuccess) le = cudaStreamWaitEvent(s, c.ev[2 * g], 0);
-        if (le == cudaSuccess) le = launch_group(kv.second, plans, rho, phi, s);
-        if (le == cudaSuccess) le = cudaEventRecord(c.ev[2 * g + 1], s);
-        if (le == cudaSuccess) le = cudaStreamWaitEvent(c.capture, c.ev[2 * g + 1], 0);
+    if (fixed != 0) {
+      e = capture_batch(c, count, plans, rho, phi, fixed, &exec);
+      if (e == cudaSuccess) g_choice[pkey] = fixed;
+    } else {
+      // auto: both candidates, each launched twice on the caller's stream (the
+      // second launch timed), the faster kept and launched once more below, so
+      // this call's results are the kept schedule's
+      cudaGraphExec_t cand[2] = {nullptr, nullptr};
+      const int sched[2] = {1, 2};
+      float ms[2] = {1e30f, 1e30f};
+      cudaEvent_t t0 = nullptr, t1 = nullptr;
+      e = cudaEventCreate(&t0);
+      if (e == cudaSuccess) e = cudaEventCreate(&t1);
+      for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = capture_batch(c, count, plans, rho, phi, sched[i], &cand[i]);
+        if (e == cudaSuccess) e = cudaGraphLaunch(cand[i], (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaEventRecord(t0, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(cand[i], (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[i], t0, t1);
       }
-      ++g;
+      if (t0) cudaEventDestroy(t0);
+      if (t1) cudaEventDestroy(t1);
+      const int win = ms[0] <= ms[1] ? 0 : 1;
+      if (cand[1 - win]) cudaGraphExecDestroy(cand[1 - win]);
+      exec = cand[win];
+      if (e == cudaSuccess) g_choice[pkey] = sched[win];
     }
-    if (e == cudaSuccess) e = cudaStreamEndCapture(c.capture, &graph);
-    if (e == cudaSuccess) e = le;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    if (graph) cudaGraphDestroy(graph);
     if (e == cudaSuccess) {
       c.graphs[sig] = exec;
       c.lru.push_front(sig);
@@ -192,7 +248,7 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
 }
 
 extern "C" fsa_status fsa_batched_mode_set(int mode) {
-  if (mode < 0 || mode > 2) return set_error(FSA_ERR_INVALID_ARG, "fsa_batched_mode_set: mode must be 0, 1 or 2");
+  if (mode < 0 || mode > 3) return set_error(FSA_ERR_INVALID_ARG, "fsa_batched_mode_set: mode must be 0 .. 3");
   batched_mode() = mode;
   return FSA_OK;
 }
@@ -202,10 +258,19 @@ extern "C" fsa_status fsa_apply_batched_launches(const fsa_plan* const* plans, i
     return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched_launches: bad arguments");
   int mixed = 0;
   std::map<GroupKey, std::pair<int, int>> groups;  // members, launches per apply
+  // the schedule: forced by the mode, else auto mode's pick for these plans
+  // once a batch of them has run, else the mixed path (its first candidate)
+  int sched = batched_mode();
+  if (sched == 0) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    std::vector<const void*> pkey(plans, plans + count);
+    auto it = g_choice.find(pkey);
+    sched = it != g_choice.end() ? it->second : 1;
+  }
   for (int k = 0; k < count; ++k) {
     const fsa_plan* p = plans[k];
     if (!p) return set_error(FSA_ERR_INVALID_ARG, "fsa_apply_batched_launches: NULL plan");
-    if (batched_mode() != 2 && mixed_eligible(p)) {
+    if (sched != 2 && mixed_eligible(p)) {
       ++mixed;
     } else {
       auto& g = groups[GroupKey{p->n[0], p->n[1], p->n[2], (int)p->dtype, p->f64_dw, p->ddi}];
@@ -215,7 +280,7 @@ extern "C" fsa_status fsa_apply_batched_launches(const fsa_plan* const* plans, i
       g.second = info.launches_per_apply;
     }
   }
-  int n = mixed_launches(mixed);
+  int n = mixed_launches(mixed, sched == 3);
   for (auto& kv : groups) n += kv.second.second * ((kv.second.first + kMaxJobs - 1) / kMaxJobs);
   *launches = n;
   return FSA_OK;
@@ -233,6 +298,9 @@ void batched_forget_plan(const fsa_plan* p) {
       for (size_t i = 1; i < it->v.size(); i += 3) uses |= (it->v[i] == p);  // v = mode, then (plan, rho, phi)...
       if (uses) {
         cudaGraphExecDestroy(c.graphs[*it]);
+        std::vector<const void*> pkey;
+        for (size_t i = 1; i < it->v.size(); i += 3) pkey.push_back(it->v[i]);
+        g_choice.erase(pkey);
         c.graphs.erase(*it);
         it = c.lru.erase(it);
       } else {

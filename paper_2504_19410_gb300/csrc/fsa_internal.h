@@ -110,10 +110,11 @@ bool radial_w_table(fsa_kernel kernel, double lam, double eps, double kmax, std:
 // The batched launcher's mixed-length path (mixed.cu, passes_mix.cuh): whether
 // a plan can join it, and the five launches for `count` such solves.
 bool mixed_eligible(const fsa_plan* p);
+// pipelined: two halves of balanced work in six launches, else one launch per pass
 cudaError_t mixed_passes(int count, const fsa_plan* const* plans, const void* const* rho, void* const* phi,
-                         cudaStream_t s);
-int mixed_launches(int count);  // launches mixed_passes makes for `count` solves
-// fsa_batched_mode_set: 0 pipelined mixed path, 1 one launch per pass, 2 shape groups only
+                         cudaStream_t s, bool pipelined);
+int mixed_launches(int count, bool pipelined);  // launches mixed_passes makes for `count` solves
+// fsa_batched_mode_set: 0 auto, 1 mixed one launch per pass, 2 shape groups, 3 mixed pipelined
 int& batched_mode();
 // The fused outer pass pair used for FP32 grids with n0 = n2 and transform
 // length M = 2 n0 (dir 0 forward, 1 inverse): 0 = the separate passes, c >= 1

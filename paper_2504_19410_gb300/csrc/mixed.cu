@@ -91,11 +91,11 @@ int& batched_mode() {
 }
 
 cudaError_t mixed_passes(int count, const fsa_plan* const* plans, const void* const* rho, void* const* phi,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool pipelined) {
   cudaError_t e = mix_prepare();
   for (int b = 0; b < count && e == cudaSuccess; b += 2 * kMaxJobs) {
     const int m = std::min(count - b, 2 * kMaxJobs);
-    if (batched_mode() == 1 || m == 1) {
+    if (!pipelined || m == 1) {
       // one launch per pass over all the solves' tiles (64 solves per table)
       for (int c = 0; c < m && e == cudaSuccess; c += kMaxJobs) {
         const int mm = std::min(m - c, kMaxJobs);
@@ -142,11 +142,11 @@ cudaError_t mixed_passes(int count, const fsa_plan* const* plans, const void* co
   return e;
 }
 
-int mixed_launches(int count) {
+int mixed_launches(int count, bool pipelined) {
   int n = 0;
   for (int b = 0; b < count; b += 2 * kMaxJobs) {
     const int m = std::min(count - b, 2 * kMaxJobs);
-    n += (batched_mode() == 1 || m == 1) ? 5 * ((m + kMaxJobs - 1) / kMaxJobs) : 6;
+    n += (!pipelined || m == 1) ? 5 * ((m + kMaxJobs - 1) / kMaxJobs) : 6;
   }
   return n;
 }

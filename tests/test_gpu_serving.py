@@ -110,11 +110,12 @@ def test_serving_rejects_bad_requests_and_unknown_tickets(lib):
 
 def test_batched_c4_mix_equals_single(lib):
     """The C4-style mix (cubic n from {64,...,256}, gamma in {1,4,8}) in one
-    batched call: these FP32 solves take the mixed-length path (one launch per
-    pass for all of them), whose transforms are factored differently from the
-    tuned single-solve kernels, so each result matches its solve alone within
-    FP32 round-off, and the oracle within the FP32 tolerance; a repeated call
-    (graph replay) gives the same bits."""
+    batched call.  Under the default (auto) schedule, whichever of the mixed
+    path and the shape groups it keeps, each result matches its solve alone
+    within FP32 round-off and the oracle within the FP32 tolerance, and a
+    repeated call (graph replay) gives the same bits.  Forced schedules: the
+    mixed path in one launch per pass and pipelined give the same bits; the
+    shape groups give fsa_apply's bits."""
     import torch
     import workloads as W
     from oracle import fsa as oracle
@@ -142,20 +143,36 @@ def test_batched_c4_mix_equals_single(lib):
     # the other schedules: one mixed launch per pass gives the same bits as the
     # pipelined default; the per-shape groups give fsa_apply's bits
     from paper_2504_19410_gb300 import capi
+    handles = [p.handle for p in plans]
+    auto_launches = capi.fsa_apply_batched_launches(handles)
     try:
-        for mode, want in ((1, first), (2, singles)):
+        capi.fsa_batched_mode_set(1)
+        mixed = None
+        for mode in (1, 3, 2):
             capi.fsa_batched_mode_set(mode)
-            assert capi.fsa_apply_batched_launches([p.handle for p in plans]) == (5 if mode == 1 else
-                                                                                    capi.fsa_apply_batched_launches([p.handle for p in plans]))
+            if mode == 1:
+                assert capi.fsa_apply_batched_launches(handles) == 5
+            if mode == 3:
+                assert capi.fsa_apply_batched_launches(handles) == 6
+            if mode == 2:
+                grouped_launches = capi.fsa_apply_batched_launches(handles)
+                assert grouped_launches > 6
             for o in outs:
                 o.fill_(float("nan"))
             lib.apply_batched(plans, rhos, outs)
             torch.cuda.synchronize()
+            if mode == 1:
+                mixed = [o.clone() for o in outs]
+            want = singles if mode == 2 else mixed
             for o, w in zip(outs, want):
                 assert torch.equal(o, w), mode
     finally:
         capi.fsa_batched_mode_set(0)
-    assert capi.fsa_apply_batched_launches([p.handle for p in plans]) == 6
+    # the auto mode kept one of the two candidates: its results are that one's
+    # bits and its launch count that one's
+    kept_mixed = all(torch.equal(f, m) for f, m in zip(first, mixed))
+    assert kept_mixed or all(torch.equal(f, s) for f, s in zip(first, singles))
+    assert auto_launches == (5 if kept_mixed else grouped_launches)
     for p in plans:
         p.close()
 
