@@ -992,29 +992,33 @@ cudaError_t tune_plan(fsa_plan* p) {
       default: j.j[0] = Job{X, Y, nullptr}; return f.c2r(j, C, s);
     }
   };
+  // a short burst first, so that the SM clock has left its idle level before
+  // anything is timed
+  for (int rep = 0; rep < 20 && e == cudaSuccess; ++rep) e = run(kColMid, 2);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   for (int k = 0; k < kNumPass && e == cudaSuccess; ++k) {
     if (g_variant[k][Ms[k]][FSA_F32].load() != 0) continue;
-    float best = 1e30f;
-    int pick = 2;
     // variant 5 (the sixth-generation middle pass) only where it exists
     const int vmax = (k == kColMid && k6_colm(Ms[k])) ? 5 : 4;
-    for (int v = 1; v <= vmax && e == cudaSuccess; ++v) {
-      e = run(k, v);  // warm-up
-      float tmin = 1e30f;
-      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+    float tmin[6] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
+    for (int v = 1; v <= vmax && e == cudaSuccess; ++v) e = run(k, v);  // warm-up
+    // rounds over all variants (not one variant after another), so that a
+    // drifting clock or a neighbour's load touches every variant alike; the
+    // best of five rounds per variant
+    for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) {
+      for (int v = 1; v <= vmax && e == cudaSuccess; ++v) {
         cudaEventRecord(e0, s);
         e = run(k, v);
         cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0;
         if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-        tmin = std::min(tmin, ms);
-      }
-      if (tmin < best) {
-        best = tmin;
-        pick = v;
+        tmin[v] = std::min(tmin[v], ms);
       }
     }
+    int pick = 2;
+    for (int v = 1; v <= vmax; ++v)
+      if (tmin[v] < tmin[pick]) pick = v;
     set_kernel_variant(k, Ms[k], FSA_F32, e == cudaSuccess ? pick : 0);
   }
   // the fused outer pairs against the separate passes just chosen (X stands
