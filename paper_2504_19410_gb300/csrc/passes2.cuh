@@ -13,6 +13,7 @@
 // (padded rows: conflict-free for both steps).
 #pragma once
 #include "ddi.cuh"
+#include "mbar.cuh"
 #include "fft_reg.cuh"
 
 namespace fsa {
@@ -216,7 +217,9 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2_col_mid(con
   const int tiles_per_plane = (M2 + W - 1) / W;
   const long long tpj = (long long)tiles_per_plane * planes;
   const int n2 = M2 / 2;
-  for (long long tile = blockIdx.x; tile < tpj * jobs.count; tile += gridDim.x) {
+  const long long total = tpj * jobs.count;
+  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+    const long long tile = kMidReverse ? total - 1 - it : it;
     const Job& jb = jobs.j[tile / tpj];
     const int lt = (int)(tile % tpj);
     const int k0 = lt / tiles_per_plane;
@@ -292,9 +295,11 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2p_col_mid(co
   const long long K = jobs.count;
   const long long total = tpj * K;
   const int n2 = M2 / 2;
-  // work item -> (job, tile of the job); SHARED orders the jobs innermost
-  auto job_of = [&](long long tile) -> int { return (int)(SHARED ? tile % K : tile / tpj); };
-  auto lt_of = [&](long long tile) -> int { return (int)(SHARED ? tile / K : tile % tpj); };
+  // work item -> (job, tile of the job); SHARED orders the jobs innermost;
+  // kMidReverse walks the items from the last
+  auto ph = [&](long long tile) -> long long { return kMidReverse ? total - 1 - tile : tile; };
+  auto job_of = [&](long long tile) -> int { return (int)(SHARED ? ph(tile) % K : ph(tile) / tpj); };
+  auto lt_of = [&](long long tile) -> int { return (int)(SHARED ? ph(tile) / K : ph(tile) % tpj); };
   auto next_of = [&](long long tile) -> long long {
     if constexpr (SHARED) return tile % K + 1 < K ? tile + 1 : (tile / K + gridDim.x) * K;
     else return tile + gridDim.x;
@@ -342,7 +347,8 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID) k2p_col_mid(co
     // this thread's staged elements are consumed: fetch the next tile's
     if (next_of(tile) < total) issue(next_of(tile));
     __syncthreads();
-    if (!SHARED || job == 0) mid_load<P>(sp, srow, u, ok, n2 + 1);
+    // SHARED: the first job of the group this CTA takes in turn loads the tile's spectrum
+    if (!SHARED || tile % K == 0) mid_load<P>(sp, srow, u, ok, n2 + 1);
     V b[R2];
 #pragma unroll
     for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
@@ -558,6 +564,15 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2_c2r_ax0(const Jobs jobs, long 
     }
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
+    if constexpr (PAD) {
+      // every X value of the tile has been read, and nothing reads X again
+      // before the next solve rewrites it: drop its L2 lines (rows 0..n of
+      // the tile's 2W columns; two 128-byte lines per row when aligned)
+      const long long c0 = (tile % tpj) * (2 * W);
+      const long long nb = (C - c0 < 2 * W ? C - c0 : 2 * W) * (long long)sizeof(V);
+      for (int kk = threadIdx.x / 2; kk <= n; kk += Geo2<P>::NT / 2)
+        l2_discard(X + kk * C + c0, nb, threadIdx.x % 2, 2);
+    }
     stepA_inv<P, V, PAD>(
         u, [&](int q, int t) { return sm[(q * R2 + t) * W + l]; },
         [&](int t, int r, V v) {
