@@ -13,7 +13,6 @@
 // (padded rows: conflict-free for both steps).
 #pragma once
 #include "ddi.cuh"
-#include "mbar.cuh"
 #include "fft_reg.cuh"
 
 namespace fsa {
@@ -564,15 +563,6 @@ __global__ void __launch_bounds__(Geo2<P>::NT) k2_c2r_ax0(const Jobs jobs, long 
     }
     stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
     __syncthreads();
-    if constexpr (PAD) {
-      // every X value of the tile has been read, and nothing reads X again
-      // before the next solve rewrites it: drop its L2 lines (rows 0..n of
-      // the tile's 2W columns; two 128-byte lines per row when aligned)
-      const long long c0 = (tile % tpj) * (2 * W);
-      const long long nb = (C - c0 < 2 * W ? C - c0 : 2 * W) * (long long)sizeof(V);
-      for (int kk = threadIdx.x / 2; kk <= n; kk += Geo2<P>::NT / 2)
-        l2_discard(X + kk * C + c0, nb, threadIdx.x % 2, 2);
-    }
     stepA_inv<P, V, PAD>(
         u, [&](int q, int t) { return sm[(q * R2 + t) * W + l]; },
         [&](int t, int r, V v) {
