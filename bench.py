@@ -82,6 +82,9 @@ def ddi_grid_pass_bytes(n, s):
     return {k: b[k] + extra[k] for k in b}
 
 
+PIPE_LENGTHS = (128, 192, 256, 384, 512)  # transform lengths with the pipelined middle passes
+
+
 def fused_text(c, M):
     """The outer pass pair in use: separate passes or a cluster configuration."""
     from paper_2504_19410_gb300 import capi
@@ -264,6 +267,8 @@ def run_ours(args):
     n = d.n
     if args.outer_pairs != "auto" and capi.fsa_fused_configs(2 * n[0]):
         capi.fsa_fused_select(2 * n[0], 2, 0 if args.outer_pairs == "separate" else int(args.outer_pairs))
+    if args.pipe != "auto" and not plane and n[1] == n[2] and 2 * n[2] in PIPE_LENGTHS:
+        capi.fsa_pipe_select(2 * n[2], int(args.pipe))
     rho64 = d.rho()
     hbm_peak, peak_kind = peaks()
     stream = torch.cuda.current_stream()
@@ -330,6 +335,13 @@ def run_ours(args):
                 pb["r2c_ax0"], pb["row_fwd"] = 0, (V + Yr) * s
             if info.fused_inv:
                 pb["row_inv"], pb["c2r_ax0"] = (Yr + V) * s, 0
+        if info.pipe:
+            # the pipelined middle passes (one kernel, reported as col_mid):
+            # X in, X out and the spectrum; Y stays in L2 between its passes
+            pb = dict(pb)
+            Xr = (n[0] + 1) * n[1] * n[2] * 2
+            pb["row_fwd"], pb["row_inv"] = 0, 0
+            pb["col_mid"] = (2 * Xr + (n[0] + 1) * (n[1] + 1) * (n[2] + 1)) * s
         dom = max(range(5), key=lambda i: pass_ms[i])
         kname = PASSES[dom]
         achieved = pb[kname] / (pass_ms[dom] * 1e-3) / 1e9
@@ -368,6 +380,7 @@ def run_ours(args):
             "launches_per_solve": plan.info.launches_per_apply,
             "outer_pairs": {"forward": fused_text(info.fused_fwd, 2 * n[0]),
                             "inverse": fused_text(info.fused_inv, 2 * n[0])},
+            "middle_passes": "pipelined (one kernel)" if info.pipe else "separate passes",
             "pass_hbm_frac": {k: round(pb[k] / (v * 1e-3) / 1e9 / hbm_peak, 4)
                               for k, v in zip(PASSES, pass_ms) if v > 0 and pb[k] > 0},
         }
@@ -819,6 +832,8 @@ def main():
     ap.add_argument("--outer-pairs", default="auto",
                     help="the outer pass pairs of FP32 cubes: auto (tuned), separate, or a fused cluster "
                          "configuration 1, 2, ... (fsa_fused_configs)")
+    ap.add_argument("--pipe", choices=["auto", "0", "1"], default="auto",
+                    help="middle passes of FP32 grids with n1 = n2: auto (tuned), 0 separate, 1 pipelined kernel")
     ap.add_argument("--kernel-gen", choices=["auto", "1", "2", "3", "4", "6"], default="auto",
                     help="auto: autotuned per plan; 1 / 2 / 3 / 4 / 6: force one kernel generation "
                          "(FP64: native for 1, double-word otherwise)")

@@ -134,7 +134,8 @@ typedef struct {
   int generated;            /* 1 once fsa_tensor_generate has been enqueued           */
   int arithmetic;           /* 0 FP32; FP64 plans: 1 native FP64, 2 double-word       */
   int launches_per_apply;   /* kernel launches of one fsa_apply: 2 + 3 x plane slabs, */
-                            /* one fewer per fused outer pair (fused_fwd, fused_inv)  */
+                            /* one fewer per fused outer pair (fused_fwd, fused_inv), */
+                            /* 3 with the pipelined middle passes (pipe)              */
   size_t workspace_bytes;   /* device scratch the plan owns                           */
   size_t spectrum_bytes;    /* device bytes of the stored spectrum octant             */
   const void* spectrum;     /* device pointer: (n0+1) x (n1+1) x (n2+1) dtype, C order */
@@ -151,6 +152,8 @@ typedef struct {
   int fused_inv;            /* separate passes, c >= 1 fused configuration c - 1     */
   int w_quadrature;         /* 1 if W comes from the quadrature table, else 0         */
   int w_panels;             /* that table's Chebyshev panels (0 without it)           */
+  int pipe;                 /* 1 if the middle passes run as the pipelined kernel    */
+                            /* (fsa_pipe_select), else 0                              */
 } fsa_plan_info;
 
 /* Create a plan (the "Precomp" object of Sec. 5, Example 2) for the grid
@@ -395,6 +398,26 @@ fsa_status fsa_autotune_set(int mode);
  * concurrent launches. */
 int fsa_fused_configs(int M, int* cluster_ctas, int* threads, int cap);
 fsa_status fsa_fused_select(int M, int dir, int c);
+
+/* Pipelined middle passes (FP32 plans of d = 3 with n1 = n2 and transform
+ * length M = 2 n2 in {128, 192, 256, 384, 512}).  The forward axis-2
+ * transform, the axis-1 middle pass with the spectrum multiply and the
+ * inverse axis-2 transform of Sec. 2.3 stay the same transforms with the same
+ * arithmetic (results bit-equal to the separate passes'), but run as one
+ * persistent kernel whose CTAs take tiles of one axis-0 frequency plane at a
+ * time from a work counter, each tile after the tiles of its plane it
+ * depends on: the planes in flight stay in L2, and the row tiles share the
+ * SMs with the middle tiles.  fsa_pipe_select(M, c): c = 1 the pipelined
+ * kernel, 0 or -1 (the default) the separate passes; autotune modes 2 to 6
+ * always run the separate passes of the forced generation.  (Measured on a
+ * GB300 at 256^3: the pipelined kernel moves 0.55 GB through HBM instead of
+ * 1.27 GB but takes 0.42 ms against 0.37 ms for the three passes, which are
+ * bound by instruction issue and latency, not by HBM; it is not timed by the
+ * tuner.)  A fused outer pair (fsa_fused_select) in use takes precedence.  The pass profiler reports the pipelined kernel under col_mid
+ * (row_fwd / row_inv then read 0).  FSA_ERR_INVALID_ARG for a length without
+ * the kernel or c outside -1..1.  Not thread-safe against concurrent
+ * launches. */
+fsa_status fsa_pipe_select(int M, int c);
 
 /* Device-side wait status (no counterpart in the paper: it reports on the
  * kernels, not on the method).  Kernels that wait on an mbarrier for their own

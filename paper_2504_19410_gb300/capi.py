@@ -58,7 +58,8 @@ class PlanInfo(C.Structure):
                 ("many_capacity", C.c_int),
                 ("ddi_derivative", C.c_int),
                 ("dipole_n", C.c_double * 3), ("dipole_m", C.c_double * 3),
-                ("fused_fwd", C.c_int), ("fused_inv", C.c_int), ("w_quadrature", C.c_int), ("w_panels", C.c_int)]
+                ("fused_fwd", C.c_int), ("fused_inv", C.c_int), ("w_quadrature", C.c_int), ("w_panels", C.c_int),
+                ("pipe", C.c_int)]
 
 
 class ServeOpts(C.Structure):
@@ -110,6 +111,7 @@ _PROTOS = {
     "fsa_autotune_set": (C.c_int, [C.c_int]),
     "fsa_fused_configs": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]),
     "fsa_fused_select": (C.c_int, [C.c_int, C.c_int, C.c_int]),
+    "fsa_pipe_select": (C.c_int, [C.c_int, C.c_int]),
     "fsa_device_fault": (C.c_int, [C.c_int, C.POINTER(C.c_uint), C.c_int]),
     "fsa_wait_selftest": (C.c_int, [C.c_int, C.POINTER(C.c_uint)]),
     "fsa_measure_alu_peak": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_float)]),
@@ -298,6 +300,12 @@ def fsa_fused_select(M, direction, c):
     """Pin the outer pair for length M: direction 0 forward, 1 inverse, 2
     both; c = 0 separate passes, c >= 1 fused configuration c - 1, -1 tuner."""
     return check(lib().fsa_fused_select(int(M), int(direction), int(c)))
+
+
+def fsa_pipe_select(M, c):
+    """Pin the middle passes for FP32 transform length M: c = 1 the pipelined
+    kernel, 0 the separate passes, -1 tuner."""
+    return check(lib().fsa_pipe_select(int(M), int(c)))
 
 
 def fsa_device_fault(device=-1, clear=False):

@@ -98,6 +98,23 @@ enum Arith {
 using ColmFn = cudaError_t (*)(const Jobs&, int, int, cudaStream_t);
 ColmFn k6_colm(int M);
 cudaError_t k6_prepare(int M);
+// The seventh generation (passes7.cuh, inst_f32g7.cu): row forward, middle
+// and row inverse of FP32 grids with n1 = n2 as one kernel fed by a work
+// dispenser.  k7_pipe_fn(M): its launcher for transform length M (null where
+// it has no instance); jobs in = X, out = Y, S = spectrum, job 0's aux = the
+// counter words (pipe_ctr_bytes at the end of job 0's workspace).
+using PipeFn = cudaError_t (*)(const Jobs&, int n1, int K0, cudaStream_t);
+PipeFn k7_pipe_fn(int M);
+cudaError_t k7_prepare(int M);
+// Bytes of a solve's workspace: X, Y, then (grids the seventh generation can
+// run) its counter words for a launch of up to kMaxJobs solves.
+size_t plan_workspace_bytes(const int* n, fsa_dtype dt);
+size_t pipe_ctr_bytes(const int* n, fsa_dtype dt);
+// Whether FP32 grids of transform length M run the seventh generation: 0 the
+// separate passes, 1 the pipelined kernel (only when pinned by
+// fsa_pipe_select; -1, unpinned, runs the separate passes).
+int pipe_config(int M);
+void set_pipe_config(int M, int c);
 // W(k) by the radial integrals of Eq. Fourier-Symmetric with adaptive
 // Gauss-Kronrod quadrature (radial_w.cpp).  radial_w_table: piecewise Chebyshev
 // series of degree kWTableDegree on [0, kmax]; layout: the P + 1 panel edges,

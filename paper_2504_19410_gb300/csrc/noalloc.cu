@@ -79,7 +79,7 @@ extern "C" fsa_status fsa_apply_noalloc(const fsa_plan* p, const void* rho, void
   const size_t s = p->dtype == FSA_F32 ? 4 : 8;
   const size_t K0 = (size_t)p->n[0] + 1;
   const size_t x_bytes = K0 * p->n[1] * p->n[2] * 2 * s;
-  const size_t need = x_bytes + K0 * p->n[1] * (2 * (size_t)p->n[2]) * 2 * s;
+  const size_t need = plan_workspace_bytes(p->n, p->dtype);  // X, Y and the pipelined kernel's counters
   if (need > kNoallocScratchBytes) {
     char buf[200];
     snprintf(buf, sizeof buf,

@@ -157,6 +157,30 @@ void set_fused_config(int M, int dir, int c) {
   g_fused[M][dir].store((signed char)c, std::memory_order_relaxed);
 }
 
+namespace {
+// Seventh generation per transform length: -1 unpinned, else as pipe_config
+// (fsa_pipe_select).
+std::atomic<signed char> g_pipe[1025];
+std::once_flag g_pipe_once;
+void pipe_table_init() {
+  std::call_once(g_pipe_once, [] {
+    for (auto& c : g_pipe) c.store(-1);
+  });
+}
+}  // namespace
+
+int pipe_config(int M) {
+  if (autotune_mode() >= 2 || M < 0 || M > 1024 || !k7_pipe_fn(M)) return 0;
+  pipe_table_init();
+  return g_pipe[M].load(std::memory_order_relaxed) == 1 ? 1 : 0;
+}
+
+void set_pipe_config(int M, int c) {
+  if (M < 0 || M > 1024) return;
+  pipe_table_init();
+  g_pipe[M].store((signed char)(c < -1 ? -1 : c > 1 ? 1 : c), std::memory_order_relaxed);
+}
+
 bool supported_n(int n) {
   if (n < 4 || n > 512 || (n & 1)) return false;
   int m = n;
@@ -309,6 +333,10 @@ cudaError_t group_passes(const int* n, int count, const void* const* rho, void* 
     // pass that reads each spectrum tile once for all of them
     bool shared = m > 1 && f3.colm_shared;
     for (int i = 1; i < m && shared; ++i) shared = j3.j[i].S == j3.j[0].S;
+    // the seventh generation: row forward, middle and row inverse as one
+    // pipelined kernel (FP32, n1 = n2, not with a fused outer pair)
+    const bool pipe = std::is_same<V, float2>::value && pc >= K0 && ff == 0 && fi == 0 && n1 == n2 &&
+                      pipe_config(2 * n2) == 1 && pipe_ctr_bytes(n, FSA_F32) > 0;
     if (ff > 0) {
       Jobs jf = j1;
       for (int i = 0; i < m; ++i) jf.j[i].out = Y[b + i];
@@ -318,7 +346,15 @@ cudaError_t group_passes(const int* n, int count, const void* const* rho, void* 
       e = e == cudaSuccess ? f1.r2c(j1, C, s) : e;
       if (e == cudaSuccess) e = trace_mark(tr, kR2C, s);
     }
-    if (pc >= K0) {
+    if (pipe) {
+      Jobs jp{};
+      jp.count = m;
+      const size_t y_bytes = (size_t)K0 * n1 * (2 * (size_t)n2) * sizeof(V);
+      for (int i = 0; i < m; ++i)
+        jp.j[i] = Job{X[b + i], Y[b + i], S[b + i], i == 0 ? (const void*)((char*)Y[b] + y_bytes) : nullptr};
+      if (e == cudaSuccess) e = k7_pipe_fn(2 * n2)(jp, n1, K0, s);
+      if (e == cudaSuccess) e = trace_mark(tr, kColMid, s);
+    } else if (pc >= K0) {
       if (ff == 0) {
         if (e == cudaSuccess) e = f2.rowf(j2, rows, s);
         if (e == cudaSuccess) e = trace_mark(tr, kRowFwd, s);
@@ -626,6 +662,7 @@ fsa_status prepare_device(int dev, fsa_dtype dt, const int* n, int d, bool unpad
     const PassFns& f5g = pass_fns(kArithF32G5, M);  // fused outer pairs (some lengths)
     if (dt == FSA_F32 && f5g.prepare && e == cudaSuccess) e = f5g.prepare();
     if (dt == FSA_F32 && e == cudaSuccess) e = k6_prepare(M);  // the sixth-generation middle pass
+    if (dt == FSA_F32 && e == cudaSuccess) e = k7_prepare(M);  // the seventh-generation pipelined kernel
     if (e == cudaSuccess) e = tensorgen_prepare(M);
     if (e != cudaSuccess) return cuda_error(e, "kernel shared-memory opt-in");
     g_prepared.insert({dev, key});
@@ -725,6 +762,14 @@ int fsa_fused_configs(int M, int* cluster_ctas, int* threads, int cap) {
   return f.nfused;
 }
 
+fsa_status fsa_pipe_select(int M, int c) {
+  if (M < 0 || M > 1024 || !k7_pipe_fn(M))
+    return set_error(FSA_ERR_INVALID_ARG, "fsa_pipe_select: no pipelined kernel for this length");
+  if (c < -1 || c > 1) return set_error(FSA_ERR_INVALID_ARG, "fsa_pipe_select: c must be -1, 0 or 1");
+  set_pipe_config(M, c);
+  return FSA_OK;
+}
+
 fsa_status fsa_fused_select(int M, int dir, int c) {
   const int nf = (M >= 0 && M <= 1024) ? pass_fns(kArithF32G5, M).nfused : 0;
   if (nf == 0) return set_error(FSA_ERR_INVALID_ARG, "fsa_fused_select: no fused configurations for this length");
@@ -754,10 +799,15 @@ double fsa_appendix_b_bound_kernel_param(fsa_kernel kernel, double param, double
 
 namespace fsa {
 
+size_t pipe_ctr_bytes(const int* n, fsa_dtype dt) {
+  if (dt != FSA_F32 || n[2] < 2 || n[1] != n[2] || !k7_pipe_fn(2 * n[2])) return 0;
+  return align256(sizeof(unsigned) * (2 + 2 * (size_t)(n[0] + 1) * kMaxJobs));
+}
+
 size_t plan_workspace_bytes(const int* n, fsa_dtype dt) {
   const size_t s = dt == FSA_F32 ? 4 : 8;
   const size_t K0 = n[0] + 1;
-  return K0 * n[1] * n[2] * 2 * s + K0 * n[1] * (2 * (size_t)n[2]) * 2 * s;
+  return K0 * n[1] * n[2] * 2 * s + K0 * n[1] * (2 * (size_t)n[2]) * 2 * s + pipe_ctr_bytes(n, dt);
 }
 
 // Reals in the spectrum octant: (n0+1)(n1+1)(n2+1), or (n0+1)(n1+1) for a
@@ -1324,6 +1374,9 @@ fsa_status fsa_plan_info_get(const fsa_plan* p, fsa_plan_info* info) {
     info->fused_fwd = fusable ? fused_pair<float2>(p->n, 0) : 0;
     info->fused_inv = fusable ? fused_pair<float2>(p->n, 1) : 0;
     info->launches_per_apply -= (info->fused_fwd > 0) + (info->fused_inv > 0);
+    info->pipe = fusable && !info->fused_fwd && !info->fused_inv && p->n[1] == p->n[2] &&
+                 pipe_config(2 * p->n[2]) == 1 && pipe_ctr_bytes(p->n, FSA_F32) > 0;
+    if (info->pipe) info->launches_per_apply = 3;
     if (p->ddi >= 0) info->launches_per_apply = p->ddi == FSA_DDI_GRID ? 10 : 5;
   }
   info->w_quadrature = p->wtab ? 1 : 0;

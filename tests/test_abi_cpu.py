@@ -216,3 +216,15 @@ def test_fused_configs_and_select_arguments(capi):
     for c in (-1, 0, 1):
         capi.fsa_fused_select(512, 2, c)
     capi.fsa_fused_select(512, 2, -1)
+
+
+def test_pipe_select_arguments(capi):
+    """The pipelined middle passes exist for FP32 lengths 128..512; selection
+    checks its arguments (host-side registry data, no device needed)."""
+    for args in ((64, 1), (96, 1), (1024, 1), (-2, 0), (512, 2), (512, -2)):
+        with pytest.raises(capi.FsaError) as ei:
+            capi.fsa_pipe_select(*args)
+        assert ei.value.status == capi.FSA_ERR_INVALID_ARG
+    for M in (128, 192, 256, 384, 512):
+        for c in (1, 0, -1):
+            capi.fsa_pipe_select(M, c)
