@@ -205,10 +205,25 @@ fsa_status fsa_tensor_generate(fsa_plan* plan, fsa_stream_t stream);
  * by the stored spectrum and inverse FFT, keeping the first n_j outputs per
  * axis (Sec. 2.3).  rho, phi: device arrays of n0*n1*n2 plan-dtype elements;
  * phi == rho is allowed.  Uses the plan's workspace, so calls on one plan
- * must not overlap on the GPU.  Asynchronous on stream.
+ * must not overlap on the GPU.  Asynchronous on stream.  From the second
+ * call with the same (plan, rho, phi) on, the passes are replayed from a
+ * CUDA graph captured at that call (fsa_apply_graphs_set).
  * Errors: FSA_ERR_INVALID_ARG (NULL pointer), FSA_ERR_NOT_GENERATED,
  * FSA_ERR_CUDA. */
 fsa_status fsa_apply(const fsa_plan* plan, const void* rho, void* phi, fsa_stream_t stream);
+
+/* Graph replay of repeated solves (no counterpart in the paper: it concerns
+ * the launches, not the method).  With enable = 1 (the default), fsa_apply
+ * and fsa_apply_host capture the pass launches of a (plan, rho, phi) triple
+ * into a CUDA graph on the second call with that triple and replay the graph
+ * on later calls (one graph launch instead of one launch per pass; results
+ * bit-equal to direct launches).  A graph keeps the kernels selected when it
+ * was captured; fsa_autotune_set, fsa_fused_select and fsa_pipe_select make
+ * later calls capture anew.  Up to 64 graphs per device are kept (least
+ * recently used dropped); a plan's graphs are dropped by fsa_plan_destroy.
+ * enable = 0: every call launches its passes directly.
+ * FSA_ERR_INVALID_ARG for enable other than 0 or 1. */
+fsa_status fsa_apply_graphs_set(int enable);
 
 /* fsa_apply for callers that cannot have device memory allocated for them
  * (the paper has no counterpart: this is a deployment variant).  Same result

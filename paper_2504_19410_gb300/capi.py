@@ -112,6 +112,7 @@ _PROTOS = {
     "fsa_fused_configs": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]),
     "fsa_fused_select": (C.c_int, [C.c_int, C.c_int, C.c_int]),
     "fsa_pipe_select": (C.c_int, [C.c_int, C.c_int]),
+    "fsa_apply_graphs_set": (C.c_int, [C.c_int]),
     "fsa_device_fault": (C.c_int, [C.c_int, C.POINTER(C.c_uint), C.c_int]),
     "fsa_wait_selftest": (C.c_int, [C.c_int, C.POINTER(C.c_uint)]),
     "fsa_measure_alu_peak": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_float)]),
@@ -300,6 +301,12 @@ def fsa_fused_select(M, direction, c):
     """Pin the outer pair for length M: direction 0 forward, 1 inverse, 2
     both; c = 0 separate passes, c >= 1 fused configuration c - 1, -1 tuner."""
     return check(lib().fsa_fused_select(int(M), int(direction), int(c)))
+
+
+def fsa_apply_graphs_set(enable):
+    """1 (default): repeated fsa_apply / fsa_apply_host calls with the same
+    plan and buffers replay a captured CUDA graph; 0: direct launches."""
+    return check(lib().fsa_apply_graphs_set(int(enable)))
 
 
 def fsa_pipe_select(M, c):

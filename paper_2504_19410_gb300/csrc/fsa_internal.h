@@ -185,6 +185,12 @@ cudaError_t spectrum_to_dw(const double* src, void* dst, size_t count, cudaStrea
 
 // Drop cached batched graphs that refer to a plan (batched.cu).
 void batched_forget_plan(const fsa_plan* p);
+// fsa_apply's graph cache (apply_graph.cu): the passes of a solve, replayed
+// from a CUDA graph once its (plan, rho, phi) has been seen before;
+// invalidate after a kernel selection changes; forget a destroyed plan.
+cudaError_t plan_apply_graph(const fsa_plan* p, const void* rho, void* phi, cudaStream_t s);
+void apply_graphs_invalidate();
+void apply_graphs_forget_plan(const fsa_plan* p);
 
 // Tensor generation (tensor_gen.cu), all FP64.
 cudaError_t tensorgen_prepare(int M);

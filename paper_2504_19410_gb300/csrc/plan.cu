@@ -749,6 +749,7 @@ fsa_status fsa_device_fault(int device, unsigned int* code, int clear) {
 fsa_status fsa_autotune_set(int mode) {
   if (mode < 0 || mode > 6) return set_error(FSA_ERR_INVALID_ARG, "fsa_autotune_set: mode must be 0..6");
   autotune_mode() = mode;
+  apply_graphs_invalidate();
   return FSA_OK;
 }
 
@@ -767,6 +768,7 @@ fsa_status fsa_pipe_select(int M, int c) {
     return set_error(FSA_ERR_INVALID_ARG, "fsa_pipe_select: no pipelined kernel for this length");
   if (c < -1 || c > 1) return set_error(FSA_ERR_INVALID_ARG, "fsa_pipe_select: c must be -1, 0 or 1");
   set_pipe_config(M, c);
+  apply_graphs_invalidate();
   return FSA_OK;
 }
 
@@ -777,6 +779,7 @@ fsa_status fsa_fused_select(int M, int dir, int c) {
   if (c < -1 || c > nf) return set_error(FSA_ERR_INVALID_ARG, "fsa_fused_select: configuration out of range");
   for (int d = 0; d < 2; ++d)
     if (dir == 2 || dir == d) set_fused_config(M, d, c);
+  apply_graphs_invalidate();
   return FSA_OK;
 }
 
@@ -1327,6 +1330,7 @@ fsa_status fsa_plan_create_ddi3d(fsa_plan** out, const double* L, const int* n, 
 fsa_status fsa_plan_destroy(fsa_plan* p) {
   if (!p) return FSA_OK;
   batched_forget_plan(p);
+  apply_graphs_forget_plan(p);
   DeviceGuard dg;
   dg.set(p->device);
   if (p->ddi_par) cudaFree(p->ddi_par);
@@ -1416,7 +1420,7 @@ fsa_status fsa_apply(const fsa_plan* p, const void* rho, void* phi, fsa_stream_t
     return set_error(FSA_ERR_INVALID_ARG, "fsa_apply: rho and phi must be 16-byte aligned");
   DeviceGuard dg;
   cudaError_t e = dg.set(p->device);
-  if (e == cudaSuccess) e = plan_apply_passes(p, rho, phi, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = plan_apply_graph(p, rho, phi, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_error(e, "fsa_apply: launch");
   return FSA_OK;
 }
@@ -1489,8 +1493,9 @@ fsa_status fsa_apply_host(const fsa_plan* p, const void* rho_host, void* phi_hos
   void* R = p->ddi >= 0 ? (void*)((char*)p->ws + align256(plan_workspace_bytes(p->n, p->dtype))) : Y;
   cudaStream_t s = (cudaStream_t)stream;
   if (e == cudaSuccess) e = cudaMemcpyAsync(R, rho_host, vbytes, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = apply_passes(p, R, R, X, Y, s);
+  (void)X;
+  (void)Y;
+  if (e == cudaSuccess) e = plan_apply_graph(p, R, R, s);  // X = ws, Y = ws + x_bytes
   if (e == cudaSuccess) e = cudaMemcpyAsync(phi_host, R, vbytes, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_error(e, "fsa_apply_host");
   return FSA_OK;

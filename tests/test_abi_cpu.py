@@ -228,3 +228,13 @@ def test_pipe_select_arguments(capi):
     for M in (128, 192, 256, 384, 512):
         for c in (1, 0, -1):
             capi.fsa_pipe_select(M, c)
+
+
+def test_apply_graphs_set_arguments(capi):
+    """The graph-replay switch takes 0 or 1 (host-side state, no device)."""
+    for bad in (-1, 2, 7):
+        with pytest.raises(capi.FsaError) as ei:
+            capi.fsa_apply_graphs_set(bad)
+        assert ei.value.status == capi.FSA_ERR_INVALID_ARG
+    capi.fsa_apply_graphs_set(0)
+    capi.fsa_apply_graphs_set(1)

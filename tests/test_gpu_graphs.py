@@ -1,0 +1,129 @@
+"""Repeated solves replayed from cached CUDA graphs (fsa_apply_graphs_set).
+
+fsa_apply and fsa_apply_host capture the pass launches of a (plan, rho,
+phi) triple on its second call and replay them afterwards.  A replay must
+compute on the buffers' CURRENT contents and give the same bits as direct
+launches; kernel selection changes must reach later calls; destroying a
+plan must drop its graphs (a new plan, possibly at the same address, solves
+correctly).
+"""
+import numpy as np
+import pytest
+
+from oracle import fsa as oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2504_19410_gb300 as fsa
+    return fsa
+
+
+@pytest.fixture
+def capi(lib):
+    from paper_2504_19410_gb300 import capi as c
+    c.fsa_device_fault(clear=True)
+    yield c
+    c.fsa_apply_graphs_set(1)
+    c.fsa_pipe_select(128, -1)
+    c.fsa_autotune_set(1)
+
+
+def dev(a, dt):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32 if dt == "f32" else np.float64)).cuda()
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_replay_uses_current_contents_and_matches_direct(lib, capi, dt):
+    import torch
+    n, L = (12, 16, 24), (2.0, 2.5, 3.0)
+    rng = np.random.default_rng(21)
+    rhos = [rng.standard_normal(n) for _ in range(4)]
+    plan = lib.Plan(L, n, dt, eps=0.5)
+    x = dev(rhos[0], dt)
+    y = torch.empty_like(x)
+    capi.fsa_apply_graphs_set(0)
+    direct = []
+    for r in rhos:
+        x.copy_(dev(r, dt))
+        plan.apply(x, y)
+        direct.append(y.clone())
+    capi.fsa_apply_graphs_set(1)
+    # call 1 direct, call 2 captured and replayed, calls 3-4 replayed: each on
+    # new contents of the same buffers
+    for k, r in enumerate(rhos):
+        x.copy_(dev(r, dt))
+        plan.apply(x, y)
+        torch.cuda.synchronize()
+        assert torch.equal(y, direct[k]), k
+    want = oracle.solve(L, n, 0.5, rhos[3])
+    assert oracle.rel_error(y.double().cpu().numpy(), want) <= (2e-6 if dt == "f32" else 1e-12)
+    plan.close()
+
+
+def test_selection_change_reaches_replayed_solves(lib, capi):
+    """A graph keeps the kernels of its capture: fsa_pipe_select after two
+    calls must still switch the next call to the pipelined kernel."""
+    import torch
+    n, L = (12, 64, 64), (2.0, 2.5, 3.0)
+    capi.fsa_autotune_set(0)
+    capi.fsa_pipe_select(128, 0)
+    plan = lib.Plan(L, n, "f32", eps=0.5)
+    x = dev(np.random.default_rng(3).standard_normal(n), "f32")
+    y0 = torch.empty_like(x)
+    for _ in range(3):
+        plan.apply(x, y0)
+    capi.fsa_pipe_select(128, 1)
+    assert plan.info.pipe == 1
+    y1 = torch.empty_like(x)
+    for _ in range(3):
+        plan.apply(x, y1)
+    torch.cuda.synchronize()
+    assert capi.fsa_device_fault(clear=True) == 0
+    assert torch.equal(y0, y1)  # the pipelined kernel is bit-equal to the passes
+    plan.close()
+
+
+def test_destroyed_plan_drops_its_graphs(lib, capi):
+    import torch
+    rng = np.random.default_rng(8)
+    for n in [(8, 12, 16), (16, 12, 8), (8, 12, 16)]:
+        L = (2.0, 2.0, 2.0)
+        plan = lib.Plan(L, n, "f64", eps=0.5)
+        r = rng.standard_normal(n)
+        x = dev(r, "f64")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            plan.apply(x, y)
+        torch.cuda.synchronize()
+        assert oracle.rel_error(y.cpu().numpy(), oracle.solve(L, n, 0.5, r)) <= 1e-12
+        plan.close()
+
+
+def test_host_entry_point_replays(lib, capi):
+    """fsa_apply_host: copies in, passes (replayed from the second call on),
+    copies out; each call computes on the host buffer's current contents."""
+    import torch
+    n, L = (12, 16, 24), (2.0, 2.5, 3.0)
+    plan = lib.Plan(L, n, "f32", eps=0.5)
+    rng = np.random.default_rng(4)
+    host_in = torch.empty(n, dtype=torch.float32).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    for k in range(4):
+        r = rng.standard_normal(n)
+        host_in.copy_(torch.from_numpy(r.astype(np.float32)))
+        plan.apply_host(host_in, host_out)
+        torch.cuda.synchronize()
+        direct = plan.apply(dev(r, "f32")).cpu()
+        torch.cuda.synchronize()
+        assert torch.equal(direct, host_out), k
+    assert oracle.rel_error(host_out.double().numpy(), oracle.solve(L, n, 0.5, r)) <= 2e-6
+    plan.close()
