@@ -258,7 +258,7 @@ def run_ours(args):
     from paper_2504_19410_gb300 import capi
     import workloads as W
 
-    capi.fsa_autotune_set({"auto": 1, "1": 2, "2": 3, "3": 4, "4": 5, "6": 6}[args.kernel_gen])
+    capi.fsa_autotune_set({"auto": 1, "1": 2, "2": 3, "3": 4, "4": 5, "6": 6, "8": 7}[args.kernel_gen])
     plane = args.kernel in PLANE_KERNELS
     ddi_kw = ({"dipoles": (W.DDI_N, W.DDI_M), "ddi_derivative": args.ddi_derivative}
               if args.kernel == "ddi3d" else {})
@@ -841,7 +841,7 @@ def main():
                          "configuration 1, 2, ... (fsa_fused_configs)")
     ap.add_argument("--pipe", choices=["auto", "0", "1"], default="auto",
                     help="middle passes of FP32 grids with n1 = n2: auto (tuned), 0 separate, 1 pipelined kernel")
-    ap.add_argument("--kernel-gen", choices=["auto", "1", "2", "3", "4", "6"], default="auto",
+    ap.add_argument("--kernel-gen", choices=["auto", "1", "2", "3", "4", "6", "8"], default="auto",
                     help="auto: autotuned per plan; 1 / 2 / 3 / 4 / 6: force one kernel generation "
                          "(FP64: native for 1, double-word otherwise)")
     ap.add_argument("--l2-chunk-mb", type=int, default=0,

@@ -377,16 +377,19 @@ fsa_status fsa_profiler_destroy(fsa_profiler* prof);
  * copies; generation 6 = generation 4 with a middle pass that splits the
  * padded and cropped step of generation 2 into two half tasks per line, so
  * each thread holds half the values and twice the warps fit on an SM
- * (lengths 128, 192, 256, 384, 512; generation 4's middle pass elsewhere).
+ * (lengths 128, 192, 256, 384, 512; generation 4's middle pass elsewhere);
+ * generation 8 = generation 4 with a middle pass whose column tiles are
+ * staged by one tiled bulk tensor copy (TMA) each, bit-equal to generation
+ * 2's (same lengths; a launch of several solves runs generation 2's).
  * mode 1 (default): each new FP32 plan times every generation for
  * each of its passes on its own workspace at creation and keeps the fastest
  * per (pass, length); choices persist for the process.  mode 0: untuned
- * passes use generation 2.  mode 2 / 3 / 4 / 5 / 6: force generation
- * 1 / 2 / 3 / 4 / 6 for every FP32 pass.  FP64 plans compute either in native FP64 or in
+ * passes use generation 2.  mode 2 / 3 / 4 / 5 / 6 / 7: force generation
+ * 1 / 2 / 3 / 4 / 6 / 8 for every FP32 pass.  FP64 plans compute either in native FP64 or in
  * double-word arithmetic (two floats, 48-bit significand, on the FP32 pipes;
  * see fsa_plan_info.arithmetic): one choice per grid shape per process, timed
  * on the first plan of the shape in mode 1, double-word in mode 0, native in
- * mode 2, double-word in modes 3 to 6.  FSA_ERR_INVALID_ARG for other modes.
+ * mode 2, double-word in modes 3 to 7.  FSA_ERR_INVALID_ARG for other modes.
  * Not thread-safe against concurrent launches. */
 fsa_status fsa_autotune_set(int mode);
 

@@ -90,7 +90,8 @@ enum Arith {
   kArithF32G4 = 5,
   kArithF32G5 = 6,  // the fused outer pass pairs only (fwd5 / inv5)
   kArithF32G6 = 7,  // generation 4 with the sixth-generation middle pass
-  kNumArith = 8
+  kArithF32G8 = 8,  // generation 4 with the eighth-generation (tensor-copy) middle pass
+  kNumArith = 9
 };
 // The sixth-generation middle pass (passes6.cuh, inst_f32g6.cu) for
 // transform length M, or null where it has no instance; k6_prepare sets its
@@ -98,6 +99,10 @@ enum Arith {
 using ColmFn = cudaError_t (*)(const Jobs&, int, int, cudaStream_t);
 ColmFn k6_colm(int M);
 cudaError_t k6_prepare(int M);
+// The eighth-generation middle pass (passes8.cuh, inst_f32g8.cu): column tiles
+// staged by one tiled bulk tensor copy each; null where it has no instance.
+ColmFn k8_colm(int M);
+cudaError_t k8_prepare(int M);
 // The seventh generation (passes7.cuh, inst_f32g7.cu): row forward, middle
 // and row inverse of FP32 grids with n1 = n2 as one kernel fed by a work
 // dispenser.  k7_pipe_fn(M): its launcher for transform length M (null where

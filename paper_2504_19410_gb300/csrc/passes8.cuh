@@ -1,0 +1,130 @@
+// Eighth-generation FP32 middle pass: generation 2's two-step register
+// transform with each column tile's inputs staged by ONE tiled bulk tensor
+// copy (TMA, cp.async.bulk.tensor.2d) per tile.
+//
+// A middle-pass tile is W = 16 adjacent columns k2 of one axis-0 plane k0,
+// over its n1 rows (Y[k0][0..n1)[k2..k2+16): n1 rows of 128 bytes, M2 x 8
+// bytes apart).  Generation 2 loads them straight from HBM at the start of
+// the tile (the load latency shows as long-scoreboard stalls); generation 3
+// stages them with per-thread cp.async copies (extra instructions, and bank
+// conflicts in its staging layout).  Here thread 0 issues one 2-D tensor copy
+// of the whole n1 x 16 box into shared memory, laid out [row][column] as the
+// plain loads would read it, with completion counted in bytes on an mbarrier;
+// the copy of the next tile is issued as soon as every thread has taken the
+// current one out of the staging buffer, and runs under the rest of the
+// current tile's work.  The arithmetic is generation 2's, so the results are
+// bit-equal to it.
+//
+// The copy needs a tensor map of Y (host-encoded per launch, passed as a
+// __grid_constant__ parameter), so a launch carries ONE solve; the launcher
+// hands launches of several solves to generation 2.  Every wait on the
+// mbarrier is bounded (kWaitLimitCycles); a CTA whose wait gives up ORs
+// kWaitTimeout into jobs.fault, waits (bounded) for its copy in flight and
+// returns, the decision taken CTA-wide at the barrier that ends step A.
+#pragma once
+#include <cuda.h>
+
+#include "mbar.cuh"
+#include "passes2.cuh"
+
+namespace fsa {
+
+// 2-D tiled copy global -> shared of the box at element coordinates (x, y)
+// of the tensor map; x * 8 bytes is a multiple of 16 (x = 16 c).
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared memory: the exchange tile (M x W complex), the staged input box
+// (n1 = M/2 rows x W columns), the mbarrier.
+template <class P> struct Geo8 {
+  static constexpr int W = Geo2<P>::W;
+  static constexpr int NT = Geo2<P>::NT;
+  static constexpr int XCH = P::M * W * 8;
+  static constexpr int STG = (P::M / 2) * W * 8;
+  static constexpr int BAR = XCH + STG;
+  static constexpr int SMEM = BAR + 16;
+  static_assert(W == 16 && XCH % 16 == 0 && STG % 16 == 0, "box of 16 columns, 16-byte aligned staging");
+};
+
+// ymap: Y of the launch's one solve as a 2-D tensor of 8-byte elements,
+// dims {M2, planes * n1}, box {16, n1}.
+template <class P>
+__global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID)
+    k8_col_mid(const Jobs jobs, int M2, int planes, const __grid_constant__ CUtensorMap ymap) {
+  using V = float2;
+  using G = Geo8<P>;
+  constexpr int M = P::M, n = M / 2, W = G::W, R2 = P::R2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const V* stg = reinterpret_cast<const V*>(smraw + G::XCH);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smraw + G::BAR);
+  const int l = threadIdx.x % W, u = mid_u<P>(threadIdx.x);
+  const int tpp = M2 / W;  // column tiles per plane
+  const long long total = (long long)tpp * planes;
+  const int n2 = M2 / 2;
+  const Job& jb = jobs.j[0];
+  auto tile_of = [&](long long it) -> long long { return kMidReverse ? total - 1 - it : it; };
+  auto issue = [&](long long it) {  // thread 0
+    const long long lt = tile_of(it);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, (unsigned)G::STG);
+    tma_load_2d(smraw + G::XCH, &ymap, (int)(lt % tpp) * W, (int)(lt / tpp) * n, bar);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && blockIdx.x < total) issue(blockIdx.x);
+  MidSpec<P> sp;
+  int k = 0;
+  for (long long it = blockIdx.x; it < total; it += gridDim.x, ++k) {
+    const long long lt = tile_of(it);
+    const int k0 = (int)(lt / tpp);
+    const int k2 = (int)(lt % tpp) * W + l;
+    V* __restrict__ col = static_cast<V*>(jb.out) + (long long)k0 * n * M2 + k2;
+    const float* __restrict__ srow =
+        static_cast<const float*>(jb.S) + (long long)k0 * (n + 1) * (n2 + 1) + min(k2, M2 - k2);
+    const bool late = !mbar_wait(bar, k & 1);
+    stepA_fwd<P, V, true>(
+        u,
+        [&](int t, int r) {
+          const int p = t + R2 * r;
+          return p < n ? stg[p * W + l] : czero<V>();
+        },
+        [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
+    if (__syncthreads_or(late)) {
+      if (threadIdx.x == 0) {
+        if (jobs.fault) atomicOr(jobs.fault, kWaitTimeout);
+        mbar_wait(bar, k & 1);  // the copy still in flight
+      }
+      __syncthreads();
+      return;
+    }
+    // every thread has taken the tile out of the staging buffer: the next one
+    if (threadIdx.x == 0 && it + gridDim.x < total) issue(it + gridDim.x);
+    mid_load<P>(sp, srow, u, true, n2 + 1);
+    V b[R2];
+#pragma unroll
+    for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
+    rfft<R2, true>(b);
+    mid_multiply<P, kMulSpectrum>(b, sp, u, jb, k0, k2, M2, true);
+    stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
+    __syncthreads();
+    stepA_inv<P, V, true>(
+        u, [&](int q, int t) { return sm[(q * R2 + t) * W + l]; },
+        [&](int t, int r, V v) {
+          const int p = t + R2 * r;
+          if (p < n) col[(long long)p * M2] = v;
+        });
+    __syncthreads();
+  }
+}
+
+}  // namespace fsa

@@ -117,6 +117,7 @@ int kernel_variant(int pass, int M, fsa_dtype dt) {
   if (mode == 4) return 3;
   if (mode == 5) return 4;
   if (mode == 6) return pass == kColMid ? 5 : 4;
+  if (mode == 7) return pass == kColMid ? 6 : 4;
   const int v = (M >= 0 && M <= 1024) ? g_variant[pass][M][dt].load(std::memory_order_relaxed) : 0;
   return v ? v : 2;
 }
@@ -234,7 +235,10 @@ cudaError_t init_all_twiddles() {
 
 // FP32 kernel variant (1..5, as kernel_variant) -> registered arithmetic.
 int arith_of_variant(int v) {
-  return v == 5 ? kArithF32G6 : v == 4 ? kArithF32G4 : (v == 3 ? kArithF32G3 : (v == 2 ? kArithF32G2 : kArithF32G1));
+  return v == 6   ? kArithF32G8
+         : v == 5 ? kArithF32G6
+         : v == 4 ? kArithF32G4
+                  : (v == 3 ? kArithF32G3 : (v == 2 ? kArithF32G2 : kArithF32G1));
 }
 
 template <typename V> int arith_for(int pass, int M) {
@@ -662,6 +666,7 @@ fsa_status prepare_device(int dev, fsa_dtype dt, const int* n, int d, bool unpad
     const PassFns& f5g = pass_fns(kArithF32G5, M);  // fused outer pairs (some lengths)
     if (dt == FSA_F32 && f5g.prepare && e == cudaSuccess) e = f5g.prepare();
     if (dt == FSA_F32 && e == cudaSuccess) e = k6_prepare(M);  // the sixth-generation middle pass
+    if (dt == FSA_F32 && e == cudaSuccess) e = k8_prepare(M);  // the eighth-generation middle pass
     if (dt == FSA_F32 && e == cudaSuccess) e = k7_prepare(M);  // the seventh-generation pipelined kernel
     if (e == cudaSuccess) e = tensorgen_prepare(M);
     if (e != cudaSuccess) return cuda_error(e, "kernel shared-memory opt-in");
@@ -747,7 +752,7 @@ fsa_status fsa_device_fault(int device, unsigned int* code, int clear) {
 }
 
 fsa_status fsa_autotune_set(int mode) {
-  if (mode < 0 || mode > 6) return set_error(FSA_ERR_INVALID_ARG, "fsa_autotune_set: mode must be 0..6");
+  if (mode < 0 || mode > 7) return set_error(FSA_ERR_INVALID_ARG, "fsa_autotune_set: mode must be 0..7");
   autotune_mode() = mode;
   apply_graphs_invalidate();
   return FSA_OK;
@@ -1051,15 +1056,21 @@ cudaError_t tune_plan(fsa_plan* p) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   for (int k = 0; k < kNumPass && e == cudaSuccess; ++k) {
     if (g_variant[k][Ms[k]][FSA_F32].load() != 0) continue;
-    // variant 5 (the sixth-generation middle pass) only where it exists
-    const int vmax = (k == kColMid && k6_colm(Ms[k])) ? 5 : 4;
-    float tmin[6] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
-    for (int v = 1; v <= vmax && e == cudaSuccess; ++v) e = run(k, v);  // warm-up
+    // variants 5 and 6 (the sixth- and eighth-generation middle passes) only
+    // where they exist
+    std::vector<int> cand = {1, 2, 3, 4};
+    if (k == kColMid && k6_colm(Ms[k])) cand.push_back(5);
+    if (k == kColMid && k8_colm(Ms[k])) cand.push_back(6);
+    float tmin[7] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
+    for (int v : cand) {
+      if (e == cudaSuccess) e = run(k, v);  // warm-up
+    }
     // rounds over all variants (not one variant after another), so that a
     // drifting clock or a neighbour's load touches every variant alike; the
     // best of five rounds per variant
     for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) {
-      for (int v = 1; v <= vmax && e == cudaSuccess; ++v) {
+      for (int v : cand) {
+        if (e != cudaSuccess) break;
         cudaEventRecord(e0, s);
         e = run(k, v);
         cudaEventRecord(e1, s);
@@ -1070,7 +1081,7 @@ cudaError_t tune_plan(fsa_plan* p) {
       }
     }
     int pick = 2;
-    for (int v = 1; v <= vmax; ++v)
+    for (int v : cand)
       if (tmin[v] < tmin[pick]) pick = v;
     set_kernel_variant(k, Ms[k], FSA_F32, e == cudaSuccess ? pick : 0);
   }

@@ -32,8 +32,8 @@ pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "f32": 2e-6}
 # autotune modes of fsa_autotune_set: 1 = tuned (the bench's configuration),
-# 2..6 = forced generations 1..4 and 6
-MODES = [("tuned", 1), ("gen1", 2), ("gen2", 3), ("gen3", 4), ("gen4", 5), ("gen6", 6)]
+# 2..7 = forced generations 1..4, 6 and 8
+MODES = [("tuned", 1), ("gen1", 2), ("gen2", 3), ("gen3", 4), ("gen4", 5), ("gen6", 6), ("gen8", 7)]
 
 
 @pytest.fixture(scope="module")

@@ -30,18 +30,19 @@ def lib():
     return fsa
 
 
-@pytest.fixture(params=["gen1", "gen2", "gen3", "gen4", "gen6"])
+@pytest.fixture(params=["gen1", "gen2", "gen3", "gen4", "gen6", "gen8"])
 def gen(request, lib):
     """Force one kernel generation for a test: gen1 = Stockham radix-8 (FP32) and
     native FP64; gen2 = two-step register kernels (FP32) and double-word FP64;
     gen3 = gen2 with the prefetching middle pass (FP32) and double-word FP64;
     gen4 = gen3 with bulk-copy row passes (FP32) and double-word FP64; gen6 =
-    gen4 with the half-task middle pass (FP32) and double-word FP64.  No
+    gen4 with the half-task middle pass (FP32) and double-word FP64; gen8 =
+    gen4 with the tensor-copy middle pass (FP32) and double-word FP64.  No
     bounded device wait may have given up during the test."""
     import torch
     from paper_2504_19410_gb300 import capi
     capi.fsa_device_fault(clear=True)
-    capi.fsa_autotune_set({"gen1": 2, "gen2": 3, "gen3": 4, "gen4": 5, "gen6": 6}[request.param])
+    capi.fsa_autotune_set({"gen1": 2, "gen2": 3, "gen3": 4, "gen4": 5, "gen6": 6, "gen8": 7}[request.param])
     yield request.param
     capi.fsa_autotune_set(1)
     torch.cuda.synchronize()
