@@ -15,6 +15,8 @@
 // current tile's work.  The arithmetic is generation 2's, so the results are
 // bit-equal to it.
 //
+// The R2C pass along axis 0 is staged the same way (k8_r2c_ax0 below).
+//
 // The copy needs a tensor map of Y (host-encoded per launch, passed as a
 // __grid_constant__ parameter), so a launch carries ONE solve; the launcher
 // hands launches of several solves to generation 2.  Every wait on the
@@ -123,6 +125,88 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID)
           const int p = t + R2 * r;
           if (p < n) col[(long long)p * M2] = v;
         });
+    __syncthreads();
+  }
+}
+
+// The pad + R2C pass along axis 0 (pass 1) with the same staging: a tile is
+// 2W = 32 adjacent real columns c of rho over its n0 rows (rows C floats
+// apart), carried as W complex lines (columns c, c + 1 as one complex
+// value), staged by one 2-D tensor copy of the n0 x 32 box ([row][column],
+// 128 bytes a row).  rmap: rho of the launch's one solve as a 2-D tensor of
+// 4-byte elements, dims {C, n0}, box {32, n0}; columns past C read as zero.
+template <class P> struct Geo8R {
+  static constexpr int W = Geo2<P>::W;
+  static constexpr int NT = Geo2<P>::NT;
+  static constexpr int XCH = Geo2<P>::SM_STRIDED;
+  static constexpr int STG = (P::M / 2) * 2 * W * 4;
+  static constexpr int BAR = XCH + STG;
+  static constexpr int SMEM = BAR + 16;
+  static_assert(W == 16 && XCH % 16 == 0 && STG % 16 == 0, "box of 32 real columns, 16-byte aligned staging");
+};
+
+template <class P>
+__global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID)
+    k8_r2c_ax0(const Jobs jobs, long long C, const __grid_constant__ CUtensorMap rmap) {
+  using V = float2;
+  using G = Geo8R<P>;
+  constexpr int M = P::M, n = M / 2, K = M / 2 + 1, W = G::W, R1 = P::R1, R2 = P::R2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const V* stg = reinterpret_cast<const V*>(smraw + G::XCH);  // [row][W complex]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smraw + G::BAR);
+  const int l = threadIdx.x % W, u = threadIdx.x / W;
+  const long long total = (C + 2 * W - 1) / (2 * W);
+  V* __restrict__ X = static_cast<V*>(jobs.j[0].out);
+  auto issue = [&](long long tile) {  // thread 0
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, (unsigned)G::STG);
+    tma_load_2d(smraw + G::XCH, &rmap, (int)(tile * 2 * W), 0, bar);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && blockIdx.x < total) issue(blockIdx.x);
+  int k = 0;
+  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x, ++k) {
+    const long long c = tile * (2 * W) + 2 * l;
+    const bool ok = c < C;
+    const bool late = !mbar_wait(bar, k & 1);
+    stepA_fwd<P, V, true>(
+        u,
+        [&](int t, int r) {
+          const int p = t + R2 * r;
+          return p < n ? stg[p * W + l] : czero<V>();
+        },
+        [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
+    if (__syncthreads_or(late)) {
+      if (threadIdx.x == 0) {
+        if (jobs.fault) atomicOr(jobs.fault, kWaitTimeout);
+        mbar_wait(bar, k & 1);  // the copy still in flight
+      }
+      __syncthreads();
+      return;
+    }
+    if (threadIdx.x == 0 && tile + gridDim.x < total) issue(tile + gridDim.x);
+    V b[R2];
+#pragma unroll
+    for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];
+    rfft<R2, true>(b);
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < R2; ++s) sm[(u + R1 * s) * W + l] = b[s];
+    __syncthreads();
+    // Z = DFT(a + i b): A[k] = (Z[k] + conj Z[M-k]) / 2, B[k] = (Z[k] - conj Z[M-k]) / 2i
+    for (int kk = u; kk < K; kk += P::T) {
+      const V zk = sm[kk * W + l];
+      const V zm = sm[((M - kk) % M) * W + l];
+      if (ok) {
+        *reinterpret_cast<float4*>(X + (long long)kk * C + c) =
+            make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y), 0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+      }
+    }
     __syncthreads();
   }
 }

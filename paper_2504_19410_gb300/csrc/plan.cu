@@ -117,7 +117,7 @@ int kernel_variant(int pass, int M, fsa_dtype dt) {
   if (mode == 4) return 3;
   if (mode == 5) return 4;
   if (mode == 6) return pass == kColMid ? 5 : 4;
-  if (mode == 7) return pass == kColMid ? 6 : 4;
+  if (mode == 7) return 6;  // generation 8's table: generation 4 elsewhere
   const int v = (M >= 0 && M <= 1024) ? g_variant[pass][M][dt].load(std::memory_order_relaxed) : 0;
   return v ? v : 2;
 }
@@ -1056,11 +1056,11 @@ cudaError_t tune_plan(fsa_plan* p) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   for (int k = 0; k < kNumPass && e == cudaSuccess; ++k) {
     if (g_variant[k][Ms[k]][FSA_F32].load() != 0) continue;
-    // variants 5 and 6 (the sixth- and eighth-generation middle passes) only
-    // where they exist
+    // variants 5 and 6 (the sixth-generation middle pass, the
+    // eighth-generation middle and R2C passes) only where they exist
     std::vector<int> cand = {1, 2, 3, 4};
     if (k == kColMid && k6_colm(Ms[k])) cand.push_back(5);
-    if (k == kColMid && k8_colm(Ms[k])) cand.push_back(6);
+    if ((k == kColMid && k8_colm(Ms[k])) || (k == kR2C && k8_r2c(Ms[k]))) cand.push_back(6);
     float tmin[7] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
     for (int v : cand) {
       if (e == cudaSuccess) e = run(k, v);  // warm-up
