@@ -380,8 +380,8 @@ fsa_status fsa_profiler_destroy(fsa_profiler* prof);
  * (lengths 128, 192, 256, 384, 512; generation 4's middle pass elsewhere);
  * generation 8 = generation 4 with a middle pass and an axis-0 R2C pass
  * whose column tiles are staged by one tiled bulk tensor copy (TMA) each,
- * bit-equal to generation 2's (same lengths; a launch of several solves runs
- * generation 2's).
+ * bit-equal to generation 2's (same lengths; one tensor map per solve of a
+ * launch).
  * mode 1 (default): each new FP32 plan times every generation for
  * each of its passes on its own workspace at creation and keeps the fastest
  * per (pass, length); choices persist for the process.  mode 0: untuned

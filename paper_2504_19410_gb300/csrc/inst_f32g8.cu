@@ -27,67 +27,76 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+// A tensor map of one 2-D array: dims {inner, rows} of `esize`-byte elements
+// (rows `inner` elements apart), box {box_inner, box_rows}; false if the
+// driver cannot encode it (then the caller takes generation 2's kernel).
+bool encode_2d(CUtensorMap* map, const void* base, CUtensorMapDataType dt, int esize, long long inner,
+               long long rows, int box_inner, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc || reinterpret_cast<uintptr_t>(base) % 16 != 0 || (inner * esize) % 16 != 0 || rows >= (1LL << 31) ||
+      inner >= (1LL << 31))
+    return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)inner * esize};
+  const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int M> struct Inst8 {
   using P = typename Plan2For<M>::type;
   using G = Geo8<P>;
   using GR = Geo8R<P>;
   static cudaError_t prepare() {
-    cudaError_t e =
-        cudaFuncSetAttribute((const void*)k8_col_mid<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute((const void*)k8_r2c_ax0<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, GR::SMEM);
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f, int bytes) {
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    };
+    set((const void*)k8_col_mid<P, 1>, G::SMEM);
+    set((const void*)k8_col_mid<P, kMaxJobs>, G::SMEM);
+    set((const void*)k8_r2c_ax0<P, 1>, GR::SMEM);
+    set((const void*)k8_r2c_ax0<P, kMaxJobs>, GR::SMEM);
     return e;
   }
-  // The R2C pass of one solve: rho as a {C, n0} tensor of floats (rows of C
-  // floats, 16-byte aligned as the copy needs); otherwise generation 2's.
-  static cudaError_t r2c(const Jobs& jobs, long long C, cudaStream_t s) {
-    constexpr int n0 = M / 2;
-    void* rho = const_cast<void*>(jobs.j[0].in);
-    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-    if (jobs.count != 1 || !enc || C % 4 != 0 || reinterpret_cast<uintptr_t>(rho) % 16 != 0 || C >= (1LL << 31))
-      return pass_fns(kArithF32G2, M).r2c(jobs, C, s);
-    CUtensorMap map;
-    const cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)n0};
-    const cuuint64_t strides[1] = {(cuuint64_t)C * 4};
-    const cuuint32_t box[2] = {(cuuint32_t)(2 * GR::W), (cuuint32_t)n0};
-    const cuuint32_t estr[2] = {1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, rho, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return pass_fns(kArithF32G2, M).r2c(jobs, C, s);
+  // The R2C pass: rho of each solve as a {C, n0} tensor of floats.  A rho
+  // the copy cannot read (not 16-byte aligned, C not a multiple of 4) sends
+  // the launch to generation 2's kernel (its registered launcher, prepared
+  // with the other instances), which computes the same values.
+  template <int NJ> static cudaError_t r2c_n(const Jobs& jobs, long long C, cudaStream_t s) {
+    TmapSet<NJ> maps;
+    for (int j = 0; j < jobs.count; ++j)
+      if (!encode_2d(&maps.m[j], jobs.j[j].in, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C, M / 2, 2 * GR::W, M / 2))
+        return pass_fns(kArithF32G2, M).r2c(jobs, C, s);
     Jobs jj = jobs;
     jj.fault = device_fault_word();
-    const long long tiles = (C + 2 * GR::W - 1) / (2 * GR::W);
-    auto f = k8_r2c_ax0<P>;
-    f<<<persistent_grid((const void*)f, GR::NT, GR::SMEM, tiles), GR::NT, GR::SMEM, s>>>(jj, C, map);
+    const long long tiles = (C + 2 * GR::W - 1) / (2 * GR::W) * jobs.count;
+    auto f = k8_r2c_ax0<P, NJ>;
+    f<<<persistent_grid((const void*)f, GR::NT, GR::SMEM, tiles), GR::NT, GR::SMEM, s>>>(jj, C, maps);
     return cudaGetLastError();
   }
-  // One solve per launch (the tensor map describes its Y); a launch of several
-  // solves, or a Y the map cannot describe, runs generation 2's middle pass
-  // (its registered launcher, prepared with the other instances), which
-  // computes the same values.
-  static cudaError_t colm(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
+  static cudaError_t r2c(const Jobs& jobs, long long C, cudaStream_t s) {
+    return jobs.count == 1 ? r2c_n<1>(jobs, C, s) : r2c_n<kMaxJobs>(jobs, C, s);
+  }
+  // The middle pass: Y of each solve as a {M2, planes * n1} tensor of
+  // 8-byte elements; the same fallback.
+  template <int NJ> static cudaError_t colm_n(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
     constexpr int n1 = M / 2;
-    void* Y = jobs.j[0].out;
-    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-    if (jobs.count != 1 || !enc || M2 % G::W != 0 || reinterpret_cast<uintptr_t>(Y) % 16 != 0 ||
-        (long long)planes * n1 >= (1LL << 31))
-      return pass_fns(kArithF32G2, M).colm(jobs, M2, planes, s);
-    CUtensorMap map;
-    const cuuint64_t dims[2] = {(cuuint64_t)M2, (cuuint64_t)planes * n1};
-    const cuuint64_t strides[1] = {(cuuint64_t)M2 * 8};
-    const cuuint32_t box[2] = {(cuuint32_t)G::W, (cuuint32_t)n1};
-    const cuuint32_t estr[2] = {1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, Y, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return pass_fns(kArithF32G2, M).colm(jobs, M2, planes, s);
+    TmapSet<NJ> maps;
+    for (int j = 0; j < jobs.count; ++j)
+      if (M2 % G::W != 0 || !encode_2d(&maps.m[j], jobs.j[j].out, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, M2,
+                                       (long long)planes * n1, G::W, n1))
+        return pass_fns(kArithF32G2, M).colm(jobs, M2, planes, s);
     Jobs jj = jobs;
     jj.fault = device_fault_word();
-    const long long tiles = (long long)(M2 / G::W) * planes;
-    auto f = k8_col_mid<P>;
-    f<<<persistent_grid((const void*)f, G::NT, G::SMEM, tiles), G::NT, G::SMEM, s>>>(jj, M2, planes, map);
+    const long long tiles = (long long)(M2 / G::W) * planes * jobs.count;
+    auto f = k8_col_mid<P, NJ>;
+    f<<<persistent_grid((const void*)f, G::NT, G::SMEM, tiles), G::NT, G::SMEM, s>>>(jj, M2, planes, maps);
     return cudaGetLastError();
+  }
+  static cudaError_t colm(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
+    return jobs.count == 1 ? colm_n<1>(jobs, M2, planes, s) : colm_n<kMaxJobs>(jobs, M2, planes, s);
   }
 };
 

@@ -17,9 +17,9 @@
 //
 // The R2C pass along axis 0 is staged the same way (k8_r2c_ax0 below).
 //
-// The copy needs a tensor map of Y (host-encoded per launch, passed as a
-// __grid_constant__ parameter), so a launch carries ONE solve; the launcher
-// hands launches of several solves to generation 2.  Every wait on the
+// The copies need a tensor map per solve of the launch (host-encoded per
+// launch, passed in a __grid_constant__ parameter: NJ maps, NJ = 1 for a
+// single solve or kMaxJobs for a launch of several).  Every wait on the
 // mbarrier is bounded (kWaitLimitCycles); a CTA whose wait gives up ORs
 // kWaitTimeout into jobs.fault, waits (bounded) for its copy in flight and
 // returns, the decision taken CTA-wide at the barrier that ends step A.
@@ -42,6 +42,11 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// The tensor maps of a launch's solves (128 bytes each, 64-byte aligned).
+template <int NJ> struct TmapSet {
+  CUtensorMap m[NJ];
+};
+
 // Shared memory: the exchange tile (M x W complex), the staged input box
 // (n1 = M/2 rows x W columns), the mbarrier.
 template <class P> struct Geo8 {
@@ -54,11 +59,11 @@ template <class P> struct Geo8 {
   static_assert(W == 16 && XCH % 16 == 0 && STG % 16 == 0, "box of 16 columns, 16-byte aligned staging");
 };
 
-// ymap: Y of the launch's one solve as a 2-D tensor of 8-byte elements,
-// dims {M2, planes * n1}, box {16, n1}.
-template <class P>
+// ymap.m[j]: Y of solve j as a 2-D tensor of 8-byte elements, dims
+// {M2, planes * n1}, box {16, n1}.
+template <class P, int NJ>
 __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID)
-    k8_col_mid(const Jobs jobs, int M2, int planes, const __grid_constant__ CUtensorMap ymap) {
+    k8_col_mid(const Jobs jobs, int M2, int planes, const __grid_constant__ TmapSet<NJ> ymap) {
   using V = float2;
   using G = Geo8<P>;
   constexpr int M = P::M, n = M / 2, W = G::W, R2 = P::R2;
@@ -68,15 +73,16 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID)
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smraw + G::BAR);
   const int l = threadIdx.x % W, u = mid_u<P>(threadIdx.x);
   const int tpp = M2 / W;  // column tiles per plane
-  const long long total = (long long)tpp * planes;
+  const long long tpj = (long long)tpp * planes;  // tiles per solve
+  const long long total = tpj * jobs.count;
   const int n2 = M2 / 2;
-  const Job& jb = jobs.j[0];
+  // work item -> (solve, tile of the solve), from the last item to the first
   auto tile_of = [&](long long it) -> long long { return kMidReverse ? total - 1 - it : it; };
   auto issue = [&](long long it) {  // thread 0
-    const long long lt = tile_of(it);
+    const long long g = tile_of(it), lt = g % tpj;
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(bar, (unsigned)G::STG);
-    tma_load_2d(smraw + G::XCH, &ymap, (int)(lt % tpp) * W, (int)(lt / tpp) * n, bar);
+    tma_load_2d(smraw + G::XCH, &ymap.m[g / tpj], (int)(lt % tpp) * W, (int)(lt / tpp) * n, bar);
   };
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
@@ -87,7 +93,8 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID)
   MidSpec<P> sp;
   int k = 0;
   for (long long it = blockIdx.x; it < total; it += gridDim.x, ++k) {
-    const long long lt = tile_of(it);
+    const long long g = tile_of(it), lt = g % tpj;
+    const Job& jb = jobs.j[g / tpj];
     const int k0 = (int)(lt / tpp);
     const int k2 = (int)(lt % tpp) * W + l;
     V* __restrict__ col = static_cast<V*>(jb.out) + (long long)k0 * n * M2 + k2;
@@ -133,8 +140,8 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID)
 // 2W = 32 adjacent real columns c of rho over its n0 rows (rows C floats
 // apart), carried as W complex lines (columns c, c + 1 as one complex
 // value), staged by one 2-D tensor copy of the n0 x 32 box ([row][column],
-// 128 bytes a row).  rmap: rho of the launch's one solve as a 2-D tensor of
-// 4-byte elements, dims {C, n0}, box {32, n0}; columns past C read as zero.
+// 128 bytes a row).  rmap.m[j]: rho of solve j as a 2-D tensor of 4-byte
+// elements, dims {C, n0}, box {32, n0}; columns past C read as zero.
 template <class P> struct Geo8R {
   static constexpr int W = Geo2<P>::W;
   static constexpr int NT = Geo2<P>::NT;
@@ -145,9 +152,9 @@ template <class P> struct Geo8R {
   static_assert(W == 16 && XCH % 16 == 0 && STG % 16 == 0, "box of 32 real columns, 16-byte aligned staging");
 };
 
-template <class P>
+template <class P, int NJ>
 __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID)
-    k8_r2c_ax0(const Jobs jobs, long long C, const __grid_constant__ CUtensorMap rmap) {
+    k8_r2c_ax0(const Jobs jobs, long long C, const __grid_constant__ TmapSet<NJ> rmap) {
   using V = float2;
   using G = Geo8R<P>;
   constexpr int M = P::M, n = M / 2, K = M / 2 + 1, W = G::W, R1 = P::R1, R2 = P::R2;
@@ -156,12 +163,12 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID)
   const V* stg = reinterpret_cast<const V*>(smraw + G::XCH);  // [row][W complex]
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smraw + G::BAR);
   const int l = threadIdx.x % W, u = threadIdx.x / W;
-  const long long total = (C + 2 * W - 1) / (2 * W);
-  V* __restrict__ X = static_cast<V*>(jobs.j[0].out);
+  const long long tpj = (C + 2 * W - 1) / (2 * W);  // tiles per solve
+  const long long total = tpj * jobs.count;
   auto issue = [&](long long tile) {  // thread 0
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(bar, (unsigned)G::STG);
-    tma_load_2d(smraw + G::XCH, &rmap, (int)(tile * 2 * W), 0, bar);
+    tma_load_2d(smraw + G::XCH, &rmap.m[tile / tpj], (int)((tile % tpj) * 2 * W), 0, bar);
   };
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
@@ -171,7 +178,8 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID)
   if (threadIdx.x == 0 && blockIdx.x < total) issue(blockIdx.x);
   int k = 0;
   for (long long tile = blockIdx.x; tile < total; tile += gridDim.x, ++k) {
-    const long long c = tile * (2 * W) + 2 * l;
+    V* __restrict__ X = static_cast<V*>(jobs.j[tile / tpj].out);
+    const long long c = (tile % tpj) * (2 * W) + 2 * l;
     const bool ok = c < C;
     const bool late = !mbar_wait(bar, k & 1);
     stepA_fwd<P, V, true>(
