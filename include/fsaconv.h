@@ -378,8 +378,8 @@ fsa_status fsa_profiler_destroy(fsa_profiler* prof);
  * padded and cropped step of generation 2 into two half tasks per line, so
  * each thread holds half the values and twice the warps fit on an SM
  * (lengths 128, 192, 256, 384, 512; generation 4's middle pass elsewhere);
- * generation 8 = generation 4 with a middle pass and an axis-0 R2C pass
- * whose column tiles are staged by one tiled bulk tensor copy (TMA) each,
+ * generation 8 = generation 4 with a middle pass and the axis-0 R2C and C2R
+ * passes whose column tiles are staged by tiled bulk tensor copies (TMA),
  * bit-equal to generation 2's (same lengths; one tensor map per solve of a
  * launch).
  * mode 1 (default): each new FP32 plan times every generation for

@@ -104,6 +104,7 @@ cudaError_t k6_prepare(int M);
 ColmFn k8_colm(int M);
 using R2cFn = cudaError_t (*)(const Jobs&, long long, cudaStream_t);
 R2cFn k8_r2c(int M);  // the R2C pass staged the same way
+R2cFn k8_c2r(int M);  // and the C2R pass (same launcher signature)
 cudaError_t k8_prepare(int M);
 // The seventh generation (passes7.cuh, inst_f32g7.cu): row forward, middle
 // and row inverse of FP32 grids with n1 = n2 as one kernel fed by a work

@@ -1,5 +1,5 @@
-// FP32 eighth-generation middle and R2C passes (passes8.cuh): the column
-// tiles staged by one tiled bulk tensor copy each, lengths 128 to 512.  Compiled as its own
+// FP32 eighth-generation middle, R2C and C2R passes (passes8.cuh): the column
+// tiles staged by tiled bulk tensor copies, lengths 128 to 512.  Compiled as its own
 // translation unit; the launchers are looked up by length (k8_colm) when the
 // other FP32 instances register their function tables.
 #include <cudaTypedefs.h>
@@ -49,6 +49,7 @@ template <int M> struct Inst8 {
   using P = typename Plan2For<M>::type;
   using G = Geo8<P>;
   using GR = Geo8R<P>;
+  using GC = Geo8C<P>;
   static cudaError_t prepare() {
     cudaError_t e = cudaSuccess;
     auto set = [&](const void* f, int bytes) {
@@ -58,7 +59,26 @@ template <int M> struct Inst8 {
     set((const void*)k8_col_mid<P, kMaxJobs>, G::SMEM);
     set((const void*)k8_r2c_ax0<P, 1>, GR::SMEM);
     set((const void*)k8_r2c_ax0<P, kMaxJobs>, GR::SMEM);
+    set((const void*)k8_c2r_ax0<P, 1>, GC::SMEM);
+    set((const void*)k8_c2r_ax0<P, kMaxJobs>, GC::SMEM);
     return e;
+  }
+  // The C2R pass: X of each solve as a {C, n0 + 1} tensor of 8-byte elements.
+  template <int NJ> static cudaError_t c2r_n(const Jobs& jobs, long long C, cudaStream_t s) {
+    TmapSet<NJ> maps;
+    for (int j = 0; j < jobs.count; ++j)
+      if (!encode_2d(&maps.m[j], jobs.j[j].in, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, C, M / 2 + 1, 2 * GC::W,
+                     GC::ROWS / 2))
+        return pass_fns(kArithF32G2, M).c2r(jobs, C, s);
+    Jobs jj = jobs;
+    jj.fault = device_fault_word();
+    const long long tiles = (C + 2 * GC::W - 1) / (2 * GC::W) * jobs.count;
+    auto f = k8_c2r_ax0<P, NJ>;
+    f<<<persistent_grid((const void*)f, GC::NT, GC::SMEM, tiles), GC::NT, GC::SMEM, s>>>(jj, C, maps);
+    return cudaGetLastError();
+  }
+  static cudaError_t c2r(const Jobs& jobs, long long C, cudaStream_t s) {
+    return jobs.count == 1 ? c2r_n<1>(jobs, C, s) : c2r_n<kMaxJobs>(jobs, C, s);
   }
   // The R2C pass: rho of each solve as a {C, n0} tensor of floats.  A rho
   // the copy cannot read (not 16-byte aligned, C not a multiple of 4) sends
@@ -120,6 +140,17 @@ R2cFn k8_r2c(int M) {
     case 256: return &Inst8<256>::r2c;
     case 384: return &Inst8<384>::r2c;
     case 512: return &Inst8<512>::r2c;
+    default: return nullptr;
+  }
+}
+
+R2cFn k8_c2r(int M) {
+  switch (M) {
+    case 128: return &Inst8<128>::c2r;
+    case 192: return &Inst8<192>::c2r;
+    case 256: return &Inst8<256>::c2r;
+    case 384: return &Inst8<384>::c2r;
+    case 512: return &Inst8<512>::c2r;
     default: return nullptr;
   }
 }

@@ -15,7 +15,8 @@
 // current tile's work.  The arithmetic is generation 2's, so the results are
 // bit-equal to it.
 //
-// The R2C pass along axis 0 is staged the same way (k8_r2c_ax0 below).
+// The R2C and C2R passes along axis 0 are staged the same way (k8_r2c_ax0,
+// k8_c2r_ax0 below).
 //
 // The copies need a tensor map per solve of the launch (host-encoded per
 // launch, passed in a __grid_constant__ parameter: NJ maps, NJ = 1 for a
@@ -215,6 +216,90 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID)
             make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y), 0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
       }
     }
+    __syncthreads();
+  }
+}
+
+// The C2R pass along axis 0 + crop (pass 5) with the same staging.  Its
+// tile reads all K0 = n0 + 1 rows of X (the half spectrum: rows k <= n0
+// directly, k > n0 from their mirror M - k), 2 x W8 complex columns a row; at
+// W = 16 the staged box and the exchange tile would take 130 KB and leave one
+// CTA per SM, so this pass runs W8 = 8 complex lines (16 real columns) per
+// CTA of 128 threads: a 258-row box of 128-byte rows (two copies of 129 rows,
+// 33 KB; the last row lies past X and reads as zero) and a 32 KB exchange
+// tile, three CTAs per SM.  xmap.m[j]: X of solve j as a 2-D tensor of
+// 8-byte elements, dims {C, K0}, box {16, 129}.
+template <class P> struct Geo8C {
+  static constexpr int W = 8;
+  static constexpr int NT = W * P::T;
+  static constexpr int ROWS = 2 * ((P::M / 2 + 2) / 2);  // K0 = M/2 + 1 rows, rounded up to two equal boxes
+  static constexpr int XCH = P::M * W * 8;
+  static constexpr int STG = ROWS * 2 * W * 8;
+  static constexpr int BAR = XCH + STG;
+  static constexpr int SMEM = BAR + 16;
+  static_assert(ROWS / 2 <= 256 && XCH % 16 == 0 && STG % 16 == 0, "two boxes of at most 256 rows");
+};
+
+template <class P, int NJ>
+__global__ void __launch_bounds__(Geo8C<P>::NT, 3)
+    k8_c2r_ax0(const Jobs jobs, long long C, const __grid_constant__ TmapSet<NJ> xmap) {
+  using V = float2;
+  using G = Geo8C<P>;
+  constexpr int M = P::M, n = M / 2, W = G::W, R1 = P::R1, R2 = P::R2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const float4* stg = reinterpret_cast<const float4*>(smraw + G::XCH);  // [row][W column pairs]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smraw + G::BAR);
+  const int l = threadIdx.x % W, u = threadIdx.x / W;
+  const long long tpj = (C + 2 * W - 1) / (2 * W);  // tiles per solve
+  const long long total = tpj * jobs.count;
+  auto issue = [&](long long tile) {  // thread 0
+    const CUtensorMap* map = &xmap.m[tile / tpj];
+    const int x = (int)((tile % tpj) * 2 * W);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, (unsigned)G::STG);
+    tma_load_2d(smraw + G::XCH, map, x, 0, bar);
+    tma_load_2d(smraw + G::XCH + G::STG / 2, map, x, G::ROWS / 2, bar);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && blockIdx.x < total) issue(blockIdx.x);
+  int it = 0;
+  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x, ++it) {
+    float* __restrict__ phi = static_cast<float*>(jobs.j[tile / tpj].out);
+    const long long c = (tile % tpj) * (2 * W) + 2 * l;
+    const bool ok = c < C;
+    const bool late = !mbar_wait(bar, it & 1);
+    // Z[k] = A[k] + i B[k] with A, B Hermitian: rebuild k > n from M - k
+    V b[R2];
+#pragma unroll
+    for (int s = 0; s < R2; ++s) {
+      const int k = u + R1 * s;
+      const bool lo = k <= n;
+      const float4 ab = stg[(lo ? k : M - k) * W + l];
+      b[s] = lo ? mk(ab.x - ab.w, ab.y + ab.z) : mk(ab.x + ab.w, ab.z - ab.y);
+    }
+    if (__syncthreads_or(late)) {
+      if (threadIdx.x == 0) {
+        if (jobs.fault) atomicOr(jobs.fault, kWaitTimeout);
+        mbar_wait(bar, it & 1);  // the copies still in flight
+      }
+      __syncthreads();
+      return;
+    }
+    // every thread holds its inputs: the next tile's copies run under this one
+    if (threadIdx.x == 0 && tile + gridDim.x < total) issue(tile + gridDim.x);
+    stepB_inv<P, V>(u, b, [&](int q, int t, V v) { sm[(q * R2 + t) * W + l] = v; });
+    __syncthreads();
+    stepA_inv<P, V, true>(
+        u, [&](int q, int t) { return sm[(q * R2 + t) * W + l]; },
+        [&](int t, int r, V v) {
+          const int p = t + R2 * r;
+          if (p < n && ok) *reinterpret_cast<V*>(phi + (long long)p * C + c) = v;
+        });
     __syncthreads();
   }
 }

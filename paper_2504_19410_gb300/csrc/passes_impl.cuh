@@ -446,12 +446,13 @@ static cudaError_t init_tu_twiddles() {
     f3.rowf = &fsa::detail::Inst2<M>::rowf_b;                                         \
     f3.rowi = &fsa::detail::Inst2<M>::rowi_b;                                         \
     fsa::register_pass_fns(fsa::kArithF32G4, M, f3);                                  \
-    /* generation 8: generation 4 with the tensor-copy middle and R2C passes */       \
+    /* generation 8: generation 4 with the tensor-copy middle, R2C, C2R passes */     \
     /* where they have an instance (inst_f32g8.cu), generation 4's elsewhere */        \
     {                                                                                 \
       fsa::PassFns f8 = f3;                                                           \
       if (fsa::ColmFn c8 = fsa::k8_colm(M)) f8.colm = c8;                             \
       if (fsa::R2cFn r8 = fsa::k8_r2c(M)) f8.r2c = r8;                                \
+      if (fsa::R2cFn c8 = fsa::k8_c2r(M)) f8.c2r = c8;                                \
       fsa::register_pass_fns(fsa::kArithF32G8, M, f8);                                \
     }                                                                                 \
     /* generation 6: generation 4 with the low-register middle pass where  */        \

@@ -1057,10 +1057,11 @@ cudaError_t tune_plan(fsa_plan* p) {
   for (int k = 0; k < kNumPass && e == cudaSuccess; ++k) {
     if (g_variant[k][Ms[k]][FSA_F32].load() != 0) continue;
     // variants 5 and 6 (the sixth-generation middle pass, the
-    // eighth-generation middle and R2C passes) only where they exist
+    // eighth-generation middle, R2C and C2R passes) only where they exist
     std::vector<int> cand = {1, 2, 3, 4};
     if (k == kColMid && k6_colm(Ms[k])) cand.push_back(5);
-    if ((k == kColMid && k8_colm(Ms[k])) || (k == kR2C && k8_r2c(Ms[k]))) cand.push_back(6);
+    if ((k == kColMid && k8_colm(Ms[k])) || (k == kR2C && k8_r2c(Ms[k])) || (k == kC2R && k8_c2r(Ms[k])))
+      cand.push_back(6);
     float tmin[7] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
     for (int v : cand) {
       if (e == cudaSuccess) e = run(k, v);  // warm-up
