@@ -67,6 +67,7 @@ __device__ __forceinline__ void bulk_prologue(const Jobs& jobs, long long tpj, l
 }
 
 // ------------------------------------------------------------ row forward --
+constexpr bool kRowFwdBulkStore = true;
 // PAD = false: rows of M inputs (the DDI grid reading's unpadded transform).
 template <class P, int WR, bool PAD = true>
 __global__ void __launch_bounds__(BulkGeo<P, WR, P::M / 2>::NT) k4_row_fwd(const Jobs jobs, long long rows) {
@@ -107,12 +108,30 @@ __global__ void __launch_bounds__(BulkGeo<P, WR, P::M / 2>::NT) k4_row_fwd(const
 #pragma unroll
     for (int t = 0; t < R2; ++t) bv[t] = line[u * (R2 + 1) + t];
     rfft<R2, true>(bv);
-    if (ok) {
+    if constexpr (PAD && kRowFwdBulkStore) {
+      // the tile's output rows go out by one bulk copy from the exchange
+      // tile, rewritten as WR contiguous rows of M values once every thread
+      // has taken its step-B inputs out of it
+      __syncthreads();
+      V* out = xch + l * M;
+#pragma unroll
+      for (int s = 0; s < R2; ++s) out[u + R1 * s] = bv[s];
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const long long row0 = (tile % tpj) * WR;
+        const long long nr = rows - row0 < WR ? rows - row0 : WR;
+        bulk_s2g(static_cast<V*>(jb.out) + row0 * M, xch, (unsigned)(nr * M * 8));
+        bulk_commit();
+        bulk_wait_read0();  // the exchange tile is free again before the barrier below
+      }
+    } else if (ok) {
 #pragma unroll
       for (int s = 0; s < R2; ++s) y[u + R1 * s] = bv[s];
     }
     __syncthreads();
   }
+  if (threadIdx.x == 0) bulk_wait0();
 }
 
 // ------------------------------------------------------------ row inverse --
