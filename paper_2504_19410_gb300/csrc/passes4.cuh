@@ -68,6 +68,7 @@ __device__ __forceinline__ void bulk_prologue(const Jobs& jobs, long long tpj, l
 
 // ------------------------------------------------------------ row forward --
 constexpr bool kRowFwdBulkStore = true;
+constexpr bool kRowInvBulkStore = true;
 // PAD = false: rows of M inputs (the DDI grid reading's unpadded transform).
 template <class P, int WR, bool PAD = true>
 __global__ void __launch_bounds__(BulkGeo<P, WR, P::M / 2>::NT) k4_row_fwd(const Jobs jobs, long long rows) {
@@ -167,14 +168,46 @@ __global__ void __launch_bounds__(BulkGeo<P, WR, P::M>::NT) k4_row_inv(const Job
       return;
     }
     if (threadIdx.x == 0 && tile + gridDim.x < total) issue_rows<WR, M>(jobs, tpj, rows, tile + gridDim.x, stg, bar);
+    constexpr bool STB = PAD && kRowInvBulkStore && R1 % 2 == 0;
+    V o[P::PA][R1 / 2];  // STB: this thread's outputs, stored after the barrier
     stepA_inv<P, V, PAD>(
         u, [&](int q, int t) { return line[q * (R2 + 1) + t]; },
         [&](int t, int r, V v) {
           const int p = t + R2 * r;
-          if (p < n && ok) x[p] = v;
+          if constexpr (STB) {
+            o[(t - u) / T][r] = v;
+          } else {
+            if (p < n && ok) x[p] = v;
+          }
         });
+    if constexpr (STB) {
+      // the tile's output rows (n values each, contiguous in X) leave by one
+      // bulk copy from the exchange tile, rewritten as WR rows of n values
+      // once every thread has read its step-A inputs out of it
+      __syncthreads();
+      V* out = xch + l * n;
+#pragma unroll
+      for (int i = 0; i < P::PA; ++i) {
+        const int t = u + T * i;
+#pragma unroll
+        for (int r = 0; r < R1 / 2; ++r) {
+          const int p = t + R2 * r;
+          if ((P::PA * T == R2 || t < R2) && p < n) out[p] = o[i][r];
+        }
+      }
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const long long row0 = (tile % tpj) * WR;
+        const long long nr = rows - row0 < WR ? rows - row0 : WR;
+        bulk_s2g(static_cast<V*>(jb.out) + row0 * n, xch, (unsigned)(nr * n * 8));
+        bulk_commit();
+        bulk_wait_read0();  // the exchange tile is free again before the barrier below
+      }
+    }
     __syncthreads();
   }
+  if (threadIdx.x == 0) bulk_wait0();
 }
 
 }  // namespace fsa
