@@ -102,6 +102,7 @@ cudaError_t k6_prepare(int M);
 // The eighth-generation middle pass (passes8.cuh, inst_f32g8.cu): column tiles
 // staged by one tiled bulk tensor copy each; null where it has no instance.
 ColmFn k8_colm(int M);
+ColmFn k8_colm_shared(int M);  // its form for densities of one plan (one spectrum read per tile)
 using R2cFn = cudaError_t (*)(const Jobs&, long long, cudaStream_t);
 R2cFn k8_r2c(int M);  // the R2C pass staged the same way
 R2cFn k8_c2r(int M);  // and the C2R pass (same launcher signature)

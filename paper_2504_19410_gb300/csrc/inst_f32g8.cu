@@ -57,6 +57,7 @@ template <int M> struct Inst8 {
     };
     set((const void*)k8_col_mid<P, 1>, G::SMEM);
     set((const void*)k8_col_mid<P, kMaxJobs>, G::SMEM);
+    set((const void*)k8_col_mid<P, kMaxJobs, true>, G::SMEM);
     set((const void*)k8_r2c_ax0<P, 1>, GR::SMEM);
     set((const void*)k8_r2c_ax0<P, kMaxJobs>, GR::SMEM);
     set((const void*)k8_c2r_ax0<P, 1>, GC::SMEM);
@@ -101,26 +102,44 @@ template <int M> struct Inst8 {
   }
   // The middle pass: Y of each solve as a {M2, planes * n1} tensor of
   // 8-byte elements; the same fallback.
-  template <int NJ> static cudaError_t colm_n(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
+  template <int NJ, bool SHARED = false>
+  static cudaError_t colm_n(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
     constexpr int n1 = M / 2;
     TmapSet<NJ> maps;
     for (int j = 0; j < jobs.count; ++j)
       if (M2 % G::W != 0 || !encode_2d(&maps.m[j], jobs.j[j].out, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, M2,
                                        (long long)planes * n1, G::W, n1))
-        return pass_fns(kArithF32G2, M).colm(jobs, M2, planes, s);
+        return SHARED ? pass_fns(kArithF32G3, M).colm_shared(jobs, M2, planes, s)
+                      : pass_fns(kArithF32G2, M).colm(jobs, M2, planes, s);
     Jobs jj = jobs;
     jj.fault = device_fault_word();
-    const long long tiles = (long long)(M2 / G::W) * planes * jobs.count;
-    auto f = k8_col_mid<P, NJ>;
+    // SHARED: one CTA slot per tile (each walks the tile for every solve)
+    const long long tiles = (long long)(M2 / G::W) * planes * (SHARED ? 1 : jobs.count);
+    auto f = k8_col_mid<P, NJ, SHARED>;
     f<<<persistent_grid((const void*)f, G::NT, G::SMEM, tiles), G::NT, G::SMEM, s>>>(jj, M2, planes, maps);
     return cudaGetLastError();
   }
   static cudaError_t colm(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
     return jobs.count == 1 ? colm_n<1>(jobs, M2, planes, s) : colm_n<kMaxJobs>(jobs, M2, planes, s);
   }
+  // densities of one plan: one spectrum read per column tile for all of them
+  static cudaError_t colm_shared(const Jobs& jobs, int M2, int planes, cudaStream_t s) {
+    return colm_n<kMaxJobs, true>(jobs, M2, planes, s);
+  }
 };
 
 }  // namespace
+
+ColmFn k8_colm_shared(int M) {
+  switch (M) {
+    case 128: return &Inst8<128>::colm_shared;
+    case 192: return &Inst8<192>::colm_shared;
+    case 256: return &Inst8<256>::colm_shared;
+    case 384: return &Inst8<384>::colm_shared;
+    case 512: return &Inst8<512>::colm_shared;
+    default: return nullptr;
+  }
+}
 
 ColmFn k8_colm(int M) {
   switch (M) {

@@ -61,8 +61,10 @@ template <class P> struct Geo8 {
 };
 
 // ymap.m[j]: Y of solve j as a 2-D tensor of 8-byte elements, dims
-// {M2, planes * n1}, box {16, n1}.
-template <class P, int NJ>
+// {M2, planes * n1}, box {16, n1}.  SHARED: every solve of the launch has the
+// same spectrum (densities of one plan); a CTA then takes one column tile for
+// all solves in turn and loads the tile's spectrum values once.
+template <class P, int NJ, bool SHARED = false>
 __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID)
     k8_col_mid(const Jobs jobs, int M2, int planes, const __grid_constant__ TmapSet<NJ> ymap) {
   using V = float2;
@@ -75,27 +77,37 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID)
   const int l = threadIdx.x % W, u = mid_u<P>(threadIdx.x);
   const int tpp = M2 / W;  // column tiles per plane
   const long long tpj = (long long)tpp * planes;  // tiles per solve
-  const long long total = tpj * jobs.count;
+  const long long K = jobs.count;
+  const long long total = tpj * K;
   const int n2 = M2 / 2;
-  // work item -> (solve, tile of the solve), from the last item to the first
-  auto tile_of = [&](long long it) -> long long { return kMidReverse ? total - 1 - it : it; };
+  // work item -> (solve, tile of the solve), walked from the last item to
+  // the first; SHARED orders the solves innermost and a CTA takes the K
+  // items of one tile in a row
+  auto phys = [&](long long it) -> long long { return kMidReverse ? total - 1 - it : it; };
+  auto job_of = [&](long long it) -> long long { return SHARED ? phys(it) % K : phys(it) / tpj; };
+  auto lt_of = [&](long long it) -> long long { return SHARED ? phys(it) / K : phys(it) % tpj; };
+  auto next_of = [&](long long it) -> long long {
+    if constexpr (SHARED) return it % K + 1 < K ? it + 1 : (it / K + gridDim.x) * K;
+    else return it + gridDim.x;
+  };
+  const long long first = SHARED ? (long long)blockIdx.x * K : (long long)blockIdx.x;
   auto issue = [&](long long it) {  // thread 0
-    const long long g = tile_of(it), lt = g % tpj;
+    const long long lt = lt_of(it);
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(bar, (unsigned)G::STG);
-    tma_load_2d(smraw + G::XCH, &ymap.m[g / tpj], (int)(lt % tpp) * W, (int)(lt / tpp) * n, bar);
+    tma_load_2d(smraw + G::XCH, &ymap.m[job_of(it)], (int)(lt % tpp) * W, (int)(lt / tpp) * n, bar);
   };
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
   }
   __syncthreads();
-  if (threadIdx.x == 0 && blockIdx.x < total) issue(blockIdx.x);
+  if (threadIdx.x == 0 && first < total) issue(first);
   MidSpec<P> sp;
   int k = 0;
-  for (long long it = blockIdx.x; it < total; it += gridDim.x, ++k) {
-    const long long g = tile_of(it), lt = g % tpj;
-    const Job& jb = jobs.j[g / tpj];
+  for (long long it = first; it < total; it = next_of(it), ++k) {
+    const long long lt = lt_of(it);
+    const Job& jb = jobs.j[job_of(it)];
     const int k0 = (int)(lt / tpp);
     const int k2 = (int)(lt % tpp) * W + l;
     V* __restrict__ col = static_cast<V*>(jb.out) + (long long)k0 * n * M2 + k2;
@@ -118,8 +130,9 @@ __global__ void __launch_bounds__(Geo2<P>::NT, Geo2<P>::MINB_MID)
       return;
     }
     // every thread has taken the tile out of the staging buffer: the next one
-    if (threadIdx.x == 0 && it + gridDim.x < total) issue(it + gridDim.x);
-    mid_load<P>(sp, srow, u, true, n2 + 1);
+    if (threadIdx.x == 0 && next_of(it) < total) issue(next_of(it));
+    // SHARED: the first solve of the tile this CTA takes in turn loads the spectrum
+    if (!SHARED || it % K == 0) mid_load<P>(sp, srow, u, true, n2 + 1);
     V b[R2];
 #pragma unroll
     for (int t = 0; t < R2; ++t) b[t] = sm[(u * R2 + t) * W + l];

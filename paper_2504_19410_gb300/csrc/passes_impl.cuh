@@ -451,6 +451,7 @@ static cudaError_t init_tu_twiddles() {
     {                                                                                 \
       fsa::PassFns f8 = f3;                                                           \
       if (fsa::ColmFn c8 = fsa::k8_colm(M)) f8.colm = c8;                             \
+      if (fsa::ColmFn s8 = fsa::k8_colm_shared(M)) f8.colm_shared = s8;               \
       if (fsa::R2cFn r8 = fsa::k8_r2c(M)) f8.r2c = r8;                                \
       if (fsa::R2cFn c8 = fsa::k8_c2r(M)) f8.c2r = c8;                                \
       fsa::register_pass_fns(fsa::kArithF32G8, M, f8);                                \
