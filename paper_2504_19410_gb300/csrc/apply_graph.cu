@@ -73,6 +73,13 @@ void apply_graphs_forget_plan(const fsa_plan* p) {
 // this triple has been seen before, else launched directly.
 cudaError_t plan_apply_graph(const fsa_plan* p, const void* rho, void* phi, cudaStream_t s) {
   if (!g_enabled.load()) return plan_apply_passes(p, rho, phi, s);
+  // a caller capturing its own stream into a graph gets the launches
+  // themselves (no capture or instantiation of ours inside its capture)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return plan_apply_passes(p, rho, phi, s);
+  }
   const Key key{p, rho, phi, g_gen.load(), launch_grid_mode()};
   cudaGraphExec_t exec = nullptr;
   cudaError_t e = cudaSuccess;

@@ -127,3 +127,30 @@ def test_host_entry_point_replays(lib, capi):
         assert torch.equal(direct, host_out), k
     assert oracle.rel_error(host_out.double().numpy(), oracle.solve(L, n, 0.5, r)) <= 2e-6
     plan.close()
+
+
+def test_apply_inside_a_callers_graph_capture(lib, capi):
+    """A caller capturing its stream into its own CUDA graph gets the pass
+    launches captured there (no capture or instantiation of the library's
+    own inside it); replaying the caller's graph solves the current contents."""
+    import torch
+    n, L = (12, 16, 24), (2.0, 2.5, 3.0)
+    plan = lib.Plan(L, n, "f32", eps=0.5)
+    rng = np.random.default_rng(12)
+    r0, r1 = rng.standard_normal(n), rng.standard_normal(n)
+    x = dev(r0, "f32")
+    y = torch.empty_like(x)
+    for _ in range(2):  # the library's own graph of this triple exists by now
+        plan.apply(x, y)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.apply(x, y, stream=s)
+    x.copy_(dev(r1, "f32"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert capi.fsa_device_fault(clear=True) == 0
+    want = oracle.solve(L, n, 0.5, r1)
+    assert oracle.rel_error(y.double().cpu().numpy(), want) <= 2e-6
+    plan.close()
