@@ -71,7 +71,9 @@ def test_replay_uses_current_contents_and_matches_direct(lib, capi, dt):
 
 def test_selection_change_reaches_replayed_solves(lib, capi):
     """A graph keeps the kernels of its capture: fsa_pipe_select after two
-    calls must still switch the next call to the pipelined kernel."""
+    calls must still switch the next calls to the pipelined kernel (which
+    computes the two-step passes' values; the separate passes of this
+    process may be another generation, so the two agree to round-off)."""
     import torch
     n, L = (12, 64, 64), (2.0, 2.5, 3.0)
     capi.fsa_autotune_set(0)
@@ -88,7 +90,9 @@ def test_selection_change_reaches_replayed_solves(lib, capi):
         plan.apply(x, y1)
     torch.cuda.synchronize()
     assert capi.fsa_device_fault(clear=True) == 0
-    assert torch.equal(y0, y1)  # the pipelined kernel is bit-equal to the passes
+    want = oracle.solve(L, n, 0.5, x.double().cpu().numpy())
+    assert oracle.rel_error(y1.double().cpu().numpy(), want) <= 2e-6
+    assert oracle.rel_error(y1.double().cpu().numpy(), y0.double().cpu().numpy()) <= 1e-6
     plan.close()
 
 
