@@ -67,8 +67,9 @@ struct DdiPar {
 // ascending order, so the planes it wrote last -- still in the 129 MB L2 --
 // are the first ones read (and overwritten in place) here, and the
 // row-inverse pass after them, reading in ascending order, starts with the
-// planes this pass wrote last (measured: row inverse 0.0880 -> 0.0857 ms at
-// 256^3; the middle pass itself is not HBM-bound and does not change).
+// planes this pass wrote last (measured at 256^3 with the tensor-copy middle
+// pass and the bulk-copy row passes: middle 0.1827 -> 0.1779 ms, row inverse
+// 0.0825 -> 0.0799 ms, the solve 0.4067 -> 0.3978 ms).
 constexpr bool kMidReverse = true;
 constexpr int kMaxJobs = 64;
 // The jobs of one launch, passed by value as a kernel parameter (about 2.6 KB):
