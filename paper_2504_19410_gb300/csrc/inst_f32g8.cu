@@ -1,7 +1,9 @@
 // FP32 eighth-generation middle, R2C and C2R passes (passes8.cuh): the column
-// tiles staged by tiled bulk tensor copies, lengths 128 to 512.  Compiled as its own
-// translation unit; the launchers are looked up by length (k8_colm) when the
-// other FP32 instances register their function tables.
+// tiles staged by tiled bulk tensor copies, lengths 128 to 512.  Compiled as
+// its own translation unit; the launchers are looked up by length (k8_colm,
+// k8_colm_shared, k8_r2c, k8_c2r) when the other FP32 instances register
+// their function tables.  A launch whose buffers a tensor map cannot describe
+// runs generation 2's kernel for that pass (its registered launcher).
 #include <cudaTypedefs.h>
 
 #include <mutex>
