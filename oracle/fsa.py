@@ -4,7 +4,8 @@ Every function follows one passage of the paper (Liu & Zhang, "Fast
 convolution solver based on far-field smooth approximation",
 arXiv 2504.19410).  Library primitives used as steps: numpy's FFT (or,
 where a caller asks for threads, scipy's FFT of the same definition run on
-several host cores) and scipy's erf / erfc / quad.  There is no pruning,
+several host cores; or, with fft="own", the oracle's own mixed-radix DFT in
+oracle/dft.py) and scipy's erf / erfc / quad.  There is no pruning,
 blocking or symmetry trick:
 the convolution tensor T is built on the full doubled grid and the
 convolution is a full-size complex FFT product, as Sec. 2.3 states it.
@@ -23,6 +24,8 @@ import math
 import numpy as np
 import scipy.integrate as si
 import scipy.special as sp
+
+from . import dft as own_dft
 
 # ---------------------------------------------------------------- kernel ----
 
@@ -451,6 +454,17 @@ def apply_fft(T, rho):
     return out.real[box].copy()
 
 
+def apply_fft_own(T, rho):
+    """apply_fft with the oracle's own mixed-radix DFT (oracle/dft.py) in
+    place of numpy's: the same route, checked against a transform that shares
+    no code with an FFT library."""
+    box = tuple(slice(0, nj) for nj in rho.shape)
+    pad = np.zeros(T.shape)
+    pad[box] = rho
+    out = own_dft.ifftn(own_dft.fftn(T) * own_dft.fftn(pad))
+    return out.real[box].copy()
+
+
 def apply_spectrum(S, rho, workers=None):
     """Same as apply_fft with the spectrum of T (from ``spectrum``) cached:
     the 'Execution' phase of Example 2.  ``workers``: host threads for the
@@ -486,8 +500,12 @@ def rel_error(a, b):
     return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(b)))
 
 
-def solve(L, n, eps, rho, kernel="coulomb3d"):
-    """Tensor generation followed by the FFT route: the whole method."""
+def solve(L, n, eps, rho, kernel="coulomb3d", fft="numpy"):
+    """Tensor generation followed by the FFT route: the whole method.
+    fft="own": every DFT (T^(2) = iDFT(W) included) by oracle/dft.py."""
+    if fft == "own":
+        T = tensor_T1(L, n, eps, kernel) + own_dft.ifftn(fourier_W(L, n, eps, kernel)).real
+        return apply_fft_own(T, rho)
     return apply_fft(tensor_T(L, n, eps, kernel), rho)
 
 
