@@ -264,9 +264,9 @@ fsa_status fsa_apply_host(const fsa_plan* plan, const void* rho_host, void* phi_
  * grid-strided persistent kernels over the tiles of all its requests, on
  * concurrent streams, and each of their results equals fsa_apply's bit for
  * bit.  Either sequence is captured once per batch signature (plans and
- * buffers) into a CUDA graph and replayed; a captured graph keeps the kernels
- * chosen when it was captured (later fsa_autotune_set / fsa_fused_select
- * calls apply to new batches).  Uses each plan's workspace, so a plan may
+ * buffers) into a CUDA graph and replayed; after fsa_autotune_set,
+ * fsa_fused_select or fsa_pipe_select the next call captures the batch again
+ * with the newly selected kernels.  Uses each plan's workspace, so a plan may
  * appear at most once per call (FSA_ERR_INVALID_ARG otherwise). */
 fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void* const* rho,
                              void* const* phi, int count, fsa_stream_t stream);

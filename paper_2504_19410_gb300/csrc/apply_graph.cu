@@ -9,8 +9,9 @@
 // selected for its transform lengths, so the graph of a (plan, rho, phi)
 // triple is captured on the SECOND call with that triple (a single call
 // costs nothing extra) and replayed from then on.  Selection changes
-// (fsa_autotune_set, fsa_fused_select, fsa_pipe_select) start new captures;
-// a plan's graphs are dropped when it is destroyed.
+// (fsa_autotune_set, fsa_fused_select, fsa_pipe_select) bump a generation
+// that is part of every graph key (here and in fsa_apply_batched), so they
+// start new captures; a plan's graphs are dropped when it is destroyed.
 #include <atomic>
 #include <list>
 #include <map>
@@ -51,6 +52,8 @@ constexpr size_t kMaxSeen = 4096;  // triples remembered before their second cal
 
 void apply_graphs_invalidate() { g_gen.fetch_add(1); }
 
+int apply_graphs_generation() { return g_gen.load(); }
+
 void apply_graphs_forget_plan(const fsa_plan* p) {
   std::lock_guard<std::mutex> lk(g_mu);
   for (auto& kv : g_ctx) {
@@ -84,6 +87,8 @@ cudaError_t plan_apply_graph(const fsa_plan* p, const void* rho, void* phi, cuda
   cudaGraphExec_t exec = nullptr;
   cudaError_t e = cudaSuccess;
   {
+    // held through the graph launch: another thread's capture may evict
+    // (destroy) this executable graph as soon as the lock is released
     std::lock_guard<std::mutex> lk(g_mu);
     DeviceCtx& c = g_ctx[p->device];
     auto it = c.graphs.find(key);
@@ -121,8 +126,8 @@ cudaError_t plan_apply_graph(const fsa_plan* p, const void* rho, void* phi, cuda
       if (c.seen.size() >= kMaxSeen) c.seen.clear();
       c.seen.insert(key);
     }
+    if (exec) return cudaGraphLaunch(exec, s);
   }
-  if (exec) return cudaGraphLaunch(exec, s);
   return plan_apply_passes(p, rho, phi, s);
 }
 

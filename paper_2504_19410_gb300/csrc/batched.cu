@@ -10,9 +10,10 @@
 // kernels take a by-value job table), and the groups run on forked streams so
 // their passes overlap on the device.  Either sequence is captured once per
 // batch signature (plans, buffers) into a CUDA graph and replayed, so a
-// repeated batch costs one graph launch on the caller's stream.  A graph
-// keeps the kernels chosen when it was captured (fsa_autotune_set and
-// fsa_fused_select apply to batches captured afterwards).
+// repeated batch costs one graph launch on the caller's stream.  The
+// signature includes the kernel-selection generation, so a batch replayed
+// after fsa_autotune_set, fsa_fused_select or fsa_pipe_select is captured
+// again with the new kernels.
 #include <algorithm>
 #include <tuple>
 #include <list>
@@ -173,6 +174,9 @@ extern "C" fsa_status fsa_apply_batched(const fsa_plan* const* plans, const void
 
   Sig sig;
   sig.v.push_back(reinterpret_cast<const void*>((uintptr_t)mode));  // the mode shapes the graph
+  // so do the kernels selected for each length: a selection change
+  // (fsa_autotune_set, fsa_fused_select, fsa_pipe_select) starts new captures
+  sig.v.push_back(reinterpret_cast<const void*>((uintptr_t)(unsigned)apply_graphs_generation()));
   std::vector<const void*> pkey;
   for (int k = 0; k < count; ++k) {
     sig.v.push_back(plans[k]);

@@ -199,6 +199,7 @@ void batched_forget_plan(const fsa_plan* p);
 // invalidate after a kernel selection changes; forget a destroyed plan.
 cudaError_t plan_apply_graph(const fsa_plan* p, const void* rho, void* phi, cudaStream_t s);
 void apply_graphs_invalidate();
+int apply_graphs_generation();  // bumped by every invalidate
 void apply_graphs_forget_plan(const fsa_plan* p);
 
 // Tensor generation (tensor_gen.cu), all FP64.

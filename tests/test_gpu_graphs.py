@@ -96,6 +96,45 @@ def test_selection_change_reaches_replayed_solves(lib, capi):
     plan.close()
 
 
+def test_selection_change_reaches_replayed_batches(lib, capi):
+    """fsa_apply_batched's graphs are keyed on the kernel selection too: a
+    batch captured with the separate passes is captured again once
+    fsa_pipe_select pins the pipelined kernel, and each result then equals the
+    single solve under the new selection bit for bit."""
+    import torch
+    n, L = (12, 64, 64), (2.0, 2.5, 3.0)
+    capi.fsa_autotune_set(0)
+    capi.fsa_pipe_select(128, 0)
+    rng = np.random.default_rng(5)
+    rhos = [dev(rng.standard_normal(n), "f32") for _ in range(2)]
+    plans = [lib.Plan(L, n, "f32", eps=0.5) for _ in range(2)]
+    solo = lib.Plan(L, n, "f32", eps=0.5)
+    outs = [torch.empty_like(r) for r in rhos]
+    capi.fsa_batched_mode_set(2)  # shape groups: the group's passes follow the selection
+    try:
+        for _ in range(2):
+            lib.apply_batched(plans, rhos, outs)
+        before = [solo.apply(r) for r in rhos]
+        torch.cuda.synchronize()
+        for k in range(2):
+            assert torch.equal(outs[k], before[k]), k
+        capi.fsa_pipe_select(128, 1)
+        assert solo.info.pipe == 1
+        for _ in range(2):
+            lib.apply_batched(plans, rhos, outs)
+        after = [solo.apply(r) for r in rhos]
+        torch.cuda.synchronize()
+    finally:
+        capi.fsa_batched_mode_set(0)
+    assert capi.fsa_device_fault(clear=True) == 0
+    for k in range(2):
+        assert torch.equal(outs[k], after[k]), k
+    want = oracle.solve(L, n, 0.5, rhos[1].double().cpu().numpy())
+    assert oracle.rel_error(outs[1].double().cpu().numpy(), want) <= 2e-6
+    for p in plans + [solo]:
+        p.close()
+
+
 def test_destroyed_plan_drops_its_graphs(lib, capi):
     import torch
     rng = np.random.default_rng(8)
