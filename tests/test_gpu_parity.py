@@ -97,6 +97,33 @@ def test_apply_random_density_matches_oracle(lib, n, dt, gen):
     assert err <= TOL[dt], err
 
 
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("n", [(4, 4, 4), (12, 16, 24), (64, 64, 64)])
+def test_point_charge_reproduces_the_tensor(lib, n, dt):
+    """Degenerate densities.  A unit charge at grid index c gives
+    phi[m] = T[m - c] (Eq. DiscConv with one nonzero term), compared with the
+    oracle's tensor T = T^(1) + T^(2) itself, no convolution on the oracle
+    side: at the first corner (offsets 0 .. n-1) and the last (offsets
+    -(n-1) .. 0).  A zero density gives exactly zero."""
+    L = (2.0, 2.5, 3.0)
+    eps = 0.5
+    T = oracle.tensor_T(L, n, eps)
+    idx = np.meshgrid(*[np.arange(nj) for nj in n], indexing="ij")
+    plan = lib.Plan(L, n, dt, eps=eps)
+    import torch
+    for c in [(0, 0, 0), tuple(nj - 1 for nj in n), tuple(nj // 2 for nj in n)]:
+        rho = np.zeros(n)
+        rho[c] = 1.0
+        got = plan.apply(to_dev(rho, dt)).double().cpu().numpy()
+        want = oracle.T_at(T, tuple(idx[j] - c[j] for j in range(3)))
+        err = oracle.rel_error(got, want)
+        assert err <= TOL[dt], (c, err)
+    zero = plan.apply(to_dev(np.zeros(n), dt))
+    torch.cuda.synchronize()
+    assert not bool(torch.any(zero != 0))
+    plan.close()
+
+
 _OWN = {}
 
 

@@ -205,6 +205,21 @@ def test_fft_route_equals_brute_force(n):
     assert np.allclose(fsa.apply_direct_at(T, rho, pts), [b[p] for p in pts], rtol=1e-13, atol=0)
 
 
+def test_fft_route_of_a_point_charge_is_the_shifted_tensor():
+    """A unit charge at index c: Eq. (DiscConv) has one nonzero term, so the
+    FFT route must return T at offsets m - c, at a corner, the opposite
+    corner and the centre (a wrong pad side, crop or sign fails one)."""
+    n, L = (6, 8, 10), (3.0, 4.0, 2.5)
+    T = fsa.tensor_T(L, n, 0.6)
+    idx = np.meshgrid(*[np.arange(nj) for nj in n], indexing="ij")
+    for c in [(0, 0, 0), (5, 7, 9), (3, 4, 5), (0, 7, 2)]:
+        rho = np.zeros(n)
+        rho[c] = 1.0
+        want = fsa.T_at(T, tuple(idx[j] - c[j] for j in range(3)))
+        assert fsa.rel_error(fsa.apply_fft(T, rho), want) < 1e-14
+    assert not np.any(fsa.apply_fft(T, np.zeros(n)))
+
+
 def test_threaded_fft_route_equals_brute_force():
     """The threaded FFT route (scipy's FFT on several host cores, used to time
     the oracle on all cores) reproduces Eq. (DiscConv) summed directly and the
