@@ -302,12 +302,20 @@ def run_ours(args):
         for i in range(args.warmup):
             plan.apply(rhos[i % 4], phis[i % 4])
         prof = capi.fsa_profiler_create(args.steps)
-        torch.cuda.synchronize()
-        barrier()
-        torch.cuda.synchronize()
         clk = ClockSampler(local)
         clk.start()
-        time.sleep(0.25)
+        # untimed applies of the same solve for about 0.6 s, so that the
+        # clock samples (every 200 ms) fall under this load and the timed
+        # steps start on a busy GPU
+        t_soak = time.perf_counter()
+        i = 0
+        while time.perf_counter() - t_soak < 0.6:
+            for _ in range(16):
+                plan.apply(rhos[i % 4], phis[i % 4])
+                i += 1
+            torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         # the timed steps: plain applies, nothing recorded between the passes
