@@ -13,12 +13,15 @@ Modules
                    the FFT route and the brute-force route of the discrete
                    convolution, the error norm, the App. B bound.
   closed_forms  -- exact potentials of the synthetic densities (not the method).
+  dft           -- the oracle's own mixed-radix (2, 3) DFT, so that the FFT
+                   route can also run with no FFT library (fsa.solve(fft="own")).
 
 Pins (each function is checked against something other than itself in
 ``tests/test_oracle_*.py``): Table 2's printed 3-D double errors, Table 1's
 W-hat against direct quadrature of Eq. (Fourier-Symmetric), App. B's printed
 c thresholds, brute force vs the FFT route, closed-form potentials checked
-against a finite-difference Laplacian, and exact invariants.  No oracle
-function is "parity unpinned".
+against a finite-difference Laplacian, the own DFT against the DFT's
+definition summed term by term, and exact invariants.  No oracle function is
+"parity unpinned".
 """
-from . import fsa, closed_forms  # noqa: F401
+from . import fsa, closed_forms, dft  # noqa: F401
