@@ -124,6 +124,27 @@ def test_point_charge_reproduces_the_tensor(lib, n, dt):
     plan.close()
 
 
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_reflection_and_permutation_on_gpu(lib, dt):
+    """Exact symmetries of Eq. (DiscConv) (T even along each axis), checked
+    GPU against GPU: reversing an axis of rho reverses that axis of phi, and
+    permuting the axes of rho with L and n permutes phi.  A permutation moves
+    each length to another pass (R2C axis, middle axis, row axis), so the
+    kernels differ; each result is within the tolerance of the same exact
+    value, hence within twice it of each other."""
+    n, L, eps = (16, 48, 96), (2.0, 3.0, 4.0), 0.5
+    rho = np.random.default_rng(77).standard_normal(n)
+    phi = gpu_solve(lib, L, n, eps, rho, dt)
+    assert oracle.rel_error(phi, oracle.solve(L, n, eps, rho)) <= TOL[dt]
+    for ax in range(3):
+        got = gpu_solve(lib, L, n, eps, np.flip(rho, axis=ax), dt)
+        assert oracle.rel_error(got, np.flip(phi, axis=ax)) <= 2 * TOL[dt], ax
+    for perm in [(1, 0, 2), (2, 1, 0), (0, 2, 1)]:
+        got = gpu_solve(lib, tuple(L[a] for a in perm), tuple(n[a] for a in perm), eps,
+                        np.transpose(rho, perm), dt)
+        assert oracle.rel_error(got, np.transpose(phi, perm)) <= 2 * TOL[dt], perm
+
+
 _OWN = {}
 
 

@@ -220,6 +220,24 @@ def test_fft_route_of_a_point_charge_is_the_shifted_tensor():
     assert not np.any(fsa.apply_fft(T, np.zeros(n)))
 
 
+def test_index_reflection_and_axis_permutation():
+    """Exact symmetries of Eq. (DiscConv) with T even along each axis:
+    reversing axis j of rho (i -> n_j - 1 - i) reverses axis j of phi, and
+    permuting the axes of rho together with L and n permutes phi.  A
+    transposed operand, a one-sided pad or crop, or an odd term in T fails."""
+    n, L, eps = (6, 8, 10), (3.0, 4.0, 2.5), 0.6
+    rho = np.random.default_rng(12).standard_normal(n)
+    phi = fsa.solve(L, n, eps, rho)
+    for ax in range(3):
+        got = fsa.solve(L, n, eps, np.flip(rho, axis=ax))
+        assert fsa.rel_error(got, np.flip(phi, axis=ax)) < 1e-13
+    for perm in [(1, 0, 2), (2, 1, 0), (0, 2, 1), (1, 2, 0)]:
+        Lp = tuple(L[a] for a in perm)
+        np_ = tuple(n[a] for a in perm)
+        got = fsa.solve(Lp, np_, eps, np.transpose(rho, perm))
+        assert fsa.rel_error(got, np.transpose(phi, perm)) < 1e-13
+
+
 def test_threaded_fft_route_equals_brute_force():
     """The threaded FFT route (scipy's FFT on several host cores, used to time
     the oracle on all cores) reproduces Eq. (DiscConv) summed directly and the
