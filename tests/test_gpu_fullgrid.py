@@ -27,6 +27,7 @@ import pytest
 import workloads as W
 from oracle import closed_forms as cf
 from oracle import fsa as oracle
+from tests.conftest import parity_record
 
 pytestmark = pytest.mark.gpu
 
@@ -85,6 +86,7 @@ def _check_all_modes(lib, d, exact_fn, label):
             e_exact = exact_fn(got)
             lines.append(f"{label} {dt} {name} (arithmetic {arith}): every output vs oracle {err:.3e}, "
                          f"vs exact potential {e_exact:.3e}")
+            parity_record(f"{label} every output", dt, err, e_exact)
             if not err <= TOL[dt]:
                 failures.append((dt, name, err))
             del got
@@ -163,6 +165,7 @@ def test_batched_c4_mix_matches_oracle(lib):
         for (d, dt), o, want in zip(specs, outs, wants):
             err = oracle.rel_error(o.double().cpu().numpy(), want)
             lines.append(f"batched call {call} n={d.n} L={tuple(round(x, 3) for x in d.L)} {dt}: vs oracle {err:.3e}")
+            parity_record("C4-style batch, each request", dt, err)
             assert err <= TOL[dt], lines[-1]
     print("\n" + "\n".join(lines))
     for p in plans:

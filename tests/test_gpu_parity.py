@@ -12,7 +12,7 @@ import pytest
 import workloads as W
 from oracle import closed_forms as cf
 from oracle import fsa as oracle
-from tests.conftest import read_golden
+from tests.conftest import parity_record, read_golden
 
 pytestmark = pytest.mark.gpu
 
@@ -94,6 +94,7 @@ def test_apply_random_density_matches_oracle(lib, n, dt, gen):
     got = gpu_solve(lib, L, n, eps, rho, dt)
     want = oracle.solve(L, n, eps, rho)
     err = oracle.rel_error(got, want)
+    parity_record(f"random densities on {len(SMALL)} small and ragged grids, every kernel generation", dt, err)
     assert err <= TOL[dt], err
 
 
@@ -163,6 +164,7 @@ def test_apply_matches_oracle_without_fft_library(lib, n, dt):
     got = gpu_solve(lib, L, n, eps, rho, dt)
     err = oracle.rel_error(got, want)
     print(f"{n} {dt}: vs own-DFT oracle {err:.2e}")
+    parity_record("oracle on its own DFT (no FFT library), 24x32x48 64^3 32x96x128", dt, err)
     assert err <= TOL[dt], err
 
 
@@ -253,8 +255,9 @@ def test_config_c2_256_sampled(lib, dt, gen):
     sampled = np.array([got[p] for p in pts])
     err = np.max(np.abs(sampled - want)) / np.max(np.abs(want))
     exact = cf.density_potential_points(d, np.array(pts))
-    print(f"C2 {dt} {gen}: sampled vs oracle {err:.2e}, vs closed form "
-          f"{np.max(np.abs(sampled - exact)) / np.max(np.abs(exact)):.2e}")
+    e_exact = np.max(np.abs(sampled - exact)) / np.max(np.abs(exact))
+    print(f"C2 {dt} {gen}: sampled vs oracle {err:.2e}, vs closed form {e_exact:.2e}")
+    parity_record("C2 256^3, 25 sampled outputs vs Eq. DiscConv summed, every kernel generation", dt, err, e_exact)
     assert err <= TOL[dt]
 
 
