@@ -238,3 +238,15 @@ def test_apply_graphs_set_arguments(capi):
         assert ei.value.status == capi.FSA_ERR_INVALID_ARG
     capi.fsa_apply_graphs_set(0)
     capi.fsa_apply_graphs_set(1)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No fallback: with the shared library absent, the binding raises on its
+    first call instead of computing anything another way."""
+    from paper_2504_19410_gb300 import capi as c
+    monkeypatch.setattr(c, "LIB_PATH", "/nonexistent/libfsaconv.so")
+    monkeypatch.setattr(c, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        c.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        c.fsa_appendix_b_bound(16.0, 1.0)
